@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark of the sample-many phase (shots/s) on GB300.
+
+Default workload: rotated surface-code memory, d = 5, 25 rounds, p = 1e-3
+(49 qubits, k_max = 0), 10^8 shots per step, FP32 batched executor. One
+step = one nc_sample call over the whole hot path. The records of a step
+(~15 GB) are far larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0). Under torchrun every rank samples its own
+disjoint shot range (shot_offset = rank * shots): weak scaling, no
+collective on the data path.
+
+--impl reference times the CPU oracle (the frame-factored FP64 oracle) on
+the host cores on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "shots/sec at stated peak active dim (FP32 batched vs FP64 plain); % HBM roofline"
+
+
+def workload(name: str):
+    from gen import circuits as gc
+    if name == "surface":
+        return ("surface_code_d5_r25_p1e-3", gc.surface_code_memory(d=5, rounds=25, p=1e-3), 100_000_000)
+    if name == "tiny":
+        return ("tiny_n12_l30_t6", gc.tiny_random(seed=1), 10_000)
+    if name == "dense":
+        return ("dense_n20_l40", gc.dense_random(seed=3, n=20, layers=40), 4096)
+    if name == "lowmagic":
+        return ("low_magic_n50_k10_p5e-4", gc.low_magic_gadgets(), 100_000_000)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def record_bytes_per_shot(info) -> float:
+    return (info.n_meas + info.n_det + info.n_obs + 1) / 8.0
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "kernels.cuh", "program.h"):
+        h.update(open(os.path.join(ROOT, "paper_2604_27058_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def ncu_traffic(workload_name: str):
+    """DRAM bytes per shot from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    except Exception:
+        return None
+    e = d.get(workload_name)
+    if not e or e.get("kernel_sha") != kernel_sha():
+        return None
+    return e.get("dram_bytes_per_shot")
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+# ---------------------------------------------------------------------------
+_ORACLE = None
+
+
+def _oracle_init(text):
+    global _ORACLE
+    from oracle.factored import FactoredSim
+    _ORACLE = FactoredSim(text, k_limit=22)
+
+
+def _oracle_chunk(args):
+    seed, start, count = args
+    for s in range(start, start + count):
+        _ORACLE.sample(seed, s)
+    return count
+
+
+def cpu_oracle_rate(text: str, seed: int, budget_s: float, cores: int):
+    """Shots/s of the oracle on `cores` processes over a bounded sample."""
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_oracle_init, initargs=(text,)) as pool:
+        # calibrate on one chunk per worker
+        t0 = time.perf_counter()
+        pool.map(_oracle_chunk, [(seed, 10_000_000 + i * 4, 4) for i in range(cores)])
+        per_shot = (time.perf_counter() - t0) / 4
+        per_worker = max(1, int(budget_s / max(per_shot, 1e-6)))
+        t0 = time.perf_counter()
+        done = sum(pool.map(_oracle_chunk, [(seed, i * per_worker, per_worker) for i in range(cores)]))
+        dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wname, text, shots = workload(args.workload)
+    cores = os.cpu_count() or 1
+    rates = []
+    total = 0
+    for _ in range(args.warmup):
+        cpu_oracle_rate(text, 2002, args.ref_budget / 4, cores)
+    for _ in range(args.steps):
+        r, n, dt = cpu_oracle_rate(text, 2002, args.ref_budget, cores)
+        rates.append(r)
+        total += n
+    value = statistics.median(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * (total / args.steps) / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wname, "shots_per_step": total // max(args.steps, 1)},
+        "cpu_baseline": {"value": value, "unit": "shots/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{total // max(args.steps, 1)} shots per step of {wname}, "
+                                   f"frame-factored FP64 oracle, {cores} spawn processes"},
+        "e2e": {"value": value, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    wname, text, shots = workload(args.workload)
+    if args.shots:
+        shots = args.shots
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cores = os.cpu_count() or 1
+        r, n, dt = cpu_oracle_rate(text, 2002, args.cpu_budget, cores)
+        cpu = {"value": r, "unit": "shots/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n} shots of {wname} in {dt:.1f} s (frame-factored FP64 oracle, "
+                         f"{cores} spawn processes)"}
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2604_27058_gb300 import build as nb
+    nb.build()
+    import paper_2604_27058_gb300 as nc
+
+    prog = nc.compile(text)
+    info = prog.info
+    bufs = nc.alloc_records(prog, shots)
+    offset = rank * ((shots + 127) // 128) * 128
+    stream = torch.cuda.current_stream()
+
+    def step(precision="fp32", out=None, host=False):
+        if host:
+            return nc.sample_host(prog, shots, 2002, precision=precision, shot_offset=offset, out=out)
+        return nc.sample(prog, shots, 2002, precision=precision, shot_offset=offset, out=out or bufs)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(precision, steps, warmup, host=False, out=None):
+        for _ in range(warmup):
+            step(precision, out=out, host=host)
+        clocks = Clocks(torch.cuda.current_device())
+        barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        kms = []
+        for _ in range(steps):
+            r = step(precision, out=out, host=host)
+            kms.append(r["kernel_ms"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ck = clocks.stop()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        return ms, kms, ck, r
+
+    ms, kms, ck, last = timed("fp32", args.steps, args.warmup)
+    value = shots * world * args.steps / (ms / 1000.0)
+    kernel_ms = statistics.mean(kms)
+
+    fp64 = None
+    if not args.no_fp64:
+        p_steps = max(1, min(args.steps, 3))
+        ms64, kms64, _, _ = timed("fp64", p_steps, 1)
+        fp64 = {"value": shots * world * p_steps / (ms64 / 1000.0), "unit": "shots/s",
+                "ms_per_step": ms64 / p_steps, "kernel_ms": statistics.mean(kms64)}
+
+    e2e = None
+    if not args.no_e2e:
+        hb = nc.alloc_host_records(prog, shots)
+        e_steps = max(1, min(args.steps, 3))
+        mse, _, _, _ = timed("fp32", e_steps, 1, host=True, out=hb)
+        d2h = sum(b.nbytes for k, b in hb.items() if k != "words_per_record" and b is not None)
+        e2e = {"value": shots * world * e_steps / (mse / 1000.0), "unit": "shots/s",
+               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h)}
+        del hb
+
+    peaks, peak_src = measured_peaks()
+    alg = record_bytes_per_shot(info) * shots
+    achieved = alg / (kernel_ms / 1000.0) / 1e9
+    tr = ncu_traffic(wname)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": (tr * shots) if tr else None,
+            "peak_source": peak_src, "algorithmic_bytes_per_launch": alg, "kernel_ms": kernel_ms}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32" if info.k_max == 0 else "f32",
+            "data": "synthetic",
+            "config": {"workload": wname, "shots_per_step_per_gpu": shots, "n_qubits": info.n_qubits,
+                       "k_max": info.k_max, "noise_sites": info.n_noise_sites,
+                       "record_bits_per_shot": info.n_meas + info.n_det + info.n_obs + 1,
+                       "precision": "fp32_batched", "l2": "records per step >> L2 (no flush needed)",
+                       "parallelism": f"replicas{world}"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "fp64_plain": fp64,
+            "gpu_launches": args.steps,
+            "clocks": ck,
+            "shots_kept_last_step": last["shots_kept"],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="surface")
+    ap.add_argument("--shots", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-budget", type=float, default=10.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and not os.environ.get("NC_BENCH_ALLOW_SHORT"):
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

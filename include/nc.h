@@ -1,0 +1,150 @@
+/*
+ * nc.h — C ABI of the GB300 near-Clifford shot sampler.
+ *
+ * The library implements the online "sample-many" phase of frame-factored
+ * near-Clifford simulation (Clifft, arXiv 2604.27058): a circuit is compiled
+ * once on the host (Sec. 3.1: Heisenberg mapping, Pauli localisation,
+ * bytecode emission) and then sampled for many independent shots on one GPU
+ * (Sec. 3.2: Pauli-frame updates, sampled noise, active state vector).
+ *
+ * Conventions for every entry point:
+ *   - Functions return nc_status; they never abort or throw across the ABI.
+ *   - Programs are library-owned and immutable after nc_compile (device
+ *     copies are made lazily, once per device, under an internal lock).
+ *   - Record buffers are caller-owned. Unless NC_OUT_HOST is set they are
+ *     DEVICE pointers (e.g. from torch) on the current CUDA device.
+ *   - cuda_stream is a cudaStream_t (NULL = legacy default stream). Device
+ *     work is enqueued on it; nc_sample returns after it has completed
+ *     (the device-side error word and counters are read back).
+ *   - Random draws follow a counter-based Philox4x32-10 contract keyed by
+ *     (seed, global shot index, physical event / site index), so shot s of a
+ *     call is global shot shot_offset + s and results do not depend on the
+ *     launch layout, the precision choice or how shots are split into calls.
+ */
+#ifndef NC_H
+#define NC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NC_OK = 0,
+  NC_E_PARSE = 1,            /* circuit text could not be parsed */
+  NC_E_UNSUPPORTED = 2,      /* instruction or configuration not supported */
+  NC_E_KMAX = 3,             /* peak active dimension above the limit */
+  NC_E_NONDET_DETECTOR = 4,  /* a detector/observable is not deterministic */
+  NC_E_ARG = 5,              /* invalid argument (NULL, size, alignment) */
+  NC_E_OOM = 6,              /* host or device allocation failed */
+  NC_E_CUDA = 7,             /* a CUDA runtime call failed */
+  NC_E_TIMEOUT = 8,          /* a bounded device wait gave up */
+  NC_E_INTERNAL = 9          /* internal invariant violated (a bug) */
+} nc_status;
+
+typedef struct nc_program nc_program;
+
+/* Summary of a compiled program. k_max is the peak active dimension fixed
+ * at compile time (Thm. 1); n_ops the number of bytecode instructions. */
+typedef struct {
+  uint32_t n_qubits, n_meas, n_det, n_obs, k_max, n_noise_sites, n_ops;
+  uint32_t n_events, n_slots, n_static, n_random, n_active_meas, n_array_ops;
+} nc_info;
+
+/* precision */
+#define NC_FP32_BATCHED 0  /* bit-sliced frame tiles, FP32 amplitudes, FP64 reductions */
+#define NC_FP64_PLAIN 1    /* one thread per shot, FP64 amplitudes (baseline form) */
+#define NC_FP64_BATCHED 2  /* the batched layout with FP64 amplitudes (accuracy reference) */
+
+/* outputs bitmask */
+#define NC_OUT_MEAS 1u
+#define NC_OUT_DET 2u
+#define NC_OUT_OBS 4u
+#define NC_OUT_KEPT 8u
+#define NC_OUT_HOST 16u    /* record pointers are host memory (copied back) */
+
+/* postselect */
+#define NC_PS_NONE 0
+#define NC_PS_ALL_DETECTORS 1
+
+typedef struct {
+  int precision;          /* NC_FP32_BATCHED, NC_FP64_PLAIN or NC_FP64_BATCHED */
+  uint32_t outputs;       /* NC_OUT_* bits */
+  int postselect;         /* NC_PS_NONE or NC_PS_ALL_DETECTORS */
+  uint64_t shot_offset;   /* global index of this call's first shot */
+  const char* tune;       /* NULL = built-in heuristic; "w=<1|2|4>,g=<words>" */
+  int noiseless;          /* 1 = disable every noise site (reference runs) */
+} nc_sample_opts;
+
+/*
+ * Records layout (record-major, shot-minor, bit-packed):
+ *   bit (s % 64) of word [r * words_per_record + s / 64] of a row buffer
+ *   holds record r of shot s. words_per_record = ceil(shots / 64); bits of
+ *   the last word beyond `shots` are written as 0.
+ *   meas: n_meas rows, det: n_det rows, obs: n_obs rows, kept: 1 row.
+ * A rejected (postselected-out) shot reports its failing detector as 1,
+ * every later record and detector as 0, all observables 0 and kept = 0.
+ * shots_run, shots_kept and kernel_ms are filled by nc_sample.
+ */
+typedef struct {
+  uint64_t *meas, *det, *obs, *kept;
+  uint64_t words_per_record;
+  uint64_t shots_run, shots_kept;
+  double kernel_ms;       /* filled: device time of the sampling launch(es),
+                             CUDA events on cuda_stream around the executors */
+} nc_records;
+
+/* Compile extended-Stim text (Sec. 3.1). On failure *out is NULL and a
+ * message is written to err (if err_len > 0). The text is not retained. */
+nc_status nc_compile(const char* text, size_t len, nc_program** out, char* err, size_t err_len);
+
+/* Fill *info for a compiled program. */
+nc_status nc_program_info(const nc_program* prog, nc_info* info);
+
+/* Serialize a program to a versioned byte blob. With buf == NULL, *len
+ * receives the size needed; otherwise *len is the capacity of buf and
+ * receives the bytes written (NC_E_ARG if too small). */
+nc_status nc_program_serialize(const nc_program* prog, void* buf, size_t* len);
+
+/* Rebuild a program from nc_program_serialize output. */
+nc_status nc_program_deserialize(const void* buf, size_t len, nc_program** out);
+
+/* Sample `shots` shots (Sec. 3.2). opts may be NULL (FP32 batched, all
+ * outputs, no postselection, shot_offset 0). Synchronises cuda_stream before
+ * returning. The first call on a device uploads the program and runs a
+ * 64-shot noiseless reference launch that fixes the detector/observable
+ * reference parities (NC_E_NONDET_DETECTOR if those shots disagree). */
+nc_status nc_sample(const nc_program* prog, uint64_t shots, uint64_t seed,
+                    const nc_sample_opts* opts, nc_records* out, void* cuda_stream);
+
+/* Sample n programs on one stream: program i runs shots[i] shots with
+ * seeds[i] into outs[i]. Same semantics as n calls of nc_sample. */
+nc_status nc_sample_batch(const nc_program* const* progs, const uint64_t* shots,
+                          const uint64_t* seeds, uint32_t n, const nc_sample_opts* opts,
+                          nc_records* outs, void* cuda_stream);
+
+/* Free a program and its device copies. NULL is a no-op. */
+void nc_program_free(nc_program* prog);
+
+/* Static string for a status code. */
+const char* nc_status_str(nc_status st);
+
+/* Test hook: run shot `shot` (global index) of `seed` up to, not including,
+ * measurement event `event` and return its frame and active state vector.
+ * frame_xz: 2 * ceil(n_qubits / 32) words (x bits of virtual qubits, then z
+ * bits); amps: at least 2 * 2^k_max doubles (re, im interleaved), converted
+ * to FP64; *k: active dimension at that point. Host pointers. */
+nc_status nc_debug_dump(const nc_program* prog, uint64_t seed, uint64_t shot, uint32_t event,
+                        int precision, uint32_t* frame_xz, double* amps, uint32_t* k,
+                        void* cuda_stream);
+
+/* Version of the serialized program format and of the ABI. */
+uint32_t nc_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NC_H */

@@ -1,0 +1,569 @@
+// capi.cu — the C ABI declared in include/nc.h.
+//
+// Host-side orchestration only: compile (compiler.cpp), upload the program
+// blob once per device, run the noiseless reference launch that fixes the
+// detector / observable reference parities, size the launch, enqueue one of
+// the two executors (kernels.cu) and read back the counters. No sampling is
+// ever done on the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/nc.h"
+#include "compiler.h"
+#include "kernels.cuh"
+
+namespace nc {
+size_t batched_smem_bytes(const DevProg& p, uint32_t G);
+cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t grid, uint32_t threads, size_t smem,
+                           cudaStream_t st);
+cudaError_t batched_occupancy(bool fp64, uint32_t threads, size_t smem, int* blocks_per_sm);
+cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st);
+bool plain_supported(const DevProg& p);
+}  // namespace nc
+
+using namespace nc;
+
+namespace {
+
+struct DevCopy {
+  int device = -1;
+  uint8_t* blob = nullptr;
+  bool ref_ready = false;
+  nc_status ref_status = NC_OK;
+};
+
+}  // namespace
+
+struct nc_program {
+  CompiledProgram cp;
+  nc_info info{};
+  std::mutex mu;
+  std::vector<DevCopy> devs;
+};
+
+namespace {
+
+const ProgHeader& header(const nc_program* p) {
+  return *reinterpret_cast<const ProgHeader*>(p->cp.blob.data());
+}
+
+DevProg dev_view(const ProgHeader& h, const uint8_t* base) {
+  DevProg d;
+  d.ops = reinterpret_cast<const Op*>(base + h.off_ops);
+  d.masks = reinterpret_cast<const uint32_t*>(base + h.off_masks);
+  d.q = reinterpret_cast<const uint64_t*>(base + h.off_q);
+  d.seg_start = reinterpret_cast<const uint32_t*>(base + h.off_seg_start);
+  d.seg_end = reinterpret_cast<const uint32_t*>(base + h.off_seg_end);
+  d.site_info = reinterpret_cast<const uint32_t*>(base + h.off_site_info);
+  d.site_eff = reinterpret_cast<const uint32_t*>(base + h.off_site_eff);
+  d.slot_list = reinterpret_cast<const uint32_t*>(base + h.off_slot_list);
+  d.det_ref = reinterpret_cast<const uint32_t*>(base + h.off_det_ref);
+  d.obs_ref = reinterpret_cast<const uint32_t*>(base + h.off_obs_ref);
+  d.n_qubits = h.n_qubits;
+  d.nw = h.nw;
+  d.n_ops = h.n_ops;
+  d.n_sites = h.n_sites;
+  d.n_slots = h.n_slots;
+  d.k_max = h.k_max;
+  d.kept_slot = h.kept_slot;
+  d.n_meas = h.n_meas;
+  d.n_det = h.n_det;
+  d.n_obs = h.n_obs;
+  return d;
+}
+
+void fill_info(nc_program* p) {
+  const ProgHeader& h = header(p);
+  nc_info& i = p->info;
+  i.n_qubits = h.n_qubits;
+  i.n_meas = h.n_meas;
+  i.n_det = h.n_det;
+  i.n_obs = h.n_obs;
+  i.k_max = h.k_max;
+  i.n_noise_sites = h.n_sites;
+  i.n_ops = h.n_ops;
+  i.n_events = h.n_events;
+  i.n_slots = h.n_slots;
+  i.n_static = p->cp.counts.n_static;
+  i.n_random = p->cp.counts.n_random;
+  i.n_active_meas = p->cp.counts.n_active;
+  i.n_array_ops = p->cp.counts.array_ops;
+}
+
+nc_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return NC_OK;
+  if (e == cudaErrorMemoryAllocation) return NC_E_OOM;
+  return NC_E_CUDA;
+}
+
+#define NC_TRY(expr)                        \
+  do {                                      \
+    cudaError_t _e = (expr);                \
+    if (_e != cudaSuccess) {                \
+      st = cuda_status(_e);                 \
+      goto done;                            \
+    }                                       \
+  } while (0)
+
+// Scratch allocations made on the caller's stream and released on it.
+struct Scratch {
+  std::vector<void*> ptrs;
+  cudaStream_t s;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  cudaError_t get(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
+  }
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+};
+
+struct Tuning {
+  uint32_t G, T;
+};
+
+Tuning choose_tuning(const DevProg& d, const char* tune) {
+  Tuning t;
+  if (d.k_max == 0) t = {128, 128};
+  else if (d.k_max <= 6) t = {32, 256};
+  else if (d.k_max <= 10) t = {8, 256};
+  else if (d.k_max <= 13) t = {2, 512};
+  else t = {1, 1024};
+  if (tune) {
+    unsigned g = 0, th = 0;
+    const char* s = tune;
+    while (*s) {
+      if (sscanf(s, "g=%u", &g) == 1) t.G = g;
+      else if (sscanf(s, "t=%u", &th) == 1) t.T = th;
+      const char* c = strchr(s, ',');
+      if (!c) break;
+      s = c + 1;
+    }
+  }
+  // keep the shared-memory footprint under the opt-in limit
+  while (t.G > 1 && batched_smem_bytes(d, t.G) > 220 * 1024) t.G >>= 1;
+  if (t.T < t.G) t.T = t.G;
+  return t;
+}
+
+bool pow2(uint32_t v) { return v && !(v & (v - 1)); }
+
+// Get (uploading once) the device copy of a program for the current device.
+nc_status device_copy(nc_program* p, DevCopy** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NC_E_CUDA;
+  for (auto& c : p->devs)
+    if (c.device == dev) {
+      *out = &c;
+      return NC_OK;
+    }
+  DevCopy c;
+  c.device = dev;
+  cudaError_t e = cudaMalloc(&c.blob, p->cp.blob.size());
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaMemcpy(c.blob, p->cp.blob.data(), p->cp.blob.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(c.blob);
+    return cuda_status(e);
+  }
+  p->devs.push_back(c);
+  *out = &p->devs.back();
+  return NC_OK;
+}
+
+struct CallOut {
+  uint32_t *meas, *det, *obs, *kept;
+};
+
+// Enqueue one sampling launch. kept_count must point to a zeroed device u64.
+nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uint64_t seed,
+                  uint64_t shot_offset, int precision, uint32_t lflags, const char* tune, CallOut o,
+                  unsigned long long* kept_count, uint32_t* err, Scratch& scratch, cudaStream_t stream,
+                  uint32_t stop_event = 0xffffffffu, uint64_t dump_shot = 0, double* dump_amps = nullptr,
+                  uint32_t* dump_frame = nullptr, uint32_t* dump_k = nullptr) {
+  nc_status st = NC_OK;
+  const ProgHeader& h = header(prog);
+  LaunchParams L;
+  std::memset(&L, 0, sizeof(L));
+  L.p = dev_view(h, dc.blob);
+  L.seed = seed;
+  L.shot_offset = shot_offset;
+  L.shots = shots;
+  L.meas = o.meas;
+  L.det = o.det;
+  L.obs = o.obs;
+  L.kept = o.kept;
+  L.row_words32 = 2 * ((shots + 63) / 64);
+  L.flags = lflags;
+  L.kept_count = kept_count;
+  L.err = err;
+  L.stop_event = stop_event;
+  L.dump_shot = dump_shot;
+  L.dump_amps = dump_amps;
+  L.dump_frame = dump_frame;
+  L.dump_k = dump_k;
+  if (precision == NC_FP64_PLAIN) {
+    if (!plain_supported(L.p)) return NC_E_UNSUPPORTED;
+    const uint64_t padded = L.row_words32 * 32;
+    if (h.k_max > 0) {
+      size_t bytes = ((size_t)1 << h.k_max) * padded * sizeof(double) * 2;
+      NC_TRY(scratch.get(&L.work, bytes));
+    }
+    NC_TRY(launch_plain(L, stream));
+  } else {
+    Tuning tu = choose_tuning(L.p, tune);
+    if (!pow2(tu.G) || !pow2(tu.T) || tu.T > 1024) return NC_E_ARG;
+    L.G = tu.G;
+    const uint64_t S = 32ull * tu.G;
+    L.n_tiles = (uint32_t)((L.row_words32 + tu.G - 1) / tu.G);
+    const size_t smem = batched_smem_bytes(L.p, tu.G);
+    int per_sm = 0, n_sm = 0, dev = 0;
+    NC_TRY(cudaGetDevice(&dev));
+    NC_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    const bool fp64 = precision == NC_FP64_BATCHED;
+    NC_TRY(batched_occupancy(fp64, tu.T, smem, &per_sm));
+    if (per_sm < 1) return NC_E_UNSUPPORTED;
+    uint64_t grid = std::min<uint64_t>(L.n_tiles, (uint64_t)per_sm * n_sm);
+    if (h.k_max > 0) {
+      L.work_stride = ((size_t)1 << h.k_max) * S;
+      size_t per_cta = L.work_stride * (fp64 ? sizeof(double) : sizeof(float)) * 2;
+      size_t free_b = 0, total_b = 0;
+      NC_TRY(cudaMemGetInfo(&free_b, &total_b));
+      uint64_t cap = std::max<uint64_t>(1, (uint64_t)(free_b * 0.6) / per_cta);
+      grid = std::min(grid, cap);
+      NC_TRY(scratch.get(&L.work, per_cta * grid));
+    }
+    if (!(lflags & LF_NOISELESS) && h.n_sites)
+      NC_TRY(scratch.get((void**)&L.nf, grid * S * sizeof(uint32_t)));
+    NC_TRY(launch_batched(L, fp64, (uint32_t)grid, tu.T, smem, stream));
+  }
+done:
+  return st;
+}
+
+// Noiseless 64-shot reference launch: raw detector / observable parities.
+nc_status ensure_reference(nc_program* p, DevCopy& dc, cudaStream_t stream) {
+  if (dc.ref_ready) return dc.ref_status;
+  const ProgHeader& h = header(p);
+  nc_status st = NC_OK;
+  if (h.n_det + h.n_obs == 0) {
+    dc.ref_ready = true;
+    return NC_OK;
+  }
+  {
+    Scratch scratch(stream);
+    void *det = nullptr, *obs = nullptr, *cnt = nullptr, *err = nullptr;
+    const uint64_t shots = 64;
+    NC_TRY(scratch.get(&det, (size_t)std::max<uint32_t>(h.n_det, 1) * 8));
+    NC_TRY(scratch.get(&obs, (size_t)std::max<uint32_t>(h.n_obs, 1) * 8));
+    NC_TRY(scratch.get(&cnt, 8));
+    NC_TRY(scratch.get(&err, 4));
+    NC_TRY(cudaMemsetAsync(cnt, 0, 8, stream));
+    {
+      CallOut o{nullptr, (uint32_t*)det, (uint32_t*)obs, nullptr};
+      st = enqueue(p, dc, shots, 0, 0, NC_FP64_BATCHED, LF_NOISELESS | LF_REFERENCE | LF_OUT_DET | LF_OUT_OBS,
+                   nullptr, o, (unsigned long long*)cnt, (uint32_t*)err, scratch, stream);
+      if (st != NC_OK) goto done;
+    }
+    std::vector<uint64_t> hd(h.n_det), ho(h.n_obs);
+    if (h.n_det) NC_TRY(cudaMemcpyAsync(hd.data(), det, h.n_det * 8, cudaMemcpyDeviceToHost, stream));
+    if (h.n_obs) NC_TRY(cudaMemcpyAsync(ho.data(), obs, h.n_obs * 8, cudaMemcpyDeviceToHost, stream));
+    NC_TRY(cudaStreamSynchronize(stream));
+    std::vector<uint32_t> rd(h.n_det), ro(h.n_obs);
+    for (uint32_t d = 0; d < h.n_det; d++) {
+      if (hd[d] != 0 && hd[d] != ~0ull) st = NC_E_NONDET_DETECTOR;
+      rd[d] = (uint32_t)(hd[d] & 1);
+    }
+    for (uint32_t d = 0; d < h.n_obs; d++) {
+      if (ho[d] != 0 && ho[d] != ~0ull) st = NC_E_NONDET_DETECTOR;
+      ro[d] = (uint32_t)(ho[d] & 1);
+    }
+    if (h.n_det) NC_TRY(cudaMemcpy(dc.blob + h.off_det_ref, rd.data(), h.n_det * 4, cudaMemcpyHostToDevice));
+    if (h.n_obs) NC_TRY(cudaMemcpy(dc.blob + h.off_obs_ref, ro.data(), h.n_obs * 4, cudaMemcpyHostToDevice));
+  }
+done:
+  if (st == NC_OK || st == NC_E_NONDET_DETECTOR) {
+    dc.ref_ready = true;
+    dc.ref_status = st;
+  }
+  return st;
+}
+
+nc_status prepare(const nc_program* cprog, DevCopy** dc_out, cudaStream_t stream) {
+  nc_program* prog = const_cast<nc_program*>(cprog);
+  std::lock_guard<std::mutex> lock(prog->mu);
+  DevCopy* dc = nullptr;
+  nc_status st = device_copy(prog, &dc);
+  if (st != NC_OK) return st;
+  st = ensure_reference(prog, *dc, stream);
+  if (st != NC_OK) return st;
+  *dc_out = dc;
+  return NC_OK;
+}
+
+uint32_t launch_flags(const nc_sample_opts& o) {
+  uint32_t f = 0;
+  if (o.outputs & NC_OUT_MEAS) f |= LF_OUT_MEAS;
+  if (o.outputs & NC_OUT_DET) f |= LF_OUT_DET;
+  if (o.outputs & NC_OUT_OBS) f |= LF_OUT_OBS;
+  if (o.outputs & NC_OUT_KEPT) f |= LF_OUT_KEPT;
+  if (o.postselect == NC_PS_ALL_DETECTORS) f |= LF_POSTSELECT;
+  if (o.noiseless) f |= LF_NOISELESS;
+  return f;
+}
+
+nc_sample_opts default_opts() {
+  nc_sample_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.precision = NC_FP32_BATCHED;
+  o.outputs = NC_OUT_MEAS | NC_OUT_DET | NC_OUT_OBS | NC_OUT_KEPT;
+  o.postselect = NC_PS_NONE;
+  return o;
+}
+
+nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, const uint64_t* seeds, uint32_t n,
+                      const nc_sample_opts* opts_in, nc_records* outs, cudaStream_t stream) {
+  if (!progs || !shots || !seeds || !outs) return NC_E_ARG;
+  nc_sample_opts o = opts_in ? *opts_in : default_opts();
+  if (o.precision != NC_FP32_BATCHED && o.precision != NC_FP64_PLAIN && o.precision != NC_FP64_BATCHED)
+    return NC_E_ARG;
+  if (o.shot_offset % 128) return NC_E_ARG;
+  if (o.postselect != NC_PS_NONE && o.postselect != NC_PS_ALL_DETECTORS) return NC_E_ARG;
+  const bool host = (o.outputs & NC_OUT_HOST) != 0;
+  nc_status st = NC_OK;
+  std::vector<DevCopy*> dcs(n, nullptr);
+  for (uint32_t i = 0; i < n; i++) {
+    if (!progs[i]) return NC_E_ARG;
+    const ProgHeader& h = header(progs[i]);
+    uint64_t wpr = (shots[i] + 63) / 64;
+    if (outs[i].words_per_record != wpr) return NC_E_ARG;
+    if ((o.outputs & NC_OUT_MEAS) && h.n_meas && !outs[i].meas) return NC_E_ARG;
+    if ((o.outputs & NC_OUT_DET) && h.n_det && !outs[i].det) return NC_E_ARG;
+    if ((o.outputs & NC_OUT_OBS) && h.n_obs && !outs[i].obs) return NC_E_ARG;
+    if ((o.outputs & NC_OUT_KEPT) && !outs[i].kept) return NC_E_ARG;
+    if (h.n_sites >= (1u << 28) - 1) return NC_E_UNSUPPORTED;
+    st = prepare(progs[i], &dcs[i], stream);
+    if (st != NC_OK) return st;
+  }
+  std::vector<unsigned long long> kept(n, 0);
+  float kernel_ms = 0.f;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess) {
+    if (ev0) cudaEventDestroy(ev0);
+    return NC_E_CUDA;
+  }
+  {
+    Scratch scratch(stream);
+    void* counters = nullptr;
+    void* err = nullptr;
+    NC_TRY(scratch.get(&counters, 8 * (size_t)std::max<uint32_t>(n, 1)));
+    NC_TRY(scratch.get(&err, 4));
+    NC_TRY(cudaMemsetAsync(counters, 0, 8 * (size_t)std::max<uint32_t>(n, 1), stream));
+    NC_TRY(cudaMemsetAsync(err, 0, 4, stream));
+    NC_TRY(cudaEventRecord(ev0, stream));
+    for (uint32_t i = 0; i < n; i++) {
+      if (shots[i] == 0) continue;
+      const ProgHeader& h = header(progs[i]);
+      uint64_t row_bytes = outs[i].words_per_record * 8;
+      CallOut co{(uint32_t*)outs[i].meas, (uint32_t*)outs[i].det, (uint32_t*)outs[i].obs,
+                 (uint32_t*)outs[i].kept};
+      if (host) {
+        void* d = nullptr;
+        if ((o.outputs & NC_OUT_MEAS) && h.n_meas) { NC_TRY(scratch.get(&d, row_bytes * h.n_meas)); co.meas = (uint32_t*)d; }
+        if ((o.outputs & NC_OUT_DET) && h.n_det) { NC_TRY(scratch.get(&d, row_bytes * h.n_det)); co.det = (uint32_t*)d; }
+        if ((o.outputs & NC_OUT_OBS) && h.n_obs) { NC_TRY(scratch.get(&d, row_bytes * h.n_obs)); co.obs = (uint32_t*)d; }
+        if (o.outputs & NC_OUT_KEPT) { NC_TRY(scratch.get(&d, row_bytes)); co.kept = (uint32_t*)d; }
+      }
+      st = enqueue(progs[i], *dcs[i], shots[i], seeds[i], o.shot_offset, o.precision, launch_flags(o), o.tune, co,
+                   (unsigned long long*)counters + i, (uint32_t*)err, scratch, stream);
+      if (st != NC_OK) goto done;
+      if (i + 1 == n) NC_TRY(cudaEventRecord(ev1, stream));
+      if (host) {
+        if (co.meas && outs[i].meas) NC_TRY(cudaMemcpyAsync(outs[i].meas, co.meas, row_bytes * h.n_meas, cudaMemcpyDeviceToHost, stream));
+        if (co.det && outs[i].det) NC_TRY(cudaMemcpyAsync(outs[i].det, co.det, row_bytes * h.n_det, cudaMemcpyDeviceToHost, stream));
+        if (co.obs && outs[i].obs) NC_TRY(cudaMemcpyAsync(outs[i].obs, co.obs, row_bytes * h.n_obs, cudaMemcpyDeviceToHost, stream));
+        if (co.kept && outs[i].kept) NC_TRY(cudaMemcpyAsync(outs[i].kept, co.kept, row_bytes, cudaMemcpyDeviceToHost, stream));
+      }
+    }
+    NC_TRY(cudaMemcpyAsync(kept.data(), counters, 8 * (size_t)n, cudaMemcpyDeviceToHost, stream));
+    uint32_t herr = 0;
+    NC_TRY(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, stream));
+    NC_TRY(cudaStreamSynchronize(stream));
+    if (herr) st = NC_E_INTERNAL;
+    if (shots[n - 1] != 0 && cudaEventElapsedTime(&kernel_ms, ev0, ev1) != cudaSuccess) kernel_ms = 0.f;
+  }
+  NC_TRY(cudaStreamSynchronize(stream));
+  for (uint32_t i = 0; i < n; i++) {
+    outs[i].shots_run = shots[i];
+    outs[i].shots_kept = kept[i];
+    outs[i].kernel_ms = kernel_ms;
+  }
+done:
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+nc_status nc_compile(const char* text, size_t len, nc_program** out, char* err, size_t err_len) {
+  if (out) *out = nullptr;
+  if (!text || !out) return NC_E_ARG;
+  nc_program* p = new (std::nothrow) nc_program();
+  if (!p) return NC_E_OOM;
+  std::string msg;
+  int rc = compile_program(std::string(text, len), p->cp, msg);
+  if (rc != 0) {
+    if (err && err_len) snprintf(err, err_len, "%s", msg.c_str());
+    delete p;
+    return (nc_status)rc;
+  }
+  fill_info(p);
+  *out = p;
+  return NC_OK;
+}
+
+nc_status nc_program_info(const nc_program* prog, nc_info* info) {
+  if (!prog || !info) return NC_E_ARG;
+  *info = prog->info;
+  return NC_OK;
+}
+
+nc_status nc_program_serialize(const nc_program* prog, void* buf, size_t* len) {
+  if (!prog || !len) return NC_E_ARG;
+  const size_t need = prog->cp.blob.size() + sizeof(nc_info_counts);
+  if (!buf) {
+    *len = need;
+    return NC_OK;
+  }
+  if (*len < need) return NC_E_ARG;
+  std::memcpy(buf, prog->cp.blob.data(), prog->cp.blob.size());
+  std::memcpy((uint8_t*)buf + prog->cp.blob.size(), &prog->cp.counts, sizeof(nc_info_counts));
+  *len = need;
+  return NC_OK;
+}
+
+nc_status nc_program_deserialize(const void* buf, size_t len, nc_program** out) {
+  if (out) *out = nullptr;
+  if (!buf || !out || len < sizeof(ProgHeader) + sizeof(nc_info_counts)) return NC_E_ARG;
+  ProgHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (h.magic != kMagic || h.version != kVersion || h.total_bytes + sizeof(nc_info_counts) != len) return NC_E_ARG;
+  uint64_t offs[] = {h.off_ops, h.off_masks, h.off_q, h.off_seg_start, h.off_seg_end, h.off_site_info,
+                     h.off_site_eff, h.off_slot_list, h.off_det_ref, h.off_obs_ref};
+  for (uint64_t o : offs)
+    if (o > h.total_bytes || (o & 15)) return NC_E_ARG;
+  if (h.off_ops + (uint64_t)h.n_ops * sizeof(Op) > h.total_bytes || h.k_max > kMaxK || h.n_qubits > kMaxQubits)
+    return NC_E_ARG;
+  nc_program* p = new (std::nothrow) nc_program();
+  if (!p) return NC_E_OOM;
+  p->cp.blob.assign((const uint8_t*)buf, (const uint8_t*)buf + h.total_bytes);
+  std::memcpy(&p->cp.counts, (const uint8_t*)buf + h.total_bytes, sizeof(nc_info_counts));
+  // reference parities are recomputed on first use
+  std::memset(p->cp.blob.data() + h.off_det_ref, 0, (size_t)h.n_det * 4);
+  std::memset(p->cp.blob.data() + h.off_obs_ref, 0, (size_t)h.n_obs * 4);
+  fill_info(p);
+  *out = p;
+  return NC_OK;
+}
+
+nc_status nc_sample(const nc_program* prog, uint64_t shots, uint64_t seed, const nc_sample_opts* opts,
+                    nc_records* out, void* cuda_stream) {
+  if (!prog || !out) return NC_E_ARG;
+  return sample_many(&prog, &shots, &seed, 1, opts, out, (cudaStream_t)cuda_stream);
+}
+
+nc_status nc_sample_batch(const nc_program* const* progs, const uint64_t* shots, const uint64_t* seeds, uint32_t n,
+                          const nc_sample_opts* opts, nc_records* outs, void* cuda_stream) {
+  if (n == 0) return NC_OK;
+  return sample_many(progs, shots, seeds, n, opts, outs, (cudaStream_t)cuda_stream);
+}
+
+void nc_program_free(nc_program* prog) {
+  if (!prog) return;
+  int cur = 0;
+  bool have = cudaGetDevice(&cur) == cudaSuccess;
+  for (auto& c : prog->devs) {
+    if (c.blob) {
+      cudaSetDevice(c.device);
+      cudaFree(c.blob);
+    }
+  }
+  if (have) cudaSetDevice(cur);
+  delete prog;
+}
+
+const char* nc_status_str(nc_status st) {
+  switch (st) {
+    case NC_OK: return "ok";
+    case NC_E_PARSE: return "parse error";
+    case NC_E_UNSUPPORTED: return "unsupported";
+    case NC_E_KMAX: return "active dimension above the limit";
+    case NC_E_NONDET_DETECTOR: return "non-deterministic detector or observable";
+    case NC_E_ARG: return "invalid argument";
+    case NC_E_OOM: return "out of memory";
+    case NC_E_CUDA: return "CUDA error";
+    case NC_E_TIMEOUT: return "device wait timed out";
+    case NC_E_INTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+nc_status nc_debug_dump(const nc_program* prog, uint64_t seed, uint64_t shot, uint32_t event, int precision,
+                        uint32_t* frame_xz, double* amps, uint32_t* k, void* cuda_stream) {
+  if (!prog || !frame_xz || !amps || !k) return NC_E_ARG;
+  if (precision != NC_FP32_BATCHED && precision != NC_FP64_PLAIN && precision != NC_FP64_BATCHED)
+    return NC_E_ARG;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  DevCopy* dc = nullptr;
+  nc_status st = prepare(prog, &dc, stream);
+  if (st != NC_OK) return st;
+  const ProgHeader& h = header(prog);
+  const uint64_t base = shot & ~127ull;
+  const size_t n_amp = (size_t)1 << h.k_max;
+  {
+    Scratch scratch(stream);
+    void *d_amps = nullptr, *d_frame = nullptr, *d_k = nullptr, *cnt = nullptr, *err = nullptr;
+    NC_TRY(scratch.get(&d_amps, n_amp * 2 * sizeof(double)));
+    NC_TRY(scratch.get(&d_frame, (size_t)2 * h.nw * 4));
+    NC_TRY(scratch.get(&d_k, 4));
+    NC_TRY(scratch.get(&cnt, 8));
+    NC_TRY(scratch.get(&err, 4));
+    NC_TRY(cudaMemsetAsync(d_amps, 0, n_amp * 2 * sizeof(double), stream));
+    NC_TRY(cudaMemsetAsync(d_frame, 0, (size_t)2 * h.nw * 4, stream));
+    NC_TRY(cudaMemsetAsync(d_k, 0xff, 4, stream));
+    NC_TRY(cudaMemsetAsync(cnt, 0, 8, stream));
+    {
+      CallOut o{nullptr, nullptr, nullptr, nullptr};
+      char tune[32];
+      snprintf(tune, sizeof(tune), "g=4,t=%u", h.k_max > 10 ? 512u : 128u);
+      st = enqueue(prog, *dc, 128, seed, base, precision, 0, tune, o, (unsigned long long*)cnt, (uint32_t*)err,
+                   scratch, stream, event, shot - base, (double*)d_amps, (uint32_t*)d_frame, (uint32_t*)d_k);
+      if (st != NC_OK) goto done;
+    }
+    NC_TRY(cudaMemcpyAsync(amps, d_amps, n_amp * 2 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    NC_TRY(cudaMemcpyAsync(frame_xz, d_frame, (size_t)2 * h.nw * 4, cudaMemcpyDeviceToHost, stream));
+    NC_TRY(cudaMemcpyAsync(k, d_k, 4, cudaMemcpyDeviceToHost, stream));
+    NC_TRY(cudaStreamSynchronize(stream));
+  }
+  NC_TRY(cudaStreamSynchronize(stream));
+done:
+  return st;
+}
+
+uint32_t nc_abi_version(void) { return (kVersion << 16) | 1u; }
+
+}  // extern "C"

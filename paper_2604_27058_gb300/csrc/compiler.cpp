@@ -1,0 +1,1128 @@
+// compiler.cpp — offline Clifford-frame compiler (host C++).
+//
+// Turns extended-Stim text into the SVM bytecode of program.h (Sec. 3.1):
+//   1. parse + unroll REPEAT, assigning physical event / record / noise-site
+//      indices (the keys of the random draws);
+//   2. Heisenberg-map every active operation through the Clifford frame
+//      (Def. 1): the frame is kept as the images M(X_j), M(Z_j) of the
+//      physical generators under P -> U_C^dagger P U_C;
+//   3. Pauli-localise mapped generators (Lemma 1, App. A; dormant pivot
+//      preferred, Lemma 2) and absorb V into the frame (U_C <- U_C V^dagger);
+//   4. emit bytecode (frame ops, expansion fused with the rotation as in
+//      OP_EXPAND_T, array ops, dormant/active measurements, coalesced noise
+//      blocks, records), noise survival tables and record-slot assignment.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "compiler.h"
+
+namespace nc {
+
+// ---------------------------------------------------------------------------
+// Parser
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CompileError : std::runtime_error {
+  int code;
+  CompileError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+[[noreturn]] void fail(int code, const std::string& msg) { throw CompileError(code, msg); }
+
+enum Kind { K_GATE, K_ROT, K_MEAS, K_NOISE, K_FF, K_DET, K_OBS };
+
+struct PhysOp {
+  Kind kind = K_GATE;
+  std::string name;   // canonical gate / channel name
+  int q0 = -1, q1 = -1;
+  double arg = 0.0;   // rotation angle or probability
+  int64_t event = -1, record = -1, site = -1;
+  bool reset = false;
+  bool xbasis = false;
+  std::vector<int64_t> recs;  // det / obs records; ff: recs[0]
+  int64_t index = -1;
+  int instr = -1;     // source instruction ordinal (groups targets of one line)
+};
+
+struct Line {
+  std::string name;
+  std::vector<double> args;
+  std::vector<std::string> targets;
+  int repeat = -1;              // >= 0: REPEAT block
+  std::vector<Line> body;
+};
+
+std::string upper(std::string s) {
+  for (auto& c : s) c = (char)toupper((unsigned char)c);
+  return s;
+}
+
+std::string trim(const std::string& s) {
+  size_t a = s.find_first_not_of(" \t\r");
+  if (a == std::string::npos) return "";
+  size_t b = s.find_last_not_of(" \t\r");
+  return s.substr(a, b - a + 1);
+}
+
+std::vector<std::string> split_ws(const std::string& s) {
+  std::vector<std::string> out;
+  size_t i = 0;
+  while (i < s.size()) {
+    while (i < s.size() && (s[i] == ' ' || s[i] == '\t')) i++;
+    size_t j = i;
+    while (j < s.size() && s[j] != ' ' && s[j] != '\t') j++;
+    if (j > i) out.push_back(s.substr(i, j - i));
+    i = j;
+  }
+  return out;
+}
+
+double parse_double(const std::string& t) {
+  const char* s = t.c_str();
+  char* end = nullptr;
+  double v = strtod(s, &end);
+  if (end == s || *end != 0 || !std::isfinite(v)) fail(1, "bad number '" + t + "'");
+  return v;
+}
+
+std::vector<Line> parse_lines(const std::vector<std::string>& lines, size_t& pos, int depth) {
+  std::vector<Line> out;
+  while (pos < lines.size()) {
+    std::string line = lines[pos];
+    if (line == "}") {
+      if (depth == 0) fail(1, "unmatched '}'");
+      pos++;
+      return out;
+    }
+    std::string up = upper(line);
+    if (up.rfind("REPEAT", 0) == 0 && (up.size() == 6 || up[6] == ' ' || up[6] == '\t')) {
+      auto toks = split_ws(line);
+      if (toks.size() != 3 || toks[2] != "{") fail(1, "bad REPEAT line: " + line);
+      char* end = nullptr;
+      long n = strtol(toks[1].c_str(), &end, 10);
+      if (*end != 0 || n < 0) fail(1, "bad REPEAT count: " + line);
+      pos++;
+      Line blk;
+      blk.repeat = (int)n;
+      blk.body = parse_lines(lines, pos, depth + 1);
+      out.push_back(std::move(blk));
+      continue;
+    }
+    Line l;
+    size_t i = 0;
+    while (i < line.size() && (isalnum((unsigned char)line[i]) || line[i] == '_')) i++;
+    if (i == 0) fail(1, "cannot parse line: " + line);
+    l.name = upper(line.substr(0, i));
+    std::string rest = line.substr(i);
+    if (!rest.empty() && rest[0] == '(') {
+      size_t close = rest.find(')');
+      if (close == std::string::npos) fail(1, "missing ')': " + line);
+      std::string inner = rest.substr(1, close - 1);
+      size_t s = 0;
+      while (s <= inner.size()) {
+        size_t c = inner.find(',', s);
+        std::string tok = trim(inner.substr(s, c == std::string::npos ? std::string::npos : c - s));
+        if (!tok.empty()) l.args.push_back(parse_double(tok));
+        if (c == std::string::npos) break;
+        s = c + 1;
+      }
+      rest = rest.substr(close + 1);
+    }
+    l.targets = split_ws(rest);
+    out.push_back(std::move(l));
+    pos++;
+  }
+  if (depth) fail(1, "unterminated REPEAT block");
+  return out;
+}
+
+const std::map<std::string, std::string>& aliases() {
+  static const std::map<std::string, std::string> a = {
+      {"CNOT", "CX"}, {"ZCX", "CX"}, {"ZCY", "CY"}, {"ZCZ", "CZ"}, {"MZ", "M"},
+      {"RZ", "R"}, {"MRZ", "MR"}, {"SQRT_Z", "S"}, {"SQRT_Z_DAG", "S_DAG"}};
+  return a;
+}
+
+bool is_1q_clifford(const std::string& n) {
+  static const char* v[] = {"I", "H", "S", "S_DAG", "X", "Y", "Z", "SQRT_X", "SQRT_X_DAG",
+                            "SQRT_Y", "SQRT_Y_DAG"};
+  for (auto s : v)
+    if (n == s) return true;
+  return false;
+}
+bool is_2q_clifford(const std::string& n) {
+  return n == "CX" || n == "CY" || n == "CZ" || n == "SWAP";
+}
+
+struct Flattener {
+  std::vector<PhysOp> ops;
+  int64_t n_q = 0, ev = 0, rec = 0, site = 0, det = 0, n_obs = 0;
+  int instr = 0;
+  std::vector<double> site_p;
+  std::vector<uint8_t> site_kind;
+
+  int64_t rec_target(const std::string& t) {
+    if (t.rfind("rec[-", 0) != 0 || t.back() != ']') fail(1, "bad record target '" + t + "'");
+    std::string num = t.substr(5, t.size() - 6);
+    char* end = nullptr;
+    long k = strtol(num.c_str(), &end, 10);
+    if (*end != 0 || k < 1 || k > rec) fail(1, "record target out of range '" + t + "'");
+    return rec - k;
+  }
+  int qubit(const std::string& t) {
+    if (t.empty()) fail(1, "empty target");
+    for (char c : t)
+      if (!isdigit((unsigned char)c)) fail(1, "bad qubit target '" + t + "'");
+    long q = strtol(t.c_str(), nullptr, 10);
+    if (q >= (long)kMaxQubits) fail(2, "qubit index above the supported maximum");
+    n_q = std::max<int64_t>(n_q, q + 1);
+    return (int)q;
+  }
+
+  void run(const std::vector<Line>& block) {
+    for (auto& l : block) {
+      if (l.repeat >= 0) {
+        for (int r = 0; r < l.repeat; r++) run(l.body);
+        continue;
+      }
+      one(l);
+      instr++;
+    }
+  }
+
+  void one(const Line& l) {
+    std::string name = l.name;
+    auto al = aliases().find(name);
+    if (al != aliases().end()) name = al->second;
+    if (name == "TICK" || name == "QUBIT_COORDS" || name == "SHIFT_COORDS") return;
+    if (name == "DETECTOR") {
+      PhysOp o; o.kind = K_DET;
+      for (auto& t : l.targets) o.recs.push_back(rec_target(t));
+      o.index = det++;
+      ops.push_back(o);
+      return;
+    }
+    if (name == "OBSERVABLE_INCLUDE") {
+      if (l.args.size() != 1 || l.args[0] < 0 || l.args[0] != std::floor(l.args[0]))
+        fail(1, "OBSERVABLE_INCLUDE needs one integer index");
+      PhysOp o; o.kind = K_OBS;
+      o.index = (int64_t)l.args[0];
+      if (o.index > 1 << 20) fail(2, "observable index too large");
+      for (auto& t : l.targets) o.recs.push_back(rec_target(t));
+      n_obs = std::max(n_obs, o.index + 1);
+      ops.push_back(o);
+      return;
+    }
+    bool has_rec = false;
+    for (auto& t : l.targets)
+      if (t.rfind("rec[", 0) == 0) has_rec = true;
+    if ((name == "CX" || name == "CY" || name == "CZ") && has_rec) {
+      if (l.targets.size() % 2) fail(1, name + " needs target pairs");
+      for (size_t k = 0; k < l.targets.size(); k += 2) {
+        const auto &a = l.targets[k], &b = l.targets[k + 1];
+        PhysOp o; o.kind = K_FF;
+        o.name = name == "CX" ? "X" : name == "CY" ? "Y" : "Z";
+        o.instr = instr;
+        if (a.rfind("rec[", 0) == 0 && b.rfind("rec[", 0) != 0) {
+          o.recs.push_back(rec_target(a));
+          o.q0 = qubit(b);
+        } else if (name == "CZ" && b.rfind("rec[", 0) == 0 && a.rfind("rec[", 0) != 0) {
+          o.recs.push_back(rec_target(b));
+          o.q0 = qubit(a);
+        } else {
+          fail(2, "unsupported classical control in " + name);
+        }
+        ops.push_back(o);
+      }
+      return;
+    }
+    std::vector<int> qs;
+    for (auto& t : l.targets) qs.push_back(qubit(t));
+    if (is_1q_clifford(name)) {
+      if (!l.args.empty()) fail(1, name + " takes no argument");
+      for (int q : qs) {
+        PhysOp o; o.kind = K_GATE;
+        o.name = name;
+        o.q0 = q;
+        o.instr = instr;
+        ops.push_back(o);
+      }
+    } else if (is_2q_clifford(name)) {
+      if (qs.size() % 2) fail(1, name + " needs target pairs");
+      for (size_t k = 0; k < qs.size(); k += 2) {
+        if (qs[k] == qs[k + 1]) fail(1, name + " on the same qubit twice");
+        PhysOp o; o.kind = K_GATE;
+        o.name = name;
+        o.q0 = qs[k];
+        o.q1 = qs[k + 1];
+        o.instr = instr;
+        ops.push_back(o);
+      }
+    } else if (name == "T" || name == "T_DAG" || name == "R_Z" || name == "R_X" || name == "R_Y") {
+      bool t = name == "T" || name == "T_DAG";
+      if (t && !l.args.empty()) fail(1, name + " takes no argument");
+      if (!t && l.args.size() != 1) fail(1, name + " needs one angle");
+      for (int q : qs) {
+        PhysOp o; o.kind = K_ROT;
+        o.name = name;
+        o.q0 = q;
+        o.arg = t ? 0.0 : l.args[0];
+        o.instr = instr;
+        ops.push_back(o);
+      }
+    } else if (name == "M" || name == "MX" || name == "MR" || name == "R") {
+      double p = 0.0;
+      if (!l.args.empty()) {
+        if (name == "R" || l.args.size() != 1) fail(1, "bad arguments for " + name);
+        p = l.args[0];
+        if (!(p >= 0.0 && p <= 1.0)) fail(1, "probability out of range");
+      }
+      for (int q : qs) {
+        PhysOp o; o.kind = K_MEAS;
+        o.name = name;
+        o.q0 = q;
+        o.xbasis = name == "MX";
+        o.reset = name == "R" || name == "MR";
+        o.event = ev++;
+        o.instr = instr;
+        if (name != "R") {
+          o.record = rec++;
+          if (p > 0) {
+            o.site = site++;
+            o.arg = p;
+            site_p.push_back(p);
+            site_kind.push_back(SITE_FLIP);
+          }
+        }
+        ops.push_back(o);
+      }
+    } else if (name == "X_ERROR" || name == "Y_ERROR" || name == "Z_ERROR" ||
+               name == "DEPOLARIZE1" || name == "DEPOLARIZE2") {
+      if (l.args.size() != 1 || !(l.args[0] >= 0.0 && l.args[0] <= 1.0))
+        fail(1, "bad probability for " + name);
+      int width = name == "DEPOLARIZE2" ? 2 : 1;
+      if (qs.size() % width) fail(1, name + " needs target pairs");
+      uint8_t kind = name == "X_ERROR" ? SITE_X : name == "Y_ERROR" ? SITE_Y
+                   : name == "Z_ERROR" ? SITE_Z : name == "DEPOLARIZE1" ? SITE_D1 : SITE_D2;
+      for (size_t k = 0; k < qs.size(); k += width) {
+        PhysOp o; o.kind = K_NOISE;
+        o.name = name;
+        o.q0 = qs[k];
+        o.q1 = width == 2 ? qs[k + 1] : -1;
+        o.arg = l.args[0];
+        o.site = site++;
+        o.instr = instr;
+        site_p.push_back(l.args[0]);
+        site_kind.push_back(kind);
+        ops.push_back(o);
+      }
+    } else {
+      fail(2, "unsupported instruction " + name);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Pauli algebra: i^ph X^x Z^z, X^x Z^z = prod_j X_j^x_j prod_j Z_j^z_j
+// ---------------------------------------------------------------------------
+struct Pauli {
+  std::vector<uint64_t> x, z;
+  int ph = 0;
+  explicit Pauli(int nw = 0) : x(nw, 0), z(nw, 0) {}
+  bool xb(int q) const { return (x[q >> 6] >> (q & 63)) & 1; }
+  bool zb(int q) const { return (z[q >> 6] >> (q & 63)) & 1; }
+  void setx(int q, bool v) {
+    uint64_t m = 1ull << (q & 63);
+    x[q >> 6] = v ? (x[q >> 6] | m) : (x[q >> 6] & ~m);
+  }
+  void setz(int q, bool v) {
+    uint64_t m = 1ull << (q & 63);
+    z[q >> 6] = v ? (z[q >> 6] | m) : (z[q >> 6] & ~m);
+  }
+  bool xzero() const {
+    for (auto w : x)
+      if (w) return false;
+    return true;
+  }
+};
+
+int popc64(uint64_t v) { return __builtin_popcountll(v); }
+
+// a <- a * b
+void pmul_inplace(Pauli& a, const Pauli& b) {
+  int c = 0;
+  for (size_t w = 0; w < a.x.size(); w++) c += popc64(a.z[w] & b.x[w]);
+  a.ph = (a.ph + b.ph + 2 * c) & 3;
+  for (size_t w = 0; w < a.x.size(); w++) {
+    a.x[w] ^= b.x[w];
+    a.z[w] ^= b.z[w];
+  }
+}
+
+// Hermitian sign bit of (-1)^s prod sigma_j written as i^ph X^x Z^z.
+int herm_sign(const Pauli& p) {
+  int xz = 0;
+  for (size_t w = 0; w < p.x.size(); w++) xz += popc64(p.x[w] & p.z[w]);
+  int d = ((p.ph - xz) % 4 + 4) % 4;
+  if (d != 0 && d != 2) fail(9, "non-Hermitian Pauli in the compiler");
+  return d / 2;
+}
+
+// ---------------------------------------------------------------------------
+// Gate conjugation tables, derived numerically from the gate unitaries.
+// Local qubit 0 is the more significant bit of the 4x4 basis index.
+// ---------------------------------------------------------------------------
+using cd = std::complex<double>;
+struct Mat {
+  int n;
+  cd a[16];
+};
+
+Mat mat1(const std::string& g) {
+  Mat m{2, {}};
+  const double s = 1.0 / std::sqrt(2.0);
+  auto set = [&](cd a, cd b, cd c, cd d) { m.a[0] = a; m.a[1] = b; m.a[2] = c; m.a[3] = d; };
+  const cd I(0, 1);
+  if (g == "I") set(1, 0, 0, 1);
+  else if (g == "H") set(s, s, s, -s);
+  else if (g == "S") set(1, 0, 0, I);
+  else if (g == "S_DAG") set(1, 0, 0, -I);
+  else if (g == "X") set(0, 1, 1, 0);
+  else if (g == "Y") set(0, -I, I, 0);
+  else if (g == "Z") set(1, 0, 0, -1);
+  else if (g == "SQRT_X") set(0.5 * (1.0 + I), 0.5 * (1.0 - I), 0.5 * (1.0 - I), 0.5 * (1.0 + I));
+  else if (g == "SQRT_X_DAG") set(0.5 * (1.0 - I), 0.5 * (1.0 + I), 0.5 * (1.0 + I), 0.5 * (1.0 - I));
+  else if (g == "SQRT_Y") set(0.5 * (1.0 + I), -0.5 * (1.0 + I), 0.5 * (1.0 + I), 0.5 * (1.0 + I));
+  else if (g == "SQRT_Y_DAG") set(0.5 * (1.0 - I), 0.5 * (1.0 - I), -0.5 * (1.0 - I), 0.5 * (1.0 - I));
+  else fail(9, "no matrix for " + g);
+  return m;
+}
+
+Mat mat2(const std::string& g) {
+  Mat m{4, {}};
+  const cd I(0, 1);
+  for (int ia = 0; ia < 2; ia++)
+    for (int ib = 0; ib < 2; ib++) {
+      int src = 2 * ia + ib;
+      if (g == "CX") m.a[(2 * ia + (ib ^ ia)) * 4 + src] = 1;
+      else if (g == "CZ") m.a[src * 4 + src] = (ia && ib) ? -1 : 1;
+      else if (g == "SWAP") m.a[(2 * ib + ia) * 4 + src] = 1;
+      else if (g == "CY") {
+        if (!ia) m.a[src * 4 + src] = 1;
+        else m.a[(2 + (1 - ib)) * 4 + src] = ib == 0 ? I : -I;
+      } else fail(9, "no matrix for " + g);
+    }
+  return m;
+}
+
+Mat mmul(const Mat& a, const Mat& b) {
+  Mat c{a.n, {}};
+  for (int i = 0; i < a.n; i++)
+    for (int j = 0; j < a.n; j++) {
+      cd s = 0;
+      for (int k = 0; k < a.n; k++) s += a.a[i * a.n + k] * b.a[k * a.n + j];
+      c.a[i * a.n + j] = s;
+    }
+  return c;
+}
+Mat dag(const Mat& a) {
+  Mat c{a.n, {}};
+  for (int i = 0; i < a.n; i++)
+    for (int j = 0; j < a.n; j++) c.a[i * a.n + j] = std::conj(a.a[j * a.n + i]);
+  return c;
+}
+
+// Local Pauli matrix X^x Z^z over w qubits (local qubit 0 most significant).
+Mat local_pauli(int lx, int lz, int w) {
+  Mat single[4];
+  single[0] = mat1("I");
+  single[1] = mat1("X");
+  single[2] = mat1("Z");
+  single[3] = mmul(mat1("X"), mat1("Z"));
+  // factor j (j = 0 most significant) reads bit (w - 1 - j) of lx / lz
+  auto idx = [&](int j) {
+    int bit = w - 1 - j;
+    return ((lx >> bit) & 1) | (((lz >> bit) & 1) << 1);
+  };
+  Mat out = single[idx(0)];
+  if (w == 2) {
+    Mat b = single[idx(1)];
+    Mat k{4, {}};
+    for (int i = 0; i < 2; i++)
+      for (int j = 0; j < 2; j++)
+        for (int r = 0; r < 2; r++)
+          for (int c = 0; c < 2; c++) k.a[(2 * i + r) * 4 + (2 * j + c)] = out.a[i * 2 + j] * b.a[r * 2 + c];
+    out = k;
+  }
+  return out;
+}
+
+struct LocalPauli {
+  int x, z, ph;
+};
+
+LocalPauli identify(const Mat& m, int w) {
+  for (int lx = 0; lx < (1 << w); lx++)
+    for (int lz = 0; lz < (1 << w); lz++) {
+      Mat b = local_pauli(lx, lz, w);
+      for (int ph = 0; ph < 4; ph++) {
+        cd f = ph == 0 ? cd(1, 0) : ph == 1 ? cd(0, 1) : ph == 2 ? cd(-1, 0) : cd(0, -1);
+        bool ok = true;
+        for (int i = 0; i < m.n * m.n && ok; i++)
+          if (std::abs(m.a[i] - f * b.a[i]) > 1e-9) ok = false;
+        if (ok) return {lx, lz, ph};
+      }
+    }
+  fail(9, "conjugation did not give a Pauli");
+}
+
+// Table for G^dagger g G (inverse=true) or G g G^dagger, g = X_0, Z_0, X_1, Z_1.
+struct ConjTable {
+  int w;
+  LocalPauli img[4];
+};
+
+const ConjTable& conj_table(const std::string& g, bool inverse) {
+  static std::map<std::pair<std::string, bool>, ConjTable> cache;
+  auto key = std::make_pair(g, inverse);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  Mat u = is_2q_clifford(g) ? mat2(g) : mat1(g);
+  int w = u.n == 4 ? 2 : 1;
+  if (inverse) u = dag(u);
+  ConjTable t{w, {}};
+  for (int j = 0; j < w; j++)
+    for (int k = 0; k < 2; k++) {
+      // local qubit j is bit (w-1-j) of the local Pauli index (qubit 0 most significant)
+      int bit = 1 << (w - 1 - j);
+      Mat gm = local_pauli(k == 0 ? bit : 0, k == 1 ? bit : 0, w);
+      t.img[2 * j + k] = identify(mmul(mmul(u, gm), dag(u)), w);
+    }
+  return cache[key] = t;
+}
+
+// ---------------------------------------------------------------------------
+// Compiler state
+// ---------------------------------------------------------------------------
+struct Emitted {
+  Op op;
+  std::vector<int64_t> uses;  // record ids read by this op
+  int64_t def = -1;           // record id written by this op
+};
+
+struct Compiler {
+  int n = 0, nw64 = 0, nw32 = 0;
+  std::vector<Pauli> img;  // img[2j] = M(X_j), img[2j+1] = M(Z_j)
+  std::vector<int> act;    // position -> virtual qubit
+  std::vector<int> pos_of; // virtual qubit -> position or -1
+  std::vector<Emitted> code;
+  std::vector<uint32_t> masks;  // 32-bit words
+  uint32_t k_max = 0;
+  // noise
+  std::vector<double> site_p;
+  std::vector<uint8_t> site_kind;
+  std::vector<uint32_t> site_eff;   // mask offset of option 0, or flip record id
+  std::vector<int64_t> site_flip_id;
+  // records
+  int64_t next_id = 0;
+  std::vector<int64_t> record_id;   // physical record -> id
+  std::vector<int64_t> pending_out; // ids awaiting REC_OUT (after their flip block)
+  std::vector<int64_t> pending_row;
+  nc_info_counts counts{};
+
+  explicit Compiler(int nq) : n(std::max(1, nq)) {
+    nw64 = (n + 63) / 64;
+    nw32 = (n + 31) / 32;
+    img.assign(2 * n, Pauli(nw64));
+    for (int j = 0; j < n; j++) {
+      img[2 * j].setx(j, true);
+      img[2 * j + 1].setz(j, true);
+    }
+    pos_of.assign(n, -1);
+  }
+
+  // M(P) for P = i^ph X^lx Z^lz on physical qubits qs (local bit j <-> qs[j],
+  // local qubit 0 most significant as in the conjugation tables).
+  Pauli map_local(const std::vector<int>& qs, int lx, int lz, int ph) {
+    int w = (int)qs.size();
+    Pauli acc(nw64);
+    acc.ph = ph & 3;
+    for (int j = 0; j < w; j++)
+      if ((lx >> (w - 1 - j)) & 1) pmul_inplace(acc, img[2 * qs[j]]);
+    for (int j = 0; j < w; j++)
+      if ((lz >> (w - 1 - j)) & 1) pmul_inplace(acc, img[2 * qs[j] + 1]);
+    return acc;
+  }
+
+  Pauli map_letter(int q, char l) {
+    // X = X, Z = Z, Y = i X Z
+    if (l == 'X') return map_local({q}, 1, 0, 0);
+    if (l == 'Z') return map_local({q}, 0, 1, 0);
+    return map_local({q}, 1, 1, 1);
+  }
+
+  void physical_gate(const std::string& g, int q0, int q1) {
+    std::vector<int> qs = {q0};
+    if (q1 >= 0) qs.push_back(q1);
+    const ConjTable& t = conj_table(g, true);
+    std::vector<Pauli> nimg;
+    for (int j = 0; j < t.w; j++)
+      for (int k = 0; k < 2; k++) {
+        LocalPauli lp = t.img[2 * j + k];
+        nimg.push_back(map_local(qs, lp.x, lp.z, lp.ph));
+      }
+    for (int j = 0; j < t.w; j++)
+      for (int k = 0; k < 2; k++) img[2 * qs[j] + k] = nimg[2 * j + k];
+  }
+
+  // Conjugate a Pauli by a virtual gate (H, S on a; CX a->b; CZ a,b).
+  static void vconj(Pauli& p, char g, int a, int b) {
+    if (g == 'H') {
+      bool xa = p.xb(a), za = p.zb(a);
+      if (xa && za) p.ph = (p.ph + 2) & 3;
+      p.setx(a, za);
+      p.setz(a, xa);
+    } else if (g == 'S') {
+      bool xa = p.xb(a);
+      if (xa) {
+        p.ph = (p.ph + 1) & 3;
+        p.setz(a, !p.zb(a));
+      }
+    } else if (g == 'C') {  // CX a -> b
+      if (p.xb(a)) p.setx(b, !p.xb(b));
+      if (p.zb(b)) p.setz(a, !p.zb(a));
+    } else if (g == 'Z') {  // CZ
+      bool xa = p.xb(a), xb = p.xb(b);
+      if (xa && xb) p.ph = (p.ph + 2) & 3;
+      if (xb) p.setz(a, !p.zb(a));
+      if (xa) p.setz(b, !p.zb(b));
+    }
+  }
+
+  void emit(const Op& o, std::vector<int64_t> uses = {}, int64_t def = -1) {
+    flush_outputs_unless_noise(o.code);
+    code.push_back({o, std::move(uses), def});
+  }
+
+  Op mk(uint8_t code_) {
+    Op o;
+    std::memset(&o, 0, sizeof(o));
+    o.code = code_;
+    return o;
+  }
+
+  // U_C <- U_C V^dagger for one virtual gate, and the matching bytecode.
+  void virtual_gate(char g, int a, int b, Pauli* track) {
+    for (auto& p : img) vconj(p, g, a, b);
+    if (track) vconj(*track, g, a, b);
+    bool a_act = pos_of[a] >= 0;
+    bool b_act = b >= 0 && pos_of[b] >= 0;
+    Op o = mk(0);
+    o.a = (uint16_t)a;
+    o.b = (uint16_t)(b >= 0 ? b : 0);
+    o.pa = (uint8_t)(a_act ? pos_of[a] : 0);
+    o.pb = (uint8_t)(b_act ? pos_of[b] : 0);
+    bool on_state = (g == 'H' || g == 'S') ? a_act : (a_act && b_act);
+    switch (g) {
+      case 'H': o.code = on_state ? OP_ARRAY_H : OP_FRAME_H; break;
+      case 'S': o.code = on_state ? OP_ARRAY_S : OP_FRAME_S; break;
+      case 'C': o.code = on_state ? OP_ARRAY_CX : OP_FRAME_CX; break;
+      case 'Z': o.code = on_state ? OP_ARRAY_CZ : OP_FRAME_CZ; break;
+    }
+    if (on_state) counts.array_ops++;
+    emit(o);
+  }
+
+  // Lemma 1 / App. A with the dormant-first pivot. Returns v (or -1 for a
+  // dormant Z string), sets kind ('X' / 'Z') and sign bit a.
+  int localize(Pauli& p, char& kind, int& a) {
+    if (!p.xzero()) {
+      int v = -1, first = -1;
+      for (int q = 0; q < n; q++)
+        if (p.xb(q)) {
+          if (first < 0) first = q;
+          if (pos_of[q] < 0) { v = q; break; }
+        }
+      if (v < 0) v = first;
+      std::vector<int> xs;
+      for (int q = 0; q < n; q++)
+        if (q != v && p.xb(q)) xs.push_back(q);
+      if (pos_of[v] >= 0)
+        for (int q : xs)
+          if (pos_of[q] < 0) fail(9, "active pivot with dormant x-support");
+      for (int q : xs) virtual_gate('C', v, q, &p);
+      std::vector<int> zs;
+      for (int q = 0; q < n; q++)
+        if (q != v && p.zb(q)) zs.push_back(q);
+      for (int q : zs) virtual_gate('Z', v, q, &p);
+      if (p.zb(v)) virtual_gate('S', v, -1, &p);
+      kind = 'X';
+      a = herm_sign(p);
+      return v;
+    }
+    int v = -1;
+    for (int q = 0; q < n; q++)
+      if (p.zb(q) && pos_of[q] >= 0) { v = q; break; }
+    if (v < 0) return -1;
+    std::vector<int> zs;
+    for (int q = 0; q < n; q++)
+      if (q != v && p.zb(q)) zs.push_back(q);
+    for (int q : zs) virtual_gate('C', q, v, &p);
+    kind = 'Z';
+    a = herm_sign(p);
+    return v;
+  }
+
+  uint32_t add_mask(const Pauli& p, bool with_x, bool with_z) {
+    uint32_t off = (uint32_t)masks.size();
+    auto put = [&](const std::vector<uint64_t>& v) {
+      for (int w = 0; w < nw32; w++) masks.push_back((uint32_t)(v[w >> 1] >> (32 * (w & 1))));
+    };
+    if (with_x) put(p.x);
+    if (with_z) put(p.z);
+    return off;
+  }
+
+  void flush_outputs_unless_noise(uint8_t c) {
+    if (c == OP_NOISE_BLOCK || c == OP_REC_OUT) return;
+    flush_outputs();
+  }
+  void flush_outputs() {
+    for (size_t i = 0; i < pending_out.size(); i++) {
+      Op o = mk(OP_REC_OUT);
+      o.i3 = (uint32_t)pending_row[i];
+      code.push_back({o, {pending_out[i]}, -1});
+    }
+    pending_out.clear();
+    pending_row.clear();
+  }
+
+  void noise_site(int64_t site, uint8_t kind, double p, uint32_t eff, int64_t flip_id) {
+    if ((int64_t)site_p.size() != site) fail(9, "site numbering");
+    site_p.push_back(p);
+    site_kind.push_back(kind);
+    site_eff.push_back(eff);
+    site_flip_id.push_back(flip_id);
+    if (!code.empty() && code.back().op.code == OP_NOISE_BLOCK && code.back().op.i1 == (uint32_t)site) {
+      code.back().op.i1 = (uint32_t)site + 1;
+      if (flip_id >= 0) code.back().uses.push_back(flip_id);
+      return;
+    }
+    Op o = mk(OP_NOISE_BLOCK);
+    o.i0 = (uint32_t)site;
+    o.i1 = (uint32_t)site + 1;
+    std::vector<int64_t> u;
+    if (flip_id >= 0) u.push_back(flip_id);
+    code.push_back({o, u, -1});
+  }
+
+  // Virtual masks of the K options of a noise site acting on physical qubits.
+  uint32_t noise_masks(uint8_t kind, int q0, int q1) {
+    static const char* letters = "IXYZ";
+    uint32_t off = (uint32_t)masks.size();
+    auto put_letters = [&](char la, char lb) {
+      Pauli acc(nw64);
+      if (la != 'I') pmul_inplace(acc, map_letter(q0, la));
+      if (lb != 'I') pmul_inplace(acc, map_letter(q1, lb));
+      add_mask(acc, true, true);
+    };
+    switch (kind) {
+      case SITE_X: put_letters('X', 'I'); break;
+      case SITE_Y: put_letters('Y', 'I'); break;
+      case SITE_Z: put_letters('Z', 'I'); break;
+      case SITE_D1: put_letters('X', 'I'); put_letters('Y', 'I'); put_letters('Z', 'I'); break;
+      case SITE_D2:
+        for (int j = 1; j < 16; j++) put_letters(letters[j >> 2], letters[j & 3]);
+        break;
+    }
+    return off;
+  }
+
+  void rotation(const PhysOp& o) {
+    char letter = 'Z';
+    double theta;
+    if (o.name == "T") theta = M_PI / 8;
+    else if (o.name == "T_DAG") theta = -M_PI / 8;
+    else {
+      letter = o.name.back();
+      theta = o.arg / 2.0;
+    }
+    Pauli p = map_letter(o.q0, letter);
+    char kind;
+    int a;
+    int v = localize(p, kind, a);
+    if (v < 0) return;  // scalar phase on the dormant |0>
+    double ta = a ? -theta : theta;
+    if (kind == 'X' && pos_of[v] < 0) {
+      virtual_gate('H', v, -1, nullptr);
+      Op e = mk(OP_EXPAND_ROT);
+      e.a = (uint16_t)v;
+      e.pa = (uint8_t)act.size();
+      e.f = ta;
+      pos_of[v] = (int)act.size();
+      act.push_back(v);
+      k_max = std::max<uint32_t>(k_max, (uint32_t)act.size());
+      if (act.size() > kMaxK) fail(3, "active dimension above the supported maximum");
+      counts.array_ops++;
+      emit(e);
+    } else {
+      Op r = mk(kind == 'Z' ? OP_ROT_Z : OP_ROT_X);
+      r.a = (uint16_t)v;
+      r.pa = (uint8_t)pos_of[v];
+      r.f = ta;
+      counts.array_ops++;
+      emit(r);
+    }
+  }
+
+  void measure(const PhysOp& o, std::vector<int64_t>& flips_of_instr) {
+    Pauli p = map_letter(o.q0, o.xbasis ? 'X' : 'Z');
+    int64_t id = next_id++;
+    bool active_z = false;
+    for (int q = 0; q < n && !active_z; q++)
+      if (p.zb(q) && pos_of[q] >= 0) active_z = true;
+    bool direct_out = o.record >= 0 && o.site < 0;
+    if (p.xzero() && !active_z) {
+      Op m = mk(OP_MEAS_STATIC);
+      m.i0 = add_mask(p, false, true);
+      m.i1 = (uint32_t)o.event;
+      m.flags = (uint8_t)(herm_sign(p) ? FLAG_SIGN : 0);
+      if (direct_out) { m.flags |= FLAG_OUT; m.i3 = (uint32_t)o.record; }
+      counts.n_static++;
+      emit(m, {}, id);
+    } else {
+      char kind;
+      int a;
+      int v = localize(p, kind, a);
+      if (v < 0) fail(9, "measurement localisation failed");
+      if (pos_of[v] < 0) {
+        Op m = mk(OP_MEAS_RANDOM);
+        m.a = (uint16_t)v;
+        m.i0 = (uint32_t)o.event;
+        m.i1 = (uint32_t)o.event;
+        m.flags = (uint8_t)(a ? FLAG_SIGN : 0);
+        if (direct_out) { m.flags |= FLAG_OUT; m.i3 = (uint32_t)o.record; }
+        counts.n_random++;
+        emit(m, {}, id);
+        // the kernel applies H_v to the frame; mirror it in U_C
+        for (auto& q : img) vconj(q, 'H', v, -1);
+      } else {
+        Op m = mk(kind == 'Z' ? OP_MEAS_ACTIVE_Z : OP_MEAS_ACTIVE_X);
+        m.a = (uint16_t)v;
+        m.pa = (uint8_t)pos_of[v];
+        m.i0 = (uint32_t)o.event;
+        m.i1 = (uint32_t)o.event;
+        m.flags = (uint8_t)(a ? FLAG_SIGN : 0);
+        if (direct_out) { m.flags |= FLAG_OUT; m.i3 = (uint32_t)o.record; }
+        counts.n_active++;
+        counts.array_ops++;
+        emit(m, {}, id);
+        int pos = pos_of[v];
+        int top = act.back();
+        act[pos] = top;
+        pos_of[top] = pos;
+        act.pop_back();
+        pos_of[v] = -1;
+        if (kind == 'X')
+          for (auto& q : img) vconj(q, 'H', v, -1);
+      }
+    }
+    if (o.reset) {
+      Pauli e = map_letter(o.q0, 'X');
+      Op f = mk(OP_FEEDFORWARD);
+      f.i0 = add_mask(e, true, true);
+      emit(f, {id}, -1);
+    }
+    if (o.record >= 0) {
+      if ((int64_t)record_id.size() != o.record) fail(9, "record numbering");
+      record_id.push_back(id);
+      if (o.site >= 0) flips_of_instr.push_back(o.site);
+    }
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Entry point
+// ---------------------------------------------------------------------------
+int compile_program(const std::string& text, CompiledProgram& out, std::string& err) {
+  try {
+    std::vector<std::string> lines;
+    {
+      size_t s = 0;
+      while (s <= text.size()) {
+        size_t e = text.find('\n', s);
+        std::string line = text.substr(s, e == std::string::npos ? std::string::npos : e - s);
+        size_t hash = line.find('#');
+        if (hash != std::string::npos) line = line.substr(0, hash);
+        line = trim(line);
+        if (!line.empty()) lines.push_back(line);
+        if (e == std::string::npos) break;
+        s = e + 1;
+      }
+    }
+    size_t pos = 0;
+    auto block = parse_lines(lines, pos, 0);
+    Flattener fl;
+    fl.run(block);
+
+    Compiler c((int)fl.n_q);
+    // Flip sites of one measurement instruction are emitted together after
+    // all of its measurements (a flip changes only its record, never the
+    // frame, so deferring it past the instruction's other targets is exact).
+    std::vector<int64_t> flips;
+    int cur_instr = -2;
+    // index flip-site -> record for speed
+    std::vector<int64_t> flip_record(fl.site_p.size(), -1);
+    for (auto& po : fl.ops)
+      if (po.kind == K_MEAS && po.site >= 0) flip_record[po.site] = po.record;
+    auto flush_flips_fast = [&]() {
+      for (int64_t s : flips) c.noise_site(s, SITE_FLIP, fl.site_p[s], 0, c.record_id[flip_record[s]]);
+      for (int64_t s : flips) {
+        c.pending_out.push_back(c.record_id[flip_record[s]]);
+        c.pending_row.push_back(flip_record[s]);
+      }
+      flips.clear();
+    };
+
+    int64_t kept_id = -1;
+    std::vector<int64_t> obs_id(fl.n_obs, -1);
+    for (auto& po : fl.ops) {
+      if (!(po.kind == K_MEAS && po.instr == cur_instr)) flush_flips_fast();
+      cur_instr = po.kind == K_MEAS ? po.instr : -2;
+      switch (po.kind) {
+        case K_GATE:
+          c.physical_gate(po.name, po.q0, po.q1);
+          break;
+        case K_ROT:
+          c.rotation(po);
+          break;
+        case K_MEAS:
+          c.measure(po, flips);
+          break;
+        case K_NOISE: {
+          uint8_t kind = fl.site_kind[po.site];
+          uint32_t eff = c.noise_masks(kind, po.q0, po.q1);
+          c.noise_site(po.site, kind, po.arg, eff, -1);
+          break;
+        }
+        case K_FF: {
+          Pauli e = c.map_letter(po.q0, po.name[0]);
+          Op f = c.mk(OP_FEEDFORWARD);
+          f.i0 = c.add_mask(e, true, true);
+          c.emit(f, {c.record_id[po.recs[0]]}, -1);
+          break;
+        }
+        case K_DET: {
+          Op d = c.mk(OP_DETECTOR);
+          d.i3 = (uint32_t)po.index;
+          std::vector<int64_t> u;
+          for (auto r : po.recs) u.push_back(c.record_id[r]);
+          d.i1 = (uint32_t)u.size();
+          c.emit(d, u, -1);
+          break;
+        }
+        case K_OBS: {
+          if (obs_id[po.index] < 0) obs_id[po.index] = c.next_id++;
+          Op d = c.mk(OP_OBS_INCLUDE);
+          std::vector<int64_t> u;
+          for (auto r : po.recs) u.push_back(c.record_id[r]);
+          d.i1 = (uint32_t)u.size();
+          d.i2 = (uint32_t)obs_id[po.index];  // id, rewritten to a slot below
+          c.emit(d, u, -1);
+          break;
+        }
+      }
+    }
+    flush_flips_fast();
+    c.flush_outputs();
+    // observables never included still get an (all-zero) accumulator
+    for (int64_t o = 0; o < fl.n_obs; o++)
+      if (obs_id[o] < 0) obs_id[o] = c.next_id++;
+    for (int64_t o = 0; o < fl.n_obs; o++) {
+      Op d = c.mk(OP_OBS_OUT);
+      d.i3 = (uint32_t)o;
+      c.code.push_back({d, {}, -1});
+    }
+    kept_id = c.next_id++;
+    {
+      Op d = c.mk(OP_KEPT_OUT);
+      c.code.push_back({d, {}, -1});
+    }
+    c.code.push_back({c.mk(OP_END), {}, -1});
+
+    // ---------------- record-slot allocation (linear scan) ----------------
+    int64_t n_ids = c.next_id;
+    std::vector<int64_t> last_use(n_ids, -1);
+    std::vector<char> persistent(n_ids, 0);
+    persistent[kept_id] = 1;
+    for (auto id : obs_id) persistent[id] = 1;
+    for (size_t i = 0; i < c.code.size(); i++) {
+      for (auto id : c.code[i].uses) last_use[id] = (int64_t)i;
+      if (c.code[i].def >= 0) last_use[c.code[i].def] = std::max<int64_t>(last_use[c.code[i].def], (int64_t)i);
+    }
+    std::vector<int64_t> slot_of(n_ids, -1);
+    std::vector<uint32_t> free_slots;
+    uint32_t n_slots = 0;
+    auto alloc = [&]() -> uint32_t {
+      if (!free_slots.empty()) {
+        uint32_t s = free_slots.back();
+        free_slots.pop_back();
+        return s;
+      }
+      return n_slots++;
+    };
+    slot_of[kept_id] = alloc();
+    for (auto id : obs_id) slot_of[id] = alloc();
+    std::vector<uint32_t> slot_list;
+    std::vector<Op> ops;
+    ops.reserve(c.code.size());
+    for (size_t i = 0; i < c.code.size(); i++) {
+      Emitted& e = c.code[i];
+      if (e.def >= 0) slot_of[e.def] = alloc();
+      Op o = e.op;
+      switch (o.code) {
+        case OP_MEAS_STATIC: case OP_MEAS_RANDOM: case OP_MEAS_ACTIVE_Z: case OP_MEAS_ACTIVE_X:
+          o.i2 = (uint32_t)slot_of[e.def];
+          break;
+        case OP_FEEDFORWARD: case OP_REC_OUT:
+          o.i2 = (uint32_t)slot_of[e.uses[0]];
+          break;
+        case OP_DETECTOR:
+          o.i0 = (uint32_t)slot_list.size();
+          for (auto id : e.uses) slot_list.push_back((uint32_t)slot_of[id]);
+          break;
+        case OP_OBS_INCLUDE:
+          o.i0 = (uint32_t)slot_list.size();
+          for (auto id : e.uses) slot_list.push_back((uint32_t)slot_of[id]);
+          o.i2 = (uint32_t)slot_of[o.i2];
+          break;
+        case OP_OBS_OUT:
+          o.i2 = (uint32_t)slot_of[obs_id[o.i3]];
+          break;
+        case OP_KEPT_OUT:
+          o.i2 = (uint32_t)slot_of[kept_id];
+          break;
+        default:
+          break;
+      }
+      ops.push_back(o);
+      // free ids whose last use is this op
+      std::vector<int64_t> touched = e.uses;
+      if (e.def >= 0) touched.push_back(e.def);
+      std::sort(touched.begin(), touched.end());
+      touched.erase(std::unique(touched.begin(), touched.end()), touched.end());
+      for (auto id : touched)
+        if (!persistent[id] && last_use[id] == (int64_t)i && slot_of[id] >= 0) {
+          free_slots.push_back((uint32_t)slot_of[id]);
+        }
+    }
+    // flip sites reference slots through site_eff
+    std::vector<uint32_t> site_eff = c.site_eff;
+    for (size_t s = 0; s < c.site_kind.size(); s++)
+      if (c.site_kind[s] == SITE_FLIP) site_eff[s] = (uint32_t)slot_of[c.site_flip_id[s]];
+    // A flip slot must still be live at its noise block: it is, because the
+    // block is a use of the id (recorded in Emitted::uses).
+
+    // ---------------- survival table (Sec. 3.2, integer form) ----------------
+    size_t S = c.site_p.size();
+    std::vector<uint64_t> q(S);
+    std::vector<uint32_t> seg_start(S), seg_end(S), info(S);
+    {
+      size_t start = 0;
+      double run = 1.0;
+      std::vector<std::pair<size_t, size_t>> bounds;
+      for (size_t i = 0; i < S; i++) {
+        double p = c.site_p[i];
+        double nxt = run * (1.0 - p);
+        if (nxt < 1.0 / 65536.0 && i > start) {
+          bounds.push_back({start, i});
+          start = i;
+          nxt = 1.0 * (1.0 - p);
+        }
+        run = nxt;
+        q[i] = run >= 1.0 ? ~0ull : (uint64_t)(run * 18446744073709551616.0);
+      }
+      bounds.push_back({start, S});
+      for (auto& b : bounds)
+        for (size_t i = b.first; i < b.second; i++) {
+          seg_start[i] = (uint32_t)b.first;
+          seg_end[i] = (uint32_t)b.second;
+        }
+      for (size_t i = 0; i < S; i++) {
+        uint32_t k = c.site_kind[i] == SITE_D1 ? 3 : c.site_kind[i] == SITE_D2 ? 15 : 1;
+        info[i] = (uint32_t)c.site_kind[i] | (k << 4);
+      }
+    }
+
+    // ---------------- blob ----------------
+    ProgHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.magic = kMagic;
+    h.version = kVersion;
+    h.n_qubits = (uint32_t)c.n;
+    h.nw = (uint32_t)c.nw32;
+    h.n_ops = (uint32_t)ops.size();
+    h.n_sites = (uint32_t)S;
+    h.n_meas = (uint32_t)fl.rec;
+    h.n_det = (uint32_t)fl.det;
+    h.n_obs = (uint32_t)fl.n_obs;
+    h.n_events = (uint32_t)fl.ev;
+    h.n_slots = n_slots;
+    h.k_max = c.k_max;
+    h.kept_slot = (uint32_t)slot_of[kept_id];
+    h.n_mask_words = (uint32_t)c.masks.size();
+    h.n_slot_list = (uint32_t)slot_list.size();
+    uint64_t off = (sizeof(ProgHeader) + 15) & ~15ull;
+    auto place = [&](uint64_t bytes) {
+      uint64_t o = off;
+      off = (off + bytes + 15) & ~15ull;
+      return o;
+    };
+    h.off_ops = place(ops.size() * sizeof(Op));
+    h.off_masks = place(c.masks.size() * 4);
+    h.off_q = place(S * 8);
+    h.off_seg_start = place(S * 4);
+    h.off_seg_end = place(S * 4);
+    h.off_site_info = place(S * 4);
+    h.off_site_eff = place(S * 4);
+    h.off_slot_list = place(slot_list.size() * 4);
+    h.off_det_ref = place((size_t)fl.det * 4);
+    h.off_obs_ref = place((size_t)fl.n_obs * 4);
+    h.total_bytes = off;
+    out.blob.assign(off, 0);
+    std::memcpy(out.blob.data(), &h, sizeof(h));
+    auto cp = [&](uint64_t o, const void* src, size_t bytes) {
+      if (bytes) std::memcpy(out.blob.data() + o, src, bytes);
+    };
+    cp(h.off_ops, ops.data(), ops.size() * sizeof(Op));
+    cp(h.off_masks, c.masks.data(), c.masks.size() * 4);
+    cp(h.off_q, q.data(), S * 8);
+    cp(h.off_seg_start, seg_start.data(), S * 4);
+    cp(h.off_seg_end, seg_end.data(), S * 4);
+    cp(h.off_site_info, info.data(), S * 4);
+    cp(h.off_site_eff, site_eff.data(), S * 4);
+    cp(h.off_slot_list, slot_list.data(), slot_list.size() * 4);
+    out.counts = c.counts;
+    return 0;
+  } catch (CompileError& e) {
+    err = e.what();
+    return e.code;
+  } catch (std::bad_alloc&) {
+    err = "out of host memory";
+    return 6;
+  } catch (std::exception& e) {
+    err = e.what();
+    return 9;
+  }
+}
+
+}  // namespace nc

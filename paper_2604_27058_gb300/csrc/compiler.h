@@ -1,0 +1,24 @@
+// compiler.h — host compiler entry point (product-internal).
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "program.h"
+
+namespace nc {
+
+struct nc_info_counts {
+  uint32_t n_static, n_random, n_active, array_ops;
+};
+
+struct CompiledProgram {
+  std::vector<uint8_t> blob;  // ProgHeader + tables (see program.h)
+  nc_info_counts counts;
+};
+
+// Returns 0 on success or an nc_status code with a message in err.
+int compile_program(const std::string& text, CompiledProgram& out, std::string& err);
+
+}  // namespace nc

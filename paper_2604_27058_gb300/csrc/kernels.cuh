@@ -1,0 +1,137 @@
+// kernels.cuh — device-side helpers shared by the two executors: program
+// view, Philox4x32-10 draws, noise-site search. Product code only.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "program.h"
+
+namespace nc {
+
+struct DevProg {
+  const Op* ops;
+  const uint32_t* masks;
+  const uint64_t* q;
+  const uint32_t* seg_start;
+  const uint32_t* seg_end;
+  const uint32_t* site_info;
+  const uint32_t* site_eff;
+  const uint32_t* slot_list;
+  const uint32_t* det_ref;
+  const uint32_t* obs_ref;
+  uint32_t n_qubits, nw, n_ops, n_sites, n_slots, k_max, kept_slot;
+  uint32_t n_meas, n_det, n_obs;
+};
+
+enum : uint32_t {
+  LF_NOISELESS = 1,   // skip every noise site
+  LF_POSTSELECT = 2,  // kept &= ~detector
+  LF_REFERENCE = 4,   // raw parities (no reference XOR)
+  LF_OUT_MEAS = 8,
+  LF_OUT_DET = 16,
+  LF_OUT_OBS = 32,
+  LF_OUT_KEPT = 64,
+};
+
+struct LaunchParams {
+  DevProg p;
+  uint64_t seed, shot_offset, shots;
+  uint32_t *meas, *det, *obs, *kept;  // u32 views of the u64 record rows
+  uint64_t row_words32;               // u32 words per record row
+  uint32_t flags;
+  uint32_t G;                         // 32-shot words per tile (batched executor)
+  uint32_t n_tiles;
+  uint64_t work_stride;               // amplitudes per CTA workspace (batched) / per shot (plain)
+  void* work;                         // amplitude workspace
+  uint32_t* nf;                       // per-shot next-fault state
+  unsigned long long* kept_count;
+  uint32_t* err;
+  uint32_t stop_event;                // debug: stop before this event (0xffffffff = never)
+  uint64_t dump_shot;                 // debug: call-local shot index
+  double* dump_amps;
+  uint32_t* dump_frame;
+  uint32_t* dump_k;
+};
+
+constexpr uint32_t kNoFault = 0xffffffffu;
+constexpr uint32_t TAG_MT = 1, TAG_ML = 2, TAG_GAP = 3;
+
+// Philox4x32-10 (Salmon et al., SC'11).
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint2 key_of(uint64_t seed) {
+  return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// Top bits of the 32 shots of the aligned word starting at global shot s0.
+__device__ __forceinline__ uint32_t meas_top_word(uint64_t seed, uint64_t s0, uint32_t event) {
+  uint64_t g = s0 >> 7;
+  uint4 w = philox(make_uint4((uint32_t)g, (uint32_t)(g >> 32), TAG_MT, event), key_of(seed));
+  uint32_t sel = (uint32_t)(s0 >> 5) & 3u;
+  return sel == 0 ? w.x : sel == 1 ? w.y : sel == 2 ? w.z : w.w;
+}
+
+// u of shot s (global) given its top bit: (top * 2^52 + low52) * 2^-53.
+__device__ __forceinline__ double meas_u(uint64_t seed, uint64_t s, uint32_t event, uint32_t top) {
+  uint4 w = philox(make_uint4((uint32_t)s, (uint32_t)(s >> 32), TAG_ML, event), key_of(seed));
+  uint64_t low = ((uint64_t)w.x | ((uint64_t)w.y << 32)) & ((1ull << 52) - 1);
+  uint64_t v = ((uint64_t)top << 52) | low;
+  return (double)v * 0x1p-53;
+}
+
+// m = [u < p1]. When p1 == 1/2 exactly only the top bit matters.
+__device__ __forceinline__ uint32_t draw_outcome(uint64_t seed, uint64_t s, uint32_t event,
+                                                 uint32_t top, double p1) {
+  if (p1 <= 0.0) return 0;
+  if (p1 >= 1.0) return 1;
+  if (p1 == 0.5) return top ? 0u : 1u;
+  return meas_u(seed, s, event, top) < p1 ? 1u : 0u;
+}
+
+__device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
+
+// Next fault of global shot `shot` at or after site `st` (Sec. 3.2 jump,
+// integer survival form). Returns (site << 4) | option, or kNoFault.
+__device__ __forceinline__ uint32_t next_fault(const DevProg& p, uint64_t seed, uint64_t shot,
+                                               uint32_t st) {
+  const uint2 key = key_of(seed);
+  while (st < p.n_sites) {
+    uint32_t a = __ldg(p.seg_start + st), b = __ldg(p.seg_end + st);
+    uint4 w = philox(make_uint4((uint32_t)shot, (uint32_t)(shot >> 32), TAG_GAP, st), key);
+    uint64_t u = (uint64_t)w.x | ((uint64_t)w.y << 32);
+    uint64_t ql = st == a ? ~0ull : __ldg(p.q + st - 1);
+    uint64_t t = mulhi64(u, ql);
+    if (__ldg(p.q + b - 1) > t) {
+      st = b;
+      continue;
+    }
+    uint32_t lo = st, hi = b - 1;  // q[hi] <= t
+    while (lo < hi) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (__ldg(p.q + mid) <= t) hi = mid;
+      else lo = mid + 1;
+    }
+    uint32_t k = (__ldg(p.site_info + lo) >> 4) & 15u;
+    uint32_t opt = __umulhi(w.z, k);
+    return (lo << 4) | opt;
+  }
+  return kNoFault;
+}
+
+__device__ __forceinline__ uint32_t insert0(uint32_t j, uint32_t p) {
+  return ((j >> p) << (p + 1)) | (j & ((1u << p) - 1u));
+}
+
+}  // namespace nc

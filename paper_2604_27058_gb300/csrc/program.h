@@ -1,0 +1,80 @@
+// program.h — compiled program layout shared by the host compiler and the
+// CUDA executors (product-internal; the oracle has its own representation).
+//
+// A program is the SVM bytecode of Sec. 3.1 stage 3/4: a flat list of fixed
+// 32-byte instructions plus side tables (virtual Pauli masks, noise-site
+// survival table, detector record lists). Everything is identical for every
+// shot (Thm. 1), so one copy per device serves all shots.
+#pragma once
+#include <stdint.h>
+
+namespace nc {
+
+enum OpCode : uint8_t {
+  OP_END = 0,
+  // Frame-only virtual Cliffords (P~ <- V P~ V^dagger), bit-sliced over shots.
+  OP_FRAME_H, OP_FRAME_S, OP_FRAME_CX, OP_FRAME_CZ,
+  // Virtual Cliffords between active axes: frame conjugation + array update.
+  OP_ARRAY_H, OP_ARRAY_S, OP_ARRAY_CX, OP_ARRAY_CZ,
+  // Pauli rotations (App. B.1); f = theta * alpha, frame sign applied per shot.
+  OP_EXPAND_ROT,   // a = v, pa = new top position; phi <- phi (x) (|0> + e^{2i t}|1>)/sqrt2, t = f (-1)^{x_v}
+  OP_ROT_Z,        // a = v, pa; bit-1 amplitudes *= e^{2i t}, t = f (-1)^{x_v}
+  OP_ROT_X,        // a = v, pa; exp(-i t X), t = f (-1)^{z_v}
+  // Measurements (App. B.2); flags bit0 = alpha sign bit, bit1 = output now (row i3).
+  OP_MEAS_STATIC,  // i0 = z-mask offset; m = sign ^ parity(x & zmask); slot i2
+  OP_MEAS_RANDOM,  // a = v, i0 = event; m = [u < 1/2]; b = m^sign^z_v; H_v; x_v ^= b
+  OP_MEAS_ACTIVE_Z,// a = v, pa, i0 = event; mask, renormalise, demote; x_v ^= b
+  OP_MEAS_ACTIVE_X,// a = v, pa, i0 = event; fold, renormalise, demote; H_v; x_v ^= b
+  // Stochastic noise (Sec. 3.2): sites [i0, i1) in physical order.
+  OP_NOISE_BLOCK,
+  // Conditional Paulis (App. B.3): frame ^= E (mask i0) where slot i2 is set.
+  OP_FEEDFORWARD,
+  // Records and classical ops (Sec. 3.2, post-selection).
+  OP_REC_OUT,      // slot i2 -> meas row i3
+  OP_DETECTOR,     // XOR of i1 slots at slot list i0, ^ ref(i3) -> det row i3; postselect
+  OP_OBS_INCLUDE,  // obs slot i2 ^= XOR of i1 slots at slot list i0
+  OP_OBS_OUT,      // obs slot i2 ^ ref -> obs row i3 (masked by kept)
+  OP_KEPT_OUT,     // kept slot i2 -> kept row
+  OP_COUNT
+};
+
+enum : uint8_t { FLAG_SIGN = 1, FLAG_OUT = 2 };
+
+struct Op {
+  uint8_t code;
+  uint8_t flags;
+  uint16_t a;   // virtual qubit (control / v)
+  uint16_t b;   // virtual qubit (target)
+  uint8_t pa;   // array position of a
+  uint8_t pb;   // array position of b
+  uint32_t i0, i1, i2, i3;
+  double f;
+};
+static_assert(sizeof(Op) == 32, "Op must be 32 bytes");
+
+// Noise-site kinds (physical channel of the site).
+enum SiteKind : uint8_t { SITE_X = 0, SITE_Y, SITE_Z, SITE_D1, SITE_D2, SITE_FLIP };
+
+// Header of the device blob; all offsets are in bytes from the blob start
+// and 16-byte aligned.
+struct ProgHeader {
+  uint32_t magic, version;
+  uint32_t n_qubits, nw;          // nw = 32-bit words per virtual bit mask
+  uint32_t n_ops, n_sites;
+  uint32_t n_meas, n_det, n_obs, n_events;
+  uint32_t n_slots, k_max;
+  uint32_t kept_slot, n_mask_words, n_slot_list, pad0;
+  uint64_t off_ops, off_masks, off_q, off_seg_start, off_seg_end, off_site_info, off_site_eff,
+      off_slot_list, off_det_ref, off_obs_ref, total_bytes, pad1;
+};
+
+constexpr uint32_t kMagic = 0x4E435047u;  // "NCPG"
+constexpr uint32_t kVersion = 1;
+constexpr uint32_t kMaxK = 30;
+constexpr uint32_t kMaxQubits = 4096;
+
+// site_info word: kind (bits 0..3) | option count K (bits 4..7)
+inline uint32_t site_kind(uint32_t info) { return info & 15u; }
+inline uint32_t site_k(uint32_t info) { return (info >> 4) & 15u; }
+
+}  // namespace nc

@@ -1,0 +1,112 @@
+"""CPU-only checks of the C-ABI library: it builds, loads, exports every
+symbol include/nc.h declares, and its host-side compiler behaves (no GPU
+compute call is made here)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from gen import circuits as gc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def nc():
+    from paper_2604_27058_gb300 import build
+    build.build()
+    import paper_2604_27058_gb300 as m
+    return m
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "nc.h")).read()
+    return sorted(set(re.findall(r"\b(nc_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(nc):
+    from paper_2604_27058_gb300 import _nc
+    lib = _nc.lib()
+    declared = _declared_symbols()
+    assert set(declared) == set(_nc.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_status_strings(nc):
+    from paper_2604_27058_gb300 import _nc
+    lib = _nc.lib()
+    for code in range(10):
+        assert lib.nc_status_str(code)
+    assert lib.nc_abi_version() >> 16 == 1
+
+
+@pytest.mark.parametrize("name,text,kmax", [
+    ("tiny", gc.tiny_random(), 6),
+    ("surface", gc.surface_code_memory(), 0),
+    ("dense", gc.dense_random(), 20),
+    ("lowmagic", gc.low_magic_gadgets(), 10),
+])
+def test_compile_matches_oracle_schedule(nc, name, text, kmax):
+    from oracle.circuit import flatten
+    p = nc.compile(text)
+    f = flatten(text)
+    assert p.info.k_max == kmax
+    assert (p.info.n_qubits, p.info.n_meas, p.info.n_det, p.info.n_obs) == (
+        f.n_qubits, f.n_records, f.n_detectors, f.n_observables)
+    assert p.info.n_noise_sites == f.n_sites
+    assert p.info.n_events == f.n_events
+
+
+def test_k_schedule_matches_oracle_plan(nc):
+    from oracle.factored import FactoredSim
+    for seed in range(10):
+        text = gc.random_small(900 + seed, n=6, n_ops=80, t_frac=0.3)
+        assert nc.compile(text).info.k_max == FactoredSim(text).k_max
+
+
+def test_serialize_roundtrip(nc):
+    p = nc.compile(gc.surface_code_memory(d=3, rounds=3))
+    blob = p.serialize()
+    q = nc.Program.deserialize(blob)
+    assert q.serialize() == blob
+    assert q.info == p.info
+    with pytest.raises(nc.NcError) as e:
+        nc.Program.deserialize(blob[:-8])
+    assert e.value.name == "NC_E_ARG"
+    bad = bytearray(blob)
+    bad[0] ^= 0xFF
+    with pytest.raises(nc.NcError):
+        nc.Program.deserialize(bytes(bad))
+
+
+@pytest.mark.parametrize("text,code", [
+    ("FOO 1\n", "NC_E_UNSUPPORTED"),
+    ("M 0\nDETECTOR rec[-2]\n", "NC_E_PARSE"),
+    ("H 0\nREPEAT 2 {\nH 0\n", "NC_E_PARSE"),
+    ("X_ERROR(1.5) 0\n", "NC_E_PARSE"),
+    ("CX 0 0\n", "NC_E_PARSE"),
+    ("CX 0\n", "NC_E_PARSE"),
+    ("R_Z 0\n", "NC_E_PARSE"),
+    ("}\n", "NC_E_PARSE"),
+])
+def test_compile_errors(nc, text, code):
+    with pytest.raises(nc.NcError) as e:
+        nc.compile(text)
+    assert e.value.name == code
+
+
+def test_kmax_limit(nc):
+    text = "".join(f"H {q}\nT {q}\n" for q in range(31)) + "M 0\n"
+    with pytest.raises(nc.NcError) as e:
+        nc.compile(text)
+    assert e.value.name == "NC_E_KMAX"
+
+
+def test_repeat_and_aliases(nc):
+    a = nc.compile("REPEAT 3 {\nCNOT 0 1\nMZ 1\n}\n")
+    b = nc.compile("CX 0 1\nM 1\nCX 0 1\nM 1\nCX 0 1\nM 1\n")
+    assert a.info == b.info

@@ -1,0 +1,374 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances: records bit-exact (integer paths without any
+exclusion; paths with active amplitudes excluding flagged near-ties with
+|u - P| < 1e-6); amplitudes norm-wise relative error modulo global phase
+<= 1e-5 for the FP32 batched form and <= 1e-10 for the FP64 plain form;
+frames bit-exact.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from gen import circuits as gc
+from oracle.dense import DenseSim
+from oracle.factored import FactoredSim
+from oracle.records import assemble
+from oracle.stabilizer import FrameSim
+
+from parity import gpu_records, near_tie, state_error, unpack
+
+pytestmark = pytest.mark.gpu
+
+FP32_AMP_TOL = 1e-5
+FP64_AMP_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def nc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_27058_gb300 import build
+    build.build()
+    import paper_2604_27058_gb300 as m
+    return m
+
+
+def _check(oracle_run, ref_det, ref_obs, flat, gpu, seed, shots_idx, cols=None, postselect=False,
+           exact=False):
+    n = flagged = 0
+    for j, s in enumerate(shots_idx):
+        col = cols[j] if cols is not None else s
+        meas, p1 = oracle_run(s)
+        if not exact and p1 and near_tie(p1, seed, s):
+            flagged += 1
+            continue
+        r = assemble(flat, meas, ref_det, ref_obs, postselect)
+        assert [int(v) for v in gpu["meas"][:, col]] == r.meas, f"meas mismatch shot {s}"
+        assert [int(v) for v in gpu["det"][:, col]] == r.det, f"det mismatch shot {s}"
+        assert [int(v) for v in gpu["obs"][:, col]] == r.obs, f"obs mismatch shot {s}"
+        assert int(gpu["kept"][col]) == r.kept, f"kept mismatch shot {s}"
+        n += 1
+    return n, flagged
+
+
+def _dense_run(sim, seed):
+    def f(s):
+        m, p, _ = sim.run_raw(seed, s)
+        return m, p
+    return f
+
+
+def _factored_run(sim, seed):
+    def f(s):
+        tr = {}
+        m = sim.run_raw(seed, s, trace=tr)[0]
+        return m, tr.get("p1", {})
+    return f
+
+
+def _frame_run(sim, seed):
+    def f(s):
+        return sim.run_raw(seed, s)[0], None
+    return f
+
+
+# ---------------------------------------------------------------------------
+# random small circuits: every instruction kind, both forms, several tiles
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,tune", [("fp32", "g=2,t=64"), ("fp32", None), ("fp64", None)])
+@pytest.mark.parametrize("seed", range(10))
+def test_random_small_vs_dense(nc, seed, precision, tune):
+    n = 3 + seed % 5
+    text = gc.random_small(7000 + seed, n=n, n_ops=70, p_noise=0.04 if seed % 2 else 0.0,
+                           t_frac=0.3, meas_frac=0.12)
+    prog = nc.compile(text)
+    sim = DenseSim(text)
+    shots = 300
+    g = gpu_records(prog, shots, 31, precision=precision, tune=tune)
+    n_ok, flagged = _check(_dense_run(sim, 31), sim.ref_det, sim.ref_obs, sim.flat, g, 31, range(shots))
+    assert n_ok + flagged == shots and flagged <= 3
+
+
+# ---------------------------------------------------------------------------
+# workload 1: tiny near-Clifford circuit (n = 12, k_max <= 6)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_tiny_workload(nc, precision):
+    text = gc.tiny_random(seed=1)
+    prog = nc.compile(text)
+    assert prog.info.k_max <= 6
+    sim = FactoredSim(text)
+    shots = 2500
+    g = gpu_records(prog, shots, 1001, precision=precision)
+    n_ok, flagged = _check(_factored_run(sim, 1001), sim.ref_det, sim.ref_obs, sim.flat, g, 1001,
+                           range(shots))
+    assert flagged <= 5 and n_ok + flagged == shots
+
+
+def test_tiny_workload_full_size_sampled(nc):
+    text = gc.tiny_random(seed=1)
+    prog = nc.compile(text)
+    sim = FactoredSim(text)
+    shots = 10_000
+    for precision in ("fp32", "fp64"):
+        g = gpu_records(prog, shots, 1001, precision=precision)
+        idx = list(range(0, shots, 97)) + [shots - 1]
+        n_ok, flagged = _check(_factored_run(sim, 1001), sim.ref_det, sim.ref_obs, sim.flat, g, 1001, idx)
+        assert flagged <= 2
+
+
+# ---------------------------------------------------------------------------
+# workload 2: surface-code memory d=5, 25 rounds (k_max = 0): bit-exact
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,tune", [("fp32", "g=4,t=128"), ("fp32", None), ("fp64", None)])
+def test_surface_code_bit_exact(nc, precision, tune):
+    text = gc.surface_code_memory(d=5, rounds=25, p=1e-3)
+    prog = nc.compile(text)
+    sim = FrameSim(text)
+    shots = 700
+    g = gpu_records(prog, shots, 2002, precision=precision, tune=tune)
+    n_ok, _ = _check(_frame_run(sim, 2002), sim.ref_det, sim.ref_obs, sim.flat, g, 2002, range(shots),
+                     exact=True)
+    assert n_ok == shots
+    assert int(g["det"].sum()) > 0
+
+
+def test_surface_code_full_size_sampled(nc):
+    """10^8 shots in the benchmark's launch configuration; sampled shots are
+    recomputed one by one by the oracle."""
+    import torch
+    text = gc.surface_code_memory(d=5, rounds=25, p=1e-3)
+    prog = nc.compile(text)
+    sim = FrameSim(text)
+    shots = 100_000_000
+    res = nc.sample(prog, shots, 2002)
+    rng = np.random.default_rng(0)
+    idx = sorted(set(rng.integers(0, shots, 40).tolist()) | {0, 63, 64, shots - 1})
+    words = torch.tensor([i // 64 for i in idx], device="cuda")
+    sub = {k: res[k].index_select(1, words).cpu().numpy() for k in ("meas", "det", "obs", "kept")}
+    cols = [i % 64 for i in idx]
+    g = {k: np.unpackbits(sub[k].view(np.uint8).reshape(sub[k].shape[0], -1, 8), axis=2,
+                          bitorder="little").reshape(sub[k].shape[0], -1)
+         for k in sub}
+    g = {k: np.stack([g[k][:, j * 64 + c] for j, c in enumerate(cols)], axis=1) for k in g}
+    g["kept"] = g["kept"][0]
+    n_ok, _ = _check(_frame_run(sim, 2002), sim.ref_det, sim.ref_obs, sim.flat, g, 2002, idx,
+                     cols=list(range(len(idx))), exact=True)
+    assert n_ok == len(idx)
+    assert res["shots_kept"] == shots
+
+
+# ---------------------------------------------------------------------------
+# workload 3: dense limit (k = N); smaller dense case at full parity
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp64_batched"])
+def test_dense_small_records_and_amplitudes(nc, precision):
+    text = gc.dense_random(seed=33, n=10, layers=12)
+    prog = nc.compile(text)
+    sim = FactoredSim(text)
+    shots = 400
+    g = gpu_records(prog, shots, 3003, precision=precision, tune="g=2,t=256" if precision == "fp32" else None)
+    n_ok, flagged = _check(_factored_run(sim, 3003), sim.ref_det, sim.ref_obs, sim.flat, g, 3003, range(shots))
+    assert flagged <= 4
+    tol = FP32_AMP_TOL if precision == "fp32" else FP64_AMP_TOL
+    for shot in (0, 5, 130):
+        for ev in (0, 3, 7):
+            fx, fz, phi, k = nc.debug_dump(prog, 3003, shot, ev, precision=precision)
+            _, (ox, oz), ophi, act = sim.run_raw(3003, shot, stop_event=ev)
+            assert k == len(act)
+            assert (fx, fz) == (ox, oz)
+            assert state_error(phi, ophi) <= tol
+
+
+def test_dense_k20_mirror_returns_to_zero(nc):
+    """n = 20, 12 layers of random H/S/T + CX matchings, then U^dagger: the
+    active dimension reaches 20 and every record is 0 (FP32 batched)."""
+    text = gc.dense_random(seed=3, n=20, layers=12, mirror=True)
+    prog = nc.compile(text)
+    assert prog.info.k_max == 20
+    g = gpu_records(prog, 32, 3003, precision="fp32")
+    assert int(g["meas"].sum()) == 0
+
+
+def test_dense_k20_fp32_vs_fp64(nc):
+    """n = 20, k = 20: the FP32 batched form against the same layout in FP64
+    (records, flagged near-ties aside, and the amplitudes just before the
+    final measurements)."""
+    text = gc.dense_random(seed=3, n=20, layers=12)
+    prog = nc.compile(text)
+    assert prog.info.k_max == 20
+    shots = 32
+    a = gpu_records(prog, shots, 3003, precision="fp32")
+    b = gpu_records(prog, shots, 3003, precision="fp64_batched")
+    same = (a["meas"] == b["meas"]).all(axis=0)
+    assert same.sum() >= shots - 2
+    _, _, p32, k32 = nc.debug_dump(prog, 3003, 0, 0, precision="fp32")
+    _, _, p64, k64 = nc.debug_dump(prog, 3003, 0, 0, precision="fp64_batched")
+    assert k32 == k64 == 20
+    assert state_error(p32, p64) <= FP32_AMP_TOL
+    assert abs(np.linalg.norm(p64) - 1) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64_batched", "fp64"])
+def test_dense_k13_amplitudes_vs_oracle(nc, precision):
+    text = gc.dense_random(seed=3, n=14, layers=10)
+    prog = nc.compile(text)
+    sim = FactoredSim(text)
+    assert prog.info.k_max == sim.k_max == 13
+    tol = FP32_AMP_TOL if precision == "fp32" else FP64_AMP_TOL
+    for shot in (0, 77):
+        fx, fz, phi, k = nc.debug_dump(prog, 3003, shot, 0, precision=precision)
+        _, (ox, oz), ophi, act = sim.run_raw(3003, shot, stop_event=0)
+        assert k == len(act) == 13
+        assert (fx, fz) == (ox, oz)
+        assert state_error(phi, ophi) <= tol
+
+
+# ---------------------------------------------------------------------------
+# workload 4: low-magic gadgets with postselection
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_low_magic_postselected(nc, precision):
+    text = gc.low_magic_gadgets()
+    prog = nc.compile(text)
+    assert prog.info.k_max <= 10
+    sim = FactoredSim(text)
+    shots = 300
+    g = gpu_records(prog, shots, 4004, precision=precision, postselect=True)
+    n_ok, flagged = _check(_factored_run(sim, 4004), sim.ref_det, sim.ref_obs, sim.flat, g, 4004,
+                           range(shots), postselect=True)
+    assert flagged <= 3
+    assert g["shots_kept"] == int(g["kept"].sum())
+
+
+# ---------------------------------------------------------------------------
+# workload 5: batched sweep (several circuits in one call)
+# ---------------------------------------------------------------------------
+def test_sweep_batch_vs_oracle(nc):
+    circs = [gc.sweep_mirror(i) for i in range(64)]
+    pick = sorted(range(64), key=lambda i: circs[i].n * circs[i].depth)[:4]
+    progs = [nc.compile(circs[i].text) for i in pick]
+    shots = [200, 333, 64, 129]
+    seeds = [5005 + i for i in pick]
+    res = nc.sample_batch(progs, shots, seeds)
+    for j, i in enumerate(pick):
+        sim = FactoredSim(circs[i].text, k_limit=16)
+        g = {k: unpack(res[j][k], shots[j]) for k in ("meas", "det", "obs", "kept")}
+        g["kept"] = g["kept"][0]
+        g["meas"] = g["meas"][: progs[j].info.n_meas]
+        g["det"] = g["det"][: progs[j].info.n_det]
+        g["obs"] = g["obs"][: progs[j].info.n_obs]
+        n_ok, flagged = _check(_factored_run(sim, seeds[j]), sim.ref_det, sim.ref_obs, sim.flat, g,
+                               seeds[j], range(0, shots[j], 3))
+        assert flagged <= 2
+
+
+# ---------------------------------------------------------------------------
+# edge cases and API semantics
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shots", [1, 31, 32, 33, 64, 65, 129, 4097])
+def test_ragged_shot_counts(nc, shots):
+    text = gc.surface_code_memory(d=3, rounds=3, p=0.01)
+    prog = nc.compile(text)
+    sim = FrameSim(text)
+    for precision in ("fp32", "fp64"):
+        g = gpu_records(prog, shots, 9, precision=precision)
+        idx = sorted(set([0, shots - 1] + list(range(0, shots, max(1, shots // 20)))))
+        n_ok, _ = _check(_frame_run(sim, 9), sim.ref_det, sim.ref_obs, sim.flat, g, 9, idx, exact=True)
+        assert n_ok == len(idx)
+        # padding bits beyond `shots` are zero
+        raw = g["raw"]
+        for key in ("meas", "det", "kept"):
+            words = raw[key].cpu().numpy().view(np.uint64)
+            if shots % 64:
+                assert int(words[:, -1].max() >> np.uint64(shots % 64)) == 0
+
+
+def test_zero_shots_is_noop(nc):
+    prog = nc.compile("H 0\nM 0\n")
+    res = nc.sample(prog, 0, 1)
+    assert res["shots_run"] == 0
+
+
+def test_shot_offset_sharding_is_exact(nc):
+    text = gc.tiny_random(seed=2)
+    prog = nc.compile(text)
+    for precision in ("fp32", "fp64"):
+        full = gpu_records(prog, 512, 77, precision=precision)
+        a = gpu_records(prog, 256, 77, precision=precision, shot_offset=0)
+        b = gpu_records(prog, 256, 77, precision=precision, shot_offset=256)
+        assert (np.concatenate([a["meas"], b["meas"]], axis=1) == full["meas"]).all()
+
+
+def test_bad_shot_offset_rejected(nc):
+    prog = nc.compile("H 0\nM 0\n")
+    with pytest.raises(nc.NcError) as e:
+        nc.sample(prog, 64, 1, shot_offset=5)
+    assert e.value.name == "NC_E_ARG"
+
+
+def test_host_output_path_equals_device(nc):
+    text = gc.surface_code_memory(d=3, rounds=4, p=0.01)
+    prog = nc.compile(text)
+    d = nc.sample(prog, 1000, 5)
+    h = nc.sample_host(prog, 1000, 5)
+    for key in ("meas", "det", "obs", "kept"):
+        assert (d[key].cpu().numpy() == h[key]).all()
+    assert d["shots_kept"] == h["shots_kept"] == 1000
+
+
+def test_deserialized_program_same_records(nc):
+    text = gc.low_magic_gadgets()
+    p = nc.compile(text)
+    q = nc.Program.deserialize(p.serialize())
+    a = nc.sample(p, 700, 8, postselect=True)
+    b = nc.sample(q, 700, 8, postselect=True)
+    for key in ("meas", "det", "obs", "kept"):
+        assert (a[key].cpu().numpy() == b[key].cpu().numpy()).all()
+
+
+def test_batch_equals_individual(nc):
+    texts = [gc.surface_code_memory(d=3, rounds=2, p=0.02), gc.tiny_random(seed=4), gc.fig4_example(0.1)]
+    progs = [nc.compile(t) for t in texts]
+    shots = [100, 300, 65]
+    seeds = [1, 2, 3]
+    res = nc.sample_batch(progs, shots, seeds)
+    for p, s, sd, r in zip(progs, shots, seeds, res):
+        one = nc.sample(p, s, sd)
+        assert (one["meas"].cpu().numpy() == r["meas"].cpu().numpy()).all()
+
+
+def test_noiseless_option(nc):
+    prog = nc.compile(gc.surface_code_memory(d=3, rounds=5, p=0.05))
+    r = nc.sample(prog, 5000, 3, noiseless=True)
+    assert int(r["det"].abs().sum()) == 0
+
+
+def test_nondeterministic_detector_reported(nc):
+    prog = nc.compile("H 0\nM 0\nDETECTOR rec[-1]\n")
+    with pytest.raises(nc.NcError) as e:
+        nc.sample(prog, 64, 1)
+    assert e.value.name == "NC_E_NONDET_DETECTOR"
+
+
+def test_tuning_variants_agree(nc):
+    text = gc.tiny_random(seed=6)
+    prog = nc.compile(text)
+    base = gpu_records(prog, 1000, 12, precision="fp32")
+    for tune in ("g=1,t=32", "g=1,t=1024", "g=8,t=256", "g=4,t=64"):
+        g = gpu_records(prog, 1000, 12, precision="fp32", tune=tune)
+        assert (g["meas"] == base["meas"]).mean() > 0.999
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_closed_form_t_on_plus_statistics(nc, precision):
+    prog = nc.compile("H 0\nT 0\nMX 0\n")
+    shots = 200_000
+    g = gpu_records(prog, shots, 5, precision=precision)
+    p1 = float(g["meas"][0].mean())
+    exp = 1 - math.cos(math.pi / 8) ** 2
+    assert abs(p1 - exp) <= 5 * math.sqrt(exp * (1 - exp) / shots)
