@@ -148,10 +148,11 @@ def cpu_oracle_rate(text: str, seed: int, budget_s: float, cores: int):
     """Shots/s of the oracle on `cores` processes over a bounded sample."""
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores, initializer=_oracle_init, initargs=(text,)) as pool:
-        # calibrate on one chunk per worker
+        # warm every worker, then calibrate on 16 shots per worker
+        pool.map(_oracle_chunk, [(seed, 20_000_000 + i * 2, 2) for i in range(cores)])
         t0 = time.perf_counter()
-        pool.map(_oracle_chunk, [(seed, 10_000_000 + i * 4, 4) for i in range(cores)])
-        per_shot = (time.perf_counter() - t0) / 4
+        pool.map(_oracle_chunk, [(seed, 10_000_000 + i * 16, 16) for i in range(cores)])
+        per_shot = (time.perf_counter() - t0) / 16
         per_worker = max(1, int(budget_s / max(per_shot, 1e-6)))
         t0 = time.perf_counter()
         done = sum(pool.map(_oracle_chunk, [(seed, i * per_worker, per_worker) for i in range(cores)]))
@@ -222,8 +223,10 @@ def run_ours(args):
 
     def step(precision="fp32", out=None, host=False):
         if host:
-            return nc.sample_host(prog, shots, 2002, precision=precision, shot_offset=offset, out=out)
-        return nc.sample(prog, shots, 2002, precision=precision, shot_offset=offset, out=out or bufs)
+            return nc.sample_host(prog, shots, 2002, precision=precision, shot_offset=offset, out=out,
+                                  tune=args.tune)
+        return nc.sample(prog, shots, 2002, precision=precision, shot_offset=offset, out=out or bufs,
+                         tune=args.tune)
 
     def barrier():
         if world > 1:
@@ -326,6 +329,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tune", default=None, help="executor tuning override, e.g. g=64,t=64")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not os.environ.get("NC_BENCH_ALLOW_SHORT"):
         args.warmup = 3

@@ -20,10 +20,12 @@
 #include "kernels.cuh"
 
 namespace nc {
-size_t batched_smem_bytes(const DevProg& p, uint32_t G);
-cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t grid, uint32_t threads, size_t smem,
-                           cudaStream_t st);
-cudaError_t batched_occupancy(bool fp64, uint32_t threads, size_t smem, int* blocks_per_sm);
+size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W);
+uint32_t coarse_stride(uint32_t n_sites);
+uint32_t coarse_count(uint32_t n_sites);
+cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, uint32_t grid, uint32_t threads,
+                           size_t smem, cudaStream_t st);
+cudaError_t batched_occupancy(bool fp64, uint32_t W, uint32_t threads, size_t smem, int* blocks_per_sm);
 cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st);
 bool plain_supported(const DevProg& p);
 }  // namespace nc
@@ -66,6 +68,9 @@ DevProg dev_view(const ProgHeader& h, const uint8_t* base) {
   d.slot_list = reinterpret_cast<const uint32_t*>(base + h.off_slot_list);
   d.det_ref = reinterpret_cast<const uint32_t*>(base + h.off_det_ref);
   d.obs_ref = reinterpret_cast<const uint32_t*>(base + h.off_obs_ref);
+  d.site_opt = reinterpret_cast<const uint32_t*>(base + h.off_site_opt);
+  d.opt_tab = reinterpret_cast<const uint32_t*>(base + h.off_opt_tab);
+  d.plist = reinterpret_cast<const uint16_t*>(base + h.off_plist);
   d.n_qubits = h.n_qubits;
   d.nw = h.nw;
   d.n_ops = h.n_ops;
@@ -129,31 +134,37 @@ struct Scratch {
   }
 };
 
+// Launch shape of the batched executor: G 32-shot words per tile, W words
+// per owner thread (G / W owners), T threads per CTA.
 struct Tuning {
-  uint32_t G, T;
+  uint32_t G, T, W;
 };
 
 Tuning choose_tuning(const DevProg& d, const char* tune) {
   Tuning t;
-  if (d.k_max == 0) t = {128, 128};
-  else if (d.k_max <= 6) t = {32, 256};
-  else if (d.k_max <= 10) t = {8, 256};
-  else if (d.k_max <= 13) t = {2, 512};
-  else t = {1, 1024};
+  if (d.k_max == 0) t = {128, 128, 1};
+  else if (d.k_max <= 6) t = {32, 256, 1};
+  else if (d.k_max <= 10) t = {8, 256, 1};
+  else if (d.k_max <= 13) t = {2, 512, 1};
+  else t = {1, 1024, 1};
   if (tune) {
-    unsigned g = 0, th = 0;
+    unsigned v = 0;
     const char* s = tune;
     while (*s) {
-      if (sscanf(s, "g=%u", &g) == 1) t.G = g;
-      else if (sscanf(s, "t=%u", &th) == 1) t.T = th;
+      if (sscanf(s, "g=%u", &v) == 1) t.G = v;
+      else if (sscanf(s, "t=%u", &v) == 1) t.T = v;
+      else if (sscanf(s, "w=%u", &v) == 1) t.W = v;
       const char* c = strchr(s, ',');
       if (!c) break;
       s = c + 1;
     }
   }
+  if (t.W != 1 && t.W != 2 && t.W != 4) t.W = 1;
+  if (t.G < t.W) t.W = t.G;
   // keep the shared-memory footprint under the opt-in limit
-  while (t.G > 1 && batched_smem_bytes(d, t.G) > 220 * 1024) t.G >>= 1;
-  if (t.T < t.G) t.T = t.G;
+  while (t.G > t.W && batched_smem_bytes(d, t.G, t.W) > 220 * 1024) t.G >>= 1;
+  if (t.T < t.G / t.W) t.T = t.G / t.W;
+  if (t.T < 32) t.T = 32;
   return t;
 }
 
@@ -223,16 +234,18 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
     NC_TRY(launch_plain(L, stream));
   } else {
     Tuning tu = choose_tuning(L.p, tune);
-    if (!pow2(tu.G) || !pow2(tu.T) || tu.T > 1024) return NC_E_ARG;
+    if (!pow2(tu.G) || !pow2(tu.T) || !pow2(tu.W) || tu.T > (tu.W == 1 ? 1024u : 256u)) return NC_E_ARG;
     L.G = tu.G;
+    L.qc_stride = coarse_stride(h.n_sites);
+    L.qc_n = coarse_count(h.n_sites);
     const uint64_t S = 32ull * tu.G;
     L.n_tiles = (uint32_t)((L.row_words32 + tu.G - 1) / tu.G);
-    const size_t smem = batched_smem_bytes(L.p, tu.G);
+    const size_t smem = batched_smem_bytes(L.p, tu.G, tu.W);
     int per_sm = 0, n_sm = 0, dev = 0;
     NC_TRY(cudaGetDevice(&dev));
     NC_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     const bool fp64 = precision == NC_FP64_BATCHED;
-    NC_TRY(batched_occupancy(fp64, tu.T, smem, &per_sm));
+    NC_TRY(batched_occupancy(fp64, tu.W, tu.T, smem, &per_sm));
     if (per_sm < 1) return NC_E_UNSUPPORTED;
     uint64_t grid = std::min<uint64_t>(L.n_tiles, (uint64_t)per_sm * n_sm);
     if (h.k_max > 0) {
@@ -244,9 +257,7 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
       grid = std::min(grid, cap);
       NC_TRY(scratch.get(&L.work, per_cta * grid));
     }
-    if (!(lflags & LF_NOISELESS) && h.n_sites)
-      NC_TRY(scratch.get((void**)&L.nf, grid * S * sizeof(uint32_t)));
-    NC_TRY(launch_batched(L, fp64, (uint32_t)grid, tu.T, smem, stream));
+    NC_TRY(launch_batched(L, fp64, tu.W, (uint32_t)grid, tu.T, smem, stream));
   }
 done:
   return st;
@@ -463,7 +474,8 @@ nc_status nc_program_deserialize(const void* buf, size_t len, nc_program** out) 
   std::memcpy(&h, buf, sizeof(h));
   if (h.magic != kMagic || h.version != kVersion || h.total_bytes + sizeof(nc_info_counts) != len) return NC_E_ARG;
   uint64_t offs[] = {h.off_ops, h.off_masks, h.off_q, h.off_seg_start, h.off_seg_end, h.off_site_info,
-                     h.off_site_eff, h.off_slot_list, h.off_det_ref, h.off_obs_ref};
+                     h.off_site_eff, h.off_slot_list, h.off_det_ref, h.off_obs_ref,
+                     h.off_site_opt, h.off_opt_tab, h.off_plist};
   for (uint64_t o : offs)
     if (o > h.total_bytes || (o & 15)) return NC_E_ARG;
   if (h.off_ops + (uint64_t)h.n_ops * sizeof(Op) > h.total_bytes || h.k_max > kMaxK || h.n_qubits > kMaxQubits)

@@ -788,7 +788,9 @@ struct Compiler {
     bool active_z = false;
     for (int q = 0; q < n && !active_z; q++)
       if (p.zb(q) && pos_of[q] >= 0) active_z = true;
-    bool direct_out = o.record >= 0 && o.site < 0;
+    // every record is written by its measurement; a later record-flip fault
+    // patches the output bit (no separate output instruction)
+    bool direct_out = o.record >= 0;
     if (p.xzero() && !active_z) {
       Op m = mk(OP_MEAS_STATIC);
       m.i0 = add_mask(p, false, true);
@@ -850,6 +852,41 @@ struct Compiler {
 
 }  // namespace
 
+// Store up to kInline u16 entries in the instruction (e[0..3], count in pa).
+void set_inline(Op& o, const std::vector<uint32_t>& v) {
+  if (v.size() > kInline) {
+    o.pa = kNoInline;
+    return;
+  }
+  for (uint32_t x : v)
+    if (x > 0xFFFF) {
+      o.pa = kNoInline;
+      return;
+    }
+  o.pa = (uint8_t)v.size();
+  o.f = 0.0;
+  for (size_t i = 0; i < v.size(); i++) o.e[i] = (uint16_t)v[i];
+}
+
+// Frame plane indices of a mask (x part then z part, nw words each).
+std::vector<uint32_t> mask_planes(const std::vector<uint32_t>& masks, uint32_t off, uint32_t nw, uint32_t n,
+                                  bool has_x, bool has_z) {
+  std::vector<uint32_t> out;
+  for (int part = 0; part < 2; part++) {
+    if ((part == 0 && !has_x) || (part == 1 && !has_z)) continue;
+    uint32_t base = off + ((part == 1 && has_x) ? nw : 0);
+    for (uint32_t w = 0; w < nw; w++) {
+      uint32_t bits = masks[base + w];
+      while (bits) {
+        uint32_t q = w * 32 + (uint32_t)__builtin_ctz(bits);
+        bits &= bits - 1;
+        out.push_back(part == 0 ? q : n + q);
+      }
+    }
+  }
+  return out;
+}
+
 // ---------------------------------------------------------------------------
 // Entry point
 // ---------------------------------------------------------------------------
@@ -886,10 +923,6 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
       if (po.kind == K_MEAS && po.site >= 0) flip_record[po.site] = po.record;
     auto flush_flips_fast = [&]() {
       for (int64_t s : flips) c.noise_site(s, SITE_FLIP, fl.site_p[s], 0, c.record_id[flip_record[s]]);
-      for (int64_t s : flips) {
-        c.pending_out.push_back(c.record_id[flip_record[s]]);
-        c.pending_row.push_back(flip_record[s]);
-      }
       flips.clear();
     };
 
@@ -959,6 +992,36 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     }
     c.code.push_back({c.mk(OP_END), {}, -1});
 
+    // ---------------- fuse static resets with their conditional X ----------------
+    {
+      std::vector<int64_t> n_uses(c.next_id, 0);
+      for (auto& e : c.code)
+        for (auto id : e.uses) n_uses[id]++;
+      std::vector<Emitted> fused;
+      fused.reserve(c.code.size());
+      for (size_t i = 0; i < c.code.size(); i++) {
+        Emitted& e = c.code[i];
+        if (e.op.code == OP_MEAS_STATIC && !(e.op.flags & FLAG_OUT) && e.def >= 0 && i + 1 < c.code.size() &&
+            c.code[i + 1].op.code == OP_FEEDFORWARD && c.code[i + 1].uses.size() == 1 &&
+            c.code[i + 1].uses[0] == e.def && n_uses[e.def] == 1) {
+          auto mp = mask_planes(c.masks, e.op.i0, (uint32_t)c.nw32, (uint32_t)c.n, true, false);
+          auto ep = mask_planes(c.masks, c.code[i + 1].op.i0, (uint32_t)c.nw32, (uint32_t)c.n, true, true);
+          if (mp.size() <= kInline && ep.size() <= 4) {
+            Op o = e.op;
+            set_inline(o, mp);
+            o.flags |= FLAG_RESET;
+            o.pb = (uint8_t)ep.size();
+            for (int j = 0; j < 4; j++) o.r[j] = j < (int)ep.size() ? (uint16_t)ep[j] : 0;
+            fused.push_back({o, {}, -1});
+            i++;
+            continue;
+          }
+        }
+        fused.push_back(e);
+      }
+      c.code.swap(fused);
+    }
+
     // ---------------- record-slot allocation (linear scan) ----------------
     int64_t n_ids = c.next_id;
     std::vector<int64_t> last_use(n_ids, -1);
@@ -990,21 +1053,33 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
       if (e.def >= 0) slot_of[e.def] = alloc();
       Op o = e.op;
       switch (o.code) {
-        case OP_MEAS_STATIC: case OP_MEAS_RANDOM: case OP_MEAS_ACTIVE_Z: case OP_MEAS_ACTIVE_X:
+        case OP_MEAS_STATIC:
+          if (o.flags & FLAG_RESET) break;
+          o.i2 = (uint32_t)slot_of[e.def];
+          // the mask is the z-support of the mapped observable; the parity
+          // reads the frame's x planes on that support
+          set_inline(o, mask_planes(c.masks, o.i0, (uint32_t)c.nw32, (uint32_t)c.n, true, false));
+          break;
+        case OP_MEAS_RANDOM: case OP_MEAS_ACTIVE_Z: case OP_MEAS_ACTIVE_X:
           o.i2 = (uint32_t)slot_of[e.def];
           break;
-        case OP_FEEDFORWARD: case OP_REC_OUT:
+        case OP_FEEDFORWARD:
+          o.i2 = (uint32_t)slot_of[e.uses[0]];
+          set_inline(o, mask_planes(c.masks, o.i0, (uint32_t)c.nw32, (uint32_t)c.n, true, true));
+          break;
+        case OP_REC_OUT:
           o.i2 = (uint32_t)slot_of[e.uses[0]];
           break;
         case OP_DETECTOR:
+        case OP_OBS_INCLUDE: {
           o.i0 = (uint32_t)slot_list.size();
-          for (auto id : e.uses) slot_list.push_back((uint32_t)slot_of[id]);
+          std::vector<uint32_t> sl;
+          for (auto id : e.uses) sl.push_back((uint32_t)slot_of[id]);
+          slot_list.insert(slot_list.end(), sl.begin(), sl.end());
+          if (o.code == OP_OBS_INCLUDE) o.i2 = (uint32_t)slot_of[o.i2];
+          set_inline(o, sl);
           break;
-        case OP_OBS_INCLUDE:
-          o.i0 = (uint32_t)slot_list.size();
-          for (auto id : e.uses) slot_list.push_back((uint32_t)slot_of[id]);
-          o.i2 = (uint32_t)slot_of[o.i2];
-          break;
+        }
         case OP_OBS_OUT:
           o.i2 = (uint32_t)slot_of[obs_id[o.i3]];
           break;
@@ -1031,6 +1106,27 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
       if (c.site_kind[s] == SITE_FLIP) site_eff[s] = (uint32_t)slot_of[c.site_flip_id[s]];
     // A flip slot must still be live at its noise block: it is, because the
     // block is a use of the id (recorded in Emitted::uses).
+
+    // ---------------- sparse noise options ----------------
+    std::vector<uint32_t> site_opt(c.site_kind.size(), 0), opt_tab;
+    std::vector<uint16_t> plist;
+    for (size_t s = 0; s < c.site_kind.size(); s++) {
+      if (c.site_kind[s] == SITE_FLIP) {
+        site_opt[s] = (uint32_t)(opt_tab.size() / 2);
+        opt_tab.push_back(site_eff[s]);
+        opt_tab.push_back((uint32_t)flip_record[s]);
+        continue;
+      }
+      uint32_t k = c.site_kind[s] == SITE_D1 ? 3 : c.site_kind[s] == SITE_D2 ? 15 : 1;
+      site_opt[s] = (uint32_t)(opt_tab.size() / 2);
+      for (uint32_t j = 0; j < k; j++) {
+        auto pl = mask_planes(c.masks, c.site_eff[s] + j * 2 * (uint32_t)c.nw32, (uint32_t)c.nw32,
+                              (uint32_t)c.n, true, true);
+        opt_tab.push_back((uint32_t)plist.size());
+        opt_tab.push_back((uint32_t)pl.size());
+        for (auto x : pl) plist.push_back((uint16_t)x);
+      }
+    }
 
     // ---------------- survival table (Sec. 3.2, integer form) ----------------
     size_t S = c.site_p.size();
@@ -1059,7 +1155,9 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
         }
       for (size_t i = 0; i < S; i++) {
         uint32_t k = c.site_kind[i] == SITE_D1 ? 3 : c.site_kind[i] == SITE_D2 ? 15 : 1;
-        info[i] = (uint32_t)c.site_kind[i] | (k << 4);
+        uint32_t idx = site_opt[i];
+        if (idx >= (1u << 24)) fail(2, "noise option table too large");
+        info[i] = (uint32_t)c.site_kind[i] | (k << 4) | (idx << 8);
       }
     }
 
@@ -1081,6 +1179,8 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     h.kept_slot = (uint32_t)slot_of[kept_id];
     h.n_mask_words = (uint32_t)c.masks.size();
     h.n_slot_list = (uint32_t)slot_list.size();
+    h.n_opt = (uint32_t)(opt_tab.size() / 2);
+    h.n_plist = (uint32_t)plist.size();
     uint64_t off = (sizeof(ProgHeader) + 15) & ~15ull;
     auto place = [&](uint64_t bytes) {
       uint64_t o = off;
@@ -1097,6 +1197,9 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     h.off_slot_list = place(slot_list.size() * 4);
     h.off_det_ref = place((size_t)fl.det * 4);
     h.off_obs_ref = place((size_t)fl.n_obs * 4);
+    h.off_site_opt = place(S * 4);
+    h.off_opt_tab = place(opt_tab.size() * 4);
+    h.off_plist = place(plist.size() * 2);
     h.total_bytes = off;
     out.blob.assign(off, 0);
     std::memcpy(out.blob.data(), &h, sizeof(h));
@@ -1111,6 +1214,9 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     cp(h.off_site_info, info.data(), S * 4);
     cp(h.off_site_eff, site_eff.data(), S * 4);
     cp(h.off_slot_list, slot_list.data(), slot_list.size() * 4);
+    cp(h.off_site_opt, site_opt.data(), S * 4);
+    cp(h.off_opt_tab, opt_tab.data(), opt_tab.size() * 4);
+    cp(h.off_plist, plist.data(), plist.size() * 2);
     out.counts = c.counts;
     return 0;
   } catch (CompileError& e) {

@@ -76,51 +76,174 @@ __device__ __forceinline__ bool is_meas(uint8_t c) {
 // ---------------------------------------------------------------------------
 // Batched executor
 // ---------------------------------------------------------------------------
-template <typename real>
-__global__ void __launch_bounds__(1024) exec_batched(LaunchParams L) {
+// A tile is G 32-shot words; thread t < G / W owns words t*W .. t*W+W-1.
+// Shared-memory layout of one CTA (u32 words unless noted):
+//   OPS Op [2][kChunk] double-buffered instruction chunks (cp.async)
+//   QC  u64 [qc_n] coarse survival index
+//   PL  [2N][G]  frame planes (x bits of virtual qubit q at plane q, z bits at N + q)
+//   SL  [n_slots][G] record slots
+//   NF  [32][G]  next fault of shot (word w, bit j) at NF[j * G + w]
+//   TMP [G]      per-word scratch (virtual outcomes of an active measurement)
+//   QU  u16 [owner warps][kQueue] warp queues of due (word, bit) noise entries
+//   RED f64 [2][S] measurement sums / scales (k_max > 0 only)
+constexpr uint32_t kChunk = 128;
+constexpr uint32_t kQueue = 512;
+
+struct SmemLayout {
+  size_t pl, sl, nf, tmp, qu, ops, qc, red, bytes;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(uint32_t n_qubits, uint32_t n_slots, uint32_t k_max, uint32_t G,
+                                                  uint32_t W, uint32_t qc_n) {
+  SmemLayout L;
+  size_t w = 0;
+  L.ops = w;
+  w += (size_t)2 * kChunk * (sizeof(Op) / 4);
+  L.qc = w;
+  w += (size_t)2 * qc_n;
+  L.pl = w;
+  w += (size_t)2 * n_qubits * G;
+  L.sl = w;
+  w += (size_t)n_slots * G;
+  L.nf = w;
+  w += (size_t)32 * G;
+  L.tmp = w;
+  w += G;
+  w = (w + 3) & ~(size_t)3;
+  L.qu = w;
+  const size_t owner_warps = (G / W + 31) / 32;
+  w += owner_warps * (kQueue / 2);
+  w = (w + 3) & ~(size_t)3;
+  L.red = w;
+  if (k_max > 0) w += (size_t)2 * 2 * 32 * G;  // 2 doubles per shot
+  L.bytes = w * 4;
+  return L;
+}
+
+template <int W>
+struct Vw {
+  uint32_t v[W];
+};
+
+template <int W>
+__device__ __forceinline__ Vw<W> vld(const uint32_t* p) {
+  Vw<W> r;
+  if constexpr (W == 4) {
+    uint4 a = *reinterpret_cast<const uint4*>(p);
+    r.v[0] = a.x; r.v[1] = a.y; r.v[2] = a.z; r.v[3] = a.w;
+  } else if constexpr (W == 2) {
+    uint2 a = *reinterpret_cast<const uint2*>(p);
+    r.v[0] = a.x; r.v[1] = a.y;
+  } else {
+    r.v[0] = *p;
+  }
+  return r;
+}
+
+template <int W>
+__device__ __forceinline__ void vst(uint32_t* p, const Vw<W>& r) {
+  if constexpr (W == 4) *reinterpret_cast<uint4*>(p) = make_uint4(r.v[0], r.v[1], r.v[2], r.v[3]);
+  else if constexpr (W == 2) *reinterpret_cast<uint2*>(p) = make_uint2(r.v[0], r.v[1]);
+  else *p = r.v[0];
+}
+
+template <int W>
+__device__ __forceinline__ Vw<W> vfill(uint32_t x) {
+  Vw<W> r;
+#pragma unroll
+  for (int i = 0; i < W; i++) r.v[i] = x;
+  return r;
+}
+
+template <int W>
+__device__ __forceinline__ void vxor(Vw<W>& a, const Vw<W>& b) {
+#pragma unroll
+  for (int i = 0; i < W; i++) a.v[i] ^= b.v[i];
+}
+
+template <int W>
+__device__ __forceinline__ Vw<W> vand(const Vw<W>& a, const Vw<W>& b) {
+  Vw<W> r;
+#pragma unroll
+  for (int i = 0; i < W; i++) r.v[i] = a.v[i] & b.v[i];
+  return r;
+}
+
+__device__ __forceinline__ uint32_t pick4(const uint4& v, uint32_t i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+// W >= 2 variants serve the frame-bound (small k) programs with at most 256
+// threads per CTA; W = 1 also serves large k with up to 1024 threads.
+template <typename real, int W>
+__global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams L) {
   using C = typename Cx<real>::T;
   extern __shared__ __align__(16) uint32_t smem[];
   const DevProg& p = L.p;
   const uint32_t G = L.G, S = 32u * G, N = p.n_qubits, T = blockDim.x, t = threadIdx.x;
-  uint32_t* X = smem;                  // [N][G]
-  uint32_t* Z = X + N * G;             // [N][G]
-  uint32_t* SL = Z + N * G;            // [n_slots][G]
-  uint32_t* TMP = SL + p.n_slots * G;  // [G]
-  size_t red_off = ((size_t)(2 * N + p.n_slots + 1) * G + 1) & ~(size_t)1;
-  double* RED = reinterpret_cast<double*>(smem + red_off);  // [2][S] when k_max > 0
+  const SmemLayout lay = smem_layout(N, p.n_slots, p.k_max, G, W, L.qc_n);
+  uint32_t* PL = smem + lay.pl;
+  uint32_t* X = PL;
+  uint32_t* Z = PL + (size_t)N * G;
+  uint32_t* SL = smem + lay.sl;
+  uint32_t* NF = smem + lay.nf;
+  uint32_t* TMP = smem + lay.tmp;
+  const uint32_t lane = t & 31u, warp = t >> 5;
+  uint16_t* QU = reinterpret_cast<uint16_t*>(smem + lay.qu) + (size_t)warp * kQueue;
+  double* RED = reinterpret_cast<double*>(smem + lay.red);
   C* work = reinterpret_cast<C*>(L.work) + (size_t)blockIdx.x * L.work_stride;
+  Op* OPB = reinterpret_cast<Op*>(smem + lay.ops);
+  uint64_t* QC = reinterpret_cast<uint64_t*>(smem + lay.qc);
 
-  const bool owner = t < G;
+  const uint32_t n_owners = G / W;
+  const bool owner = t < n_owners;
+  const bool owner_warp = (t & ~31u) < n_owners;
+  const uint32_t tw = t * W;  // first word of this thread
   const uint32_t R = T >= S ? T / S : 1u;  // threads per shot in array loops
   const uint32_t sub = T >= S ? t / S : 0u;
-  const uint32_t noiseless = L.flags & LF_NOISELESS;
+  const bool noisy = !(L.flags & LF_NOISELESS) && p.n_sites > 0;
+  const uint32_t kept_off = p.kept_slot * G;
+  const uint32_t n_chunks = (p.n_ops + kChunk - 1) / kChunk;
+
+  auto load_chunk = [&](uint32_t c) {
+    const uint32_t first = c * kChunk, cnt = min(kChunk, p.n_ops - first);
+    const uint4* src = reinterpret_cast<const uint4*>(p.ops + first);
+    uint4* dst = reinterpret_cast<uint4*>(OPB + (c & 1u) * kChunk);
+    for (uint32_t i = t; i < 2 * cnt; i += T) cp_async16(dst + i, src + i);
+    cp_async_commit();
+  };
+  for (uint32_t c = t; c < L.qc_n; c += T) QC[c] = __ldg(p.q + (size_t)c * L.qc_stride);
+  __syncthreads();
 
   for (uint32_t tile = blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
-    const uint64_t my_word = (uint64_t)tile * G + t;
-    const bool word_ok = owner && my_word < L.row_words32;
-    const uint64_t s0_local = my_word * 32u;
-    const uint64_t s0 = L.shot_offset + s0_local;
-    uint32_t valid = 0;
-    if (word_ok) {
-      if (s0_local + 32 <= L.shots) valid = ~0u;
-      else if (s0_local < L.shots) valid = (1u << (uint32_t)(L.shots - s0_local)) - 1u;
-    }
-    uint32_t* nf = L.nf + ((size_t)blockIdx.x * S) + (size_t)t * 32u;
-    uint32_t minsite = kNoFault >> 4;
+    const uint64_t word0 = (uint64_t)tile * G + tw;  // call-local index of my first word
+    const uint64_t tile_s0 = L.shot_offset + (uint64_t)tile * S;
+    const uint64_t s0 = tile_s0 + (uint64_t)tw * 32u;  // global shot of my first word
+    Vw<W> valid = vfill<W>(0u);
     if (owner) {
-      for (uint32_t q = 0; q < N; q++) {
-        X[q * G + t] = 0;
-        Z[q * G + t] = 0;
-      }
-      for (uint32_t s = 0; s < p.n_slots; s++) SL[s * G + t] = 0;
-      SL[p.kept_slot * G + t] = valid;
-      if (!noiseless && p.n_sites) {
-        for (uint32_t j = 0; j < 32; j++) {
-          uint32_t f = ((valid >> j) & 1u) ? next_fault(p, L.seed, s0 + j, 0) : kNoFault;
-          nf[j] = f;
-          minsite = min(minsite, f >> 4);
+#pragma unroll
+      for (int i = 0; i < W; i++) {
+        const uint64_t sl0 = (word0 + i) * 32u;
+        if (word0 + i < L.row_words32) {
+          if (sl0 + 32 <= L.shots) valid.v[i] = ~0u;
+          else if (sl0 < L.shots) valid.v[i] = (1u << (uint32_t)(L.shots - sl0)) - 1u;
         }
       }
+    }
+    uint32_t minsite = kNoFault >> 4;
+    if (owner) {
+      for (uint32_t q = 0; q < 2 * N; q++) vst<W>(PL + q * G + tw, vfill<W>(0u));
+      for (uint32_t s = 0; s < p.n_slots; s++) vst<W>(SL + s * G + tw, vfill<W>(0u));
+      vst<W>(SL + kept_off + tw, valid);
+#pragma unroll
+      for (int i = 0; i < W; i++)
+        for (uint32_t j = 0; j < 32; j++) {
+          uint32_t f = (noisy && ((valid.v[i] >> j) & 1u))
+                           ? next_fault_coarse(p, L.seed, s0 + (uint64_t)i * 32u + j, 0, QC, L.qc_stride)
+                           : kNoFault;
+          NF[j * G + tw + i] = f;
+          minsite = min(minsite, f >> 4);
+        }
     }
     if (p.k_max > 0) {
       for (uint32_t s = t; s < S; s += T) {
@@ -131,22 +254,500 @@ __global__ void __launch_bounds__(1024) exec_batched(LaunchParams L) {
       }
     }
     uint32_t k = 0;
-    __syncthreads();
 
-    auto store = [&](uint32_t* base, uint32_t row, uint32_t v) {
-      if (word_ok) base[(size_t)row * L.row_words32 + my_word] = v;
+    auto store = [&](uint32_t* base, uint32_t row, const Vw<W>& v) {
+      uint32_t* dst = base + (size_t)row * L.row_words32 + word0;
+#pragma unroll
+      for (int i = 0; i < W; i++)
+        if (word0 + i < L.row_words32) dst[i] = v.v[i];
     };
     auto fbit = [&](const uint32_t* plane, uint32_t s) -> uint32_t {
       return (plane[s >> 5] >> (s & 31u)) & 1u;
     };
+    auto plane = [&](uint32_t q) -> uint32_t* { return PL + q * G + tw; };
+    auto slot = [&](uint32_t s) -> uint32_t* { return SL + s * G + tw; };
 
-    for (uint32_t pc = 0; pc < p.n_ops; pc++) {
-      const Op op = p.ops[pc];
-      const uint32_t code = op.code;
-      if (L.stop_event != 0xffffffffu && is_meas(op.code) && op.i1 == L.stop_event) {
+    load_chunk(0);
+    cp_async_wait_all();
+    __syncthreads();
+    for (uint32_t ch = 0; ch < n_chunks; ch++) {
+      if (ch + 1 < n_chunks) load_chunk(ch + 1);
+      const Op* ops = OPB + (ch & 1u) * kChunk;
+      const uint32_t n_here = min(kChunk, p.n_ops - ch * kChunk);
+      Op nxt = ops[0];
+      for (uint32_t pi = 0; pi < n_here; pi++) {
+        const Op op = nxt;
+        if (pi + 1 < n_here) nxt = ops[pi + 1];
+        switch (op.code) {
+          case OP_FRAME_H:
+          case OP_FRAME_S:
+          case OP_FRAME_CX:
+          case OP_FRAME_CZ:
+            if (owner) {
+              if (op.code == OP_FRAME_H) {
+                Vw<W> a = vld<W>(plane(op.a)), b = vld<W>(plane(N + op.a));
+                vst<W>(plane(op.a), b);
+                vst<W>(plane(N + op.a), a);
+              } else if (op.code == OP_FRAME_S) {
+                Vw<W> zz = vld<W>(plane(N + op.a));
+                vxor<W>(zz, vld<W>(plane(op.a)));
+                vst<W>(plane(N + op.a), zz);
+              } else if (op.code == OP_FRAME_CX) {
+                Vw<W> xb = vld<W>(plane(op.b)), za = vld<W>(plane(N + op.a));
+                vxor<W>(xb, vld<W>(plane(op.a)));
+                vxor<W>(za, vld<W>(plane(N + op.b)));
+                vst<W>(plane(op.b), xb);
+                vst<W>(plane(N + op.a), za);
+              } else {
+                Vw<W> xa = vld<W>(plane(op.a)), xb = vld<W>(plane(op.b));
+                Vw<W> za = vld<W>(plane(N + op.a)), zb = vld<W>(plane(N + op.b));
+                vxor<W>(za, xb);
+                vxor<W>(zb, xa);
+                vst<W>(plane(N + op.a), za);
+                vst<W>(plane(N + op.b), zb);
+              }
+            }
+            break;
+          case OP_MEAS_STATIC:
+            if (L.stop_event != 0xffffffffu && op.i1 == L.stop_event) goto dump;
+            if (owner) {
+              Vw<W> m = vfill<W>((op.flags & FLAG_SIGN) ? ~0u : 0u);
+              if (op.pa != kNoInline) {
+                switch (op.pa) {
+                  case 4: vxor<W>(m, vld<W>(plane(op.e[3]))); [[fallthrough]];
+                  case 3: vxor<W>(m, vld<W>(plane(op.e[2]))); [[fallthrough]];
+                  case 2: vxor<W>(m, vld<W>(plane(op.e[1]))); [[fallthrough]];
+                  case 1: vxor<W>(m, vld<W>(plane(op.e[0]))); [[fallthrough]];
+                  default: break;
+                }
+              } else {
+                const uint32_t* zm = p.masks + op.i0;
+                for (uint32_t w = 0; w < p.nw; w++) {
+                  uint32_t bits = __ldg(zm + w);
+                  while (bits) {
+                    uint32_t q = w * 32u + (__ffs(bits) - 1);
+                    bits &= bits - 1;
+                    vxor<W>(m, vld<W>(plane(q)));
+                  }
+                }
+              }
+              if (op.flags & FLAG_RESET) {
+                // fused reset: frame ^= X-image where m is set
+                for (uint32_t r = 0; r < op.pb; r++) {
+                  Vw<W> v = vld<W>(plane(op.r[r]));
+                  vxor<W>(v, m);
+                  vst<W>(plane(op.r[r]), v);
+                }
+              } else {
+                vst<W>(slot(op.i2), m);
+                if ((op.flags & FLAG_OUT) && (L.flags & LF_OUT_MEAS))
+                  store(L.meas, op.i3, vand<W>(m, vld<W>(slot(p.kept_slot))));
+              }
+            }
+            break;
+          case OP_MEAS_RANDOM:
+            if (L.stop_event != 0xffffffffu && op.i1 == L.stop_event) goto dump;
+            if (owner) {
+              const uint64_t g = s0 >> 7;
+              const uint4 tb = philox(make_uint4((uint32_t)g, (uint32_t)(g >> 32), TAG_MT, op.i0), key_of(L.seed));
+              const uint32_t sel = (uint32_t)(s0 >> 5) & 3u;
+              Vw<W> m, xa, za;
+              const uint32_t sg = (op.flags & FLAG_SIGN) ? ~0u : 0u;
+#pragma unroll
+              for (int i = 0; i < W; i++) m.v[i] = ~pick4(tb, (sel + i) & 3u);
+              // H_v then x_v ^= b: new x = old z ^ b, new z = old x
+              Vw<W> ox = vld<W>(plane(op.a)), oz = vld<W>(plane(N + op.a));
+#pragma unroll
+              for (int i = 0; i < W; i++) {
+                const uint32_t b = m.v[i] ^ sg ^ oz.v[i];
+                xa.v[i] = oz.v[i] ^ b;
+                za.v[i] = ox.v[i];
+              }
+              vst<W>(plane(op.a), xa);
+              vst<W>(plane(N + op.a), za);
+              vst<W>(slot(op.i2), m);
+              if ((op.flags & FLAG_OUT) && (L.flags & LF_OUT_MEAS))
+                store(L.meas, op.i3, vand<W>(m, vld<W>(slot(p.kept_slot))));
+            }
+            break;
+          case OP_NOISE_BLOCK:
+            if (owner_warp) {
+              while (true) {
+                // due entries of this lane's words, compacted warp-wide
+                uint32_t due[W];
+                uint32_t cnt = 0;
+#pragma unroll
+                for (int i = 0; i < W; i++) {
+                  due[i] = 0;
+                  if (owner && minsite < op.i1)
+                    for (uint32_t j = 0; j < 32; j++)
+                      if ((NF[j * G + tw + i] >> 4) < op.i1) due[i] |= 1u << j;
+                  cnt += __popc(due[i]);
+                }
+                uint32_t incl = cnt;
+#pragma unroll
+                for (uint32_t d = 1; d < 32; d <<= 1) {
+                  uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+                  if (lane >= d) incl += v;
+                }
+                const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                if (total == 0) break;
+                uint32_t pos = incl - cnt;
+#pragma unroll
+                for (int i = 0; i < W; i++) {
+                  uint32_t d = due[i];
+                  while (d && pos < kQueue) {
+                    uint32_t j = __ffs(d) - 1;
+                    d &= d - 1;
+                    QU[pos++] = (uint16_t)((((lane * W) + i) << 5) | j);
+                  }
+                }
+                __syncwarp();
+                const uint32_t n_q = min(total, kQueue);
+                for (uint32_t qi = lane; qi < n_q; qi += 32) {
+                  const uint32_t e = QU[qi];
+                  const uint32_t w = (warp * 32u * W) + (e >> 5), j = e & 31u, bit = 1u << j;
+                  const uint64_t shot = tile_s0 + (uint64_t)w * 32u + j;
+                  uint32_t f = NF[j * G + w];
+                  do {
+                    const uint32_t site = f >> 4, opt = f & 15u;
+                    const uint32_t info = __ldg(p.site_info + site);
+                    const uint2* ot = reinterpret_cast<const uint2*>(p.opt_tab) + (info >> 8);
+                    if ((info & 15u) == SITE_FLIP) {
+                      const uint2 sr = __ldg(ot);
+                      atomicXor(&SL[sr.x * G + w], bit);
+                      if ((L.flags & LF_OUT_MEAS) && (SL[kept_off + w] & bit) &&
+                          (uint64_t)w + (uint64_t)tile * G < L.row_words32)
+                        atomicXor(&L.meas[(size_t)sr.y * L.row_words32 + (uint64_t)tile * G + w], bit);
+                    } else {
+                      const uint2 o2 = __ldg(ot + opt);
+                      for (uint32_t r = 0; r < o2.y; r++)
+                        atomicXor(&PL[(uint32_t)__ldg(p.plist + o2.x + r) * G + w], bit);
+                    }
+                    f = next_fault_coarse(p, L.seed, shot, site + 1, QC, L.qc_stride);
+                  } while ((f >> 4) < op.i1);
+                  NF[j * G + w] = f;
+                }
+                __syncwarp();
+                if (owner) {
+                  uint32_t m = kNoFault >> 4;
+#pragma unroll
+                  for (int i = 0; i < W; i++)
+                    for (uint32_t j = 0; j < 32; j++) m = min(m, NF[j * G + tw + i] >> 4);
+                  minsite = m;
+                }
+                if (total <= kQueue) break;
+              }
+            }
+            break;
+          case OP_FEEDFORWARD:
+            if (owner) {
+              const Vw<W> c = vld<W>(slot(op.i2));
+              if (op.pa != kNoInline) {
+                for (uint32_t r = 0; r < op.pa; r++) {
+                  Vw<W> v = vld<W>(plane(op.e[r]));
+                  vxor<W>(v, c);
+                  vst<W>(plane(op.e[r]), v);
+                }
+              } else {
+                const uint32_t* mk = p.masks + op.i0;
+                for (uint32_t part = 0; part < 2; part++)
+                  for (uint32_t w = 0; w < p.nw; w++) {
+                    uint32_t bits = __ldg(mk + part * p.nw + w);
+                    while (bits) {
+                      uint32_t q = w * 32u + (__ffs(bits) - 1);
+                      bits &= bits - 1;
+                      Vw<W> v = vld<W>(plane(part * N + q));
+                      vxor<W>(v, c);
+                      vst<W>(plane(part * N + q), v);
+                    }
+                  }
+              }
+            }
+            break;
+          case OP_REC_OUT:
+            if (owner && (L.flags & LF_OUT_MEAS))
+              store(L.meas, op.i3, vand<W>(vld<W>(slot(op.i2)), vld<W>(slot(p.kept_slot))));
+            break;
+          case OP_DETECTOR:
+          case OP_OBS_INCLUDE:
+            if (owner) {
+              Vw<W> d = vfill<W>(0u);
+              if (op.pa != kNoInline) {
+                switch (op.pa) {
+                  case 4: vxor<W>(d, vld<W>(slot(op.e[3]))); [[fallthrough]];
+                  case 3: vxor<W>(d, vld<W>(slot(op.e[2]))); [[fallthrough]];
+                  case 2: vxor<W>(d, vld<W>(slot(op.e[1]))); [[fallthrough]];
+                  case 1: vxor<W>(d, vld<W>(slot(op.e[0]))); [[fallthrough]];
+                  default: break;
+                }
+              } else {
+                for (uint32_t j = 0; j < op.i1; j++) vxor<W>(d, vld<W>(slot(__ldg(p.slot_list + op.i0 + j))));
+              }
+              if (op.code == OP_OBS_INCLUDE) {
+                Vw<W> o = vld<W>(slot(op.i2));
+                vxor<W>(o, d);
+                vst<W>(slot(op.i2), o);
+              } else {
+                if (!(L.flags & LF_REFERENCE) && __ldg(p.det_ref + op.i3)) vxor<W>(d, vfill<W>(~0u));
+                Vw<W> kept = vld<W>(slot(p.kept_slot));
+                if (L.flags & LF_OUT_DET) store(L.det, op.i3, vand<W>(d, kept));
+                if (L.flags & LF_POSTSELECT) {
+#pragma unroll
+                  for (int i = 0; i < W; i++) kept.v[i] &= ~d.v[i];
+                  vst<W>(slot(p.kept_slot), kept);
+                }
+              }
+            }
+            break;
+          case OP_OBS_OUT:
+            if (owner && (L.flags & LF_OUT_OBS)) {
+              Vw<W> v = vld<W>(slot(op.i2));
+              if (!(L.flags & LF_REFERENCE) && __ldg(p.obs_ref + op.i3)) vxor<W>(v, vfill<W>(~0u));
+              store(L.obs, op.i3, vand<W>(v, vld<W>(slot(p.kept_slot))));
+            }
+            break;
+          case OP_KEPT_OUT:
+            if (owner) {
+              const Vw<W> kept = vld<W>(slot(p.kept_slot));
+              if (L.flags & LF_OUT_KEPT) store(L.kept, 0, kept);
+              uint32_t c = 0;
+#pragma unroll
+              for (int i = 0; i < W; i++) c += __popc(kept.v[i]);
+              if (c) atomicAdd(L.kept_count, (unsigned long long)c);
+            }
+            break;
+          default: {
+            // ---- instructions on the active array (all threads) ----
+            if (is_meas(op.code) && L.stop_event != 0xffffffffu && op.i1 == L.stop_event) goto dump;
+            const uint32_t code = op.code;
+            if (owner && code >= OP_ARRAY_H && code <= OP_ARRAY_CZ) {
+              // frame part of the array Clifford
+              if (code == OP_ARRAY_H) {
+                Vw<W> a = vld<W>(plane(op.a)), b = vld<W>(plane(N + op.a));
+                vst<W>(plane(op.a), b);
+                vst<W>(plane(N + op.a), a);
+              } else if (code == OP_ARRAY_S) {
+                Vw<W> zz = vld<W>(plane(N + op.a));
+                vxor<W>(zz, vld<W>(plane(op.a)));
+                vst<W>(plane(N + op.a), zz);
+              } else if (code == OP_ARRAY_CX) {
+                Vw<W> xb = vld<W>(plane(op.b)), za = vld<W>(plane(N + op.a));
+                vxor<W>(xb, vld<W>(plane(op.a)));
+                vxor<W>(za, vld<W>(plane(N + op.b)));
+                vst<W>(plane(op.b), xb);
+                vst<W>(plane(N + op.a), za);
+              } else {
+                Vw<W> xa = vld<W>(plane(op.a)), xb = vld<W>(plane(op.b));
+                Vw<W> za = vld<W>(plane(N + op.a)), zb = vld<W>(plane(N + op.b));
+                vxor<W>(za, xb);
+                vxor<W>(zb, xa);
+                vst<W>(plane(N + op.a), za);
+                vst<W>(plane(N + op.b), zb);
+              }
+            }
+            if (code < OP_ARRAY_H || code > OP_MEAS_ACTIVE_X) break;
+            __syncthreads();
+            const uint32_t pa = op.pa;
+            if (code == OP_EXPAND_ROT) {
+              const double c2 = cos(2.0 * op.f), s2 = sin(2.0 * op.f);
+              const real rs = (real)0.70710678118654752440;
+              const uint32_t n = 1u << k;
+              for (uint32_t s = t % S; s < S; s += T) {
+                const real sn = (real)(fbit(X + op.a * G, s) ? -s2 : s2);
+                C ph;
+                ph.x = (real)c2 * rs;
+                ph.y = sn * rs;
+                for (uint32_t j = sub; j < n; j += R) {
+                  C a = work[(size_t)j * S + s];
+                  work[(size_t)j * S + s] = cscale(a, rs);
+                  work[(size_t)(j + n) * S + s] = cmul(a, ph);
+                }
+              }
+              k++;
+            } else if (code == OP_ROT_Z) {
+              const double c2 = cos(2.0 * op.f), s2 = sin(2.0 * op.f);
+              const uint32_t half = 1u << (k - 1);
+              for (uint32_t s = t % S; s < S; s += T) {
+                C ph;
+                ph.x = (real)c2;
+                ph.y = (real)(fbit(X + op.a * G, s) ? -s2 : s2);
+                for (uint32_t j = sub; j < half; j += R) {
+                  size_t i1 = (size_t)(insert0(j, pa) | (1u << pa)) * S + s;
+                  work[i1] = cmul(work[i1], ph);
+                }
+              }
+            } else if (code == OP_ROT_X) {
+              const double c1 = cos(op.f), s1 = sin(op.f);
+              const uint32_t half = 1u << (k - 1);
+              for (uint32_t s = t % S; s < S; s += T) {
+                const real cr = (real)c1, sr = (real)(fbit(Z + op.a * G, s) ? -s1 : s1);
+                for (uint32_t j = sub; j < half; j += R) {
+                  size_t i0 = (size_t)insert0(j, pa) * S + s, i1 = i0 + ((size_t)1 << pa) * S;
+                  C a = work[i0], b = work[i1], na, nb;
+                  na.x = cr * a.x + sr * b.y;
+                  na.y = cr * a.y - sr * b.x;
+                  nb.x = sr * a.y + cr * b.x;
+                  nb.y = -sr * a.x + cr * b.y;
+                  work[i0] = na;
+                  work[i1] = nb;
+                }
+              }
+            } else if (code == OP_ARRAY_H) {
+              const real rs = (real)0.70710678118654752440;
+              const uint32_t half = 1u << (k - 1);
+              for (uint32_t s = t % S; s < S; s += T)
+                for (uint32_t j = sub; j < half; j += R) {
+                  size_t i0 = (size_t)insert0(j, pa) * S + s, i1 = i0 + ((size_t)1 << pa) * S;
+                  C a = work[i0], b = work[i1];
+                  work[i0] = cscale(cadd(a, b), rs);
+                  work[i1] = cscale(csub(a, b), rs);
+                }
+            } else if (code == OP_ARRAY_S) {
+              const uint32_t half = 1u << (k - 1);
+              for (uint32_t s = t % S; s < S; s += T)
+                for (uint32_t j = sub; j < half; j += R) {
+                  size_t i1 = (size_t)(insert0(j, pa) | (1u << pa)) * S + s;
+                  C a = work[i1], r;
+                  r.x = -a.y;
+                  r.y = a.x;
+                  work[i1] = r;
+                }
+            } else if (code == OP_ARRAY_CX || code == OP_ARRAY_CZ) {
+              const uint32_t pb = op.pb, lo = min(pa, pb), hi = max(pa, pb);
+              const uint32_t quarter = 1u << (k - 2);
+              for (uint32_t s = t % S; s < S; s += T)
+                for (uint32_t j = sub; j < quarter; j += R) {
+                  uint32_t base = insert0(insert0(j, lo), hi);
+                  if (code == OP_ARRAY_CX) {
+                    size_t i0 = (size_t)(base | (1u << pa)) * S + s;
+                    size_t i1 = (size_t)(base | (1u << pa) | (1u << pb)) * S + s;
+                    C a = work[i0];
+                    work[i0] = work[i1];
+                    work[i1] = a;
+                  } else {
+                    size_t i = (size_t)(base | (1u << pa) | (1u << pb)) * S + s;
+                    C a = work[i];
+                    a.x = -a.x;
+                    a.y = -a.y;
+                    work[i] = a;
+                  }
+                }
+            } else {  // active measurement
+              const bool xm = code == OP_MEAS_ACTIVE_X;
+              const uint32_t half = 1u << (k - 1);
+              const real rs = (real)0.70710678118654752440;
+              for (uint32_t s = t; s < S; s += T) {
+                RED[s] = 0.0;
+                RED[S + s] = 0.0;
+              }
+              __syncthreads();
+              for (uint32_t s = t % S; s < S; s += T) {
+                double a0 = 0.0, a1 = 0.0;
+                for (uint32_t j = sub; j < half; j += R) {
+                  size_t i0 = (size_t)insert0(j, pa) * S + s, i1 = i0 + ((size_t)1 << pa) * S;
+                  C u = work[i0], v = work[i1];
+                  if (xm) {
+                    double ux = u.x, uy = u.y, vx = v.x, vy = v.y;
+                    double px = ux + vx, py = uy + vy, mx = ux - vx, my = uy - vy;
+                    a0 += 0.5 * (px * px + py * py);
+                    a1 += 0.5 * (mx * mx + my * my);
+                  } else {
+                    a0 += cnorm2(u);
+                    a1 += cnorm2(v);
+                  }
+                }
+                atomicAdd(&RED[s], a0);
+                atomicAdd(&RED[S + s], a1);
+              }
+              __syncthreads();
+              if (owner) {
+                const uint64_t g = s0 >> 7;
+                const uint4 tb = philox(make_uint4((uint32_t)g, (uint32_t)(g >> 32), TAG_MT, op.i0), key_of(L.seed));
+                const uint32_t sel = (uint32_t)(s0 >> 5) & 3u;
+                const uint32_t abit = (op.flags & FLAG_SIGN) ? 1u : 0u;
+                const Vw<W> kept = vld<W>(slot(p.kept_slot));
+                Vw<W> mw, xa = vld<W>(plane(op.a)), za = vld<W>(plane(N + op.a));
+#pragma unroll
+                for (int i = 0; i < W; i++) {
+                  const uint32_t top = pick4(tb, (sel + i) & 3u);
+                  const uint32_t pw = xm ? za.v[i] : xa.v[i];
+                  uint32_t m32 = 0, b32 = 0;
+                  for (uint32_t j = 0; j < 32; j++) {
+                    const uint32_t s = (tw + i) * 32u + j;
+                    const double S0 = RED[s], S1 = RED[S + s], tot = S0 + S1;
+                    const uint32_t pbit = (pw >> j) & 1u;
+                    const double p1 = tot > 0.0 ? ((1u ^ abit ^ pbit) ? S1 : S0) / tot : 0.0;
+                    const uint32_t m = ((valid.v[i] >> j) & 1u)
+                                           ? draw_outcome(L.seed, s0 + (uint64_t)i * 32u + j, op.i0, (top >> j) & 1u, p1)
+                                           : 0u;
+                    const uint32_t b = m ^ abit ^ pbit;
+                    const double sb = b ? S1 : S0;
+                    RED[s] = sb > 0.0 ? 1.0 / sqrt(sb) : 0.0;
+                    m32 |= m << j;
+                    b32 |= b << j;
+                  }
+                  mw.v[i] = m32;
+                  TMP[tw + i] = b32;
+                  if (xm) {
+                    const uint32_t ox = xa.v[i];
+                    xa.v[i] = za.v[i] ^ b32;
+                    za.v[i] = ox;
+                  } else {
+                    xa.v[i] ^= b32;
+                  }
+                }
+                vst<W>(plane(op.a), xa);
+                vst<W>(plane(N + op.a), za);
+                vst<W>(slot(op.i2), mw);
+                if ((op.flags & FLAG_OUT) && (L.flags & LF_OUT_MEAS)) store(L.meas, op.i3, vand<W>(mw, kept));
+              }
+              __syncthreads();
+              const uint32_t top_pos = k - 1;
+              for (uint32_t s = t % S; s < S; s += T) {
+                const uint32_t b = fbit(TMP, s);
+                const real sc = (real)RED[s];
+                if (pa == top_pos) {
+                  for (uint32_t j = sub; j < half; j += R) {
+                    C o0 = work[(size_t)j * S + s], o1 = work[(size_t)(j + half) * S + s], v;
+                    if (xm) v = cscale(b ? csub(o0, o1) : cadd(o0, o1), rs);
+                    else v = b ? o1 : o0;
+                    work[(size_t)j * S + s] = cscale(v, sc);
+                  }
+                } else {
+                  const uint32_t quarter = 1u << (k - 2);
+                  for (uint32_t j = sub; j < quarter; j += R) {
+                    uint32_t base = insert0(insert0(j, pa), top_pos);
+                    size_t p00 = (size_t)base * S + s, p10 = (size_t)(base | (1u << pa)) * S + s;
+                    size_t p01 = (size_t)(base | (1u << top_pos)) * S + s;
+                    size_t p11 = (size_t)(base | (1u << pa) | (1u << top_pos)) * S + s;
+                    C n0, n1;
+                    if (xm) {
+                      C o00 = work[p00], o10 = work[p10], o01 = work[p01], o11 = work[p11];
+                      n0 = cscale(b ? csub(o00, o10) : cadd(o00, o10), rs);
+                      n1 = cscale(b ? csub(o01, o11) : cadd(o01, o11), rs);
+                    } else {
+                      n0 = b ? work[p10] : work[p00];
+                      n1 = b ? work[p11] : work[p01];
+                    }
+                    work[p00] = cscale(n0, sc);
+                    work[p10] = cscale(n1, sc);
+                  }
+                }
+              }
+              k--;
+            }
+            __syncthreads();
+            break;
+          }
+        }
+        continue;
+      dump:
+        // debug stop: copy the frame and amplitudes of one shot, then leave
+        cp_async_wait_all();
         __syncthreads();
         if (t == 0) {
-          uint32_t ds = (uint32_t)(L.dump_shot - tile * (uint64_t)S);
+          const uint32_t ds = (uint32_t)(L.dump_shot - tile * (uint64_t)S);
           for (uint32_t q = 0; q < p.nw * 2; q++) L.dump_frame[q] = 0;
           for (uint32_t q = 0; q < N; q++) {
             L.dump_frame[q >> 5] |= fbit(X + q * G, ds) << (q & 31);
@@ -161,345 +762,9 @@ __global__ void __launch_bounds__(1024) exec_batched(LaunchParams L) {
         }
         return;
       }
-      switch (code) {
-        case OP_FRAME_H:
-        case OP_ARRAY_H:
-          if (owner) {
-            uint32_t a = X[op.a * G + t];
-            X[op.a * G + t] = Z[op.a * G + t];
-            Z[op.a * G + t] = a;
-          }
-          break;
-        case OP_FRAME_S:
-        case OP_ARRAY_S:
-          if (owner) Z[op.a * G + t] ^= X[op.a * G + t];
-          break;
-        case OP_FRAME_CX:
-        case OP_ARRAY_CX:
-          if (owner) {
-            X[op.b * G + t] ^= X[op.a * G + t];
-            Z[op.a * G + t] ^= Z[op.b * G + t];
-          }
-          break;
-        case OP_FRAME_CZ:
-        case OP_ARRAY_CZ:
-          if (owner) {
-            uint32_t xa = X[op.a * G + t], xb = X[op.b * G + t];
-            Z[op.a * G + t] ^= xb;
-            Z[op.b * G + t] ^= xa;
-          }
-          break;
-        case OP_MEAS_STATIC:
-          if (owner) {
-            uint32_t m = (op.flags & FLAG_SIGN) ? ~0u : 0u;
-            const uint32_t* zm = p.masks + op.i0;
-            for (uint32_t w = 0; w < p.nw; w++) {
-              uint32_t bits = __ldg(zm + w);
-              while (bits) {
-                uint32_t q = w * 32u + (__ffs(bits) - 1);
-                bits &= bits - 1;
-                m ^= X[q * G + t];
-              }
-            }
-            SL[op.i2 * G + t] = m;
-            if ((op.flags & FLAG_OUT) && (L.flags & LF_OUT_MEAS))
-              store(L.meas, op.i3, m & SL[p.kept_slot * G + t]);
-          }
-          break;
-        case OP_MEAS_RANDOM:
-          if (owner) {
-            uint32_t top = meas_top_word(L.seed, s0, op.i0);
-            uint32_t m = ~top;
-            uint32_t b = m ^ ((op.flags & FLAG_SIGN) ? ~0u : 0u) ^ Z[op.a * G + t];
-            uint32_t xa = X[op.a * G + t];
-            X[op.a * G + t] = Z[op.a * G + t] ^ b;
-            Z[op.a * G + t] = xa;
-            SL[op.i2 * G + t] = m;
-            if ((op.flags & FLAG_OUT) && (L.flags & LF_OUT_MEAS))
-              store(L.meas, op.i3, m & SL[p.kept_slot * G + t]);
-          }
-          break;
-        case OP_NOISE_BLOCK:
-          if (owner && minsite < op.i1) {
-            uint32_t nmin = kNoFault >> 4;
-            for (uint32_t j = 0; j < 32; j++) {
-              uint32_t f = nf[j];
-              if ((f >> 4) >= op.i1) {
-                nmin = min(nmin, f >> 4);
-                continue;
-              }
-              const uint32_t bit = 1u << j;
-              while ((f >> 4) < op.i1) {
-                uint32_t site = f >> 4, opt = f & 15u;
-                uint32_t info = __ldg(p.site_info + site), eff = __ldg(p.site_eff + site);
-                if ((info & 15u) == SITE_FLIP) {
-                  SL[eff * G + t] ^= bit;
-                } else {
-                  const uint32_t* mk = p.masks + eff + opt * 2u * p.nw;
-                  for (uint32_t w = 0; w < p.nw; w++) {
-                    uint32_t xb = __ldg(mk + w), zb = __ldg(mk + p.nw + w);
-                    while (xb) {
-                      uint32_t q = w * 32u + (__ffs(xb) - 1);
-                      xb &= xb - 1;
-                      X[q * G + t] ^= bit;
-                    }
-                    while (zb) {
-                      uint32_t q = w * 32u + (__ffs(zb) - 1);
-                      zb &= zb - 1;
-                      Z[q * G + t] ^= bit;
-                    }
-                  }
-                }
-                f = next_fault(p, L.seed, s0 + j, site + 1);
-              }
-              nf[j] = f;
-              nmin = min(nmin, f >> 4);
-            }
-            minsite = nmin;
-          }
-          break;
-        case OP_FEEDFORWARD:
-          if (owner) {
-            uint32_t c = SL[op.i2 * G + t];
-            if (c) {
-              const uint32_t* mk = p.masks + op.i0;
-              for (uint32_t w = 0; w < p.nw; w++) {
-                uint32_t xb = __ldg(mk + w), zb = __ldg(mk + p.nw + w);
-                while (xb) {
-                  uint32_t q = w * 32u + (__ffs(xb) - 1);
-                  xb &= xb - 1;
-                  X[q * G + t] ^= c;
-                }
-                while (zb) {
-                  uint32_t q = w * 32u + (__ffs(zb) - 1);
-                  zb &= zb - 1;
-                  Z[q * G + t] ^= c;
-                }
-              }
-            }
-          }
-          break;
-        case OP_REC_OUT:
-          if (owner && (L.flags & LF_OUT_MEAS)) store(L.meas, op.i3, SL[op.i2 * G + t] & SL[p.kept_slot * G + t]);
-          break;
-        case OP_DETECTOR:
-          if (owner) {
-            uint32_t d = 0;
-            for (uint32_t j = 0; j < op.i1; j++) d ^= SL[__ldg(p.slot_list + op.i0 + j) * G + t];
-            if (!(L.flags & LF_REFERENCE) && __ldg(p.det_ref + op.i3)) d = ~d;
-            uint32_t kept = SL[p.kept_slot * G + t];
-            if (L.flags & LF_OUT_DET) store(L.det, op.i3, d & kept);
-            if (L.flags & LF_POSTSELECT) SL[p.kept_slot * G + t] = kept & ~d;
-          }
-          break;
-        case OP_OBS_INCLUDE:
-          if (owner) {
-            uint32_t d = 0;
-            for (uint32_t j = 0; j < op.i1; j++) d ^= SL[__ldg(p.slot_list + op.i0 + j) * G + t];
-            SL[op.i2 * G + t] ^= d;
-          }
-          break;
-        case OP_OBS_OUT:
-          if (owner && (L.flags & LF_OUT_OBS)) {
-            uint32_t v = SL[op.i2 * G + t];
-            if (!(L.flags & LF_REFERENCE) && __ldg(p.obs_ref + op.i3)) v = ~v;
-            store(L.obs, op.i3, v & SL[p.kept_slot * G + t]);
-          }
-          break;
-        case OP_KEPT_OUT:
-          if (owner) {
-            uint32_t kept = SL[p.kept_slot * G + t];
-            if (L.flags & LF_OUT_KEPT) store(L.kept, 0, kept);
-            if (word_ok && kept) atomicAdd(L.kept_count, (unsigned long long)__popc(kept));
-          }
-          break;
-        default:
-          break;
-      }
-      // ---- active-array part (all threads) ----
-      if (code >= OP_ARRAY_H && code <= OP_MEAS_ACTIVE_X && code != OP_MEAS_STATIC &&
-          code != OP_MEAS_RANDOM) {
-        __syncthreads();
-        const uint32_t pa = op.pa;
-        if (code == OP_EXPAND_ROT) {
-          const double c2 = cos(2.0 * op.f), s2 = sin(2.0 * op.f);
-          const real rs = (real)0.70710678118654752440;
-          const uint32_t n = 1u << k;
-          for (uint32_t s = t % S; s < S; s += T) {
-            const real sn = (real)(fbit(X + op.a * G, s) ? -s2 : s2);
-            C ph;
-            ph.x = (real)c2 * rs;
-            ph.y = sn * rs;
-            for (uint32_t j = sub; j < n; j += R) {
-              C a = work[(size_t)j * S + s];
-              work[(size_t)j * S + s] = cscale(a, rs);
-              work[(size_t)(j + n) * S + s] = cmul(a, ph);
-            }
-          }
-          k++;
-        } else if (code == OP_ROT_Z) {
-          const double c2 = cos(2.0 * op.f), s2 = sin(2.0 * op.f);
-          const uint32_t half = 1u << (k - 1);
-          for (uint32_t s = t % S; s < S; s += T) {
-            C ph;
-            ph.x = (real)c2;
-            ph.y = (real)(fbit(X + op.a * G, s) ? -s2 : s2);
-            for (uint32_t j = sub; j < half; j += R) {
-              size_t i1 = (size_t)(insert0(j, pa) | (1u << pa)) * S + s;
-              work[i1] = cmul(work[i1], ph);
-            }
-          }
-        } else if (code == OP_ROT_X) {
-          const double c1 = cos(op.f), s1 = sin(op.f);
-          const uint32_t half = 1u << (k - 1);
-          for (uint32_t s = t % S; s < S; s += T) {
-            const real cr = (real)c1, sr = (real)(fbit(Z + op.a * G, s) ? -s1 : s1);
-            for (uint32_t j = sub; j < half; j += R) {
-              size_t i0 = (size_t)insert0(j, pa) * S + s, i1 = i0 + ((size_t)1 << pa) * S;
-              C a = work[i0], b = work[i1], na, nb;
-              na.x = cr * a.x + sr * b.y;
-              na.y = cr * a.y - sr * b.x;
-              nb.x = sr * a.y + cr * b.x;
-              nb.y = -sr * a.x + cr * b.y;
-              work[i0] = na;
-              work[i1] = nb;
-            }
-          }
-        } else if (code == OP_ARRAY_H) {
-          const real rs = (real)0.70710678118654752440;
-          const uint32_t half = 1u << (k - 1);
-          for (uint32_t s = t % S; s < S; s += T)
-            for (uint32_t j = sub; j < half; j += R) {
-              size_t i0 = (size_t)insert0(j, pa) * S + s, i1 = i0 + ((size_t)1 << pa) * S;
-              C a = work[i0], b = work[i1];
-              work[i0] = cscale(cadd(a, b), rs);
-              work[i1] = cscale(csub(a, b), rs);
-            }
-        } else if (code == OP_ARRAY_S) {
-          const uint32_t half = 1u << (k - 1);
-          for (uint32_t s = t % S; s < S; s += T)
-            for (uint32_t j = sub; j < half; j += R) {
-              size_t i1 = (size_t)(insert0(j, pa) | (1u << pa)) * S + s;
-              C a = work[i1], r;
-              r.x = -a.y;
-              r.y = a.x;
-              work[i1] = r;
-            }
-        } else if (code == OP_ARRAY_CX || code == OP_ARRAY_CZ) {
-          const uint32_t pb = op.pb, lo = min(pa, pb), hi = max(pa, pb);
-          const uint32_t quarter = 1u << (k - 2);
-          for (uint32_t s = t % S; s < S; s += T)
-            for (uint32_t j = sub; j < quarter; j += R) {
-              uint32_t base = insert0(insert0(j, lo), hi);
-              if (code == OP_ARRAY_CX) {
-                size_t i0 = (size_t)(base | (1u << pa)) * S + s, i1 = (size_t)(base | (1u << pa) | (1u << pb)) * S + s;
-                C a = work[i0];
-                work[i0] = work[i1];
-                work[i1] = a;
-              } else {
-                size_t i = (size_t)(base | (1u << pa) | (1u << pb)) * S + s;
-                C a = work[i];
-                a.x = -a.x;
-                a.y = -a.y;
-                work[i] = a;
-              }
-            }
-        } else {  // active measurement
-          const bool xm = code == OP_MEAS_ACTIVE_X;
-          const uint32_t half = 1u << (k - 1);
-          const real rs = (real)0.70710678118654752440;
-          for (uint32_t s = t; s < S; s += T) {
-            RED[s] = 0.0;
-            RED[S + s] = 0.0;
-          }
-          __syncthreads();
-          for (uint32_t s = t % S; s < S; s += T) {
-            double a0 = 0.0, a1 = 0.0;
-            for (uint32_t j = sub; j < half; j += R) {
-              size_t i0 = (size_t)insert0(j, pa) * S + s, i1 = i0 + ((size_t)1 << pa) * S;
-              C u = work[i0], v = work[i1];
-              if (xm) {
-                double ux = u.x, uy = u.y, vx = v.x, vy = v.y;
-                double px = ux + vx, py = uy + vy, mx = ux - vx, my = uy - vy;
-                a0 += 0.5 * (px * px + py * py);
-                a1 += 0.5 * (mx * mx + my * my);
-              } else {
-                a0 += cnorm2(u);
-                a1 += cnorm2(v);
-              }
-            }
-            atomicAdd(&RED[s], a0);
-            atomicAdd(&RED[S + s], a1);
-          }
-          __syncthreads();
-          if (owner) {
-            const uint32_t top = meas_top_word(L.seed, s0, op.i0);
-            const uint32_t pw = xm ? Z[op.a * G + t] : X[op.a * G + t];
-            const uint32_t abit = (op.flags & FLAG_SIGN) ? 1u : 0u;
-            uint32_t mw = 0, bw = 0;
-            for (uint32_t j = 0; j < 32; j++) {
-              const uint32_t s = t * 32u + j;
-              const double S0 = RED[s], S1 = RED[S + s], tot = S0 + S1;
-              const uint32_t pbit = (pw >> j) & 1u;
-              const double p1 = tot > 0.0 ? ((1u ^ abit ^ pbit) ? S1 : S0) / tot : 0.0;
-              const uint32_t m = ((valid >> j) & 1u) ? draw_outcome(L.seed, s0 + j, op.i0, (top >> j) & 1u, p1) : 0u;
-              const uint32_t b = m ^ abit ^ pbit;
-              const double sb = b ? S1 : S0;
-              RED[s] = sb > 0.0 ? 1.0 / sqrt(sb) : 0.0;
-              mw |= m << j;
-              bw |= b << j;
-            }
-            TMP[t] = bw;
-            SL[op.i2 * G + t] = mw;
-            if ((op.flags & FLAG_OUT) && (L.flags & LF_OUT_MEAS))
-              store(L.meas, op.i3, mw & SL[p.kept_slot * G + t]);
-            if (xm) {
-              uint32_t xa = X[op.a * G + t];
-              X[op.a * G + t] = Z[op.a * G + t] ^ bw;
-              Z[op.a * G + t] = xa;
-            } else {
-              X[op.a * G + t] ^= bw;
-            }
-          }
-          __syncthreads();
-          const uint32_t top_pos = k - 1;
-          for (uint32_t s = t % S; s < S; s += T) {
-            const uint32_t b = fbit(TMP, s);
-            const real sc = (real)RED[s];
-            if (pa == top_pos) {
-              for (uint32_t j = sub; j < half; j += R) {
-                C o0 = work[(size_t)j * S + s], o1 = work[(size_t)(j + half) * S + s], v;
-                if (xm) v = cscale(b ? csub(o0, o1) : cadd(o0, o1), rs);
-                else v = b ? o1 : o0;
-                work[(size_t)j * S + s] = cscale(v, sc);
-              }
-            } else {
-              const uint32_t quarter = 1u << (k - 2);
-              for (uint32_t j = sub; j < quarter; j += R) {
-                uint32_t base = insert0(insert0(j, pa), top_pos);
-                size_t p00 = (size_t)base * S + s, p10 = (size_t)(base | (1u << pa)) * S + s;
-                size_t p01 = (size_t)(base | (1u << top_pos)) * S + s;
-                size_t p11 = (size_t)(base | (1u << pa) | (1u << top_pos)) * S + s;
-                C n0, n1;
-                if (xm) {
-                  C o00 = work[p00], o10 = work[p10], o01 = work[p01], o11 = work[p11];
-                  n0 = cscale(b ? csub(o00, o10) : cadd(o00, o10), rs);
-                  n1 = cscale(b ? csub(o01, o11) : cadd(o01, o11), rs);
-                } else {
-                  n0 = b ? work[p10] : work[p00];
-                  n1 = b ? work[p11] : work[p01];
-                }
-                work[p00] = cscale(n0, sc);
-                work[p10] = cscale(n1, sc);
-              }
-            }
-          }
-          k--;
-        }
-        __syncthreads();
-      }
+      cp_async_wait_all();
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -652,8 +917,17 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
       case OP_MEAS_STATIC: {
         uint32_t par = (op.flags & FLAG_SIGN) ? 1u : 0u;
         for (uint32_t w = 0; w < p.nw; w++) par ^= __popc(x[w] & __ldg(p.masks + op.i0 + w)) & 1u;
-        setb(slots, op.i2, par);
-        if ((op.flags & FLAG_OUT) && (L.flags & LF_OUT_MEAS)) store(L.meas, op.i3, par & kept);
+        if (op.flags & FLAG_RESET) {
+          // fused reset: conditional X-image on the inline planes r[0..pb)
+          for (uint32_t r = 0; r < op.pb; r++) {
+            const uint32_t pl = op.r[r];
+            if (pl < p.n_qubits) flipb(x, pl, par);
+            else flipb(z, pl - p.n_qubits, par);
+          }
+        } else {
+          setb(slots, op.i2, par);
+          if ((op.flags & FLAG_OUT) && (L.flags & LF_OUT_MEAS)) store(L.meas, op.i3, par & kept);
+        }
         break;
       }
       case OP_MEAS_RANDOM: {
@@ -737,6 +1011,10 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
           uint32_t info = __ldg(p.site_info + site), eff = __ldg(p.site_eff + site);
           if ((info & 15u) == SITE_FLIP) {
             flipb(slots, eff, 1u);
+            if ((L.flags & LF_OUT_MEAS) && getb(slots, p.kept_slot)) {
+              const uint32_t row = __ldg(p.opt_tab + 2 * (info >> 8) + 1);
+              atomicXor(&L.meas[(size_t)row * L.row_words32 + word], 1u << lane);
+            }
           } else {
             const uint32_t* mk = p.masks + eff + opt * 2u * p.nw;
             for (uint32_t w = 0; w < p.nw; w++) {
@@ -793,34 +1071,52 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
 // ---------------------------------------------------------------------------
 // Host-side launchers (called from capi.cu)
 // ---------------------------------------------------------------------------
-size_t batched_smem_bytes(const DevProg& p, uint32_t G) {
-  size_t words = ((size_t)(2 * p.n_qubits + p.n_slots + 1) * G + 1) & ~(size_t)1;
-  size_t bytes = words * 4;
-  if (p.k_max > 0) bytes += 2 * sizeof(double) * 32 * (size_t)G;
-  return bytes;
+uint32_t coarse_stride(uint32_t n_sites) { return n_sites <= 512 ? 1u : (n_sites + 511) / 512; }
+uint32_t coarse_count(uint32_t n_sites) {
+  uint32_t s = coarse_stride(n_sites);
+  return n_sites ? (n_sites + s - 1) / s : 0;
 }
 
-cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t grid, uint32_t threads,
-                           size_t smem, cudaStream_t st) {
-  if (fp64) {
-    cudaError_t e = cudaFuncSetAttribute(exec_batched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    exec_batched<double><<<grid, threads, smem, st>>>(L);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(exec_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    exec_batched<float><<<grid, threads, smem, st>>>(L);
-  }
+size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W) {
+  return smem_layout(p.n_qubits, p.n_slots, p.k_max, G, W, coarse_count(p.n_sites)).bytes;
+}
+
+template <typename real, int W>
+static cudaError_t launch_one(const LaunchParams& L, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(exec_batched<real, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  exec_batched<real, W><<<grid, threads, smem, st>>>(L);
   return cudaGetLastError();
 }
 
-cudaError_t batched_occupancy(bool fp64, uint32_t threads, size_t smem, int* blocks_per_sm) {
+template <typename real, int W>
+static cudaError_t occ_one(uint32_t threads, size_t smem, int* per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(exec_batched<real, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, exec_batched<real, W>, (int)threads, smem);
+}
+
+cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, uint32_t grid, uint32_t threads,
+                           size_t smem, cudaStream_t st) {
   if (fp64) {
-    cudaFuncSetAttribute(exec_batched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, exec_batched<double>, (int)threads, smem);
+    if (W == 4) return launch_one<double, 4>(L, grid, threads, smem, st);
+    if (W == 2) return launch_one<double, 2>(L, grid, threads, smem, st);
+    return launch_one<double, 1>(L, grid, threads, smem, st);
   }
-  cudaFuncSetAttribute(exec_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, exec_batched<float>, (int)threads, smem);
+  if (W == 4) return launch_one<float, 4>(L, grid, threads, smem, st);
+  if (W == 2) return launch_one<float, 2>(L, grid, threads, smem, st);
+  return launch_one<float, 1>(L, grid, threads, smem, st);
+}
+
+cudaError_t batched_occupancy(bool fp64, uint32_t W, uint32_t threads, size_t smem, int* per_sm) {
+  if (fp64) {
+    if (W == 4) return occ_one<double, 4>(threads, smem, per_sm);
+    if (W == 2) return occ_one<double, 2>(threads, smem, per_sm);
+    return occ_one<double, 1>(threads, smem, per_sm);
+  }
+  if (W == 4) return occ_one<float, 4>(threads, smem, per_sm);
+  if (W == 2) return occ_one<float, 2>(threads, smem, per_sm);
+  return occ_one<float, 1>(threads, smem, per_sm);
 }
 
 cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st) {

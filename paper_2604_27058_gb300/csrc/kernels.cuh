@@ -19,6 +19,9 @@ struct DevProg {
   const uint32_t* slot_list;
   const uint32_t* det_ref;
   const uint32_t* obs_ref;
+  const uint32_t* site_opt;
+  const uint32_t* opt_tab;
+  const uint16_t* plist;
   uint32_t n_qubits, nw, n_ops, n_sites, n_slots, k_max, kept_slot;
   uint32_t n_meas, n_det, n_obs;
 };
@@ -43,9 +46,9 @@ struct LaunchParams {
   uint32_t n_tiles;
   uint64_t work_stride;               // amplitudes per CTA workspace (batched) / per shot (plain)
   void* work;                         // amplitude workspace
-  uint32_t* nf;                       // per-shot next-fault state
   unsigned long long* kept_count;
   uint32_t* err;
+  uint32_t qc_stride, qc_n;            // coarse survival index: every qc_stride-th Q, qc_n entries
   uint32_t stop_event;                // debug: stop before this event (0xffffffff = never)
   uint64_t dump_shot;                 // debug: call-local shot index
   double* dump_amps;
@@ -129,6 +132,50 @@ __device__ __forceinline__ uint32_t next_fault(const DevProg& p, uint64_t seed, 
   }
   return kNoFault;
 }
+
+// next_fault with a shared-memory coarse index qc[c] = Q[c * stride] of the
+// whole site table: the search narrows to one stride of the global table.
+__device__ __forceinline__ uint32_t next_fault_coarse(const DevProg& p, uint64_t seed, uint64_t shot,
+                                                      uint32_t st, const uint64_t* qc, uint32_t stride) {
+  const uint2 key = key_of(seed);
+  while (st < p.n_sites) {
+    uint32_t a = __ldg(p.seg_start + st), b = __ldg(p.seg_end + st);
+    uint4 w = philox(make_uint4((uint32_t)shot, (uint32_t)(shot >> 32), TAG_GAP, st), key);
+    uint64_t u = (uint64_t)w.x | ((uint64_t)w.y << 32);
+    uint64_t ql = st == a ? ~0ull : __ldg(p.q + st - 1);
+    uint64_t t = mulhi64(u, ql);
+    if (__ldg(p.q + b - 1) > t) {
+      st = b;
+      continue;
+    }
+    // coarse entries c with st <= c * stride <= b - 1
+    const uint32_t c_lo = (st + stride - 1) / stride, c_hi = (b - 1) / stride + 1;
+    uint32_t lo = c_lo, hi = c_hi;
+    while (lo < hi) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (qc[mid] <= t) hi = mid;
+      else lo = mid + 1;
+    }
+    uint32_t flo = lo == c_lo ? st : (lo - 1) * stride + 1;
+    uint32_t fhi = lo < c_hi ? lo * stride : b - 1;  // q[fhi] <= t
+    while (flo < fhi) {
+      uint32_t mid = (flo + fhi) >> 1;
+      if (__ldg(p.q + mid) <= t) fhi = mid;
+      else flo = mid + 1;
+    }
+    uint32_t k = (__ldg(p.site_info + flo) >> 4) & 15u;
+    uint32_t opt = __umulhi(w.z, k);
+    return (flo << 4) | opt;
+  }
+  return kNoFault;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t insert0(uint32_t j, uint32_t p) {
   return ((j >> p) << (p + 1)) | (j & ((1u << p) - 1u));

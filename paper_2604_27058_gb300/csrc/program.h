@@ -38,19 +38,37 @@ enum OpCode : uint8_t {
   OP_COUNT
 };
 
-enum : uint8_t { FLAG_SIGN = 1, FLAG_OUT = 2 };
+enum : uint8_t { FLAG_SIGN = 1, FLAG_OUT = 2, FLAG_RESET = 4 };
 
 struct Op {
   uint8_t code;
   uint8_t flags;
   uint16_t a;   // virtual qubit (control / v)
   uint16_t b;   // virtual qubit (target)
-  uint8_t pa;   // array position of a
-  uint8_t pb;   // array position of b
-  uint32_t i0, i1, i2, i3;
-  double f;
+  uint8_t pa;   // array position of a; for list ops: inline entry count (kNoInline = use tables)
+  uint8_t pb;   // array position of b; for a fused reset: count of its inline X-image entries
+  union {
+    struct { uint32_t i0, i1, i2, i3; };
+    struct { uint32_t j0, j1; uint16_t r[4]; };  // fused reset: r = inline X-image planes
+  };
+  union {
+    double f;        // rotation angle
+    uint16_t e[4];   // inline entries of list ops
+  };
 };
 static_assert(sizeof(Op) == 32, "Op must be 32 bytes");
+
+// List ops (MEAS_STATIC, FEEDFORWARD: frame planes; DETECTOR, OBS_INCLUDE:
+// record slots) carry up to kInline entries in the instruction itself. A
+// frame plane index is q for the x bit of virtual qubit q and n_qubits + q
+// for its z bit. Longer lists use the mask / slot-list tables.
+//
+// A reset whose measurement is static (a dormant Z string, App. B.2) is fused
+// into one MEAS_STATIC with FLAG_RESET: m = sign ^ parity(inline planes e),
+// then the frame planes r[0..pb) are XORed with m (the conditional X of the
+// reset, App. B.3). It writes no record slot.
+constexpr uint32_t kInline = 4;
+constexpr uint8_t kNoInline = 0xFF;
 
 // Noise-site kinds (physical channel of the site).
 enum SiteKind : uint8_t { SITE_X = 0, SITE_Y, SITE_Z, SITE_D1, SITE_D2, SITE_FLIP };
@@ -63,17 +81,23 @@ struct ProgHeader {
   uint32_t n_ops, n_sites;
   uint32_t n_meas, n_det, n_obs, n_events;
   uint32_t n_slots, k_max;
-  uint32_t kept_slot, n_mask_words, n_slot_list, pad0;
+  uint32_t kept_slot, n_mask_words, n_slot_list, n_opt;
+  uint32_t n_plist, pad0[3];
   uint64_t off_ops, off_masks, off_q, off_seg_start, off_seg_end, off_site_info, off_site_eff,
-      off_slot_list, off_det_ref, off_obs_ref, total_bytes, pad1;
+      off_slot_list, off_det_ref, off_obs_ref, off_site_opt, off_opt_tab, off_plist, total_bytes;
 };
+// Noise options in sparse form: site_info >> 8 indexes opt_tab;
+// opt_tab[2 * (index + option)] = (plist offset, entry count); plist holds
+// frame plane indices (u16). A FLIP site has one entry (record slot, record
+// row): its fault flips the slot and, if the shot is kept, the output bit.
 
 constexpr uint32_t kMagic = 0x4E435047u;  // "NCPG"
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 3;
 constexpr uint32_t kMaxK = 30;
 constexpr uint32_t kMaxQubits = 4096;
 
-// site_info word: kind (bits 0..3) | option count K (bits 4..7)
+// site_info word: kind (bits 0..3) | option count K (bits 4..7) | first
+// opt_tab entry (bits 8..31).
 inline uint32_t site_kind(uint32_t info) { return info & 15u; }
 inline uint32_t site_k(uint32_t info) { return (info >> 4) & 15u; }
 
