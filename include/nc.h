@@ -125,6 +125,35 @@ nc_status nc_sample_batch(const nc_program* const* progs, const uint64_t* shots,
                           const uint64_t* seeds, uint32_t n, const nc_sample_opts* opts,
                           nc_records* outs, void* cuda_stream);
 
+/*
+ * Allocation-free sampling. Some callers cannot allocate device memory once
+ * they are running: an application whose device memory is owned entirely by
+ * another framework's caching pool, code that must not hit the implicit
+ * synchronisation of an allocation inside a latency-critical loop, or a
+ * process that is only allowed to allocate during start-up. For them
+ * nc_sample_noalloc behaves like nc_sample with precision NC_FP32_BATCHED,
+ * but it calls no cudaMalloc / cudaFree (nor any allocating library routine):
+ * the device copy of the program, the reference-parity launch, the counters
+ * and the amplitude workspace all live in one fixed array that the library
+ * reserves statically on every device that loads it (NC_NOALLOC_SCRATCH_BYTES,
+ * held until the process exits). The paper has no counterpart of this entry
+ * point; it is an integration convenience.
+ *   - Record buffers are caller-owned device memory (NC_OUT_HOST: NC_E_ARG).
+ *   - opts->precision must be NC_FP32_BATCHED (else NC_E_ARG); opts->tune is
+ *     ignored.
+ *   - NC_E_ARG if the program blob plus its workspace cannot fit in
+ *     NC_NOALLOC_SCRATCH_BYTES (large k_max or very long programs).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call reuses the same array and leaves the last call's contents in
+ *     it; calls whose work overlaps on the GPU (different streams, or host
+ *     threads without ordering) race on it and must be serialised by the
+ *     caller. Each call synchronises cuda_stream before returning.
+ */
+#define NC_NOALLOC_SCRATCH_BYTES (64u << 20)
+nc_status nc_sample_noalloc(const nc_program* prog, uint64_t shots, uint64_t seed,
+                            const nc_sample_opts* opts, nc_records* out, void* cuda_stream);
+
 /* Free a program and its device copies. NULL is a no-op. */
 void nc_program_free(nc_program* prog);
 

@@ -22,6 +22,7 @@ NC_OUT_DET = 2
 NC_OUT_OBS = 4
 NC_OUT_KEPT = 8
 NC_OUT_HOST = 16
+NC_NOALLOC_SCRATCH_BYTES = 64 << 20
 NC_OUT_ALL = NC_OUT_MEAS | NC_OUT_DET | NC_OUT_OBS | NC_OUT_KEPT
 NC_PS_NONE = 0
 NC_PS_ALL_DETECTORS = 1
@@ -32,7 +33,7 @@ STATUS = {0: "NC_OK", 1: "NC_E_PARSE", 2: "NC_E_UNSUPPORTED", 3: "NC_E_KMAX",
 
 EXPORTS = ["nc_compile", "nc_program_info", "nc_program_serialize", "nc_program_deserialize",
            "nc_sample", "nc_sample_batch", "nc_program_free", "nc_status_str", "nc_debug_dump",
-           "nc_abi_version"]
+           "nc_abi_version", "nc_sample_noalloc"]
 
 
 class NcError(RuntimeError):
@@ -86,12 +87,10 @@ def lib() -> ctypes.CDLL:
     L.nc_status_str.restype = ctypes.c_char_p
     L.nc_debug_dump.argtypes = [vp, u64, u64, u32, ctypes.c_int, ctypes.POINTER(u32),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32), vp]
+    L.nc_sample_noalloc.argtypes = [vp, u64, u64, ctypes.POINTER(SampleOpts), ctypes.POINTER(Records), vp]
+    L.nc_sample_noalloc.restype = ctypes.c_int
     L.nc_abi_version.argtypes = []
     L.nc_abi_version.restype = u32
-    for name in EXPORTS[:-2] + ["nc_debug_dump"]:
-        f = getattr(L, name)
-        if f.restype is None and name != "nc_program_free":
-            f.restype = ctypes.c_int
     for name in ("nc_compile", "nc_program_info", "nc_program_serialize", "nc_program_deserialize",
                  "nc_sample", "nc_sample_batch", "nc_debug_dump"):
         getattr(L, name).restype = ctypes.c_int

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnc.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["compiler.cpp", "kernels.cu", "capi.cu"]
+SOURCES = ["compiler.cpp", "kernels.cu", "capi.cu", "noalloc.cu"]
 HEADERS = ["program.h", "compiler.h", "kernels.cuh"]
 
 

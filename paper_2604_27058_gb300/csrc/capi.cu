@@ -579,3 +579,12 @@ done:
 uint32_t nc_abi_version(void) { return (kVersion << 16) | 1u; }
 
 }  // extern "C"
+
+// Host blob of a program, for the allocation-free entry point (noalloc.cu).
+namespace nc {
+const std::vector<uint8_t>& program_blob(const nc_program* p) { return p->cp.blob; }
+}  // namespace nc
+
+extern "C" {
+
+}  // extern "C"
