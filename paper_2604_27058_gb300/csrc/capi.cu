@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -27,6 +28,9 @@ cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, uint32_
                            size_t smem, cudaStream_t st);
 cudaError_t batched_occupancy(bool fp64, uint32_t W, uint32_t threads, size_t smem, int* blocks_per_sm);
 cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st);
+cudaError_t launch_patch_ref(Op* ops, uint32_t n_ops, const uint32_t* det_ref, const uint32_t* obs_ref,
+                             cudaStream_t st);
+cudaError_t launch_presample(const LaunchParams& L, cudaStream_t st);
 bool plain_supported(const DevProg& p);
 }  // namespace nc
 
@@ -71,6 +75,7 @@ DevProg dev_view(const ProgHeader& h, const uint8_t* base) {
   d.site_opt = reinterpret_cast<const uint32_t*>(base + h.off_site_opt);
   d.opt_tab = reinterpret_cast<const uint32_t*>(base + h.off_opt_tab);
   d.plist = reinterpret_cast<const uint16_t*>(base + h.off_plist);
+  d.orec = reinterpret_cast<const uint4*>(base + h.off_orec);
   d.n_qubits = h.n_qubits;
   d.nw = h.nw;
   d.n_ops = h.n_ops;
@@ -234,7 +239,8 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
     NC_TRY(launch_plain(L, stream));
   } else {
     Tuning tu = choose_tuning(L.p, tune);
-    if (!pow2(tu.G) || !pow2(tu.T) || !pow2(tu.W) || tu.T > (tu.W == 1 ? 1024u : 256u)) return NC_E_ARG;
+    if (!pow2(tu.G) || !pow2(tu.T) || !pow2(tu.W) || tu.T > (tu.W == 1 ? 1024u : 256u) || tu.T < 32)
+      return NC_E_ARG;
     L.G = tu.G;
     L.qc_stride = coarse_stride(h.n_sites);
     L.qc_n = coarse_count(h.n_sites);
@@ -256,6 +262,24 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
       uint64_t cap = std::max<uint64_t>(1, (uint64_t)(free_b * 0.6) / per_cta);
       grid = std::min(grid, cap);
       NC_TRY(scratch.get(&L.work, per_cta * grid));
+    }
+    // pre-sample every shot's faults when the list buffer fits comfortably
+    if (!(lflags & LF_NOISELESS) && h.n_sites && stop_event == 0xffffffffu) {
+      const double mean = (double)h.mean_faults;
+      const uint32_t cap = (uint32_t)std::min(127.0, std::ceil(mean + 6.0 * std::sqrt(mean) + 4.0));
+      const uint64_t padded = L.row_words32 * 32;
+      const size_t bytes = (size_t)cap * padded * 4 + padded;
+      size_t free_b = 0, total_b = 0;
+      NC_TRY(cudaMemGetInfo(&free_b, &total_b));
+      if (bytes < free_b / 2) {
+        void* buf = nullptr;
+        NC_TRY(scratch.get(&buf, bytes));
+        L.flist = (const uint32_t*)buf;
+        L.fcount = (const uint8_t*)buf + (size_t)cap * padded * 4;
+        L.fcap = cap;
+        L.fstride = padded;
+        NC_TRY(launch_presample(L, stream));
+      }
     }
     NC_TRY(launch_batched(L, fp64, tu.W, (uint32_t)grid, tu.T, smem, stream));
   }
@@ -302,6 +326,10 @@ nc_status ensure_reference(nc_program* p, DevCopy& dc, cudaStream_t stream) {
     }
     if (h.n_det) NC_TRY(cudaMemcpy(dc.blob + h.off_det_ref, rd.data(), h.n_det * 4, cudaMemcpyHostToDevice));
     if (h.n_obs) NC_TRY(cudaMemcpy(dc.blob + h.off_obs_ref, ro.data(), h.n_obs * 4, cudaMemcpyHostToDevice));
+    NC_TRY(launch_patch_ref(reinterpret_cast<Op*>(dc.blob + h.off_ops), h.n_ops,
+                            reinterpret_cast<const uint32_t*>(dc.blob + h.off_det_ref),
+                            reinterpret_cast<const uint32_t*>(dc.blob + h.off_obs_ref), stream));
+    NC_TRY(cudaStreamSynchronize(stream));
   }
 done:
   if (st == NC_OK || st == NC_E_NONDET_DETECTOR) {
@@ -475,7 +503,7 @@ nc_status nc_program_deserialize(const void* buf, size_t len, nc_program** out) 
   if (h.magic != kMagic || h.version != kVersion || h.total_bytes + sizeof(nc_info_counts) != len) return NC_E_ARG;
   uint64_t offs[] = {h.off_ops, h.off_masks, h.off_q, h.off_seg_start, h.off_seg_end, h.off_site_info,
                      h.off_site_eff, h.off_slot_list, h.off_det_ref, h.off_obs_ref,
-                     h.off_site_opt, h.off_opt_tab, h.off_plist};
+                     h.off_site_opt, h.off_opt_tab, h.off_plist, h.off_orec};
   for (uint64_t o : offs)
     if (o > h.total_bytes || (o & 15)) return NC_E_ARG;
   if (h.off_ops + (uint64_t)h.n_ops * sizeof(Op) > h.total_bytes || h.k_max > kMaxK || h.n_qubits > kMaxQubits)

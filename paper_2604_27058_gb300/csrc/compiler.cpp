@@ -766,6 +766,8 @@ struct Compiler {
       e.a = (uint16_t)v;
       e.pa = (uint8_t)act.size();
       e.f = ta;
+      e.cs = std::cos(2.0 * ta);
+      e.sn = std::sin(2.0 * ta);
       pos_of[v] = (int)act.size();
       act.push_back(v);
       k_max = std::max<uint32_t>(k_max, (uint32_t)act.size());
@@ -777,6 +779,8 @@ struct Compiler {
       r.a = (uint16_t)v;
       r.pa = (uint8_t)pos_of[v];
       r.f = ta;
+      r.cs = kind == 'Z' ? std::cos(2.0 * ta) : std::cos(ta);
+      r.sn = kind == 'Z' ? std::sin(2.0 * ta) : std::sin(ta);
       counts.array_ops++;
       emit(r);
     }
@@ -852,9 +856,11 @@ struct Compiler {
 
 }  // namespace
 
-// Store up to kInline u16 entries in the instruction (e[0..3], count in pa).
-void set_inline(Op& o, const std::vector<uint32_t>& v) {
-  if (v.size() > kInline) {
+// Store up to kInline u16 entries in the instruction (e[0..3], count in pa);
+// entries past the count hold `pad` (an all-zero row for reads, a scratch
+// row for writes).
+void set_inline(Op& o, const std::vector<uint32_t>& v, uint32_t pad) {
+  if (v.size() > kInline || pad > 0xFFFF) {
     o.pa = kNoInline;
     return;
   }
@@ -865,7 +871,14 @@ void set_inline(Op& o, const std::vector<uint32_t>& v) {
     }
   o.pa = (uint8_t)v.size();
   o.f = 0.0;
-  for (size_t i = 0; i < v.size(); i++) o.e[i] = (uint16_t)v[i];
+  for (size_t i = 0; i < kInline; i++) o.e[i] = (uint16_t)(i < v.size() ? v[i] : pad);
+}
+
+Op mk_op(uint8_t code) {
+  Op o;
+  std::memset(&o, 0, sizeof(o));
+  o.code = code;
+  return o;
 }
 
 // Frame plane indices of a mask (x part then z part, nw words each).
@@ -1006,12 +1019,12 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
             c.code[i + 1].uses[0] == e.def && n_uses[e.def] == 1) {
           auto mp = mask_planes(c.masks, e.op.i0, (uint32_t)c.nw32, (uint32_t)c.n, true, false);
           auto ep = mask_planes(c.masks, c.code[i + 1].op.i0, (uint32_t)c.nw32, (uint32_t)c.n, true, true);
-          if (mp.size() <= kInline && ep.size() <= 4) {
+          if (mp.size() <= kInline && ep.size() <= 4 && 2 * (uint32_t)c.n + 1 <= 0xFFFF) {
             Op o = e.op;
-            set_inline(o, mp);
+            set_inline(o, mp, 2 * (uint32_t)c.n);
             o.flags |= FLAG_RESET;
             o.pb = (uint8_t)ep.size();
-            for (int j = 0; j < 4; j++) o.r[j] = j < (int)ep.size() ? (uint16_t)ep[j] : 0;
+            for (int j = 0; j < 4; j++) o.r[j] = j < (int)ep.size() ? (uint16_t)ep[j] : (uint16_t)(2 * c.n + 1);
             fused.push_back({o, {}, -1});
             i++;
             continue;
@@ -1058,14 +1071,14 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
           o.i2 = (uint32_t)slot_of[e.def];
           // the mask is the z-support of the mapped observable; the parity
           // reads the frame's x planes on that support
-          set_inline(o, mask_planes(c.masks, o.i0, (uint32_t)c.nw32, (uint32_t)c.n, true, false));
+          set_inline(o, mask_planes(c.masks, o.i0, (uint32_t)c.nw32, (uint32_t)c.n, true, false), 2 * (uint32_t)c.n);
           break;
         case OP_MEAS_RANDOM: case OP_MEAS_ACTIVE_Z: case OP_MEAS_ACTIVE_X:
           o.i2 = (uint32_t)slot_of[e.def];
           break;
         case OP_FEEDFORWARD:
           o.i2 = (uint32_t)slot_of[e.uses[0]];
-          set_inline(o, mask_planes(c.masks, o.i0, (uint32_t)c.nw32, (uint32_t)c.n, true, true));
+          set_inline(o, mask_planes(c.masks, o.i0, (uint32_t)c.nw32, (uint32_t)c.n, true, true), 2 * (uint32_t)c.n + 1);
           break;
         case OP_REC_OUT:
           o.i2 = (uint32_t)slot_of[e.uses[0]];
@@ -1077,7 +1090,7 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
           for (auto id : e.uses) sl.push_back((uint32_t)slot_of[id]);
           slot_list.insert(slot_list.end(), sl.begin(), sl.end());
           if (o.code == OP_OBS_INCLUDE) o.i2 = (uint32_t)slot_of[o.i2];
-          set_inline(o, sl);
+          set_inline(o, sl, 0);  // re-padded below with the zero slot row, once n_slots is known
           break;
         }
         case OP_OBS_OUT:
@@ -1100,6 +1113,75 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
           free_slots.push_back((uint32_t)slot_of[id]);
         }
     }
+    // slot lists: pad with the zero slot row (index n_slots), or give up inlining
+    for (auto& o : ops)
+      if ((o.code == OP_DETECTOR || o.code == OP_OBS_INCLUDE) && o.pa != kNoInline) {
+        if (n_slots > 0xFFFF) {
+          o.pa = kNoInline;
+          continue;
+        }
+        for (uint32_t i = o.pa; i < kInline; i++) o.e[i] = (uint16_t)n_slots;
+      }
+
+    // batch runs of independent list instructions (Sec. 3.1 stage 4: cut
+    // dispatch; here also to give the executor independent loads to overlap)
+    {
+      auto kind_of = [&](const Op& o) -> int {
+        if (o.code == OP_MEAS_STATIC && o.pa != kNoInline) return (o.flags & FLAG_RESET) ? 2 : 1;
+        if (o.code == OP_DETECTOR && o.pa != kNoInline) return 3;
+        return 0;
+      };
+      const uint32_t trash = 2 * (uint32_t)c.n + 1;
+      auto writes = [&](const Op& o, std::vector<uint32_t>& w) {
+        w.clear();
+        for (int j = 0; j < (int)o.pb; j++) w.push_back(o.r[j]);
+      };
+      auto reads = [&](const Op& o, std::vector<uint32_t>& r) {
+        r.clear();
+        for (uint32_t j = 0; j < o.pa; j++) r.push_back(o.e[j]);
+        for (int j = 0; j < (int)o.pb; j++) r.push_back(o.r[j]);
+      };
+      std::vector<Op> out;
+      out.reserve(ops.size() + ops.size() / 4);
+      size_t i = 0;
+      std::vector<uint32_t> wi, rj, wj;
+      while (i < ops.size()) {
+        const int kd = kind_of(ops[i]);
+        size_t n = 1;
+        if (kd) {
+          std::vector<uint32_t> written;  // planes written by earlier members (resets)
+          if (kd == 2) writes(ops[i], written);
+          while (i + n < ops.size() && n < kMaxBatch && kind_of(ops[i + n]) == kd) {
+            if (kd == 2) {
+              reads(ops[i + n], rj);
+              writes(ops[i + n], wj);
+              bool clash = false;
+              for (auto x : rj)
+                if (x != trash && std::find(written.begin(), written.end(), x) != written.end()) clash = true;
+              if (clash) break;
+              written.insert(written.end(), wj.begin(), wj.end());
+            }
+            n++;
+          }
+          // header + n payloads must stay inside one staging chunk
+          const size_t room = kChunk - (out.size() % kChunk);
+          if (n + 1 > room) n = room > 1 ? room - 1 : 0;
+        }
+        if (kd && n >= 2) {
+          Op hdr = mk_op(OP_BATCH);
+          hdr.a = (uint16_t)kd;
+          hdr.pa = (uint8_t)n;
+          out.push_back(hdr);
+          for (size_t u = 0; u < n; u++) out.push_back(ops[i + u]);
+          i += n;
+        } else {
+          out.push_back(ops[i]);
+          i++;
+        }
+      }
+      ops.swap(out);
+    }
+
     // flip sites reference slots through site_eff
     std::vector<uint32_t> site_eff = c.site_eff;
     for (size_t s = 0; s < c.site_kind.size(); s++)
@@ -1125,6 +1207,29 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
         opt_tab.push_back((uint32_t)plist.size());
         opt_tab.push_back((uint32_t)pl.size());
         for (auto x : pl) plist.push_back((uint16_t)x);
+      }
+    }
+
+    // ---------------- option records (site, option) -> 16 bytes ----------------
+    std::vector<uint16_t> orec((size_t)c.site_kind.size() * kRecPerSite * 8, 0);
+    for (size_t s = 0; s < c.site_kind.size(); s++) {
+      const uint32_t k = c.site_kind[s] == SITE_D1 ? 3 : c.site_kind[s] == SITE_D2 ? 15 : 1;
+      for (uint32_t j = 0; j < k; j++) {
+        uint16_t* r = &orec[(s * kRecPerSite + j) * 8];
+        const uint32_t oi = 2 * (site_opt[s] + (c.site_kind[s] == SITE_FLIP ? 0 : j));
+        if (c.site_kind[s] == SITE_FLIP) {
+          const uint32_t slot = opt_tab[oi], row = opt_tab[oi + 1];
+          r[0] = kRecFlip;
+          r[1] = (uint16_t)slot;
+          r[2] = (uint16_t)(slot >> 16);
+          r[3] = (uint16_t)row;
+          r[4] = (uint16_t)(row >> 16);
+        } else if (opt_tab[oi + 1] <= 7) {
+          r[0] = (uint16_t)opt_tab[oi + 1];
+          for (uint32_t e = 0; e < opt_tab[oi + 1]; e++) r[1 + e] = plist[opt_tab[oi] + e];
+        } else {
+          r[0] = kRecLong;
+        }
       }
     }
 
@@ -1181,6 +1286,11 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     h.n_slot_list = (uint32_t)slot_list.size();
     h.n_opt = (uint32_t)(opt_tab.size() / 2);
     h.n_plist = (uint32_t)plist.size();
+    {
+      double mean = 0.0;
+      for (double sp : c.site_p) mean += sp;
+      h.mean_faults = (float)mean;
+    }
     uint64_t off = (sizeof(ProgHeader) + 15) & ~15ull;
     auto place = [&](uint64_t bytes) {
       uint64_t o = off;
@@ -1200,6 +1310,7 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     h.off_site_opt = place(S * 4);
     h.off_opt_tab = place(opt_tab.size() * 4);
     h.off_plist = place(plist.size() * 2);
+    h.off_orec = place(orec.size() * 2);
     h.total_bytes = off;
     out.blob.assign(off, 0);
     std::memcpy(out.blob.data(), &h, sizeof(h));
@@ -1217,6 +1328,7 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     cp(h.off_site_opt, site_opt.data(), S * 4);
     cp(h.off_opt_tab, opt_tab.data(), opt_tab.size() * 4);
     cp(h.off_plist, plist.data(), plist.size() * 2);
+    cp(h.off_orec, orec.data(), orec.size() * 2);
     out.counts = c.counts;
     return 0;
   } catch (CompileError& e) {

@@ -80,17 +80,18 @@ __device__ __forceinline__ bool is_meas(uint8_t c) {
 // Shared-memory layout of one CTA (u32 words unless noted):
 //   OPS Op [2][kChunk] double-buffered instruction chunks (cp.async)
 //   QC  u64 [qc_n] coarse survival index
-//   PL  [2N][G]  frame planes (x bits of virtual qubit q at plane q, z bits at N + q)
-//   SL  [n_slots][G] record slots
+//   PL  [2N+2][G] frame planes (x bits of virtual qubit q at plane q, z bits at N + q),
+//                 an all-zero plane 2N and a scratch plane 2N + 1 (padding targets)
+//   SL  [n_slots+1][G] record slots and an all-zero slot n_slots
 //   NF  [32][G]  next fault of shot (word w, bit j) at NF[j * G + w]
+//   CUR u8 [32][G] list cursor of each shot (pre-sampled faults)
 //   TMP [G]      per-word scratch (virtual outcomes of an active measurement)
 //   QU  u16 [owner warps][kQueue] warp queues of due (word, bit) noise entries
 //   RED f64 [2][S] measurement sums / scales (k_max > 0 only)
-constexpr uint32_t kChunk = 128;
-constexpr uint32_t kQueue = 512;
+constexpr uint32_t kQueue = 256;
 
 struct SmemLayout {
-  size_t pl, sl, nf, tmp, qu, ops, qc, red, bytes;
+  size_t pl, sl, nf, cur, tmp, qu, ops, qc, red, bytes;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(uint32_t n_qubits, uint32_t n_slots, uint32_t k_max, uint32_t G,
@@ -102,11 +103,13 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t n_qubits, uint32_t n_
   L.qc = w;
   w += (size_t)2 * qc_n;
   L.pl = w;
-  w += (size_t)2 * n_qubits * G;
+  w += (size_t)(2 * n_qubits + 2) * G;  // + zero plane (2N) and scratch plane (2N + 1)
   L.sl = w;
-  w += (size_t)n_slots * G;
+  w += (size_t)(n_slots + 1) * G;       // + zero slot (n_slots)
   L.nf = w;
   w += (size_t)32 * G;
+  L.cur = w;  // u8 [32][G]: next index into the pre-sampled fault list
+  w += (size_t)8 * G;
   L.tmp = w;
   w += G;
   w = (w + 3) & ~(size_t)3;
@@ -169,14 +172,23 @@ __device__ __forceinline__ Vw<W> vand(const Vw<W>& a, const Vw<W>& b) {
   return r;
 }
 
+// Inline entries of list instructions, read with register bit operations
+// (the u16 views of program.h would force the instruction into local memory).
+__device__ __forceinline__ uint32_t ent(const Op& op, uint32_t i) {
+  return (uint32_t)((unsigned long long)__double_as_longlong(op.f) >> (16 * i)) & 0xFFFFu;
+}
+__device__ __forceinline__ uint32_t rent(const Op& op, uint32_t i) {
+  return ((i < 2 ? op.i2 : op.i3) >> (16 * (i & 1))) & 0xFFFFu;
+}
+
 __device__ __forceinline__ uint32_t pick4(const uint4& v, uint32_t i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-// W >= 2 variants serve the frame-bound (small k) programs with at most 256
-// threads per CTA; W = 1 also serves large k with up to 1024 threads.
-template <typename real, int W>
-__global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams L) {
+// BIG variants allow 1024 threads per CTA (large-k tiles, at most 64
+// registers per thread); the others allow 256 threads and more registers.
+template <typename real, int W, bool BIG>
+__global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams L) {
   using C = typename Cx<real>::T;
   extern __shared__ __align__(16) uint32_t smem[];
   const DevProg& p = L.p;
@@ -187,6 +199,7 @@ __global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams
   uint32_t* Z = PL + (size_t)N * G;
   uint32_t* SL = smem + lay.sl;
   uint32_t* NF = smem + lay.nf;
+  uint8_t* CUR = reinterpret_cast<uint8_t*>(smem + lay.cur);
   uint32_t* TMP = smem + lay.tmp;
   const uint32_t lane = t & 31u, warp = t >> 5;
   uint16_t* QU = reinterpret_cast<uint16_t*>(smem + lay.qu) + (size_t)warp * kQueue;
@@ -232,18 +245,28 @@ __global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams
     }
     uint32_t minsite = kNoFault >> 4;
     if (owner) {
-      for (uint32_t q = 0; q < 2 * N; q++) vst<W>(PL + q * G + tw, vfill<W>(0u));
-      for (uint32_t s = 0; s < p.n_slots; s++) vst<W>(SL + s * G + tw, vfill<W>(0u));
+      for (uint32_t q = 0; q < 2 * N + 2; q++) vst<W>(PL + q * G + tw, vfill<W>(0u));
+      for (uint32_t s = 0; s <= p.n_slots; s++) vst<W>(SL + s * G + tw, vfill<W>(0u));
       vst<W>(SL + kept_off + tw, valid);
 #pragma unroll
-      for (int i = 0; i < W; i++)
+      for (int i = 0; i < W; i++) {
+        const uint64_t sl0 = (word0 + i) * 32u;  // call-local shot of bit 0
         for (uint32_t j = 0; j < 32; j++) {
-          uint32_t f = (noisy && ((valid.v[i] >> j) & 1u))
-                           ? next_fault_coarse(p, L.seed, s0 + (uint64_t)i * 32u + j, 0, QC, L.qc_stride)
-                           : kNoFault;
+          uint32_t f = kNoFault;
+          if (noisy && ((valid.v[i] >> j) & 1u)) {
+            if (L.flist) {
+              const uint32_t c = L.fcount[sl0 + j];
+              if (c & 127u) f = L.flist[sl0 + j];
+              else if (c & 128u) f = next_fault_coarse(p, L.seed, s0 + (uint64_t)i * 32u + j, 0, QC, L.qc_stride);
+            } else {
+              f = next_fault_coarse(p, L.seed, s0 + (uint64_t)i * 32u + j, 0, QC, L.qc_stride);
+            }
+          }
           NF[j * G + tw + i] = f;
+          CUR[j * G + tw + i] = 1;
           minsite = min(minsite, f >> 4);
         }
+      }
     }
     if (p.k_max > 0) {
       for (uint32_t s = t; s < S; s += T) {
@@ -275,10 +298,90 @@ __global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams
       const Op* ops = OPB + (ch & 1u) * kChunk;
       const uint32_t n_here = min(kChunk, p.n_ops - ch * kChunk);
       Op nxt = ops[0];
-      for (uint32_t pi = 0; pi < n_here; pi++) {
+      uint32_t skip = 0;  // payload instructions consumed by a batch
+      for (uint32_t pi = 0; pi < n_here; pi += 1 + skip) {
         const Op op = nxt;
-        if (pi + 1 < n_here) nxt = ops[pi + 1];
+        skip = 0;
+        if (op.code == OP_BATCH && L.stop_event == 0xffffffffu) skip = op.pa;
+        if (pi + 1 + skip < n_here) nxt = ops[pi + 1 + skip];
         switch (op.code) {
+          case OP_BATCH:
+            // skip == 0 in debug-stop mode: the payloads then run one by one
+            if (owner && skip) {
+              const Op* b = ops + pi + 1;
+              const uint32_t n = skip;
+              if (op.a == 1 || op.a == 2) {
+                // static measurements (a = 1) or fused static resets (a = 2):
+                // all loads of the batch first, then all stores
+                Vw<W> m[kMaxBatch];
+#pragma unroll
+                for (uint32_t u = 0; u < kMaxBatch; u++) {
+                  if (u < n) {
+                    const Op o = b[u];
+                    m[u] = vfill<W>((o.flags & FLAG_SIGN) ? ~0u : 0u);
+                    vxor<W>(m[u], vld<W>(plane(ent(o, 0))));
+                    vxor<W>(m[u], vld<W>(plane(ent(o, 1))));
+                    vxor<W>(m[u], vld<W>(plane(ent(o, 2))));
+                    vxor<W>(m[u], vld<W>(plane(ent(o, 3))));
+                  }
+                }
+                if (op.a == 1) {
+                  const Vw<W> kept = vld<W>(slot(p.kept_slot));
+#pragma unroll
+                  for (uint32_t u = 0; u < kMaxBatch; u++) {
+                    if (u < n) {
+                      const Op o = b[u];
+                      vst<W>(slot(o.i2), m[u]);
+                      if ((o.flags & FLAG_OUT) && (L.flags & LF_OUT_MEAS)) store(L.meas, o.i3, vand<W>(m[u], kept));
+                    }
+                  }
+                } else {
+                  // conditional X-images; members write disjoint planes
+                  // (scratch plane padding aside), checked by the compiler
+#pragma unroll
+                  for (uint32_t u = 0; u < kMaxBatch; u++) {
+                    if (u < n) {
+                      const Op o = b[u];
+#pragma unroll
+                      for (uint32_t e = 0; e < 4; e++) {
+                        const uint32_t pl = rent(o, e);
+                        Vw<W> v = vld<W>(plane(pl));
+                        vxor<W>(v, m[u]);
+                        vst<W>(plane(pl), v);
+                      }
+                    }
+                  }
+                }
+              } else {
+                // detectors: parities, reference, kept chain in registers
+                Vw<W> d[kMaxBatch];
+#pragma unroll
+                for (uint32_t u = 0; u < kMaxBatch; u++) {
+                  if (u < n) {
+                    const Op o = b[u];
+                    d[u] = vld<W>(slot(ent(o, 0)));
+                    vxor<W>(d[u], vld<W>(slot(ent(o, 1))));
+                    vxor<W>(d[u], vld<W>(slot(ent(o, 2))));
+                    vxor<W>(d[u], vld<W>(slot(ent(o, 3))));
+                  }
+                }
+                Vw<W> kept = vld<W>(slot(p.kept_slot));
+#pragma unroll
+                for (uint32_t u = 0; u < kMaxBatch; u++) {
+                  if (u < n) {
+                    const Op o = b[u];
+                    if (!(L.flags & LF_REFERENCE) && (o.flags & FLAG_REF)) vxor<W>(d[u], vfill<W>(~0u));
+                    if (L.flags & LF_OUT_DET) store(L.det, o.i3, vand<W>(d[u], kept));
+                    if (L.flags & LF_POSTSELECT) {
+#pragma unroll
+                      for (int i = 0; i < W; i++) kept.v[i] &= ~d[u].v[i];
+                    }
+                  }
+                }
+                if (L.flags & LF_POSTSELECT) vst<W>(slot(p.kept_slot), kept);
+              }
+            }
+            break;
           case OP_FRAME_H:
           case OP_FRAME_S:
           case OP_FRAME_CX:
@@ -313,13 +416,11 @@ __global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams
             if (owner) {
               Vw<W> m = vfill<W>((op.flags & FLAG_SIGN) ? ~0u : 0u);
               if (op.pa != kNoInline) {
-                switch (op.pa) {
-                  case 4: vxor<W>(m, vld<W>(plane(op.e[3]))); [[fallthrough]];
-                  case 3: vxor<W>(m, vld<W>(plane(op.e[2]))); [[fallthrough]];
-                  case 2: vxor<W>(m, vld<W>(plane(op.e[1]))); [[fallthrough]];
-                  case 1: vxor<W>(m, vld<W>(plane(op.e[0]))); [[fallthrough]];
-                  default: break;
-                }
+                // entries past the count point at the zero plane
+                vxor<W>(m, vld<W>(plane(ent(op, 0))));
+                vxor<W>(m, vld<W>(plane(ent(op, 1))));
+                vxor<W>(m, vld<W>(plane(ent(op, 2))));
+                vxor<W>(m, vld<W>(plane(ent(op, 3))));
               } else {
                 const uint32_t* zm = p.masks + op.i0;
                 for (uint32_t w = 0; w < p.nw; w++) {
@@ -333,10 +434,17 @@ __global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams
               }
               if (op.flags & FLAG_RESET) {
                 // fused reset: frame ^= X-image where m is set
-                for (uint32_t r = 0; r < op.pb; r++) {
-                  Vw<W> v = vld<W>(plane(op.r[r]));
+                auto flip = [&](uint32_t pl) {
+                  Vw<W> v = vld<W>(plane(pl));
                   vxor<W>(v, m);
-                  vst<W>(plane(op.r[r]), v);
+                  vst<W>(plane(pl), v);
+                };
+                switch (op.pb) {
+                  case 4: flip(rent(op, 3)); [[fallthrough]];
+                  case 3: flip(rent(op, 2)); [[fallthrough]];
+                  case 2: flip(rent(op, 1)); [[fallthrough]];
+                  case 1: flip(rent(op, 0)); [[fallthrough]];
+                  default: break;
                 }
               } else {
                 vst<W>(slot(op.i2), m);
@@ -373,15 +481,20 @@ __global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams
           case OP_NOISE_BLOCK:
             if (owner_warp) {
               while (true) {
-                // due entries of this lane's words, compacted warp-wide
+                // due entries of this lane's words (site < block end) and the
+                // minimum site among the others, then warp-wide compaction
                 uint32_t due[W];
-                uint32_t cnt = 0;
+                uint32_t cnt = 0, nmin = kNoFault >> 4;
+                const bool scanned = owner && minsite < op.i1;
 #pragma unroll
                 for (int i = 0; i < W; i++) {
                   due[i] = 0;
-                  if (owner && minsite < op.i1)
-                    for (uint32_t j = 0; j < 32; j++)
-                      if ((NF[j * G + tw + i] >> 4) < op.i1) due[i] |= 1u << j;
+                  if (scanned)
+                    for (uint32_t j = 0; j < 32; j++) {
+                      const uint32_t sv = NF[j * G + tw + i] >> 4;
+                      if (sv < op.i1) due[i] |= 1u << j;
+                      else nmin = min(nmin, sv);
+                    }
                   cnt += __popc(due[i]);
                 }
                 uint32_t incl = cnt;
@@ -408,32 +521,64 @@ __global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams
                   const uint32_t e = QU[qi];
                   const uint32_t w = (warp * 32u * W) + (e >> 5), j = e & 31u, bit = 1u << j;
                   const uint64_t shot = tile_s0 + (uint64_t)w * 32u + j;
+                  const uint64_t sl = ((uint64_t)tile * G + w) * 32u + j;  // call-local shot
                   uint32_t f = NF[j * G + w];
                   do {
                     const uint32_t site = f >> 4, opt = f & 15u;
-                    const uint32_t info = __ldg(p.site_info + site);
-                    const uint2* ot = reinterpret_cast<const uint2*>(p.opt_tab) + (info >> 8);
-                    if ((info & 15u) == SITE_FLIP) {
-                      const uint2 sr = __ldg(ot);
-                      atomicXor(&SL[sr.x * G + w], bit);
+                    // next fault of this shot (independent of the application below)
+                    uint32_t fn = kNoFault;
+                    bool search = false;
+                    if (L.flist) {
+                      const uint32_t c = CUR[j * G + w];
+                      const uint32_t cn = L.fcount[sl];
+                      if (c < (cn & 127u)) {
+                        fn = L.flist[(uint64_t)c * L.fstride + sl];
+                        CUR[j * G + w] = (uint8_t)(c + 1);
+                      } else {
+                        search = (cn & 128u) != 0;
+                      }
+                    } else {
+                      search = true;
+                    }
+                    const uint4 r = __ldg(p.orec + (size_t)site * kRecPerSite + opt);
+                    const uint32_t tag = r.x & 0xFFFFu;
+                    if (tag == kRecFlip) {
+                      const uint32_t sl_idx = (r.x >> 16) | ((r.y & 0xFFFFu) << 16);
+                      const uint32_t row = (r.y >> 16) | ((r.z & 0xFFFFu) << 16);
+                      atomicXor(&SL[sl_idx * G + w], bit);
                       if ((L.flags & LF_OUT_MEAS) && (SL[kept_off + w] & bit) &&
                           (uint64_t)w + (uint64_t)tile * G < L.row_words32)
-                        atomicXor(&L.meas[(size_t)sr.y * L.row_words32 + (uint64_t)tile * G + w], bit);
+                        atomicXor(&L.meas[(size_t)row * L.row_words32 + (uint64_t)tile * G + w], bit);
+                    } else if (tag == kRecLong) {
+                      const uint32_t info = __ldg(p.site_info + site);
+                      const uint2 o2 = __ldg(reinterpret_cast<const uint2*>(p.opt_tab) + (info >> 8) + opt);
+                      for (uint32_t q = 0; q < o2.y; q++)
+                        atomicXor(&PL[(uint32_t)__ldg(p.plist + o2.x + q) * G + w], bit);
                     } else {
-                      const uint2 o2 = __ldg(ot + opt);
-                      for (uint32_t r = 0; r < o2.y; r++)
-                        atomicXor(&PL[(uint32_t)__ldg(p.plist + o2.x + r) * G + w], bit);
+                      const uint32_t ent7[7] = {r.x >> 16, r.y & 0xFFFFu, r.y >> 16, r.z & 0xFFFFu,
+                                                r.z >> 16, r.w & 0xFFFFu, r.w >> 16};
+#pragma unroll
+                      for (uint32_t q = 0; q < 7; q++)
+                        if (q < tag) atomicXor(&PL[ent7[q] * G + w], bit);
                     }
-                    f = next_fault_coarse(p, L.seed, shot, site + 1, QC, L.qc_stride);
+                    if (search) fn = next_fault_coarse(p, L.seed, shot, site + 1, QC, L.qc_stride);
+                    f = fn;
                   } while ((f >> 4) < op.i1);
                   NF[j * G + w] = f;
                 }
                 __syncwarp();
-                if (owner) {
-                  uint32_t m = kNoFault >> 4;
+                if (scanned) {
+                  // only the entries just processed can have moved
+                  uint32_t m = nmin;
 #pragma unroll
-                  for (int i = 0; i < W; i++)
-                    for (uint32_t j = 0; j < 32; j++) m = min(m, NF[j * G + tw + i] >> 4);
+                  for (int i = 0; i < W; i++) {
+                    uint32_t d = due[i];
+                    while (d) {
+                      uint32_t j = __ffs(d) - 1;
+                      d &= d - 1;
+                      m = min(m, NF[j * G + tw + i] >> 4);
+                    }
+                  }
                   minsite = m;
                 }
                 if (total <= kQueue) break;
@@ -444,10 +589,17 @@ __global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams
             if (owner) {
               const Vw<W> c = vld<W>(slot(op.i2));
               if (op.pa != kNoInline) {
-                for (uint32_t r = 0; r < op.pa; r++) {
-                  Vw<W> v = vld<W>(plane(op.e[r]));
+                auto flip = [&](uint32_t pl) {
+                  Vw<W> v = vld<W>(plane(pl));
                   vxor<W>(v, c);
-                  vst<W>(plane(op.e[r]), v);
+                  vst<W>(plane(pl), v);
+                };
+                switch (op.pa) {
+                  case 4: flip(ent(op, 3)); [[fallthrough]];
+                  case 3: flip(ent(op, 2)); [[fallthrough]];
+                  case 2: flip(ent(op, 1)); [[fallthrough]];
+                  case 1: flip(ent(op, 0)); [[fallthrough]];
+                  default: break;
                 }
               } else {
                 const uint32_t* mk = p.masks + op.i0;
@@ -474,13 +626,11 @@ __global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams
             if (owner) {
               Vw<W> d = vfill<W>(0u);
               if (op.pa != kNoInline) {
-                switch (op.pa) {
-                  case 4: vxor<W>(d, vld<W>(slot(op.e[3]))); [[fallthrough]];
-                  case 3: vxor<W>(d, vld<W>(slot(op.e[2]))); [[fallthrough]];
-                  case 2: vxor<W>(d, vld<W>(slot(op.e[1]))); [[fallthrough]];
-                  case 1: vxor<W>(d, vld<W>(slot(op.e[0]))); [[fallthrough]];
-                  default: break;
-                }
+                // entries past the count point at the zero slot
+                vxor<W>(d, vld<W>(slot(ent(op, 0))));
+                vxor<W>(d, vld<W>(slot(ent(op, 1))));
+                vxor<W>(d, vld<W>(slot(ent(op, 2))));
+                vxor<W>(d, vld<W>(slot(ent(op, 3))));
               } else {
                 for (uint32_t j = 0; j < op.i1; j++) vxor<W>(d, vld<W>(slot(__ldg(p.slot_list + op.i0 + j))));
               }
@@ -489,7 +639,7 @@ __global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams
                 vxor<W>(o, d);
                 vst<W>(slot(op.i2), o);
               } else {
-                if (!(L.flags & LF_REFERENCE) && __ldg(p.det_ref + op.i3)) vxor<W>(d, vfill<W>(~0u));
+                if (!(L.flags & LF_REFERENCE) && (op.flags & FLAG_REF)) vxor<W>(d, vfill<W>(~0u));
                 Vw<W> kept = vld<W>(slot(p.kept_slot));
                 if (L.flags & LF_OUT_DET) store(L.det, op.i3, vand<W>(d, kept));
                 if (L.flags & LF_POSTSELECT) {
@@ -503,7 +653,7 @@ __global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams
           case OP_OBS_OUT:
             if (owner && (L.flags & LF_OUT_OBS)) {
               Vw<W> v = vld<W>(slot(op.i2));
-              if (!(L.flags & LF_REFERENCE) && __ldg(p.obs_ref + op.i3)) vxor<W>(v, vfill<W>(~0u));
+              if (!(L.flags & LF_REFERENCE) && (op.flags & FLAG_REF)) vxor<W>(v, vfill<W>(~0u));
               store(L.obs, op.i3, vand<W>(v, vld<W>(slot(p.kept_slot))));
             }
             break;
@@ -550,7 +700,7 @@ __global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams
             __syncthreads();
             const uint32_t pa = op.pa;
             if (code == OP_EXPAND_ROT) {
-              const double c2 = cos(2.0 * op.f), s2 = sin(2.0 * op.f);
+              const double c2 = op.cs, s2 = op.sn;
               const real rs = (real)0.70710678118654752440;
               const uint32_t n = 1u << k;
               for (uint32_t s = t % S; s < S; s += T) {
@@ -566,7 +716,7 @@ __global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams
               }
               k++;
             } else if (code == OP_ROT_Z) {
-              const double c2 = cos(2.0 * op.f), s2 = sin(2.0 * op.f);
+              const double c2 = op.cs, s2 = op.sn;
               const uint32_t half = 1u << (k - 1);
               for (uint32_t s = t % S; s < S; s += T) {
                 C ph;
@@ -578,7 +728,7 @@ __global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams
                 }
               }
             } else if (code == OP_ROT_X) {
-              const double c1 = cos(op.f), s1 = sin(op.f);
+              const double c1 = op.cs, s1 = op.sn;
               const uint32_t half = 1u << (k - 1);
               for (uint32_t s = t % S; s < S; s += T) {
                 const real cr = (real)c1, sr = (real)(fbit(Z + op.a * G, s) ? -s1 : s1);
@@ -769,6 +919,60 @@ __global__ void __launch_bounds__(W == 1 ? 1024 : 256) exec_batched(LaunchParams
 }
 
 // ---------------------------------------------------------------------------
+// Reference parities into instruction flags: FLAG_REF on DETECTOR / OBS_OUT
+// instructions whose det_ref / obs_ref entry is 1 (cleared otherwise).
+// ---------------------------------------------------------------------------
+__global__ void patch_ref_flags(Op* ops, uint32_t n_ops, const uint32_t* det_ref, const uint32_t* obs_ref) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_ops) return;
+  const uint8_t c = ops[i].code;
+  if (c != OP_DETECTOR && c != OP_OBS_OUT) return;
+  const uint32_t r = c == OP_DETECTOR ? det_ref[ops[i].i3] : obs_ref[ops[i].i3];
+  ops[i].flags = (uint8_t)((ops[i].flags & ~FLAG_REF) | (r ? FLAG_REF : 0));
+}
+
+cudaError_t launch_patch_ref(Op* ops, uint32_t n_ops, const uint32_t* det_ref, const uint32_t* obs_ref,
+                             cudaStream_t st) {
+  if (!n_ops) return cudaSuccess;
+  patch_ref_flags<<<(n_ops + 255) / 256, 256, 0, st>>>(ops, n_ops, det_ref, obs_ref);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Fault pre-sampling: one thread per shot, no shared memory, so the latency-
+// bound search of Sec. 3.2's jump runs at full occupancy. Fault j of shot s
+// is stored at flist[j * fstride + s] (shot-minor: coalesced stores).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) presample_faults(LaunchParams L) {
+  const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= L.fstride) return;
+  uint32_t n = 0;
+  bool ovf = false;
+  if (s < L.shots) {
+    const uint64_t shot = L.shot_offset + s;
+    uint32_t f = next_fault(L.p, L.seed, shot, 0);
+    uint32_t* dst = const_cast<uint32_t*>(L.flist);
+    while (f != kNoFault) {
+      if (n == L.fcap) {
+        ovf = true;
+        break;
+      }
+      dst[(uint64_t)n * L.fstride + s] = f;
+      n++;
+      f = next_fault(L.p, L.seed, shot, (f >> 4) + 1);
+    }
+  }
+  const_cast<uint8_t*>(L.fcount)[s] = (uint8_t)(n | (ovf ? 128u : 0u));
+}
+
+cudaError_t launch_presample(const LaunchParams& L, cudaStream_t st) {
+  const uint32_t threads = 256;
+  const uint64_t blocks = (L.fstride + threads - 1) / threads;
+  presample_faults<<<(uint32_t)blocks, threads, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Plain FP64 executor: one thread per shot.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kPlainMaxW = 8;       // N <= 256
@@ -882,8 +1086,7 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
         break;
       }
       case OP_EXPAND_ROT: {
-        const double th = getb(x, op.a) ? -op.f : op.f;
-        const double c2 = cos(2.0 * th) * rs, s2 = sin(2.0 * th) * rs;
+        const double c2 = op.cs * rs, s2 = (getb(x, op.a) ? -op.sn : op.sn) * rs;
         const uint32_t n = 1u << k;
         for (uint32_t i = 0; i < n; i++) {
           double2 u = amp(i);
@@ -894,8 +1097,7 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
         break;
       }
       case OP_ROT_Z: {
-        const double th = getb(x, op.a) ? -op.f : op.f;
-        const double c2 = cos(2.0 * th), s2 = sin(2.0 * th);
+        const double c2 = op.cs, s2 = getb(x, op.a) ? -op.sn : op.sn;
         for (uint32_t j = 0; j < (1u << (k - 1)); j++) {
           uint32_t i1 = insert0(j, op.pa) | (1u << op.pa);
           double2 u = amp(i1);
@@ -904,8 +1106,7 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
         break;
       }
       case OP_ROT_X: {
-        const double th = getb(z, op.a) ? -op.f : op.f;
-        const double c1 = cos(th), s1 = sin(th);
+        const double c1 = op.cs, s1 = getb(z, op.a) ? -op.sn : op.sn;
         for (uint32_t j = 0; j < (1u << (k - 1)); j++) {
           uint32_t i0 = insert0(j, op.pa), i1 = i0 | (1u << op.pa);
           double2 a = amp(i0), b = amp(i1);
@@ -920,7 +1121,7 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
         if (op.flags & FLAG_RESET) {
           // fused reset: conditional X-image on the inline planes r[0..pb)
           for (uint32_t r = 0; r < op.pb; r++) {
-            const uint32_t pl = op.r[r];
+            const uint32_t pl = rent(op, r);
             if (pl < p.n_qubits) flipb(x, pl, par);
             else flipb(z, pl - p.n_qubits, par);
           }
@@ -1081,42 +1282,49 @@ size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W) {
   return smem_layout(p.n_qubits, p.n_slots, p.k_max, G, W, coarse_count(p.n_sites)).bytes;
 }
 
-template <typename real, int W>
+template <typename real, int W, bool BIG>
 static cudaError_t launch_one(const LaunchParams& L, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(exec_batched<real, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto fn = exec_batched<real, W, BIG>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  exec_batched<real, W><<<grid, threads, smem, st>>>(L);
+  fn<<<grid, threads, smem, st>>>(L);
   return cudaGetLastError();
 }
 
-template <typename real, int W>
+template <typename real, int W, bool BIG>
 static cudaError_t occ_one(uint32_t threads, size_t smem, int* per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(exec_batched<real, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto fn = exec_batched<real, W, BIG>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, exec_batched<real, W>, (int)threads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, (int)threads, smem);
+}
+
+// Dispatch over (precision, words per thread, CTA size class). W > 1 is only
+// instantiated for CTAs of at most 256 threads.
+template <typename real>
+static cudaError_t launch_t(const LaunchParams& L, uint32_t W, uint32_t grid, uint32_t threads, size_t smem,
+                            cudaStream_t st) {
+  if (threads > 256) return launch_one<real, 1, true>(L, grid, threads, smem, st);
+  if (W == 4) return launch_one<real, 4, false>(L, grid, threads, smem, st);
+  if (W == 2) return launch_one<real, 2, false>(L, grid, threads, smem, st);
+  return launch_one<real, 1, false>(L, grid, threads, smem, st);
+}
+
+template <typename real>
+static cudaError_t occ_t(uint32_t W, uint32_t threads, size_t smem, int* per_sm) {
+  if (threads > 256) return occ_one<real, 1, true>(threads, smem, per_sm);
+  if (W == 4) return occ_one<real, 4, false>(threads, smem, per_sm);
+  if (W == 2) return occ_one<real, 2, false>(threads, smem, per_sm);
+  return occ_one<real, 1, false>(threads, smem, per_sm);
 }
 
 cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, uint32_t grid, uint32_t threads,
                            size_t smem, cudaStream_t st) {
-  if (fp64) {
-    if (W == 4) return launch_one<double, 4>(L, grid, threads, smem, st);
-    if (W == 2) return launch_one<double, 2>(L, grid, threads, smem, st);
-    return launch_one<double, 1>(L, grid, threads, smem, st);
-  }
-  if (W == 4) return launch_one<float, 4>(L, grid, threads, smem, st);
-  if (W == 2) return launch_one<float, 2>(L, grid, threads, smem, st);
-  return launch_one<float, 1>(L, grid, threads, smem, st);
+  return fp64 ? launch_t<double>(L, W, grid, threads, smem, st) : launch_t<float>(L, W, grid, threads, smem, st);
 }
 
 cudaError_t batched_occupancy(bool fp64, uint32_t W, uint32_t threads, size_t smem, int* per_sm) {
-  if (fp64) {
-    if (W == 4) return occ_one<double, 4>(threads, smem, per_sm);
-    if (W == 2) return occ_one<double, 2>(threads, smem, per_sm);
-    return occ_one<double, 1>(threads, smem, per_sm);
-  }
-  if (W == 4) return occ_one<float, 4>(threads, smem, per_sm);
-  if (W == 2) return occ_one<float, 2>(threads, smem, per_sm);
-  return occ_one<float, 1>(threads, smem, per_sm);
+  return fp64 ? occ_t<double>(W, threads, smem, per_sm) : occ_t<float>(W, threads, smem, per_sm);
 }
 
 cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st) {

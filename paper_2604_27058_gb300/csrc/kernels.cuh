@@ -22,6 +22,7 @@ struct DevProg {
   const uint32_t* site_opt;
   const uint32_t* opt_tab;
   const uint16_t* plist;
+  const uint4* orec;
   uint32_t n_qubits, nw, n_ops, n_sites, n_slots, k_max, kept_slot;
   uint32_t n_meas, n_det, n_obs;
 };
@@ -49,6 +50,13 @@ struct LaunchParams {
   unsigned long long* kept_count;
   uint32_t* err;
   uint32_t qc_stride, qc_n;            // coarse survival index: every qc_stride-th Q, qc_n entries
+  // pre-sampled faults (batched executor; null = sample inline): fault j of
+  // call-local shot s at flist[j * fstride + s] for j < fcount[s] & 127;
+  // bit 7 of fcount marks a list truncated at fcap entries.
+  const uint32_t* flist;
+  const uint8_t* fcount;
+  uint32_t fcap;
+  uint64_t fstride;
   uint32_t stop_event;                // debug: stop before this event (0xffffffff = never)
   uint64_t dump_shot;                 // debug: call-local shot index
   double* dump_amps;

@@ -32,6 +32,8 @@ cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, uint32_
                            size_t smem, cudaStream_t st);
 cudaError_t batched_occupancy(bool fp64, uint32_t W, uint32_t threads, size_t smem, int* blocks_per_sm);
 const std::vector<uint8_t>& program_blob(const nc_program* p);
+cudaError_t launch_patch_ref(Op* ops, uint32_t n_ops, const uint32_t* det_ref, const uint32_t* obs_ref,
+                             cudaStream_t st);
 }  // namespace nc
 
 using namespace nc;
@@ -77,6 +79,7 @@ DevProg view(const ProgHeader& h, const uint8_t* base) {
   d.site_opt = reinterpret_cast<const uint32_t*>(base + h.off_site_opt);
   d.opt_tab = reinterpret_cast<const uint32_t*>(base + h.off_opt_tab);
   d.plist = reinterpret_cast<const uint16_t*>(base + h.off_plist);
+  d.orec = reinterpret_cast<const uint4*>(base + h.off_orec);
   d.n_qubits = h.n_qubits;
   d.nw = h.nw;
   d.n_ops = h.n_ops;
@@ -224,6 +227,10 @@ extern "C" nc_status nc_sample_noalloc(const nc_program* prog, uint64_t shots, u
         i += run;
       }
     }
+    if (launch_patch_ref(reinterpret_cast<Op*>(dblob + h.off_ops), h.n_ops,
+                         reinterpret_cast<const uint32_t*>(dblob + h.off_det_ref),
+                         reinterpret_cast<const uint32_t*>(dblob + h.off_obs_ref), stream) != cudaSuccess)
+      return NC_E_CUDA;
   }
   if (cudaMemsetAsync(cnt, 0, 16, stream) != cudaSuccess) return NC_E_CUDA;
   uint32_t flags = 0;

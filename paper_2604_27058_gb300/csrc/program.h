@@ -18,8 +18,9 @@ enum OpCode : uint8_t {
   OP_ARRAY_H, OP_ARRAY_S, OP_ARRAY_CX, OP_ARRAY_CZ,
   // Pauli rotations (App. B.1); f = theta * alpha, frame sign applied per shot.
   OP_EXPAND_ROT,   // a = v, pa = new top position; phi <- phi (x) (|0> + e^{2i t}|1>)/sqrt2, t = f (-1)^{x_v}
-  OP_ROT_Z,        // a = v, pa; bit-1 amplitudes *= e^{2i t}, t = f (-1)^{x_v}
-  OP_ROT_X,        // a = v, pa; exp(-i t X), t = f (-1)^{z_v}
+                   // (cs, sn) = (cos 2f, sin 2f)
+  OP_ROT_Z,        // a = v, pa; bit-1 amplitudes *= e^{2i t}, t = f (-1)^{x_v}; (cs, sn) = (cos 2f, sin 2f)
+  OP_ROT_X,        // a = v, pa; exp(-i t X), t = f (-1)^{z_v}; (cs, sn) = (cos f, sin f)
   // Measurements (App. B.2); flags bit0 = alpha sign bit, bit1 = output now (row i3).
   OP_MEAS_STATIC,  // i0 = z-mask offset; m = sign ^ parity(x & zmask); slot i2
   OP_MEAS_RANDOM,  // a = v, i0 = event; m = [u < 1/2]; b = m^sign^z_v; H_v; x_v ^= b
@@ -35,10 +36,16 @@ enum OpCode : uint8_t {
   OP_OBS_INCLUDE,  // obs slot i2 ^= XOR of i1 slots at slot list i0
   OP_OBS_OUT,      // obs slot i2 ^ ref -> obs row i3 (masked by kept)
   OP_KEPT_OUT,     // kept slot i2 -> kept row
+  // Batch headers: the next pa instructions (same kind, mutually independent,
+  // all inside one staging chunk) may run together. An executor may also
+  // ignore the header and run them one by one.
+  OP_BATCH,
   OP_COUNT
 };
 
-enum : uint8_t { FLAG_SIGN = 1, FLAG_OUT = 2, FLAG_RESET = 4 };
+// FLAG_REF (DETECTOR, OBS_OUT): the noiseless reference parity is 1. It is
+// set on the device copy after the reference launch (patch_ref_flags).
+enum : uint8_t { FLAG_SIGN = 1, FLAG_OUT = 2, FLAG_RESET = 4, FLAG_REF = 8 };
 
 struct Op {
   uint8_t code;
@@ -50,6 +57,7 @@ struct Op {
   union {
     struct { uint32_t i0, i1, i2, i3; };
     struct { uint32_t j0, j1; uint16_t r[4]; };  // fused reset: r = inline X-image planes
+    struct { double cs, sn; };                   // rotations: cos / sin of the phase (see OpCode)
   };
   union {
     double f;        // rotation angle
@@ -70,6 +78,13 @@ static_assert(sizeof(Op) == 32, "Op must be 32 bytes");
 constexpr uint32_t kInline = 4;
 constexpr uint8_t kNoInline = 0xFF;
 
+// Padding of inline entries beyond the count: reads use an all-zero row
+// (frame plane 2N, record slot n_slots), writes a scratch plane (2N + 1), so
+// every instruction touches exactly kInline entries without branching.
+// Instructions are staged in chunks of kChunk; a batch never crosses one.
+constexpr uint32_t kChunk = 128;
+constexpr uint32_t kMaxBatch = 8;
+
 // Noise-site kinds (physical channel of the site).
 enum SiteKind : uint8_t { SITE_X = 0, SITE_Y, SITE_Z, SITE_D1, SITE_D2, SITE_FLIP };
 
@@ -82,17 +97,25 @@ struct ProgHeader {
   uint32_t n_meas, n_det, n_obs, n_events;
   uint32_t n_slots, k_max;
   uint32_t kept_slot, n_mask_words, n_slot_list, n_opt;
-  uint32_t n_plist, pad0[3];
+  uint32_t n_plist;
+  float mean_faults;               // sum of site probabilities (expected faults per shot)
+  uint32_t pad0[2];
   uint64_t off_ops, off_masks, off_q, off_seg_start, off_seg_end, off_site_info, off_site_eff,
-      off_slot_list, off_det_ref, off_obs_ref, off_site_opt, off_opt_tab, off_plist, total_bytes;
+      off_slot_list, off_det_ref, off_obs_ref, off_site_opt, off_opt_tab, off_plist, off_orec, total_bytes;
 };
+// Option records: orec[site * 15 + option] is 16 bytes (8 x u16). Word 0 is
+// a tag: n <= 7 -> n frame-plane indices follow; kRecFlip -> the site flips
+// record slot (words 1, 2) / output row (words 3, 4); kRecLong -> use
+// opt_tab / plist. Indexed directly, so applying a fault is one load.
+constexpr uint16_t kRecFlip = 0xFFFE, kRecLong = 0xFFFF;
+constexpr uint32_t kRecPerSite = 15;
 // Noise options in sparse form: site_info >> 8 indexes opt_tab;
 // opt_tab[2 * (index + option)] = (plist offset, entry count); plist holds
 // frame plane indices (u16). A FLIP site has one entry (record slot, record
 // row): its fault flips the slot and, if the shot is kept, the output bit.
 
 constexpr uint32_t kMagic = 0x4E435047u;  // "NCPG"
-constexpr uint32_t kVersion = 3;
+constexpr uint32_t kVersion = 6;
 constexpr uint32_t kMaxK = 30;
 constexpr uint32_t kMaxQubits = 4096;
 
