@@ -21,16 +21,18 @@
 #include "kernels.cuh"
 
 namespace nc {
-size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W);
+size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W, bool bk);
 uint32_t coarse_stride(uint32_t n_sites);
 uint32_t coarse_count(uint32_t n_sites);
-cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, uint32_t grid, uint32_t threads,
+cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, bool bk, uint32_t grid, uint32_t threads,
                            size_t smem, cudaStream_t st);
-cudaError_t batched_occupancy(bool fp64, uint32_t W, uint32_t threads, size_t smem, int* blocks_per_sm);
+cudaError_t batched_occupancy(bool fp64, uint32_t W, bool bk, uint32_t threads, size_t smem, int* blocks_per_sm);
 cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st);
 cudaError_t launch_patch_ref(Op* ops, uint32_t n_ops, const uint32_t* det_ref, const uint32_t* obs_ref,
                              cudaStream_t st);
 cudaError_t launch_presample(const LaunchParams& L, cudaStream_t st);
+cudaError_t launch_bucket(const LaunchParams& L, uint32_t n_wt, uint32_t* ents, uint32_t* offs, uint64_t cap_total,
+                          unsigned long long* total, uint32_t* ovf, cudaStream_t st);
 bool plain_supported(const DevProg& p);
 }  // namespace nc
 
@@ -76,6 +78,7 @@ DevProg dev_view(const ProgHeader& h, const uint8_t* base) {
   d.opt_tab = reinterpret_cast<const uint32_t*>(base + h.off_opt_tab);
   d.plist = reinterpret_cast<const uint16_t*>(base + h.off_plist);
   d.orec = reinterpret_cast<const uint4*>(base + h.off_orec);
+  d.site_blk = reinterpret_cast<const uint32_t*>(base + h.off_site_blk);
   d.n_qubits = h.n_qubits;
   d.nw = h.nw;
   d.n_ops = h.n_ops;
@@ -86,6 +89,7 @@ DevProg dev_view(const ProgHeader& h, const uint8_t* base) {
   d.n_meas = h.n_meas;
   d.n_det = h.n_det;
   d.n_obs = h.n_obs;
+  d.n_blocks = h.n_blocks;
   return d;
 }
 
@@ -140,18 +144,19 @@ struct Scratch {
 };
 
 // Launch shape of the batched executor: G 32-shot words per tile, W words
-// per owner thread (G / W owners), T threads per CTA.
+// per owner thread (G / W owners), T threads per CTA; B = 0 turns the
+// bucketed noise path off.
 struct Tuning {
-  uint32_t G, T, W;
+  uint32_t G, T, W, B;
 };
 
 Tuning choose_tuning(const DevProg& d, const char* tune) {
   Tuning t;
-  if (d.k_max == 0) t = {128, 128, 1};
-  else if (d.k_max <= 6) t = {32, 256, 1};
-  else if (d.k_max <= 10) t = {8, 256, 1};
-  else if (d.k_max <= 13) t = {2, 512, 1};
-  else t = {1, 1024, 1};
+  if (d.k_max == 0) t = {128, 128, 1, 1};
+  else if (d.k_max <= 6) t = {32, 256, 1, 1};
+  else if (d.k_max <= 10) t = {8, 256, 1, 1};
+  else if (d.k_max <= 13) t = {2, 512, 1, 1};
+  else t = {1, 1024, 1, 1};
   if (tune) {
     unsigned v = 0;
     const char* s = tune;
@@ -159,6 +164,7 @@ Tuning choose_tuning(const DevProg& d, const char* tune) {
       if (sscanf(s, "g=%u", &v) == 1) t.G = v;
       else if (sscanf(s, "t=%u", &v) == 1) t.T = v;
       else if (sscanf(s, "w=%u", &v) == 1) t.W = v;
+      else if (sscanf(s, "b=%u", &v) == 1) t.B = v;
       const char* c = strchr(s, ',');
       if (!c) break;
       s = c + 1;
@@ -167,7 +173,7 @@ Tuning choose_tuning(const DevProg& d, const char* tune) {
   if (t.W != 1 && t.W != 2 && t.W != 4) t.W = 1;
   if (t.G < t.W) t.W = t.G;
   // keep the shared-memory footprint under the opt-in limit
-  while (t.G > t.W && batched_smem_bytes(d, t.G, t.W) > 220 * 1024) t.G >>= 1;
+  while (t.G > t.W && batched_smem_bytes(d, t.G, t.W, false) > 220 * 1024) t.G >>= 1;
   if (t.T < t.G / t.W) t.T = t.G / t.W;
   if (t.T < 32) t.T = 32;
   return t;
@@ -246,12 +252,45 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
     L.qc_n = coarse_count(h.n_sites);
     const uint64_t S = 32ull * tu.G;
     L.n_tiles = (uint32_t)((L.row_words32 + tu.G - 1) / tu.G);
-    const size_t smem = batched_smem_bytes(L.p, tu.G, tu.W);
+    const bool noisy = !(lflags & LF_NOISELESS) && h.n_sites && stop_event == 0xffffffffu;
+    const double mean = (double)h.mean_faults;
+    const double per_shot_cap = std::ceil(mean + 6.0 * std::sqrt(mean) + 4.0);
+    // Bucketed noise: every shot's faults sampled up front and sorted by
+    // noise block per 1024-shot warp-tile (one owner word per lane).
+    bool bk = false;
+    if (noisy && tu.B && tu.W == 1 && tu.T <= 256 && tu.G >= 32 && h.n_blocks <= 8192 &&
+        (uint64_t)h.n_sites * kRecPerSite < (1ull << 22) && per_shot_cap <= 32.0) {
+      const uint32_t n_wt = L.n_tiles * (tu.G / 32);
+      const double lam = mean * (double)shots;
+      const uint64_t cap_total = (uint64_t)(lam * 1.02 + 12.0 * std::sqrt(lam) + 65536.0);
+      const size_t ents_b = cap_total * 4, offs_b = (size_t)n_wt * (h.n_blocks + 1) * 4;
+      size_t free_b = 0, total_b = 0;
+      NC_TRY(cudaMemGetInfo(&free_b, &total_b));
+      if (cap_total < (1ull << 32) && ents_b + offs_b < free_b / 2) {
+        void *ents = nullptr, *offs = nullptr, *ctr = nullptr;
+        NC_TRY(scratch.get(&ents, ents_b));
+        NC_TRY(scratch.get(&offs, offs_b));
+        NC_TRY(scratch.get(&ctr, 16));
+        NC_TRY(cudaMemsetAsync(ctr, 0, 16, stream));
+        unsigned long long* total = (unsigned long long*)ctr;
+        uint32_t* ovf = (uint32_t*)((char*)ctr + 8);
+        NC_TRY(launch_bucket(L, n_wt, (uint32_t*)ents, (uint32_t*)offs, cap_total, total, ovf, stream));
+        uint32_t h_ovf = 1;
+        NC_TRY(cudaMemcpyAsync(&h_ovf, ovf, 4, cudaMemcpyDeviceToHost, stream));
+        NC_TRY(cudaStreamSynchronize(stream));
+        if (!h_ovf) {
+          bk = true;
+          L.bents = (const uint32_t*)ents;
+          L.boffs = (const uint32_t*)offs;
+        }
+      }
+    }
+    const size_t smem = batched_smem_bytes(L.p, tu.G, tu.W, bk);
     int per_sm = 0, n_sm = 0, dev = 0;
     NC_TRY(cudaGetDevice(&dev));
     NC_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     const bool fp64 = precision == NC_FP64_BATCHED;
-    NC_TRY(batched_occupancy(fp64, tu.W, tu.T, smem, &per_sm));
+    NC_TRY(batched_occupancy(fp64, tu.W, bk, tu.T, smem, &per_sm));
     if (per_sm < 1) return NC_E_UNSUPPORTED;
     uint64_t grid = std::min<uint64_t>(L.n_tiles, (uint64_t)per_sm * n_sm);
     if (h.k_max > 0) {
@@ -263,10 +302,9 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
       grid = std::min(grid, cap);
       NC_TRY(scratch.get(&L.work, per_cta * grid));
     }
-    // pre-sample every shot's faults when the list buffer fits comfortably
-    if (!(lflags & LF_NOISELESS) && h.n_sites && stop_event == 0xffffffffu) {
-      const double mean = (double)h.mean_faults;
-      const uint32_t cap = (uint32_t)std::min(127.0, std::ceil(mean + 6.0 * std::sqrt(mean) + 4.0));
+    // otherwise pre-sample every shot's faults when the list buffer fits
+    if (noisy && !bk) {
+      const uint32_t cap = (uint32_t)std::min(127.0, per_shot_cap);
       const uint64_t padded = L.row_words32 * 32;
       const size_t bytes = (size_t)cap * padded * 4 + padded;
       size_t free_b = 0, total_b = 0;
@@ -281,7 +319,7 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
         NC_TRY(launch_presample(L, stream));
       }
     }
-    NC_TRY(launch_batched(L, fp64, tu.W, (uint32_t)grid, tu.T, smem, stream));
+    NC_TRY(launch_batched(L, fp64, tu.W, bk, (uint32_t)grid, tu.T, smem, stream));
   }
 done:
   return st;
@@ -503,7 +541,7 @@ nc_status nc_program_deserialize(const void* buf, size_t len, nc_program** out) 
   if (h.magic != kMagic || h.version != kVersion || h.total_bytes + sizeof(nc_info_counts) != len) return NC_E_ARG;
   uint64_t offs[] = {h.off_ops, h.off_masks, h.off_q, h.off_seg_start, h.off_seg_end, h.off_site_info,
                      h.off_site_eff, h.off_slot_list, h.off_det_ref, h.off_obs_ref,
-                     h.off_site_opt, h.off_opt_tab, h.off_plist, h.off_orec};
+                     h.off_site_opt, h.off_opt_tab, h.off_plist, h.off_orec, h.off_site_blk};
   for (uint64_t o : offs)
     if (o > h.total_bytes || (o & 15)) return NC_E_ARG;
   if (h.off_ops + (uint64_t)h.n_ops * sizeof(Op) > h.total_bytes || h.k_max > kMaxK || h.n_qubits > kMaxQubits)

@@ -1182,6 +1182,16 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
       ops.swap(out);
     }
 
+    // noise-block ordinals and the site -> block table
+    std::vector<uint32_t> site_blk(c.site_kind.size(), 0);
+    uint32_t n_blocks = 0;
+    for (auto& o : ops)
+      if (o.code == OP_NOISE_BLOCK) {
+        o.i2 = n_blocks;
+        for (uint32_t s = o.i0; s < o.i1; s++) site_blk[s] = n_blocks;
+        n_blocks++;
+      }
+
     // flip sites reference slots through site_eff
     std::vector<uint32_t> site_eff = c.site_eff;
     for (size_t s = 0; s < c.site_kind.size(); s++)
@@ -1286,6 +1296,7 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     h.n_slot_list = (uint32_t)slot_list.size();
     h.n_opt = (uint32_t)(opt_tab.size() / 2);
     h.n_plist = (uint32_t)plist.size();
+    h.n_blocks = n_blocks;
     {
       double mean = 0.0;
       for (double sp : c.site_p) mean += sp;
@@ -1311,6 +1322,7 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     h.off_opt_tab = place(opt_tab.size() * 4);
     h.off_plist = place(plist.size() * 2);
     h.off_orec = place(orec.size() * 2);
+    h.off_site_blk = place(site_blk.size() * 4);
     h.total_bytes = off;
     out.blob.assign(off, 0);
     std::memcpy(out.blob.data(), &h, sizeof(h));
@@ -1329,6 +1341,7 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     cp(h.off_opt_tab, opt_tab.data(), opt_tab.size() * 4);
     cp(h.off_plist, plist.data(), plist.size() * 2);
     cp(h.off_orec, orec.data(), orec.size() * 2);
+    cp(h.off_site_blk, site_blk.data(), site_blk.size() * 4);
     out.counts = c.counts;
     return 0;
   } catch (CompileError& e) {

@@ -95,7 +95,9 @@ struct SmemLayout {
 };
 
 __host__ __device__ inline SmemLayout smem_layout(uint32_t n_qubits, uint32_t n_slots, uint32_t k_max, uint32_t G,
-                                                  uint32_t W, uint32_t qc_n) {
+                                                  uint32_t W, uint32_t qc_n, bool bk = false) {
+  // the bucketed executor keeps no per-shot noise state (NF, CUR, QU, QC)
+  if (bk) qc_n = 0;
   SmemLayout L;
   size_t w = 0;
   L.ops = w;
@@ -107,15 +109,15 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t n_qubits, uint32_t n_
   L.sl = w;
   w += (size_t)(n_slots + 1) * G;       // + zero slot (n_slots)
   L.nf = w;
-  w += (size_t)32 * G;
+  if (!bk) w += (size_t)32 * G;
   L.cur = w;  // u8 [32][G]: next index into the pre-sampled fault list
-  w += (size_t)8 * G;
+  if (!bk) w += (size_t)8 * G;
   L.tmp = w;
   w += G;
   w = (w + 3) & ~(size_t)3;
   L.qu = w;
   const size_t owner_warps = (G / W + 31) / 32;
-  w += owner_warps * (kQueue / 2);
+  if (!bk) w += owner_warps * (kQueue / 2);
   w = (w + 3) & ~(size_t)3;
   L.red = w;
   if (k_max > 0) w += (size_t)2 * 2 * 32 * G;  // 2 doubles per shot
@@ -187,13 +189,13 @@ __device__ __forceinline__ uint32_t pick4(const uint4& v, uint32_t i) {
 
 // BIG variants allow 1024 threads per CTA (large-k tiles, at most 64
 // registers per thread); the others allow 256 threads and more registers.
-template <typename real, int W, bool BIG>
+template <typename real, int W, bool BIG, bool BK>
 __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams L) {
   using C = typename Cx<real>::T;
   extern __shared__ __align__(16) uint32_t smem[];
   const DevProg& p = L.p;
   const uint32_t G = L.G, S = 32u * G, N = p.n_qubits, T = blockDim.x, t = threadIdx.x;
-  const SmemLayout lay = smem_layout(N, p.n_slots, p.k_max, G, W, L.qc_n);
+  const SmemLayout lay = smem_layout(N, p.n_slots, p.k_max, G, W, L.qc_n, BK);
   uint32_t* PL = smem + lay.pl;
   uint32_t* X = PL;
   uint32_t* Z = PL + (size_t)N * G;
@@ -225,7 +227,8 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
     for (uint32_t i = t; i < 2 * cnt; i += T) cp_async16(dst + i, src + i);
     cp_async_commit();
   };
-  for (uint32_t c = t; c < L.qc_n; c += T) QC[c] = __ldg(p.q + (size_t)c * L.qc_stride);
+  if (!BK)
+    for (uint32_t c = t; c < L.qc_n; c += T) QC[c] = __ldg(p.q + (size_t)c * L.qc_stride);
   __syncthreads();
 
   for (uint32_t tile = blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
@@ -249,7 +252,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
       for (uint32_t s = 0; s <= p.n_slots; s++) vst<W>(SL + s * G + tw, vfill<W>(0u));
       vst<W>(SL + kept_off + tw, valid);
 #pragma unroll
-      for (int i = 0; i < W; i++) {
+      for (int i = 0; i < W && !BK; i++) {
         const uint64_t sl0 = (word0 + i) * 32u;  // call-local shot of bit 0
         for (uint32_t j = 0; j < 32; j++) {
           uint32_t f = kNoFault;
@@ -479,6 +482,43 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
             }
             break;
           case OP_NOISE_BLOCK:
+            if constexpr (BK) {
+              // faults of this warp's 1024 shots in this block, one per lane
+              if (owner_warp) {
+                const uint32_t wt = tile * (G / 32u) + warp;
+                const uint32_t* bo = L.boffs + (size_t)wt * (p.n_blocks + 1) + op.i2;
+                const uint32_t beg = bo[0], end = bo[1];
+                for (uint32_t e = beg + lane; e < end; e += 32) {
+                  const uint32_t ent = L.bents[e];
+                  const uint32_t sl = ent & 1023u;
+                  const uint32_t w = warp * 32u + (sl >> 5), bit = 1u << (sl & 31u);
+                  const uint4 r = __ldg(p.orec + (ent >> 10));
+                  const uint32_t tag = r.x & 0xFFFFu;
+                  if (tag == kRecFlip) {
+                    const uint32_t sl_idx = (r.x >> 16) | ((r.y & 0xFFFFu) << 16);
+                    const uint32_t row = (r.y >> 16) | ((r.z & 0xFFFFu) << 16);
+                    atomicXor(&SL[sl_idx * G + w], bit);
+                    if ((L.flags & LF_OUT_MEAS) && (SL[kept_off + w] & bit) &&
+                        (uint64_t)w + (uint64_t)tile * G < L.row_words32)
+                      atomicXor(&L.meas[(size_t)row * L.row_words32 + (uint64_t)tile * G + w], bit);
+                  } else if (tag == kRecLong) {
+                    const uint32_t site = (ent >> 10) / kRecPerSite, opt = (ent >> 10) % kRecPerSite;
+                    const uint32_t info = __ldg(p.site_info + site);
+                    const uint2 o2 = __ldg(reinterpret_cast<const uint2*>(p.opt_tab) + (info >> 8) + opt);
+                    for (uint32_t q = 0; q < o2.y; q++)
+                      atomicXor(&PL[(uint32_t)__ldg(p.plist + o2.x + q) * G + w], bit);
+                  } else {
+                    const uint32_t ent7[7] = {r.x >> 16, r.y & 0xFFFFu, r.y >> 16, r.z & 0xFFFFu,
+                                              r.z >> 16, r.w & 0xFFFFu, r.w >> 16};
+#pragma unroll
+                    for (uint32_t q = 0; q < 7; q++)
+                      if (q < tag) atomicXor(&PL[ent7[q] * G + w], bit);
+                  }
+                }
+                __syncwarp();
+              }
+              break;
+            }
             if (owner_warp) {
               while (true) {
                 // due entries of this lane's words (site < block end) and the
@@ -939,6 +979,105 @@ cudaError_t launch_patch_ref(Op* ops, uint32_t n_ops, const uint32_t* det_ref, c
 }
 
 // ---------------------------------------------------------------------------
+// Fault bucketing: one CTA of 1024 threads per 1024-shot warp-tile, one
+// thread per shot. Each thread samples its shot's faults (Sec. 3.2 jump),
+// then the CTA counting-sorts them by noise block into a compact global
+// array (the order inside a block is free: fault effects are XORs). A shot
+// with more than kBucketCap faults or a full global array sets *ovf, and the
+// host then uses the per-shot path.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kBucketCap = 32;
+
+__global__ void __launch_bounds__(1024) bucket_faults(LaunchParams L, uint32_t* ents, uint32_t* offs,
+                                                      uint64_t cap_total, unsigned long long* total,
+                                                      uint32_t* ovf) {
+  extern __shared__ uint32_t bsm[];
+  const uint32_t nb = L.p.n_blocks;
+  uint32_t* cnt = bsm;            // [nb]
+  uint32_t* pre = bsm + nb;       // [nb + 1]
+  __shared__ uint32_t wsum[32];
+  __shared__ unsigned long long base_s;
+  const uint32_t t = threadIdx.x, wt = blockIdx.x;
+  for (uint32_t i = t; i < nb; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
+  const uint64_t sl = (uint64_t)wt * 1024u + t;
+  uint32_t loc[kBucketCap];
+  uint32_t n = 0;
+  if (sl < L.shots) {
+    const uint64_t shot = L.shot_offset + sl;
+    uint32_t f = next_fault(L.p, L.seed, shot, 0);
+    while (f != kNoFault) {
+      if (n == kBucketCap) {
+        atomicOr(ovf, 1u);
+        break;
+      }
+      const uint32_t site = f >> 4;
+      loc[n++] = f;
+      atomicAdd(&cnt[__ldg(L.p.site_blk + site)], 1u);
+      f = next_fault(L.p, L.seed, shot, site + 1);
+    }
+  }
+  __syncthreads();
+  // exclusive scan of cnt: each thread sums a contiguous run, then a block scan
+  const uint32_t per = (nb + blockDim.x - 1) / blockDim.x;
+  const uint32_t lo = min(nb, t * per), hi = min(nb, lo + per);
+  uint32_t s = 0;
+  for (uint32_t i = lo; i < hi; i++) s += cnt[i];
+  uint32_t incl = s;
+  const uint32_t lane = t & 31u, wid = t >> 5;
+#pragma unroll
+  for (uint32_t d = 1; d < 32; d <<= 1) {
+    uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += v;
+  }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t v = lane < (blockDim.x >> 5) ? wsum[lane] : 0u, inc = v;
+#pragma unroll
+    for (uint32_t d = 1; d < 32; d <<= 1) {
+      uint32_t u = __shfl_up_sync(0xffffffffu, inc, d);
+      if (lane >= d) inc += u;
+    }
+    wsum[lane] = inc - v;  // exclusive warp offsets
+    if (lane == 31) {
+      const unsigned long long b = atomicAdd(total, (unsigned long long)inc);
+      base_s = b;
+      if (b + inc > cap_total) atomicOr(ovf, 1u);
+    }
+  }
+  __syncthreads();
+  uint32_t run = wsum[wid] + incl - s;
+  for (uint32_t i = lo; i < hi; i++) {
+    pre[i] = run;
+    run += cnt[i];
+  }
+  if (hi == nb && lo < hi) pre[nb] = run;
+  if (nb == 0 && t == 0) pre[0] = 0;
+  __syncthreads();
+  const unsigned long long base = base_s;
+  for (uint32_t i = t; i <= nb; i += blockDim.x) offs[(size_t)wt * (nb + 1) + i] = (uint32_t)(base + pre[i]);
+  __syncthreads();
+  // cursors start at the block offsets
+  for (uint32_t i = t; i < nb; i += blockDim.x) cnt[i] = pre[i];
+  __syncthreads();
+  for (uint32_t i = 0; i < n; i++) {
+    const uint32_t site = loc[i] >> 4, opt = loc[i] & 15u;
+    const uint32_t pos = atomicAdd(&cnt[__ldg(L.p.site_blk + site)], 1u);
+    if (base + pos < cap_total) ents[base + pos] = ((site * kRecPerSite + opt) << 10) | t;
+  }
+}
+
+cudaError_t launch_bucket(const LaunchParams& L, uint32_t n_wt, uint32_t* ents, uint32_t* offs, uint64_t cap_total,
+                          unsigned long long* total, uint32_t* ovf, cudaStream_t st) {
+  const size_t smem = (size_t)(2 * L.p.n_blocks + 1) * 4;
+  cudaError_t e = cudaFuncSetAttribute(bucket_faults, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  bucket_faults<<<n_wt, 1024, smem, st>>>(L, ents, offs, cap_total, total, ovf);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Fault pre-sampling: one thread per shot, no shared memory, so the latency-
 // bound search of Sec. 3.2's jump runs at full occupancy. Fault j of shot s
 // is stored at flist[j * fstride + s] (shot-minor: coalesced stores).
@@ -1278,53 +1417,57 @@ uint32_t coarse_count(uint32_t n_sites) {
   return n_sites ? (n_sites + s - 1) / s : 0;
 }
 
-size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W) {
-  return smem_layout(p.n_qubits, p.n_slots, p.k_max, G, W, coarse_count(p.n_sites)).bytes;
+size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W, bool bk) {
+  return smem_layout(p.n_qubits, p.n_slots, p.k_max, G, W, coarse_count(p.n_sites), bk).bytes;
 }
 
-template <typename real, int W, bool BIG>
+template <typename real, int W, bool BIG, bool BK>
 static cudaError_t launch_one(const LaunchParams& L, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t st) {
-  auto fn = exec_batched<real, W, BIG>;
+  auto fn = exec_batched<real, W, BIG, BK>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   fn<<<grid, threads, smem, st>>>(L);
   return cudaGetLastError();
 }
 
-template <typename real, int W, bool BIG>
+template <typename real, int W, bool BIG, bool BK>
 static cudaError_t occ_one(uint32_t threads, size_t smem, int* per_sm) {
-  auto fn = exec_batched<real, W, BIG>;
+  auto fn = exec_batched<real, W, BIG, BK>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, (int)threads, smem);
 }
 
-// Dispatch over (precision, words per thread, CTA size class). W > 1 is only
-// instantiated for CTAs of at most 256 threads.
+// Dispatch over (precision, words per thread, CTA size class, bucketed
+// noise). W > 1 and the bucketed variant exist only for CTAs of at most 256
+// threads; the bucketed variant only for W = 1.
 template <typename real>
-static cudaError_t launch_t(const LaunchParams& L, uint32_t W, uint32_t grid, uint32_t threads, size_t smem,
+static cudaError_t launch_t(const LaunchParams& L, uint32_t W, bool bk, uint32_t grid, uint32_t threads, size_t smem,
                             cudaStream_t st) {
-  if (threads > 256) return launch_one<real, 1, true>(L, grid, threads, smem, st);
-  if (W == 4) return launch_one<real, 4, false>(L, grid, threads, smem, st);
-  if (W == 2) return launch_one<real, 2, false>(L, grid, threads, smem, st);
-  return launch_one<real, 1, false>(L, grid, threads, smem, st);
+  if (threads > 256) return launch_one<real, 1, true, false>(L, grid, threads, smem, st);
+  if (bk) return launch_one<real, 1, false, true>(L, grid, threads, smem, st);
+  if (W == 4) return launch_one<real, 4, false, false>(L, grid, threads, smem, st);
+  if (W == 2) return launch_one<real, 2, false, false>(L, grid, threads, smem, st);
+  return launch_one<real, 1, false, false>(L, grid, threads, smem, st);
 }
 
 template <typename real>
-static cudaError_t occ_t(uint32_t W, uint32_t threads, size_t smem, int* per_sm) {
-  if (threads > 256) return occ_one<real, 1, true>(threads, smem, per_sm);
-  if (W == 4) return occ_one<real, 4, false>(threads, smem, per_sm);
-  if (W == 2) return occ_one<real, 2, false>(threads, smem, per_sm);
-  return occ_one<real, 1, false>(threads, smem, per_sm);
+static cudaError_t occ_t(uint32_t W, bool bk, uint32_t threads, size_t smem, int* per_sm) {
+  if (threads > 256) return occ_one<real, 1, true, false>(threads, smem, per_sm);
+  if (bk) return occ_one<real, 1, false, true>(threads, smem, per_sm);
+  if (W == 4) return occ_one<real, 4, false, false>(threads, smem, per_sm);
+  if (W == 2) return occ_one<real, 2, false, false>(threads, smem, per_sm);
+  return occ_one<real, 1, false, false>(threads, smem, per_sm);
 }
 
-cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, uint32_t grid, uint32_t threads,
+cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, bool bk, uint32_t grid, uint32_t threads,
                            size_t smem, cudaStream_t st) {
-  return fp64 ? launch_t<double>(L, W, grid, threads, smem, st) : launch_t<float>(L, W, grid, threads, smem, st);
+  return fp64 ? launch_t<double>(L, W, bk, grid, threads, smem, st)
+              : launch_t<float>(L, W, bk, grid, threads, smem, st);
 }
 
-cudaError_t batched_occupancy(bool fp64, uint32_t W, uint32_t threads, size_t smem, int* per_sm) {
-  return fp64 ? occ_t<double>(W, threads, smem, per_sm) : occ_t<float>(W, threads, smem, per_sm);
+cudaError_t batched_occupancy(bool fp64, uint32_t W, bool bk, uint32_t threads, size_t smem, int* per_sm) {
+  return fp64 ? occ_t<double>(W, bk, threads, smem, per_sm) : occ_t<float>(W, bk, threads, smem, per_sm);
 }
 
 cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st) {

@@ -23,8 +23,9 @@ struct DevProg {
   const uint32_t* opt_tab;
   const uint16_t* plist;
   const uint4* orec;
+  const uint32_t* site_blk;
   uint32_t n_qubits, nw, n_ops, n_sites, n_slots, k_max, kept_slot;
-  uint32_t n_meas, n_det, n_obs;
+  uint32_t n_meas, n_det, n_obs, n_blocks;
 };
 
 enum : uint32_t {
@@ -57,6 +58,11 @@ struct LaunchParams {
   const uint8_t* fcount;
   uint32_t fcap;
   uint64_t fstride;
+  // faults bucketed by noise block (bucketed executor): warp-tile wt (1024
+  // call-local shots) has its block-k entries at bents[boffs[wt*(nb+1)+k] ..
+  // boffs[wt*(nb+1)+k+1]); an entry is (option record << 10) | shot in tile.
+  const uint32_t* bents;
+  const uint32_t* boffs;
   uint32_t stop_event;                // debug: stop before this event (0xffffffff = never)
   uint64_t dump_shot;                 // debug: call-local shot index
   double* dump_amps;

@@ -25,12 +25,12 @@
 #include "kernels.cuh"
 
 namespace nc {
-size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W);
+size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W, bool bk);
 uint32_t coarse_stride(uint32_t n_sites);
 uint32_t coarse_count(uint32_t n_sites);
-cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, uint32_t grid, uint32_t threads,
+cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, bool bk, uint32_t grid, uint32_t threads,
                            size_t smem, cudaStream_t st);
-cudaError_t batched_occupancy(bool fp64, uint32_t W, uint32_t threads, size_t smem, int* blocks_per_sm);
+cudaError_t batched_occupancy(bool fp64, uint32_t W, bool bk, uint32_t threads, size_t smem, int* blocks_per_sm);
 const std::vector<uint8_t>& program_blob(const nc_program* p);
 cudaError_t launch_patch_ref(Op* ops, uint32_t n_ops, const uint32_t* det_ref, const uint32_t* obs_ref,
                              cudaStream_t st);
@@ -80,6 +80,7 @@ DevProg view(const ProgHeader& h, const uint8_t* base) {
   d.opt_tab = reinterpret_cast<const uint32_t*>(base + h.off_opt_tab);
   d.plist = reinterpret_cast<const uint16_t*>(base + h.off_plist);
   d.orec = reinterpret_cast<const uint4*>(base + h.off_orec);
+  d.site_blk = reinterpret_cast<const uint32_t*>(base + h.off_site_blk);
   d.n_qubits = h.n_qubits;
   d.nw = h.nw;
   d.n_ops = h.n_ops;
@@ -90,6 +91,7 @@ DevProg view(const ProgHeader& h, const uint8_t* base) {
   d.n_meas = h.n_meas;
   d.n_det = h.n_det;
   d.n_obs = h.n_obs;
+  d.n_blocks = h.n_blocks;
   return d;
 }
 
@@ -125,17 +127,17 @@ nc_status launch(const DevProg& d, uint64_t shots, uint64_t seed, uint64_t shot_
   L.stop_event = 0xffffffffu;
   uint32_t G, T;
   shape(d.k_max, &G, &T);
-  while (G > 1 && batched_smem_bytes(d, G, 1) > 220 * 1024) G >>= 1;
+  while (G > 1 && batched_smem_bytes(d, G, 1, false) > 220 * 1024) G >>= 1;
   if (T < G) T = G;
   L.G = G;
   L.qc_stride = coarse_stride(d.n_sites);
   L.qc_n = coarse_count(d.n_sites);
   L.n_tiles = (uint32_t)((L.row_words32 + G - 1) / G);
-  const size_t smem = batched_smem_bytes(d, G, 1);
+  const size_t smem = batched_smem_bytes(d, G, 1, false);
   int per_sm = 0, n_sm = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return NC_E_CUDA;
   if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return NC_E_CUDA;
-  if (batched_occupancy(false, 1, T, smem, &per_sm) != cudaSuccess) return NC_E_CUDA;
+  if (batched_occupancy(false, 1, false, T, smem, &per_sm) != cudaSuccess) return NC_E_CUDA;
   if (per_sm < 1) return NC_E_UNSUPPORTED;
   uint64_t grid = std::min<uint64_t>(L.n_tiles, (uint64_t)per_sm * n_sm);
   if (d.k_max > 0) {
@@ -147,7 +149,7 @@ nc_status launch(const DevProg& d, uint64_t shots, uint64_t seed, uint64_t shot_
     L.work = work;
   }
   if (grid == 0) return NC_OK;
-  if (launch_batched(L, false, 1, (uint32_t)grid, T, smem, stream) != cudaSuccess) return NC_E_CUDA;
+  if (launch_batched(L, false, 1, false, (uint32_t)grid, T, smem, stream) != cudaSuccess) return NC_E_CUDA;
   return NC_OK;
 }
 

@@ -99,10 +99,13 @@ struct ProgHeader {
   uint32_t kept_slot, n_mask_words, n_slot_list, n_opt;
   uint32_t n_plist;
   float mean_faults;               // sum of site probabilities (expected faults per shot)
-  uint32_t pad0[2];
+  uint32_t n_blocks;               // NOISE_BLOCK instructions (their ordinal is in i2)
+  uint32_t pad0;
   uint64_t off_ops, off_masks, off_q, off_seg_start, off_seg_end, off_site_info, off_site_eff,
-      off_slot_list, off_det_ref, off_obs_ref, off_site_opt, off_opt_tab, off_plist, off_orec, total_bytes;
+      off_slot_list, off_det_ref, off_obs_ref, off_site_opt, off_opt_tab, off_plist, off_orec, off_site_blk,
+      total_bytes;
 };
+// site_blk[site] = ordinal of the NOISE_BLOCK instruction that covers the site.
 // Option records: orec[site * 15 + option] is 16 bytes (8 x u16). Word 0 is
 // a tag: n <= 7 -> n frame-plane indices follow; kRecFlip -> the site flips
 // record slot (words 1, 2) / output row (words 3, 4); kRecLong -> use
@@ -115,7 +118,7 @@ constexpr uint32_t kRecPerSite = 15;
 // row): its fault flips the slot and, if the shot is kept, the output bit.
 
 constexpr uint32_t kMagic = 0x4E435047u;  // "NCPG"
-constexpr uint32_t kVersion = 6;
+constexpr uint32_t kVersion = 7;
 constexpr uint32_t kMaxK = 30;
 constexpr uint32_t kMaxQubits = 4096;
 

@@ -124,7 +124,8 @@ def test_tiny_workload_full_size_sampled(nc):
 # ---------------------------------------------------------------------------
 # workload 2: surface-code memory d=5, 25 rounds (k_max = 0): bit-exact
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("precision,tune", [("fp32", "g=4,t=128"), ("fp32", None), ("fp64", None)])
+@pytest.mark.parametrize("precision,tune", [("fp32", "g=4,t=128"), ("fp32", None), ("fp64", None),
+                                            ("fp32", "b=0"), ("fp32", "g=32,t=32")])
 def test_surface_code_bit_exact(nc, precision, tune):
     text = gc.surface_code_memory(d=5, rounds=25, p=1e-3)
     prog = nc.compile(text)
@@ -135,6 +136,21 @@ def test_surface_code_bit_exact(nc, precision, tune):
                      exact=True)
     assert n_ok == shots
     assert int(g["det"].sum()) > 0
+
+
+@pytest.mark.parametrize("tune", [None, "g=64,t=64", "b=0"])
+def test_surface_code_many_warp_tiles(nc, tune):
+    """Several 1024-shot warp-tiles and a ragged last tile: the bucketed
+    noise path (faults sorted per warp-tile and noise block) and the per-shot
+    path (b=0) give the oracle's records on shots spread over every tile."""
+    text = gc.surface_code_memory(d=5, rounds=25, p=1e-3)
+    prog = nc.compile(text)
+    sim = FrameSim(text)
+    shots = 9_000
+    g = gpu_records(prog, shots, 2003, precision="fp32", tune=tune)
+    idx = sorted(set(range(0, shots, 61)) | {1023, 1024, 4095, 4096, shots - 1})
+    n_ok, _ = _check(_frame_run(sim, 2003), sim.ref_det, sim.ref_obs, sim.flat, g, 2003, idx, exact=True)
+    assert n_ok == len(idx)
 
 
 def test_surface_code_full_size_sampled(nc):
@@ -359,7 +375,7 @@ def test_tuning_variants_agree(nc):
     text = gc.tiny_random(seed=6)
     prog = nc.compile(text)
     base = gpu_records(prog, 1000, 12, precision="fp32")
-    for tune in ("g=1,t=32", "g=1,t=1024", "g=8,t=256", "g=4,t=64"):
+    for tune in ("g=1,t=32", "g=1,t=1024", "g=8,t=256", "g=4,t=64", "b=0", "g=64,t=64"):
         g = gpu_records(prog, 1000, 12, precision="fp32", tune=tune)
         assert (g["meas"] == base["meas"]).mean() > 0.999
 
