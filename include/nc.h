@@ -86,14 +86,21 @@ typedef struct {
  *   meas: n_meas rows, det: n_det rows, obs: n_obs rows, kept: 1 row.
  * A rejected (postselected-out) shot reports its failing detector as 1,
  * every later record and detector as 0, all observables 0 and kept = 0.
- * shots_run, shots_kept and kernel_ms are filled by nc_sample.
+ * shots_run, shots_kept, kernel_ms, exec_ms and launches are filled by
+ * nc_sample.
  */
 typedef struct {
   uint64_t *meas, *det, *obs, *kept;
   uint64_t words_per_record;
   uint64_t shots_run, shots_kept;
-  double kernel_ms;       /* filled: device time of the sampling launch(es),
-                             CUDA events on cuda_stream around the executors */
+  double kernel_ms;       /* filled: device time of the whole sampling call
+                             (fault bucketing, executors), CUDA events on
+                             cuda_stream */
+  double exec_ms;         /* filled: device time of this program's executor
+                             launch alone, CUDA events on cuda_stream */
+  uint32_t launches;      /* filled: kernels this call launched for this
+                             program (memsets and copies not counted) */
+  uint32_t reserved;
 } nc_records;
 
 /* Compile extended-Stim text (Sec. 3.1). On failure *out is NULL and a

@@ -2,8 +2,10 @@
 
 State (Def. 2): |psi> = gamma U_C P~ (|phi>_A (x) |0>_D). The global scalar
 gamma only carries phase and normalisation here: phases are dropped and phi
-is renormalised at every active measurement (readings 3 and 4 of the design
-notes).
+is renormalised at every active measurement (the paper allows lazy
+normalisation; eager renormalisation with probabilities taken relative to
+S0 + S1 is the reading used here, and the dormant convention after an active
+measurement is x_v ^= b, preceded by H_v for an X measurement).
 
 Plan (shot independent, Thm. 1): walk the physical circuit keeping the map
 M(P) = U_C^dagger P U_C as the images of every physical X_j and Z_j

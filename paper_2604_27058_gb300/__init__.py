@@ -135,6 +135,8 @@ def sample(prog: Program, shots: int, seed: int, precision="fp32", outputs=NC_OU
     res["shots_run"] = rec.shots_run
     res["shots_kept"] = rec.shots_kept
     res["kernel_ms"] = rec.kernel_ms
+    res["exec_ms"] = rec.exec_ms
+    res["launches"] = rec.launches
     return res
 
 
@@ -171,6 +173,8 @@ def sample_host(prog: Program, shots: int, seed: int, precision="fp32", outputs=
     res["shots_run"] = rec.shots_run
     res["shots_kept"] = rec.shots_kept
     res["kernel_ms"] = rec.kernel_ms
+    res["exec_ms"] = rec.exec_ms
+    res["launches"] = rec.launches
     return res
 
 
@@ -191,6 +195,8 @@ def sample_batch(progs, shots, seeds, precision="fp32", outputs=NC_OUT_ALL, post
         d["shots_run"] = r.shots_run
         d["shots_kept"] = r.shots_kept
         d["kernel_ms"] = r.kernel_ms
+        d["exec_ms"] = r.exec_ms
+        d["launches"] = r.launches
         res.append(d)
     return res
 

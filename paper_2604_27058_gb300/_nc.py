@@ -59,7 +59,8 @@ class Records(ctypes.Structure):
     _fields_ = [("meas", ctypes.c_void_p), ("det", ctypes.c_void_p), ("obs", ctypes.c_void_p),
                 ("kept", ctypes.c_void_p), ("words_per_record", ctypes.c_uint64),
                 ("shots_run", ctypes.c_uint64), ("shots_kept", ctypes.c_uint64),
-                ("kernel_ms", ctypes.c_double)]
+                ("kernel_ms", ctypes.c_double), ("exec_ms", ctypes.c_double),
+                ("launches", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 _lib = None

@@ -208,12 +208,19 @@ struct CallOut {
   uint32_t *meas, *det, *obs, *kept;
 };
 
+// Optional per-program timing: events around the executor launch and the
+// number of kernels launched.
+struct Timing {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  uint32_t launches = 0;
+};
+
 // Enqueue one sampling launch. kept_count must point to a zeroed device u64.
 nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uint64_t seed,
                   uint64_t shot_offset, int precision, uint32_t lflags, const char* tune, CallOut o,
                   unsigned long long* kept_count, uint32_t* err, Scratch& scratch, cudaStream_t stream,
                   uint32_t stop_event = 0xffffffffu, uint64_t dump_shot = 0, double* dump_amps = nullptr,
-                  uint32_t* dump_frame = nullptr, uint32_t* dump_k = nullptr) {
+                  uint32_t* dump_frame = nullptr, uint32_t* dump_k = nullptr, Timing* tm = nullptr) {
   nc_status st = NC_OK;
   const ProgHeader& h = header(prog);
   LaunchParams L;
@@ -242,7 +249,12 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
       size_t bytes = ((size_t)1 << h.k_max) * padded * sizeof(double) * 2;
       NC_TRY(scratch.get(&L.work, bytes));
     }
+    if (tm) NC_TRY(cudaEventRecord(tm->e0, stream));
     NC_TRY(launch_plain(L, stream));
+    if (tm) {
+      NC_TRY(cudaEventRecord(tm->e1, stream));
+      tm->launches += 1;
+    }
   } else {
     Tuning tu = choose_tuning(L.p, tune);
     if (!pow2(tu.G) || !pow2(tu.T) || !pow2(tu.W) || tu.T > (tu.W == 1 ? 1024u : 256u) || tu.T < 32)
@@ -275,6 +287,7 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
         unsigned long long* total = (unsigned long long*)ctr;
         uint32_t* ovf = (uint32_t*)((char*)ctr + 8);
         NC_TRY(launch_bucket(L, n_wt, (uint32_t*)ents, (uint32_t*)offs, cap_total, total, ovf, stream));
+        if (tm) tm->launches += 1;
         uint32_t h_ovf = 1;
         NC_TRY(cudaMemcpyAsync(&h_ovf, ovf, 4, cudaMemcpyDeviceToHost, stream));
         NC_TRY(cudaStreamSynchronize(stream));
@@ -317,9 +330,15 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
         L.fcap = cap;
         L.fstride = padded;
         NC_TRY(launch_presample(L, stream));
+        if (tm) tm->launches += 1;
       }
     }
+    if (tm) NC_TRY(cudaEventRecord(tm->e0, stream));
     NC_TRY(launch_batched(L, fp64, tu.W, bk, (uint32_t)grid, tu.T, smem, stream));
+    if (tm) {
+      NC_TRY(cudaEventRecord(tm->e1, stream));
+      tm->launches += 1;
+    }
   }
 done:
   return st;
@@ -436,10 +455,16 @@ nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, con
   std::vector<unsigned long long> kept(n, 0);
   float kernel_ms = 0.f;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<Timing> tms(n);
   if (cudaEventCreate(&ev0) != cudaSuccess || cudaEventCreate(&ev1) != cudaSuccess) {
     if (ev0) cudaEventDestroy(ev0);
     return NC_E_CUDA;
   }
+  for (auto& tm : tms)
+    if (cudaEventCreate(&tm.e0) != cudaSuccess || cudaEventCreate(&tm.e1) != cudaSuccess) {
+      st = NC_E_CUDA;
+      goto done;
+    }
   {
     Scratch scratch(stream);
     void* counters = nullptr;
@@ -463,7 +488,8 @@ nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, con
         if (o.outputs & NC_OUT_KEPT) { NC_TRY(scratch.get(&d, row_bytes)); co.kept = (uint32_t*)d; }
       }
       st = enqueue(progs[i], *dcs[i], shots[i], seeds[i], o.shot_offset, o.precision, launch_flags(o), o.tune, co,
-                   (unsigned long long*)counters + i, (uint32_t*)err, scratch, stream);
+                   (unsigned long long*)counters + i, (uint32_t*)err, scratch, stream, 0xffffffffu, 0, nullptr,
+                   nullptr, nullptr, &tms[i]);
       if (st != NC_OK) goto done;
       if (i + 1 == n) NC_TRY(cudaEventRecord(ev1, stream));
       if (host) {
@@ -485,10 +511,18 @@ nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, con
     outs[i].shots_run = shots[i];
     outs[i].shots_kept = kept[i];
     outs[i].kernel_ms = kernel_ms;
+    float ems = 0.f;
+    if (shots[i] == 0 || cudaEventElapsedTime(&ems, tms[i].e0, tms[i].e1) != cudaSuccess) ems = 0.f;
+    outs[i].exec_ms = ems;
+    outs[i].launches = tms[i].launches;
   }
 done:
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
+  for (auto& tm : tms) {
+    if (tm.e0) cudaEventDestroy(tm.e0);
+    if (tm.e1) cudaEventDestroy(tm.e1);
+  }
   return st;
 }
 
@@ -642,7 +676,7 @@ done:
   return st;
 }
 
-uint32_t nc_abi_version(void) { return (kVersion << 16) | 1u; }
+uint32_t nc_abi_version(void) { return (kVersion << 16) | 2u; }
 
 }  // extern "C"
 

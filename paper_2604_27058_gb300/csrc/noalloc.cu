@@ -256,5 +256,7 @@ extern "C" nc_status nc_sample_noalloc(const nc_program* prog, uint64_t shots, u
   out->shots_run = shots;
   out->shots_kept = shots ? kept : 0;
   out->kernel_ms = 0.0;
+  out->exec_ms = 0.0;
+  out->launches = (h.n_det + h.n_obs ? 2u : 0u) + (shots ? 1u : 0u);
   return herr ? NC_E_INTERNAL : NC_OK;
 }
