@@ -1,7 +1,7 @@
 """Build libnc.so (the C-ABI library) in-tree for sm_103a.
 
-Three translation units are compiled in parallel (the host compiler with
-g++, the kernels and the C ABI with nvcc) and linked into
+The translation units are compiled in parallel (the host compiler passes
+with g++, the kernels and the C ABI with nvcc) and linked into
 ``paper_2604_27058_gb300/libnc.so`` against the shared CUDA runtime.
 """
 
@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnc.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["compiler.cpp", "kernels.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["compiler.cpp", "affine.cpp", "kernels.cu", "affine_kernel.cu", "capi.cu", "noalloc.cu"]
 HEADERS = ["program.h", "compiler.h", "kernels.cuh"]
 
 

@@ -1,0 +1,323 @@
+// affine.cpp — record-level fault propagation for programs without active
+// axes (k_max = 0), computed once at compile time on the host.
+//
+// With no active vector every instruction of the program is a GF(2)-affine
+// map of the bit-packed state (virtual frame planes, record slots, output
+// rows): frame Cliffords and conditional Paulis XOR planes (Sec. 2.3,
+// App. B.3), a static measurement is a parity of planes (Sec. 2.4, App. B.2),
+// a random dormant measurement draws a fresh bit m and then updates the frame
+// affinely, and a fault XORs its fixed image M(E) into the frame (Sec. 3.2).
+// The records of a shot are therefore const ^ A m ^ F f, where m are the
+// shot's random measurement bits and f its fault indicators. This pass finds
+// const, A and F by running the compiled program on 64 probe lanes at a time
+// (lane = "no fault, all m = 0", "only m_j = 1", or "only fault option f")
+// and XORing each lane's rows with the baseline's. The sampler then needs,
+// per shot, only its faults and its random bits; the frame work is done once
+// here instead of once per shot.
+//
+// The probe interpreter follows the bytecode as the executors run it
+// (program.h); it never runs on a program with active-array instructions.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "compiler.h"
+
+namespace nc {
+
+namespace {
+
+constexpr uint64_t kMaxEntries = 1ull << 26;  // 256 MB of column entries
+
+struct Blob {
+  const ProgHeader* h;
+  const uint8_t* base;
+  template <typename T>
+  const T* at(uint64_t off) const {
+    return reinterpret_cast<const T*>(base + off);
+  }
+};
+
+uint32_t entry(const Op& o, uint32_t i) { return o.e[i]; }
+uint32_t rentry(const Op& o, uint32_t i) { return ((i < 2 ? o.i2 : o.i3) >> (16 * (i & 1))) & 0xFFFFu; }
+
+// State of one probe run over 64 lanes: frame planes, record slots and the
+// output rows (meas, det, obs).
+struct Probe {
+  std::vector<uint64_t> planes, slots, rows;
+};
+
+bool supported(uint8_t code) {
+  switch (code) {
+    case OP_END: case OP_BATCH: case OP_FRAME_H: case OP_FRAME_S: case OP_FRAME_CX: case OP_FRAME_CZ:
+    case OP_MEAS_STATIC: case OP_MEAS_RANDOM: case OP_NOISE_BLOCK: case OP_FEEDFORWARD: case OP_REC_OUT:
+    case OP_DETECTOR: case OP_OBS_INCLUDE: case OP_OBS_OUT: case OP_KEPT_OUT:
+      return true;
+    default:
+      return false;
+  }
+}
+
+void run_probe(const Blob& b, const std::vector<uint32_t>& rand_ord, const std::vector<uint64_t>& rand_mask,
+               const std::vector<std::vector<std::pair<uint32_t, uint64_t>>>& site_faults, Probe& pr) {
+  const ProgHeader& h = *b.h;
+  const uint32_t N = h.n_qubits, R = h.n_meas + h.n_det + h.n_obs;
+  pr.planes.assign(2 * N + 2, 0);
+  pr.slots.assign(h.n_slots + 1, 0);
+  pr.rows.assign(R, 0);
+  uint64_t* P = pr.planes.data();
+  uint64_t* SL = pr.slots.data();
+  uint64_t* RW = pr.rows.data();
+  SL[h.kept_slot] = ~0ull;
+  const Op* ops = b.at<Op>(h.off_ops);
+  const uint32_t* masks = b.at<uint32_t>(h.off_masks);
+  const uint32_t* slot_list = b.at<uint32_t>(h.off_slot_list);
+  const uint32_t* site_info = b.at<uint32_t>(h.off_site_info);
+  const uint32_t* opt_tab = b.at<uint32_t>(h.off_opt_tab);
+  const uint16_t* plist = b.at<uint16_t>(h.off_plist);
+  const uint16_t* orec = b.at<uint16_t>(h.off_orec);
+  const uint64_t kept = ~0ull;
+  for (uint32_t pc = 0; pc < h.n_ops; pc++) {
+    const Op& o = ops[pc];
+    switch (o.code) {
+      case OP_FRAME_H: {
+        uint64_t t = P[o.a];
+        P[o.a] = P[N + o.a];
+        P[N + o.a] = t;
+        break;
+      }
+      case OP_FRAME_S:
+        P[N + o.a] ^= P[o.a];
+        break;
+      case OP_FRAME_CX:
+        P[o.b] ^= P[o.a];
+        P[N + o.a] ^= P[N + o.b];
+        break;
+      case OP_FRAME_CZ: {
+        const uint64_t xa = P[o.a], xb = P[o.b];
+        P[N + o.a] ^= xb;
+        P[N + o.b] ^= xa;
+        break;
+      }
+      case OP_MEAS_STATIC: {
+        uint64_t m = (o.flags & FLAG_SIGN) ? ~0ull : 0ull;
+        if (o.pa != kNoInline) {
+          for (uint32_t i = 0; i < kInline; i++) m ^= P[entry(o, i)];
+        } else {
+          for (uint32_t w = 0; w < h.nw; w++) {
+            uint32_t bits = masks[o.i0 + w];
+            while (bits) {
+              const uint32_t q = w * 32u + (uint32_t)__builtin_ctz(bits);
+              bits &= bits - 1;
+              m ^= P[q];
+            }
+          }
+        }
+        if (o.flags & FLAG_RESET) {
+          for (uint32_t i = 0; i < o.pb && i < kInline; i++) P[rentry(o, i)] ^= m;
+        } else {
+          SL[o.i2] = m;
+          if (o.flags & FLAG_OUT) RW[o.i3] = m & kept;
+        }
+        break;
+      }
+      case OP_MEAS_RANDOM: {
+        const uint64_t m = rand_mask[rand_ord[pc]];
+        const uint64_t sg = (o.flags & FLAG_SIGN) ? ~0ull : 0ull;
+        const uint64_t ox = P[o.a], oz = P[N + o.a];
+        const uint64_t bb = m ^ sg ^ oz;
+        P[o.a] = oz ^ bb;
+        P[N + o.a] = ox;
+        SL[o.i2] = m;
+        if (o.flags & FLAG_OUT) RW[o.i3] = m & kept;
+        break;
+      }
+      case OP_NOISE_BLOCK:
+        for (uint32_t s = o.i0; s < o.i1; s++) {
+          for (const auto& fl : site_faults[s]) {
+            const uint32_t opt = fl.first;
+            const uint64_t lanes = fl.second;
+            const uint16_t* r = orec + ((size_t)s * kRecPerSite + opt) * 8;
+            if (r[0] == kRecFlip) {
+              const uint32_t slot = (uint32_t)r[1] | ((uint32_t)r[2] << 16);
+              const uint32_t row = (uint32_t)r[3] | ((uint32_t)r[4] << 16);
+              SL[slot] ^= lanes;
+              RW[row] ^= lanes & kept;
+            } else if (r[0] == kRecLong) {
+              const uint32_t oi = 2 * ((site_info[s] >> 8) + opt);
+              for (uint32_t q = 0; q < opt_tab[oi + 1]; q++) P[plist[opt_tab[oi] + q]] ^= lanes;
+            } else {
+              for (uint32_t q = 0; q < r[0]; q++) P[r[1 + q]] ^= lanes;
+            }
+          }
+        }
+        break;
+      case OP_FEEDFORWARD: {
+        const uint64_t c = SL[o.i2];
+        if (o.pa != kNoInline) {
+          for (uint32_t i = 0; i < o.pa && i < kInline; i++) P[entry(o, i)] ^= c;
+        } else {
+          for (uint32_t part = 0; part < 2; part++)
+            for (uint32_t w = 0; w < h.nw; w++) {
+              uint32_t bits = masks[o.i0 + part * h.nw + w];
+              while (bits) {
+                const uint32_t q = w * 32u + (uint32_t)__builtin_ctz(bits);
+                bits &= bits - 1;
+                P[part * N + q] ^= c;
+              }
+            }
+        }
+        break;
+      }
+      case OP_REC_OUT:
+        RW[o.i3] = SL[o.i2] & kept;
+        break;
+      case OP_DETECTOR:
+      case OP_OBS_INCLUDE: {
+        uint64_t d = 0;
+        if (o.pa != kNoInline) {
+          for (uint32_t i = 0; i < kInline; i++) d ^= SL[entry(o, i)];
+        } else {
+          for (uint32_t j = 0; j < o.i1; j++) d ^= SL[slot_list[o.i0 + j]];
+        }
+        if (o.code == OP_OBS_INCLUDE) SL[o.i2] ^= d;
+        else RW[h.n_meas + o.i3] = d & kept;
+        break;
+      }
+      case OP_OBS_OUT:
+        RW[h.n_meas + h.n_det + o.i3] = SL[o.i2] & kept;
+        break;
+      default:  // OP_END, OP_BATCH (payloads run one by one), OP_KEPT_OUT
+        break;
+    }
+    if (o.code == OP_END) break;
+  }
+}
+
+}  // namespace
+
+// Appends the propagation tables to a compiled blob when the program has no
+// active axes and the tables stay under kMaxEntries; otherwise leaves
+// aff_ok = 0. Returns the (possibly reallocated) blob through `blob`.
+void append_affine(std::vector<uint8_t>& blob) {
+  ProgHeader h;
+  std::memcpy(&h, blob.data(), sizeof(h));
+  if (h.k_max != 0) return;
+  Blob b{&h, blob.data()};
+  const Op* ops = b.at<Op>(h.off_ops);
+  for (uint32_t pc = 0; pc < h.n_ops; pc++)
+    if (!supported(ops[pc].code)) return;
+  const uint32_t R = h.n_meas + h.n_det + h.n_obs;
+  const uint32_t* site_info = b.at<uint32_t>(h.off_site_info);
+
+  // random dormant measurements, in program order
+  std::vector<uint32_t> rand_ord(h.n_ops, 0), rand_ev;
+  for (uint32_t pc = 0; pc < h.n_ops; pc++)
+    if (ops[pc].code == OP_MEAS_RANDOM) {
+      rand_ord[pc] = (uint32_t)rand_ev.size();
+      rand_ev.push_back(ops[pc].i0);
+    }
+  // probes: baseline, then one per random measurement, then one per fault option
+  struct Item {
+    bool is_rand;
+    uint32_t a, b;  // rand: ordinal; fault: site, option
+  };
+  std::vector<Item> items;
+  for (uint32_t j = 0; j < rand_ev.size(); j++) items.push_back({true, j, 0});
+  for (uint32_t s = 0; s < h.n_sites; s++) {
+    const uint32_t k = site_k(site_info[s]);
+    for (uint32_t o = 0; o < k; o++) items.push_back({false, s, o});
+  }
+
+  Probe base;
+  std::vector<uint64_t> zero_rand(rand_ev.size(), 0);
+  std::vector<std::vector<std::pair<uint32_t, uint64_t>>> site_faults(h.n_sites);
+  run_probe(b, rand_ord, zero_rand, site_faults, base);
+
+  std::vector<std::vector<uint32_t>> rand_rows(rand_ev.size());
+  std::vector<uint32_t> col_off((size_t)h.n_sites * kRecPerSite + 1, 0);
+  std::vector<std::vector<uint32_t>> col_rows((size_t)h.n_sites * kRecPerSite);
+  uint64_t n_entries = 0;
+  Probe pr;
+  for (size_t i0 = 0; i0 < items.size(); i0 += 64) {
+    const size_t n = std::min<size_t>(64, items.size() - i0);
+    std::vector<uint64_t> rm(rand_ev.size(), 0);
+    std::vector<uint32_t> touched;
+    for (size_t l = 0; l < n; l++) {
+      const Item& it = items[i0 + l];
+      if (it.is_rand) {
+        rm[it.a] |= 1ull << l;
+      } else {
+        auto& v = site_faults[it.a];
+        if (v.empty()) touched.push_back(it.a);
+        v.push_back({it.b, 1ull << l});
+      }
+    }
+    run_probe(b, rand_ord, rm, site_faults, pr);
+    for (uint32_t s : touched) site_faults[s].clear();
+    for (uint32_t r = 0; r < R; r++) {
+      uint64_t d = pr.rows[r] ^ base.rows[r];
+      while (d) {
+        const uint32_t l = (uint32_t)__builtin_ctzll(d);
+        d &= d - 1;
+        const Item& it = items[i0 + l];
+        if (it.is_rand) rand_rows[it.a].push_back(r);
+        else col_rows[(size_t)it.a * kRecPerSite + it.b].push_back(r);
+        if (++n_entries > kMaxEntries) return;
+      }
+    }
+  }
+
+  // row-major random-event lists
+  std::vector<uint32_t> rowev_off(R + 1, 0), rowev;
+  {
+    std::vector<std::vector<uint32_t>> per_row(R);
+    for (uint32_t j = 0; j < rand_rows.size(); j++)
+      for (uint32_t r : rand_rows[j]) per_row[r].push_back(j);
+    for (uint32_t r = 0; r < R; r++) {
+      rowev_off[r] = (uint32_t)rowev.size();
+      rowev.insert(rowev.end(), per_row[r].begin(), per_row[r].end());
+    }
+    rowev_off[R] = (uint32_t)rowev.size();
+  }
+  std::vector<uint32_t> col;
+  col.reserve(n_entries);
+  for (size_t c = 0; c < col_rows.size(); c++) {
+    col_off[c] = (uint32_t)col.size();
+    col.insert(col.end(), col_rows[c].begin(), col_rows[c].end());
+  }
+  col_off[col_rows.size()] = (uint32_t)col.size();
+  std::vector<uint32_t> cst(R);
+  for (uint32_t r = 0; r < R; r++) cst[r] = (uint32_t)(base.rows[r] & 1ull);
+
+  uint64_t off = h.total_bytes;
+  auto place = [&](uint64_t bytes) {
+    uint64_t o = off;
+    off = (off + bytes + 15) & ~15ull;
+    return o;
+  };
+  h.off_aff_const = place((uint64_t)R * 4);
+  h.off_aff_rowev_off = place((uint64_t)(R + 1) * 4);
+  h.off_aff_rowev = place((uint64_t)rowev.size() * 4);
+  h.off_aff_rand_ev = place((uint64_t)rand_ev.size() * 4);
+  h.off_aff_col_off = place((uint64_t)col_off.size() * 4);
+  h.off_aff_col = place((uint64_t)col.size() * 4);
+  h.total_bytes = off;
+  h.aff_ok = 1;
+  h.aff_rows = R;
+  h.aff_n_rand = (uint32_t)rand_ev.size();
+  h.aff_n_entries = (uint32_t)col.size();
+  blob.resize(off, 0);
+  auto cp = [&](uint64_t o, const void* src, size_t bytes) {
+    if (bytes) std::memcpy(blob.data() + o, src, bytes);
+  };
+  cp(h.off_aff_const, cst.data(), cst.size() * 4);
+  cp(h.off_aff_rowev_off, rowev_off.data(), rowev_off.size() * 4);
+  cp(h.off_aff_rowev, rowev.data(), rowev.size() * 4);
+  cp(h.off_aff_rand_ev, rand_ev.data(), rand_ev.size() * 4);
+  cp(h.off_aff_col_off, col_off.data(), col_off.size() * 4);
+  cp(h.off_aff_col, col.data(), col.size() * 4);
+  std::memcpy(blob.data(), &h, sizeof(h));
+}
+
+}  // namespace nc

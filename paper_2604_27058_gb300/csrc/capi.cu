@@ -31,6 +31,9 @@ cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st);
 cudaError_t launch_patch_ref(Op* ops, uint32_t n_ops, const uint32_t* det_ref, const uint32_t* obs_ref,
                              cudaStream_t st);
 cudaError_t launch_presample(const LaunchParams& L, cudaStream_t st);
+size_t affine_smem_bytes(const DevProg& p, uint32_t wpt, bool qsm);
+cudaError_t launch_affine(const LaunchParams& L, uint32_t wpt, bool qsm, uint32_t grid, size_t smem,
+                          cudaStream_t st, int* per_sm);
 cudaError_t launch_bucket(const LaunchParams& L, uint32_t n_wt, uint32_t* ents, uint32_t* offs, uint64_t cap_total,
                           unsigned long long* total, uint32_t* ovf, cudaStream_t st);
 bool plain_supported(const DevProg& p);
@@ -63,7 +66,7 @@ const ProgHeader& header(const nc_program* p) {
 }
 
 DevProg dev_view(const ProgHeader& h, const uint8_t* base) {
-  DevProg d;
+  DevProg d{};
   d.ops = reinterpret_cast<const Op*>(base + h.off_ops);
   d.masks = reinterpret_cast<const uint32_t*>(base + h.off_masks);
   d.q = reinterpret_cast<const uint64_t*>(base + h.off_q);
@@ -90,6 +93,16 @@ DevProg dev_view(const ProgHeader& h, const uint8_t* base) {
   d.n_det = h.n_det;
   d.n_obs = h.n_obs;
   d.n_blocks = h.n_blocks;
+  if (h.aff_ok) {
+    d.aff_const = reinterpret_cast<const uint32_t*>(base + h.off_aff_const);
+    d.aff_rowev_off = reinterpret_cast<const uint32_t*>(base + h.off_aff_rowev_off);
+    d.aff_rowev = reinterpret_cast<const uint32_t*>(base + h.off_aff_rowev);
+    d.aff_rand_ev = reinterpret_cast<const uint32_t*>(base + h.off_aff_rand_ev);
+    d.aff_col_off = reinterpret_cast<const uint32_t*>(base + h.off_aff_col_off);
+    d.aff_col = reinterpret_cast<const uint32_t*>(base + h.off_aff_col);
+    d.aff_rows = h.aff_rows;
+    d.aff_n_rand = h.aff_n_rand;
+  }
   return d;
 }
 
@@ -145,18 +158,19 @@ struct Scratch {
 
 // Launch shape of the batched executor: G 32-shot words per tile, W words
 // per owner thread (G / W owners), T threads per CTA; B = 0 turns the
-// bucketed noise path off.
+// bucketed noise path off. A = 0 turns the record-level propagation path
+// (programs with k_max = 0) off; AW forces its 32-shot words per tile.
 struct Tuning {
-  uint32_t G, T, W, B;
+  uint32_t G, T, W, B, A, AW;
 };
 
 Tuning choose_tuning(const DevProg& d, const char* tune) {
   Tuning t;
-  if (d.k_max == 0) t = {128, 128, 1, 1};
-  else if (d.k_max <= 6) t = {32, 256, 1, 1};
-  else if (d.k_max <= 10) t = {8, 256, 1, 1};
-  else if (d.k_max <= 13) t = {2, 512, 1, 1};
-  else t = {1, 1024, 1, 1};
+  if (d.k_max == 0) t = {128, 128, 1, 1, 1, 0};
+  else if (d.k_max <= 6) t = {32, 256, 1, 1, 1, 0};
+  else if (d.k_max <= 10) t = {8, 256, 1, 1, 1, 0};
+  else if (d.k_max <= 13) t = {2, 512, 1, 1, 1, 0};
+  else t = {1, 1024, 1, 1, 1, 0};
   if (tune) {
     unsigned v = 0;
     const char* s = tune;
@@ -165,6 +179,8 @@ Tuning choose_tuning(const DevProg& d, const char* tune) {
       else if (sscanf(s, "t=%u", &v) == 1) t.T = v;
       else if (sscanf(s, "w=%u", &v) == 1) t.W = v;
       else if (sscanf(s, "b=%u", &v) == 1) t.B = v;
+      else if (sscanf(s, "a=%u", &v) == 1) t.A = v;
+      else if (sscanf(s, "aw=%u", &v) == 1) t.AW = v;
       const char* c = strchr(s, ',');
       if (!c) break;
       s = c + 1;
@@ -257,6 +273,41 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
     }
   } else {
     Tuning tu = choose_tuning(L.p, tune);
+    if (h.aff_ok && tu.A && !(lflags & (LF_POSTSELECT | LF_REFERENCE)) && stop_event == 0xffffffffu) {
+      // record-level propagation sampler: tile of 32 * wpt shots per CTA,
+      // survival table staged in shared memory when it is small
+      const bool qsm = (size_t)h.n_sites * 8 <= 48 * 1024;
+      uint32_t wpt = 0;
+      if (tu.AW) {
+        if ((tu.AW == 4 || tu.AW == 8 || tu.AW == 16 || tu.AW == 32) &&
+            affine_smem_bytes(L.p, tu.AW, qsm) <= 220 * 1024)
+          wpt = tu.AW;
+      } else {
+        for (uint32_t c : {16u, 8u, 4u})
+          if (affine_smem_bytes(L.p, c, qsm) <= 113 * 1024) {
+            wpt = c;
+            break;
+          }
+        if (!wpt && affine_smem_bytes(L.p, 4, qsm) <= 220 * 1024) wpt = 4;
+      }
+      if (wpt) {
+        const size_t smem = affine_smem_bytes(L.p, wpt, qsm);
+        L.n_tiles = (uint32_t)((L.row_words32 + wpt - 1) / wpt);
+        int per_sm = 0, n_sm = 0, dev = 0;
+        NC_TRY(cudaGetDevice(&dev));
+        NC_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+        NC_TRY(launch_affine(L, wpt, qsm, 0, smem, stream, &per_sm));
+        if (per_sm < 1) return NC_E_UNSUPPORTED;
+        const uint64_t grid = std::min<uint64_t>(L.n_tiles, (uint64_t)per_sm * n_sm);
+        if (tm) NC_TRY(cudaEventRecord(tm->e0, stream));
+        NC_TRY(launch_affine(L, wpt, qsm, (uint32_t)grid, smem, stream, nullptr));
+        if (tm) {
+          NC_TRY(cudaEventRecord(tm->e1, stream));
+          tm->launches += 1;
+        }
+        return NC_OK;
+      }
+    }
     if (!pow2(tu.G) || !pow2(tu.T) || !pow2(tu.W) || tu.T > (tu.W == 1 ? 1024u : 256u) || tu.T < 32)
       return NC_E_ARG;
     L.G = tu.G;
@@ -575,7 +626,9 @@ nc_status nc_program_deserialize(const void* buf, size_t len, nc_program** out) 
   if (h.magic != kMagic || h.version != kVersion || h.total_bytes + sizeof(nc_info_counts) != len) return NC_E_ARG;
   uint64_t offs[] = {h.off_ops, h.off_masks, h.off_q, h.off_seg_start, h.off_seg_end, h.off_site_info,
                      h.off_site_eff, h.off_slot_list, h.off_det_ref, h.off_obs_ref,
-                     h.off_site_opt, h.off_opt_tab, h.off_plist, h.off_orec, h.off_site_blk};
+                     h.off_site_opt, h.off_opt_tab, h.off_plist, h.off_orec, h.off_site_blk,
+                     h.off_aff_const, h.off_aff_rowev_off, h.off_aff_rowev, h.off_aff_rand_ev,
+                     h.off_aff_col_off, h.off_aff_col};
   for (uint64_t o : offs)
     if (o > h.total_bytes || (o & 15)) return NC_E_ARG;
   if (h.off_ops + (uint64_t)h.n_ops * sizeof(Op) > h.total_bytes || h.k_max > kMaxK || h.n_qubits > kMaxQubits)

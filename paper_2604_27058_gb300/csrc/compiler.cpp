@@ -1342,6 +1342,7 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     cp(h.off_plist, plist.data(), plist.size() * 2);
     cp(h.off_orec, orec.data(), orec.size() * 2);
     cp(h.off_site_blk, site_blk.data(), site_blk.size() * 4);
+    append_affine(out.blob);
     out.counts = c.counts;
     return 0;
   } catch (CompileError& e) {

@@ -21,4 +21,8 @@ struct CompiledProgram {
 // Returns 0 on success or an nc_status code with a message in err.
 int compile_program(const std::string& text, CompiledProgram& out, std::string& err);
 
+// Appends the record-level propagation tables (program.h) to a blob of a
+// program with k_max = 0 (affine.cpp).
+void append_affine(std::vector<uint8_t>& blob);
+
 }  // namespace nc

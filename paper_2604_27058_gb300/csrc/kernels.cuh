@@ -24,8 +24,16 @@ struct DevProg {
   const uint16_t* plist;
   const uint4* orec;
   const uint32_t* site_blk;
+  // record-level propagation tables (program.h; null when absent)
+  const uint32_t* aff_const;
+  const uint32_t* aff_rowev_off;
+  const uint32_t* aff_rowev;
+  const uint32_t* aff_rand_ev;
+  const uint32_t* aff_col_off;
+  const uint32_t* aff_col;
   uint32_t n_qubits, nw, n_ops, n_sites, n_slots, k_max, kept_slot;
   uint32_t n_meas, n_det, n_obs, n_blocks;
+  uint32_t aff_rows, aff_n_rand;
 };
 
 enum : uint32_t {
@@ -121,23 +129,25 @@ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) { return __u
 
 // Next fault of global shot `shot` at or after site `st` (Sec. 3.2 jump,
 // integer survival form). Returns (site << 4) | option, or kNoFault.
-__device__ __forceinline__ uint32_t next_fault(const DevProg& p, uint64_t seed, uint64_t shot,
-                                               uint32_t st) {
+// The survival table is read through `q`: the program's global copy, or a
+// copy staged in shared memory by the caller.
+__device__ __forceinline__ uint32_t next_fault_tab(const DevProg& p, const uint64_t* q, uint64_t seed,
+                                                   uint64_t shot, uint32_t st) {
   const uint2 key = key_of(seed);
   while (st < p.n_sites) {
     uint32_t a = __ldg(p.seg_start + st), b = __ldg(p.seg_end + st);
     uint4 w = philox(make_uint4((uint32_t)shot, (uint32_t)(shot >> 32), TAG_GAP, st), key);
     uint64_t u = (uint64_t)w.x | ((uint64_t)w.y << 32);
-    uint64_t ql = st == a ? ~0ull : __ldg(p.q + st - 1);
+    uint64_t ql = st == a ? ~0ull : q[st - 1];
     uint64_t t = mulhi64(u, ql);
-    if (__ldg(p.q + b - 1) > t) {
+    if (q[b - 1] > t) {
       st = b;
       continue;
     }
     uint32_t lo = st, hi = b - 1;  // q[hi] <= t
     while (lo < hi) {
       uint32_t mid = (lo + hi) >> 1;
-      if (__ldg(p.q + mid) <= t) hi = mid;
+      if (q[mid] <= t) hi = mid;
       else lo = mid + 1;
     }
     uint32_t k = (__ldg(p.site_info + lo) >> 4) & 15u;
@@ -145,6 +155,11 @@ __device__ __forceinline__ uint32_t next_fault(const DevProg& p, uint64_t seed, 
     return (lo << 4) | opt;
   }
   return kNoFault;
+}
+
+__device__ __forceinline__ uint32_t next_fault(const DevProg& p, uint64_t seed, uint64_t shot,
+                                               uint32_t st) {
+  return next_fault_tab(p, p.q, seed, shot, st);
 }
 
 // next_fault with a shared-memory coarse index qc[c] = Q[c * stride] of the

@@ -65,7 +65,7 @@ nc_status scratch_base(uint8_t** out) {
 uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
 DevProg view(const ProgHeader& h, const uint8_t* base) {
-  DevProg d;
+  DevProg d{};
   d.ops = reinterpret_cast<const Op*>(base + h.off_ops);
   d.masks = reinterpret_cast<const uint32_t*>(base + h.off_masks);
   d.q = reinterpret_cast<const uint64_t*>(base + h.off_q);
@@ -92,6 +92,16 @@ DevProg view(const ProgHeader& h, const uint8_t* base) {
   d.n_det = h.n_det;
   d.n_obs = h.n_obs;
   d.n_blocks = h.n_blocks;
+  if (h.aff_ok) {
+    d.aff_const = reinterpret_cast<const uint32_t*>(base + h.off_aff_const);
+    d.aff_rowev_off = reinterpret_cast<const uint32_t*>(base + h.off_aff_rowev_off);
+    d.aff_rowev = reinterpret_cast<const uint32_t*>(base + h.off_aff_rowev);
+    d.aff_rand_ev = reinterpret_cast<const uint32_t*>(base + h.off_aff_rand_ev);
+    d.aff_col_off = reinterpret_cast<const uint32_t*>(base + h.off_aff_col_off);
+    d.aff_col = reinterpret_cast<const uint32_t*>(base + h.off_aff_col);
+    d.aff_rows = h.aff_rows;
+    d.aff_n_rand = h.aff_n_rand;
+  }
   return d;
 }
 

@@ -100,11 +100,25 @@ struct ProgHeader {
   uint32_t n_plist;
   float mean_faults;               // sum of site probabilities (expected faults per shot)
   uint32_t n_blocks;               // NOISE_BLOCK instructions (their ordinal is in i2)
-  uint32_t pad0;
+  uint32_t aff_ok;                 // 1: the record-level propagation tables below are present
+  uint32_t aff_rows, aff_n_rand;   // rows = n_meas + n_det + n_obs; random dormant measurements
+  uint32_t aff_n_entries, pad1;    // total (fault option, row) entries
   uint64_t off_ops, off_masks, off_q, off_seg_start, off_seg_end, off_site_info, off_site_eff,
       off_slot_list, off_det_ref, off_obs_ref, off_site_opt, off_opt_tab, off_plist, off_orec, off_site_blk,
+      off_aff_const, off_aff_rowev_off, off_aff_rowev, off_aff_rand_ev, off_aff_col_off, off_aff_col,
       total_bytes;
 };
+// Record-level propagation (programs with k_max = 0). With every frame
+// update GF(2)-linear, a shot's records are an affine function of its fault
+// indicators and of its random dormant measurement outcomes:
+//   row r = const[r] ^ XOR_{j in rowev(r)} m_j ^ XOR_{faults f} [r in col(f)]
+// where rows are meas rows, then det rows, then obs rows (detector and
+// observable rows before their reference parity), m_j is the outcome of
+// the j-th random dormant measurement (event rand_ev[j]) and col(f) lists
+// the rows flipped by fault option f = site * kRecPerSite + option.
+//   const: u32 per row (0 / 1); rowev_off: rows + 1 u32; rowev: u32 ordinals
+//   rand_ev: u32 event per ordinal; col_off: n_sites * kRecPerSite + 1 u32;
+//   col: u32 rows.
 // site_blk[site] = ordinal of the NOISE_BLOCK instruction that covers the site.
 // Option records: orec[site * 15 + option] is 16 bytes (8 x u16). Word 0 is
 // a tag: n <= 7 -> n frame-plane indices follow; kRecFlip -> the site flips
@@ -118,7 +132,7 @@ constexpr uint32_t kRecPerSite = 15;
 // row): its fault flips the slot and, if the shot is kept, the output bit.
 
 constexpr uint32_t kMagic = 0x4E435047u;  // "NCPG"
-constexpr uint32_t kVersion = 7;
+constexpr uint32_t kVersion = 8;
 constexpr uint32_t kMaxK = 30;
 constexpr uint32_t kMaxQubits = 4096;
 

@@ -1,0 +1,105 @@
+"""CPU check of the compiler's record-level propagation tables (programs with
+k_max = 0): for sampled shots, const ^ A m ^ F f built from the serialized
+tables must equal the oracle's records. The faults f and the random
+measurement bits m come from the oracle's own sampler and Philox, and the
+expected records come from the oracle's Pauli-frame simulator.
+No GPU is used."""
+
+import struct
+
+import numpy as np
+import pytest
+
+from gen import circuits as gc
+from oracle.noise import sample_faults
+from oracle.philox import meas_u
+from oracle.records import raw_parities
+from oracle.stabilizer import FrameSim
+
+HEAD_U32 = 24   # 17 counts, mean_faults (f32), n_blocks, aff_ok, aff_rows, aff_n_rand, aff_n_entries, pad
+N_OFFS = 22     # 21 table offsets + total_bytes
+OFF_NAMES = ["ops", "masks", "q", "seg_start", "seg_end", "site_info", "site_eff", "slot_list", "det_ref",
+             "obs_ref", "site_opt", "opt_tab", "plist", "orec", "site_blk", "aff_const", "aff_rowev_off",
+             "aff_rowev", "aff_rand_ev", "aff_col_off", "aff_col", "total_bytes"]
+REC_PER_SITE = 15
+
+
+@pytest.fixture(scope="module")
+def nc():
+    from paper_2604_27058_gb300 import build
+    build.build()
+    import paper_2604_27058_gb300 as m
+    return m
+
+
+def _tables(blob: bytes):
+    u = struct.unpack_from("<17If6I", blob, 0)
+    n_sites, n_meas, n_det, n_obs = u[5], u[6], u[7], u[8]
+    aff_ok, rows, n_rand, n_ent = u[19], u[20], u[21], u[22]
+    offs = dict(zip(OFF_NAMES, struct.unpack_from(f"<{N_OFFS}Q", blob, HEAD_U32 * 4)))
+    assert aff_ok == 1
+    assert rows == n_meas + n_det + n_obs
+
+    def arr(name, n):
+        return np.frombuffer(blob, dtype=np.uint32, count=n, offset=offs[name])
+
+    col_off = arr("aff_col_off", n_sites * REC_PER_SITE + 1)
+    return {
+        "rows": rows, "n_meas": n_meas, "n_det": n_det,
+        "const": arr("aff_const", rows),
+        "rowev_off": arr("aff_rowev_off", rows + 1),
+        "rowev": arr("aff_rowev", int(arr("aff_rowev_off", rows + 1)[-1])),
+        "rand_ev": arr("aff_rand_ev", n_rand),
+        "col_off": col_off,
+        "col": arr("aff_col", int(col_off[-1])),
+        "n_entries": n_ent,
+    }
+
+
+def _rows(t, faults, m):
+    v = t["const"].astype(np.uint8).copy()
+    for r in range(t["rows"]):
+        for e in t["rowev"][t["rowev_off"][r]:t["rowev_off"][r + 1]]:
+            v[r] ^= m[e]
+    for site, opt in faults.items():
+        c = site * REC_PER_SITE + opt
+        for r in t["col"][t["col_off"][c]:t["col_off"][c + 1]]:
+            v[r] ^= 1
+    return v
+
+
+CIRCUITS = {
+    "surface_d3_r3": lambda: gc.surface_code_memory(d=3, rounds=3, p=0.02),
+    "surface_d5_r25": lambda: gc.surface_code_memory(d=5, rounds=25, p=1e-3),
+    "random_clifford_ff_reset": lambda: gc.random_small(41, n=6, n_ops=120, p_noise=0.05, t_frac=0.0),
+    "random_clifford_ff_reset_b": lambda: gc.random_small(42, n=8, n_ops=200, p_noise=0.03, t_frac=0.0),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CIRCUITS))
+def test_affine_tables_reproduce_oracle_records(nc, name):
+    text = CIRCUITS[name]()
+    prog = nc.compile(text)
+    assert prog.info.k_max == 0
+    t = _tables(prog.serialize())
+    sim = FrameSim(text)
+    flat = sim.flat
+    seed = 777
+    n_faulty = 0
+    for shot in range(40):
+        faults = sample_faults(sim.table, seed, shot)
+        n_faulty += bool(faults)
+        m = np.array([1 if meas_u(seed, shot, int(ev)) < 0.5 else 0 for ev in t["rand_ev"]], dtype=np.uint8)
+        got = _rows(t, faults, m)
+        meas, _ = sim.run_raw(seed, shot, faults=faults)
+        det, obs = raw_parities(flat, meas)
+        want = np.array(list(meas) + list(det) + list(obs), dtype=np.uint8)
+        assert np.array_equal(got, want), f"shot {shot}"
+    assert n_faulty > 0
+
+
+def test_affine_tables_absent_with_active_axes(nc):
+    prog = nc.compile(gc.tiny_random(seed=1))
+    assert prog.info.k_max > 0
+    blob = prog.serialize()
+    assert struct.unpack_from("<17If6I", blob, 0)[19] == 0

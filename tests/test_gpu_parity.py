@@ -37,6 +37,11 @@ def nc():
     return m
 
 
+def torch_equal(a, b) -> bool:
+    import torch
+    return bool(torch.equal(a, b))
+
+
 def _check(oracle_run, ref_det, ref_obs, flat, gpu, seed, shots_idx, cols=None, postselect=False,
            exact=False):
     n = flagged = 0
@@ -124,8 +129,9 @@ def test_tiny_workload_full_size_sampled(nc):
 # ---------------------------------------------------------------------------
 # workload 2: surface-code memory d=5, 25 rounds (k_max = 0): bit-exact
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("precision,tune", [("fp32", "g=4,t=128"), ("fp32", None), ("fp64", None),
-                                            ("fp32", "b=0"), ("fp32", "g=32,t=32")])
+@pytest.mark.parametrize("precision,tune", [("fp32", "a=0,g=4,t=128"), ("fp32", None), ("fp64", None),
+                                            ("fp32", "a=0"), ("fp32", "a=0,b=0"), ("fp32", "a=0,g=32,t=32"),
+                                            ("fp32", "aw=4"), ("fp32", "aw=32"), ("fp64", "a=0")])
 def test_surface_code_bit_exact(nc, precision, tune):
     text = gc.surface_code_memory(d=5, rounds=25, p=1e-3)
     prog = nc.compile(text)
@@ -138,11 +144,12 @@ def test_surface_code_bit_exact(nc, precision, tune):
     assert int(g["det"].sum()) > 0
 
 
-@pytest.mark.parametrize("tune", [None, "g=64,t=64", "b=0"])
+@pytest.mark.parametrize("tune", [None, "aw=8", "a=0", "a=0,g=64,t=64", "a=0,b=0"])
 def test_surface_code_many_warp_tiles(nc, tune):
-    """Several 1024-shot warp-tiles and a ragged last tile: the bucketed
-    noise path (faults sorted per warp-tile and noise block) and the per-shot
-    path (b=0) give the oracle's records on shots spread over every tile."""
+    """Several tiles and a ragged last tile: the record-level propagation
+    sampler (default for k_max = 0), the executor with bucketed noise (a=0)
+    and with per-shot noise (a=0,b=0) give the oracle's records on shots
+    spread over every tile."""
     text = gc.surface_code_memory(d=5, rounds=25, p=1e-3)
     prog = nc.compile(text)
     sim = FrameSim(text)
@@ -151,6 +158,26 @@ def test_surface_code_many_warp_tiles(nc, tune):
     idx = sorted(set(range(0, shots, 61)) | {1023, 1024, 4095, 4096, shots - 1})
     n_ok, _ = _check(_frame_run(sim, 2003), sim.ref_det, sim.ref_obs, sim.flat, g, 2003, idx, exact=True)
     assert n_ok == len(idx)
+
+
+@pytest.mark.parametrize("name", ["surface", "random_ff_reset", "random_ff_reset_b"])
+def test_affine_sampler_equals_executor(nc, name):
+    """k_max = 0: the record-level propagation sampler and the bytecode
+    executor give identical records, bit for bit, on every shot (random
+    dormant measurements, resets, feed-forward, record flips, detectors)."""
+    text = {"surface": lambda: gc.surface_code_memory(d=5, rounds=25, p=1e-3),
+            "random_ff_reset": lambda: gc.random_small(41, n=6, n_ops=120, p_noise=0.05, t_frac=0.0),
+            "random_ff_reset_b": lambda: gc.random_small(42, n=8, n_ops=200, p_noise=0.03, t_frac=0.0)}[name]()
+    prog = nc.compile(text)
+    assert prog.info.k_max == 0
+    info = prog.info
+    rows = {"meas": info.n_meas, "det": info.n_det, "obs": info.n_obs, "kept": 1}
+    for shots, off in ((100_003, 0), (777, 128 * 5)):
+        a = nc.sample(prog, shots, 99, shot_offset=off)
+        b = nc.sample(prog, shots, 99, shot_offset=off, tune="a=0")
+        for key, n in rows.items():
+            assert torch_equal(a[key][:n], b[key][:n]), key
+        assert a["shots_kept"] == b["shots_kept"] == shots
 
 
 def test_surface_code_full_size_sampled(nc):
