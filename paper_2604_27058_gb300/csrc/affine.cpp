@@ -280,13 +280,34 @@ void append_affine(std::vector<uint8_t>& blob) {
     }
     rowev_off[R] = (uint32_t)rowev.size();
   }
-  std::vector<uint32_t> col;
-  col.reserve(n_entries);
+  // fault columns in chunks of 8 u16 rows (padding: row R, a scratch row)
+  if (R >= 0xFFFFu) return;
+  std::vector<uint16_t> chunks;
   for (size_t c = 0; c < col_rows.size(); c++) {
-    col_off[c] = (uint32_t)col.size();
-    col.insert(col.end(), col_rows[c].begin(), col_rows[c].end());
+    col_off[c] = (uint32_t)(chunks.size() / 8);
+    const auto& rows = col_rows[c];
+    for (size_t j = 0; j < rows.size(); j += 8)
+      for (size_t e = 0; e < 8; e++) chunks.push_back((uint16_t)(j + e < rows.size() ? rows[j + e] : R));
   }
-  col_off[col_rows.size()] = (uint32_t)col.size();
+  col_off[col_rows.size()] = (uint32_t)(chunks.size() / 8);
+  if (chunks.size() / 8 >= (1u << 22)) return;
+  // expected chunks per shot: sum over sites of p * mean chunk count of its options
+  double cps = 0.0;
+  {
+    const uint64_t* q = b.at<uint64_t>(h.off_q);
+    const uint32_t* seg_start = b.at<uint32_t>(h.off_seg_start);
+    for (uint32_t s = 0; s < h.n_sites; s++) {
+      // the site's probability from consecutive survival thresholds
+      const double qs = (double)q[s] * 0x1p-64;
+      const double qp = seg_start[s] == s ? 1.0 : (double)q[s - 1] * 0x1p-64;
+      const double p = qp > 0.0 ? 1.0 - qs / qp : 0.0;
+      const uint32_t kk = site_k(site_info[s]);
+      double mean = 0.0;
+      for (uint32_t o = 0; o < kk; o++)
+        mean += col_off[(size_t)s * kRecPerSite + o + 1] - col_off[(size_t)s * kRecPerSite + o];
+      cps += p * (kk ? mean / kk : 0.0);
+    }
+  }
   std::vector<uint32_t> cst(R);
   for (uint32_t r = 0; r < R; r++) cst[r] = (uint32_t)(base.rows[r] & 1ull);
 
@@ -301,12 +322,13 @@ void append_affine(std::vector<uint8_t>& blob) {
   h.off_aff_rowev = place((uint64_t)rowev.size() * 4);
   h.off_aff_rand_ev = place((uint64_t)rand_ev.size() * 4);
   h.off_aff_col_off = place((uint64_t)col_off.size() * 4);
-  h.off_aff_col = place((uint64_t)col.size() * 4);
+  h.off_aff_col = place((uint64_t)chunks.size() * 2);
   h.total_bytes = off;
   h.aff_ok = 1;
   h.aff_rows = R;
   h.aff_n_rand = (uint32_t)rand_ev.size();
-  h.aff_n_entries = (uint32_t)col.size();
+  h.aff_n_chunks = (uint32_t)(chunks.size() / 8);
+  h.aff_chunks_per_shot = (float)cps;
   blob.resize(off, 0);
   auto cp = [&](uint64_t o, const void* src, size_t bytes) {
     if (bytes) std::memcpy(blob.data() + o, src, bytes);
@@ -316,7 +338,7 @@ void append_affine(std::vector<uint8_t>& blob) {
   cp(h.off_aff_rowev, rowev.data(), rowev.size() * 4);
   cp(h.off_aff_rand_ev, rand_ev.data(), rand_ev.size() * 4);
   cp(h.off_aff_col_off, col_off.data(), col_off.size() * 4);
-  cp(h.off_aff_col, col.data(), col.size() * 4);
+  cp(h.off_aff_col, chunks.data(), chunks.size() * 2);
   std::memcpy(blob.data(), &h, sizeof(h));
 }
 

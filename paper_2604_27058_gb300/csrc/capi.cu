@@ -31,9 +31,9 @@ cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st);
 cudaError_t launch_patch_ref(Op* ops, uint32_t n_ops, const uint32_t* det_ref, const uint32_t* obs_ref,
                              cudaStream_t st);
 cudaError_t launch_presample(const LaunchParams& L, cudaStream_t st);
-size_t affine_smem_bytes(const DevProg& p, uint32_t wpt, bool qsm);
-cudaError_t launch_affine(const LaunchParams& L, uint32_t wpt, bool qsm, uint32_t grid, size_t smem,
-                          cudaStream_t st, int* per_sm);
+size_t affine_smem_bytes(const DevProg& p, uint32_t wpt, uint32_t qc_n);
+cudaError_t launch_affine(const LaunchParams& L, uint32_t wpt, uint32_t grid, size_t smem, cudaStream_t st,
+                          int* per_sm);
 cudaError_t launch_bucket(const LaunchParams& L, uint32_t n_wt, uint32_t* ents, uint32_t* offs, uint64_t cap_total,
                           unsigned long long* total, uint32_t* ovf, cudaStream_t st);
 bool plain_supported(const DevProg& p);
@@ -99,7 +99,8 @@ DevProg dev_view(const ProgHeader& h, const uint8_t* base) {
     d.aff_rowev = reinterpret_cast<const uint32_t*>(base + h.off_aff_rowev);
     d.aff_rand_ev = reinterpret_cast<const uint32_t*>(base + h.off_aff_rand_ev);
     d.aff_col_off = reinterpret_cast<const uint32_t*>(base + h.off_aff_col_off);
-    d.aff_col = reinterpret_cast<const uint32_t*>(base + h.off_aff_col);
+    d.aff_chunks = reinterpret_cast<const uint4*>(base + h.off_aff_col);
+    d.aff_chunks_per_shot = h.aff_chunks_per_shot;
     d.aff_rows = h.aff_rows;
     d.aff_n_rand = h.aff_n_rand;
   }
@@ -274,33 +275,34 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
   } else {
     Tuning tu = choose_tuning(L.p, tune);
     if (h.aff_ok && tu.A && !(lflags & (LF_POSTSELECT | LF_REFERENCE)) && stop_event == 0xffffffffu) {
-      // record-level propagation sampler: tile of 32 * wpt shots per CTA,
-      // survival table staged in shared memory when it is small
-      const bool qsm = (size_t)h.n_sites * 8 <= 48 * 1024;
+      // record-level propagation sampler: tile of 32 * wpt shots per CTA of
+      // 16 * wpt threads; the shape with the most resident warps wins
+      L.qc_stride = coarse_stride(h.n_sites);
+      L.qc_n = coarse_count(h.n_sites);
+      int n_sm = 0, dev = 0;
+      NC_TRY(cudaGetDevice(&dev));
+      NC_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
       uint32_t wpt = 0;
-      if (tu.AW) {
-        if ((tu.AW == 4 || tu.AW == 8 || tu.AW == 16 || tu.AW == 32) &&
-            affine_smem_bytes(L.p, tu.AW, qsm) <= 220 * 1024)
-          wpt = tu.AW;
-      } else {
-        for (uint32_t c : {16u, 8u, 4u})
-          if (affine_smem_bytes(L.p, c, qsm) <= 113 * 1024) {
-            wpt = c;
-            break;
-          }
-        if (!wpt && affine_smem_bytes(L.p, 4, qsm) <= 220 * 1024) wpt = 4;
+      int best_warps = 0, best_ctas = 0;
+      for (uint32_t c : {16u, 32u, 8u}) {
+        if (tu.AW && tu.AW != c) continue;
+        const size_t smem = affine_smem_bytes(L.p, c, L.qc_n);
+        if (smem > 227 * 1024) continue;
+        int per_sm = 0;
+        NC_TRY(launch_affine(L, c, 0, smem, stream, &per_sm));
+        const int warps = per_sm * (int)(c / 2);
+        if (per_sm > 0 && warps > best_warps) {
+          best_warps = warps;
+          best_ctas = per_sm;
+          wpt = c;
+        }
       }
       if (wpt) {
-        const size_t smem = affine_smem_bytes(L.p, wpt, qsm);
+        const size_t smem = affine_smem_bytes(L.p, wpt, L.qc_n);
         L.n_tiles = (uint32_t)((L.row_words32 + wpt - 1) / wpt);
-        int per_sm = 0, n_sm = 0, dev = 0;
-        NC_TRY(cudaGetDevice(&dev));
-        NC_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-        NC_TRY(launch_affine(L, wpt, qsm, 0, smem, stream, &per_sm));
-        if (per_sm < 1) return NC_E_UNSUPPORTED;
-        const uint64_t grid = std::min<uint64_t>(L.n_tiles, (uint64_t)per_sm * n_sm);
+        const uint64_t grid = std::min<uint64_t>(L.n_tiles, (uint64_t)best_ctas * n_sm);
         if (tm) NC_TRY(cudaEventRecord(tm->e0, stream));
-        NC_TRY(launch_affine(L, wpt, qsm, (uint32_t)grid, smem, stream, nullptr));
+        NC_TRY(launch_affine(L, wpt, (uint32_t)grid, smem, stream, nullptr));
         if (tm) {
           NC_TRY(cudaEventRecord(tm->e1, stream));
           tm->launches += 1;

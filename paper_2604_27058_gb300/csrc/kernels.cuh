@@ -30,10 +30,11 @@ struct DevProg {
   const uint32_t* aff_rowev;
   const uint32_t* aff_rand_ev;
   const uint32_t* aff_col_off;
-  const uint32_t* aff_col;
+  const uint4* aff_chunks;
   uint32_t n_qubits, nw, n_ops, n_sites, n_slots, k_max, kept_slot;
   uint32_t n_meas, n_det, n_obs, n_blocks;
   uint32_t aff_rows, aff_n_rand;
+  float aff_chunks_per_shot;
 };
 
 enum : uint32_t {

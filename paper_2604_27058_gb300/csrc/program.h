@@ -102,7 +102,8 @@ struct ProgHeader {
   uint32_t n_blocks;               // NOISE_BLOCK instructions (their ordinal is in i2)
   uint32_t aff_ok;                 // 1: the record-level propagation tables below are present
   uint32_t aff_rows, aff_n_rand;   // rows = n_meas + n_det + n_obs; random dormant measurements
-  uint32_t aff_n_entries, pad1;    // total (fault option, row) entries
+  uint32_t aff_n_chunks;           // 8-row chunks of the fault columns
+  float aff_chunks_per_shot;       // expected chunks of a shot's faults
   uint64_t off_ops, off_masks, off_q, off_seg_start, off_seg_end, off_site_info, off_site_eff,
       off_slot_list, off_det_ref, off_obs_ref, off_site_opt, off_opt_tab, off_plist, off_orec, off_site_blk,
       off_aff_const, off_aff_rowev_off, off_aff_rowev, off_aff_rand_ev, off_aff_col_off, off_aff_col,
@@ -117,8 +118,9 @@ struct ProgHeader {
 // the j-th random dormant measurement (event rand_ev[j]) and col(f) lists
 // the rows flipped by fault option f = site * kRecPerSite + option.
 //   const: u32 per row (0 / 1); rowev_off: rows + 1 u32; rowev: u32 ordinals
-//   rand_ev: u32 event per ordinal; col_off: n_sites * kRecPerSite + 1 u32;
-//   col: u32 rows.
+//   rand_ev: u32 event per ordinal; col_off: n_sites * kRecPerSite + 1 u32
+//   chunk offsets; col: chunks of 8 u16 rows (16 bytes), each column's rows
+//   ascending and padded with row index `rows` (a scratch row).
 // site_blk[site] = ordinal of the NOISE_BLOCK instruction that covers the site.
 // Option records: orec[site * 15 + option] is 16 bytes (8 x u16). Word 0 is
 // a tag: n <= 7 -> n frame-plane indices follow; kRecFlip -> the site flips

@@ -16,7 +16,7 @@ from oracle.philox import meas_u
 from oracle.records import raw_parities
 from oracle.stabilizer import FrameSim
 
-HEAD_U32 = 24   # 17 counts, mean_faults (f32), n_blocks, aff_ok, aff_rows, aff_n_rand, aff_n_entries, pad
+HEAD_U32 = 24   # 17 counts, mean_faults (f32), n_blocks, aff_ok, aff_rows, aff_n_rand, aff_n_chunks, f32
 N_OFFS = 22     # 21 table offsets + total_bytes
 OFF_NAMES = ["ops", "masks", "q", "seg_start", "seg_end", "site_info", "site_eff", "slot_list", "det_ref",
              "obs_ref", "site_opt", "opt_tab", "plist", "orec", "site_blk", "aff_const", "aff_rowev_off",
@@ -35,7 +35,7 @@ def nc():
 def _tables(blob: bytes):
     u = struct.unpack_from("<17If6I", blob, 0)
     n_sites, n_meas, n_det, n_obs = u[5], u[6], u[7], u[8]
-    aff_ok, rows, n_rand, n_ent = u[19], u[20], u[21], u[22]
+    aff_ok, rows, n_rand = u[19], u[20], u[21]
     offs = dict(zip(OFF_NAMES, struct.unpack_from(f"<{N_OFFS}Q", blob, HEAD_U32 * 4)))
     assert aff_ok == 1
     assert rows == n_meas + n_det + n_obs
@@ -44,6 +44,9 @@ def _tables(blob: bytes):
         return np.frombuffer(blob, dtype=np.uint32, count=n, offset=offs[name])
 
     col_off = arr("aff_col_off", n_sites * REC_PER_SITE + 1)
+    n_chunks = int(col_off[-1])
+    assert n_chunks == u[22]
+    chunks = np.frombuffer(blob, dtype=np.uint16, count=8 * n_chunks, offset=offs["aff_col"]).reshape(-1, 8)
     return {
         "rows": rows, "n_meas": n_meas, "n_det": n_det,
         "const": arr("aff_const", rows),
@@ -51,8 +54,7 @@ def _tables(blob: bytes):
         "rowev": arr("aff_rowev", int(arr("aff_rowev_off", rows + 1)[-1])),
         "rand_ev": arr("aff_rand_ev", n_rand),
         "col_off": col_off,
-        "col": arr("aff_col", int(col_off[-1])),
-        "n_entries": n_ent,
+        "chunks": chunks,
     }
 
 
@@ -63,8 +65,10 @@ def _rows(t, faults, m):
             v[r] ^= m[e]
     for site, opt in faults.items():
         c = site * REC_PER_SITE + opt
-        for r in t["col"][t["col_off"][c]:t["col_off"][c + 1]]:
-            v[r] ^= 1
+        for ch in t["chunks"][t["col_off"][c]:t["col_off"][c + 1]]:
+            for r in ch:
+                if r != t["rows"]:  # padding entries name the scratch row
+                    v[r] ^= 1
     return v
 
 
