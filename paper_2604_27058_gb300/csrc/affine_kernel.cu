@@ -12,7 +12,7 @@
 //      parity and the XOR of the random bits it depends on (thread per row);
 //   3. fault sampling: each warp owns 64 shots and keeps its 32 lanes busy
 //      by handing a finished lane the next shot, one survival-jump draw per
-//      lane per step (Sec. 3.2; coarse survival index in shared memory);
+//      lane per step (Sec. 3.2; guide-table search of the survival table);
 //      every fault appends its column's 8-row chunks to the warp's list, and
 //      the warp applies a full list one chunk per lane: eight shared-memory
 //      atomic XORs of the shot's bit;
@@ -37,16 +37,13 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
   constexpr uint32_t S = 32u * WPT, T = 16u * WPT, STR = WPT + 1;
   const uint32_t R = p.aff_rows, NR = p.aff_n_rand, t = threadIdx.x, lane = t & 31u, warp = t >> 5;
   // word offsets, each region 16-byte aligned (MW rows are read as uint4)
-  const uint32_t o_tile = (2u * L.qc_n + 3u) & ~3u;
-  const uint32_t o_mw = (o_tile + (R + 1) * STR + 3u) & ~3u;
-  uint64_t* QC = reinterpret_cast<uint64_t*>(sm);     // coarse survival index
-  uint32_t* TILE = sm + o_tile;                       // (R + 1) rows; row R is scratch
+  const uint32_t o_mw = ((R + 1) * STR + 3u) & ~3u;
+  uint32_t* TILE = sm;                                // (R + 1) rows; row R is scratch
   uint32_t* MW = sm + o_mw;                           // random bits [NR][WPT]
   uint32_t* LW = MW + NR * WPT + warp * kAffList;     // this warp's chunk list
   const bool noisy = !(L.flags & LF_NOISELESS) && p.n_sites > 0;
   const uint2 key = key_of(L.seed);
   const uint32_t n_det_end = p.n_meas + p.n_det;
-  for (uint32_t c = t; c < L.qc_n; c += T) QC[c] = __ldg(p.q + (size_t)c * L.qc_stride);
 
   // eight atomic XORs of one chunk into the column of shot s (tile-local)
   auto apply_chunk = [&](uint32_t chunk, uint32_t s) {
@@ -122,34 +119,14 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
         bool fin = false;
         if (live) {
           const uint64_t shot = L.shot_offset + pool0 + sh;
-          const uint32_t a = __ldg(p.seg_start + st), b = __ldg(p.seg_end + st);
-          const uint4 w = philox(make_uint4((uint32_t)shot, (uint32_t)(shot >> 32), TAG_GAP, st), key);
-          const uint64_t u = (uint64_t)w.x | ((uint64_t)w.y << 32);
-          const uint64_t tq = mulhi64(u, st == a ? ~0ull : __ldg(p.q + st - 1));
-          if (__ldg(p.q + b - 1) > tq) {
-            st = b;
-          } else {
-            // coarse entries c with st <= c * stride <= b - 1, then the stride
-            const uint32_t stride = L.qc_stride;
-            const uint32_t c_lo = (st + stride - 1) / stride, c_hi = (b - 1) / stride + 1;
-            uint32_t lo = c_lo, hi = c_hi;
-            while (lo < hi) {
-              const uint32_t mid = (lo + hi) >> 1;
-              if (QC[mid] <= tq) hi = mid;
-              else lo = mid + 1;
-            }
-            uint32_t flo = lo == c_lo ? st : (lo - 1) * stride + 1;
-            uint32_t fhi = lo < c_hi ? lo * stride : b - 1;  // q[fhi] <= tq
-            while (flo < fhi) {
-              const uint32_t mid = (flo + fhi) >> 1;
-              if (__ldg(p.q + mid) <= tq) fhi = mid;
-              else flo = mid + 1;
-            }
-            const uint32_t kk = (__ldg(p.site_info + flo) >> 4) & 15u;
-            const uint32_t c = flo * kRecPerSite + __umulhi(w.z, kk);
+          uint4 w;
+          const uint32_t i = jump_draw(p, key, shot, st, &w, &st);
+          if (i != kNoFault) {
+            const uint32_t kk = (__ldg(p.site_info + i) >> 4) & 15u;
+            const uint32_t c = i * kRecPerSite + __umulhi(w.z, kk);
             c0 = __ldg(p.aff_col_off + c);
             nch = __ldg(p.aff_col_off + c + 1) - c0;
-            st = flo + 1;
+            st = i + 1;
           }
           fin = st >= p.n_sites;
         }
@@ -228,12 +205,11 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
   }
 }
 
-// Shared memory of one CTA: the coarse survival index, the record tile
+// Shared memory of one CTA: the record tile
 // (with its scratch row and padding word), the random-bit words and one
 // chunk list per warp.
-size_t affine_smem_bytes(const DevProg& p, uint32_t wpt, uint32_t qc_n) {
-  const size_t o_tile = (2 * (size_t)qc_n + 3) & ~(size_t)3;
-  const size_t o_mw = (o_tile + (size_t)(wpt + 1) * (p.aff_rows + 1) + 3) & ~(size_t)3;
+size_t affine_smem_bytes(const DevProg& p, uint32_t wpt) {
+  const size_t o_mw = ((size_t)(wpt + 1) * (p.aff_rows + 1) + 3) & ~(size_t)3;
   return 4 * (o_mw + (size_t)wpt * p.aff_n_rand + (size_t)(wpt / 2) * kAffList);
 }
 

@@ -31,7 +31,7 @@ cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st);
 cudaError_t launch_patch_ref(Op* ops, uint32_t n_ops, const uint32_t* det_ref, const uint32_t* obs_ref,
                              cudaStream_t st);
 cudaError_t launch_presample(const LaunchParams& L, cudaStream_t st);
-size_t affine_smem_bytes(const DevProg& p, uint32_t wpt, uint32_t qc_n);
+size_t affine_smem_bytes(const DevProg& p, uint32_t wpt);
 cudaError_t launch_affine(const LaunchParams& L, uint32_t wpt, uint32_t grid, size_t smem, cudaStream_t st,
                           int* per_sm);
 cudaError_t launch_bucket(const LaunchParams& L, uint32_t n_wt, uint32_t* ents, uint32_t* offs, uint64_t cap_total,
@@ -93,6 +93,8 @@ DevProg dev_view(const ProgHeader& h, const uint8_t* base) {
   d.n_det = h.n_det;
   d.n_obs = h.n_obs;
   d.n_blocks = h.n_blocks;
+  d.srch = reinterpret_cast<const uint32_t*>(base + h.off_srch);
+  d.guide = reinterpret_cast<const uint32_t*>(base + h.off_guide);
   if (h.aff_ok) {
     d.aff_const = reinterpret_cast<const uint32_t*>(base + h.off_aff_const);
     d.aff_rowev_off = reinterpret_cast<const uint32_t*>(base + h.off_aff_rowev_off);
@@ -277,8 +279,6 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
     if (h.aff_ok && tu.A && !(lflags & (LF_POSTSELECT | LF_REFERENCE)) && stop_event == 0xffffffffu) {
       // record-level propagation sampler: tile of 32 * wpt shots per CTA of
       // 16 * wpt threads; the shape with the most resident warps wins
-      L.qc_stride = coarse_stride(h.n_sites);
-      L.qc_n = coarse_count(h.n_sites);
       int n_sm = 0, dev = 0;
       NC_TRY(cudaGetDevice(&dev));
       NC_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -286,7 +286,7 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
       int best_warps = 0, best_ctas = 0;
       for (uint32_t c : {16u, 32u, 8u}) {
         if (tu.AW && tu.AW != c) continue;
-        const size_t smem = affine_smem_bytes(L.p, c, L.qc_n);
+        const size_t smem = affine_smem_bytes(L.p, c);
         if (smem > 227 * 1024) continue;
         int per_sm = 0;
         NC_TRY(launch_affine(L, c, 0, smem, stream, &per_sm));
@@ -298,7 +298,7 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
         }
       }
       if (wpt) {
-        const size_t smem = affine_smem_bytes(L.p, wpt, L.qc_n);
+        const size_t smem = affine_smem_bytes(L.p, wpt);
         L.n_tiles = (uint32_t)((L.row_words32 + wpt - 1) / wpt);
         const uint64_t grid = std::min<uint64_t>(L.n_tiles, (uint64_t)best_ctas * n_sm);
         if (tm) NC_TRY(cudaEventRecord(tm->e0, stream));
@@ -630,7 +630,7 @@ nc_status nc_program_deserialize(const void* buf, size_t len, nc_program** out) 
                      h.off_site_eff, h.off_slot_list, h.off_det_ref, h.off_obs_ref,
                      h.off_site_opt, h.off_opt_tab, h.off_plist, h.off_orec, h.off_site_blk,
                      h.off_aff_const, h.off_aff_rowev_off, h.off_aff_rowev, h.off_aff_rand_ev,
-                     h.off_aff_col_off, h.off_aff_col};
+                     h.off_aff_col_off, h.off_aff_col, h.off_srch, h.off_guide};
   for (uint64_t o : offs)
     if (o > h.total_bytes || (o & 15)) return NC_E_ARG;
   if (h.off_ops + (uint64_t)h.n_ops * sizeof(Op) > h.total_bytes || h.k_max > kMaxK || h.n_qubits > kMaxQubits)

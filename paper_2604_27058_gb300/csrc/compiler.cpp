@@ -1276,6 +1276,34 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
       }
     }
 
+    // ---------------- survival search records and guide tables ----------------
+    std::vector<SrchRec> srch(S);
+    std::vector<uint32_t> guide;
+    for (size_t a = 0; a < S;) {
+      const size_t b = seg_end[a];
+      // smallest shift with at most max(16, 2 (b - a)) buckets
+      const uint64_t target = std::max<uint64_t>(16, 2 * (uint64_t)(b - a));
+      uint32_t shift = 0;
+      while (((uint64_t)guide_key(q[b - 1], shift) + 1) > target) shift++;
+      const uint32_t base = (uint32_t)guide.size(), m = guide_key(q[b - 1], shift) + 1;
+      // g[j] = first site i of the segment with key(Q[i]) >= j
+      size_t i = a;
+      for (uint32_t j = 0; j < m; j++) {
+        while (i < b - 1 && guide_key(q[i], shift) < j) i++;
+        guide.push_back((uint32_t)i);
+      }
+      for (size_t st = a; st < b; st++) {
+        SrchRec& r = srch[st];
+        r.a = (uint32_t)a;
+        r.b = (uint32_t)b;
+        r.gbase = base;
+        r.shift = shift;
+        r.q_end = q[b - 1];
+        r.q_l = st == a ? ~0ull : q[st - 1];
+      }
+      a = b;
+    }
+
     // ---------------- blob ----------------
     ProgHeader h;
     std::memset(&h, 0, sizeof(h));
@@ -1297,6 +1325,7 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     h.n_opt = (uint32_t)(opt_tab.size() / 2);
     h.n_plist = (uint32_t)plist.size();
     h.n_blocks = n_blocks;
+    h.n_guide = (uint32_t)guide.size();
     {
       double mean = 0.0;
       for (double sp : c.site_p) mean += sp;
@@ -1323,6 +1352,8 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     h.off_plist = place(plist.size() * 2);
     h.off_orec = place(orec.size() * 2);
     h.off_site_blk = place(site_blk.size() * 4);
+    h.off_srch = place(S * sizeof(SrchRec));
+    h.off_guide = place(guide.size() * 4);
     h.total_bytes = off;
     out.blob.assign(off, 0);
     std::memcpy(out.blob.data(), &h, sizeof(h));
@@ -1342,6 +1373,8 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     cp(h.off_plist, plist.data(), plist.size() * 2);
     cp(h.off_orec, orec.data(), orec.size() * 2);
     cp(h.off_site_blk, site_blk.data(), site_blk.size() * 4);
+    cp(h.off_srch, srch.data(), S * sizeof(SrchRec));
+    cp(h.off_guide, guide.data(), guide.size() * 4);
     append_affine(out.blob);
     out.counts = c.counts;
     return 0;

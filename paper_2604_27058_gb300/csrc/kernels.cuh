@@ -31,6 +31,8 @@ struct DevProg {
   const uint32_t* aff_rand_ev;
   const uint32_t* aff_col_off;
   const uint4* aff_chunks;
+  const uint32_t* srch;   // SrchRec per site (program.h)
+  const uint32_t* guide;
   uint32_t n_qubits, nw, n_ops, n_sites, n_slots, k_max, kept_slot;
   uint32_t n_meas, n_det, n_obs, n_blocks;
   uint32_t aff_rows, aff_n_rand;
@@ -130,74 +132,55 @@ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) { return __u
 
 // Next fault of global shot `shot` at or after site `st` (Sec. 3.2 jump,
 // integer survival form). Returns (site << 4) | option, or kNoFault.
-// The survival table is read through `q`: the program's global copy, or a
-// copy staged in shared memory by the caller.
-__device__ __forceinline__ uint32_t next_fault_tab(const DevProg& p, const uint64_t* q, uint64_t seed,
-                                                   uint64_t shot, uint32_t st) {
+__device__ __forceinline__ uint32_t guide_key_dev(uint64_t t, uint32_t shift) {
+  t = t < (1ull << kGuideBits) ? (1ull << kGuideBits) : t;
+  const uint32_t e = 63u - (uint32_t)__clzll((long long)t);
+  const uint32_t m = (uint32_t)(t >> (e - kGuideBits)) & ((1u << kGuideBits) - 1u);
+  const uint32_t lv = (e << kGuideBits) | m, lmax = (63u << kGuideBits) | ((1u << kGuideBits) - 1u);
+  return (lmax - lv) >> shift;
+}
+
+// One survival-jump draw from site st (Sec. 3.2, integer form): returns the
+// fault site (and leaves the draw in *w for the option), or kNoFault with
+// *next = the end of st's segment.
+__device__ __forceinline__ uint32_t jump_draw(const DevProg& p, uint2 key, uint64_t shot, uint32_t st, uint4* w,
+                                              uint32_t* next) {
+  const uint4 r0 = __ldg(reinterpret_cast<const uint4*>(p.srch) + 2 * st);
+  const uint4 r1 = __ldg(reinterpret_cast<const uint4*>(p.srch) + 2 * st + 1);
+  *w = philox(make_uint4((uint32_t)shot, (uint32_t)(shot >> 32), TAG_GAP, st), key);
+  const uint64_t u = (uint64_t)w->x | ((uint64_t)w->y << 32);
+  const uint64_t q_end = (uint64_t)r1.x | ((uint64_t)r1.y << 32), q_l = (uint64_t)r1.z | ((uint64_t)r1.w << 32);
+  const uint64_t t = mulhi64(u, q_l);
+  if (q_end > t) {
+    *next = r0.y;
+    return kNoFault;
+  }
+  uint32_t i = __ldg(p.guide + r0.z + guide_key_dev(t, r0.w));
+  while (__ldg(p.q + i) > t) i++;
+  return i;
+}
+
+// Next fault of a shot at or after site st: (site << 4) | option, or kNoFault.
+__device__ __forceinline__ uint32_t next_fault(const DevProg& p, uint64_t seed, uint64_t shot, uint32_t st) {
   const uint2 key = key_of(seed);
   while (st < p.n_sites) {
-    uint32_t a = __ldg(p.seg_start + st), b = __ldg(p.seg_end + st);
-    uint4 w = philox(make_uint4((uint32_t)shot, (uint32_t)(shot >> 32), TAG_GAP, st), key);
-    uint64_t u = (uint64_t)w.x | ((uint64_t)w.y << 32);
-    uint64_t ql = st == a ? ~0ull : q[st - 1];
-    uint64_t t = mulhi64(u, ql);
-    if (q[b - 1] > t) {
-      st = b;
-      continue;
+    uint4 w;
+    uint32_t nx;
+    const uint32_t i = jump_draw(p, key, shot, st, &w, &nx);
+    if (i != kNoFault) {
+      const uint32_t k = (__ldg(p.site_info + i) >> 4) & 15u;
+      return (i << 4) | __umulhi(w.z, k);
     }
-    uint32_t lo = st, hi = b - 1;  // q[hi] <= t
-    while (lo < hi) {
-      uint32_t mid = (lo + hi) >> 1;
-      if (q[mid] <= t) hi = mid;
-      else lo = mid + 1;
-    }
-    uint32_t k = (__ldg(p.site_info + lo) >> 4) & 15u;
-    uint32_t opt = __umulhi(w.z, k);
-    return (lo << 4) | opt;
+    st = nx;
   }
   return kNoFault;
 }
 
-__device__ __forceinline__ uint32_t next_fault(const DevProg& p, uint64_t seed, uint64_t shot,
-                                               uint32_t st) {
-  return next_fault_tab(p, p.q, seed, shot, st);
-}
-
-// next_fault with a shared-memory coarse index qc[c] = Q[c * stride] of the
-// whole site table: the search narrows to one stride of the global table.
+// Older call form with a shared-memory coarse index; the guide table makes
+// the index unnecessary.
 __device__ __forceinline__ uint32_t next_fault_coarse(const DevProg& p, uint64_t seed, uint64_t shot,
-                                                      uint32_t st, const uint64_t* qc, uint32_t stride) {
-  const uint2 key = key_of(seed);
-  while (st < p.n_sites) {
-    uint32_t a = __ldg(p.seg_start + st), b = __ldg(p.seg_end + st);
-    uint4 w = philox(make_uint4((uint32_t)shot, (uint32_t)(shot >> 32), TAG_GAP, st), key);
-    uint64_t u = (uint64_t)w.x | ((uint64_t)w.y << 32);
-    uint64_t ql = st == a ? ~0ull : __ldg(p.q + st - 1);
-    uint64_t t = mulhi64(u, ql);
-    if (__ldg(p.q + b - 1) > t) {
-      st = b;
-      continue;
-    }
-    // coarse entries c with st <= c * stride <= b - 1
-    const uint32_t c_lo = (st + stride - 1) / stride, c_hi = (b - 1) / stride + 1;
-    uint32_t lo = c_lo, hi = c_hi;
-    while (lo < hi) {
-      uint32_t mid = (lo + hi) >> 1;
-      if (qc[mid] <= t) hi = mid;
-      else lo = mid + 1;
-    }
-    uint32_t flo = lo == c_lo ? st : (lo - 1) * stride + 1;
-    uint32_t fhi = lo < c_hi ? lo * stride : b - 1;  // q[fhi] <= t
-    while (flo < fhi) {
-      uint32_t mid = (flo + fhi) >> 1;
-      if (__ldg(p.q + mid) <= t) fhi = mid;
-      else flo = mid + 1;
-    }
-    uint32_t k = (__ldg(p.site_info + flo) >> 4) & 15u;
-    uint32_t opt = __umulhi(w.z, k);
-    return (flo << 4) | opt;
-  }
-  return kNoFault;
+                                                      uint32_t st, const uint64_t*, uint32_t) {
+  return next_fault(p, seed, shot, st);
 }
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {

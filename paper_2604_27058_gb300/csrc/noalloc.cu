@@ -92,6 +92,8 @@ DevProg view(const ProgHeader& h, const uint8_t* base) {
   d.n_det = h.n_det;
   d.n_obs = h.n_obs;
   d.n_blocks = h.n_blocks;
+  d.srch = reinterpret_cast<const uint32_t*>(base + h.off_srch);
+  d.guide = reinterpret_cast<const uint32_t*>(base + h.off_guide);
   if (h.aff_ok) {
     d.aff_const = reinterpret_cast<const uint32_t*>(base + h.off_aff_const);
     d.aff_rowev_off = reinterpret_cast<const uint32_t*>(base + h.off_aff_rowev_off);

@@ -104,11 +104,35 @@ struct ProgHeader {
   uint32_t aff_rows, aff_n_rand;   // rows = n_meas + n_det + n_obs; random dormant measurements
   uint32_t aff_n_chunks;           // 8-row chunks of the fault columns
   float aff_chunks_per_shot;       // expected chunks of a shot's faults
+  uint32_t n_guide, pad2;          // survival guide-table entries
   uint64_t off_ops, off_masks, off_q, off_seg_start, off_seg_end, off_site_info, off_site_eff,
       off_slot_list, off_det_ref, off_obs_ref, off_site_opt, off_opt_tab, off_plist, off_orec, off_site_blk,
       off_aff_const, off_aff_rowev_off, off_aff_rowev, off_aff_rand_ev, off_aff_col_off, off_aff_col,
-      total_bytes;
+      off_srch, off_guide, total_bytes;
 };
+// Survival-jump search (Sec. 3.2 jump, integer form). srch[st] (32 bytes)
+// holds, for a jump starting at site st: the segment [a, b), its guide-table
+// base and shift, Q[b - 1] and Q_L (Q[st - 1], or 2^64 - 1 at a segment
+// start). The next fault is the first i in [st, b) with Q[i] <= t; guide
+// entry g[base + guide_key(t, shift)] is a site at or before it, so a short
+// forward scan from there finds it exactly.
+struct SrchRec {
+  uint32_t a, b, gbase, shift;
+  uint64_t q_end, q_l;
+};
+static_assert(sizeof(SrchRec) == 32, "SrchRec must be 32 bytes");
+constexpr uint32_t kGuideBits = 16;
+// Piecewise-linear log2 of t (exponent, then kGuideBits mantissa bits),
+// non-decreasing in t; the key counts down from its value at 2^64 - 1.
+// (Host form; the device form in kernels.cuh computes the same value.)
+inline uint32_t guide_key(uint64_t t, uint32_t shift) {
+  if (t < (1ull << kGuideBits)) t = 1ull << kGuideBits;
+  uint32_t e = 63;
+  while (!(t >> e)) e--;
+  const uint32_t m = (uint32_t)(t >> (e - kGuideBits)) & ((1u << kGuideBits) - 1u);
+  const uint32_t lv = (e << kGuideBits) | m, lmax = (63u << kGuideBits) | ((1u << kGuideBits) - 1u);
+  return (lmax - lv) >> shift;
+}
 // Record-level propagation (programs with k_max = 0). With every frame
 // update GF(2)-linear, a shot's records are an affine function of its fault
 // indicators and of its random dormant measurement outcomes:

@@ -16,11 +16,12 @@ from oracle.philox import meas_u
 from oracle.records import raw_parities
 from oracle.stabilizer import FrameSim
 
-HEAD_U32 = 24   # 17 counts, mean_faults (f32), n_blocks, aff_ok, aff_rows, aff_n_rand, aff_n_chunks, f32
-N_OFFS = 22     # 21 table offsets + total_bytes
+HEAD = "<17If8I"  # 17 counts, mean_faults, n_blocks, aff_ok, aff_rows, aff_n_rand, aff_n_chunks,
+                  # aff_chunks_per_shot (read as u32), n_guide, pad
+HEAD_BYTES = struct.calcsize(HEAD)
 OFF_NAMES = ["ops", "masks", "q", "seg_start", "seg_end", "site_info", "site_eff", "slot_list", "det_ref",
              "obs_ref", "site_opt", "opt_tab", "plist", "orec", "site_blk", "aff_const", "aff_rowev_off",
-             "aff_rowev", "aff_rand_ev", "aff_col_off", "aff_col", "total_bytes"]
+             "aff_rowev", "aff_rand_ev", "aff_col_off", "aff_col", "srch", "guide", "total_bytes"]
 REC_PER_SITE = 15
 
 
@@ -33,10 +34,10 @@ def nc():
 
 
 def _tables(blob: bytes):
-    u = struct.unpack_from("<17If6I", blob, 0)
+    u = struct.unpack_from(HEAD, blob, 0)
     n_sites, n_meas, n_det, n_obs = u[5], u[6], u[7], u[8]
     aff_ok, rows, n_rand = u[19], u[20], u[21]
-    offs = dict(zip(OFF_NAMES, struct.unpack_from(f"<{N_OFFS}Q", blob, HEAD_U32 * 4)))
+    offs = dict(zip(OFF_NAMES, struct.unpack_from(f"<{len(OFF_NAMES)}Q", blob, HEAD_BYTES)))
     assert aff_ok == 1
     assert rows == n_meas + n_det + n_obs
 
@@ -106,4 +107,54 @@ def test_affine_tables_absent_with_active_axes(nc):
     prog = nc.compile(gc.tiny_random(seed=1))
     assert prog.info.k_max > 0
     blob = prog.serialize()
-    assert struct.unpack_from("<17If6I", blob, 0)[19] == 0
+    assert struct.unpack_from(HEAD, blob, 0)[19] == 0
+
+
+def _guide_key(t: int, shift: int) -> int:
+    t = max(t, 1 << 16)
+    e = t.bit_length() - 1
+    lv = (e << 16) | ((t >> (e - 16)) & 0xFFFF)
+    return (((63 << 16) | 0xFFFF) - lv) >> shift
+
+
+@pytest.mark.parametrize("name", ["surface", "sweep_many_segments", "certain_fault"])
+def test_guide_search_matches_bisection(nc, name):
+    """The compiled survival search records and guide tables give, for any
+    threshold t, the same first site with Q[i] <= t as plain bisection of
+    the oracle's survival table."""
+    from oracle.noise import _first_at_or_below, build_table
+    from oracle.circuit import flatten
+    text = {"surface": lambda: gc.surface_code_memory(d=5, rounds=25, p=1e-3),
+            "sweep_many_segments": lambda: gc.sweep_mirror(1).text,
+            "certain_fault": lambda: "X_ERROR(1) 0\nX_ERROR(0.5) 0 1\nDEPOLARIZE1(0.999999) 1\nM 0 1\n"}[name]()
+    blob = nc.compile(text).serialize()
+    u = struct.unpack_from(HEAD, blob, 0)
+    n_sites, n_guide = u[5], u[24]
+    offs = dict(zip(OFF_NAMES, struct.unpack_from(f"<{len(OFF_NAMES)}Q", blob, HEAD_BYTES)))
+    srch = np.frombuffer(blob, dtype=np.uint32, count=8 * n_sites, offset=offs["srch"]).reshape(-1, 8)
+    guide = np.frombuffer(blob, dtype=np.uint32, count=n_guide, offset=offs["guide"])
+    f = flatten(text)
+    table = build_table(f.site_p, f.site_kind)
+    q = table.q
+    rng = np.random.default_rng(5)
+    sts = sorted(set(rng.integers(0, n_sites, 300).tolist()) | {0, n_sites - 1})
+    checked = 0
+    for st in sts:
+        a, b, gbase, shift = (int(x) for x in srch[st][:4])
+        q_end = int(srch[st][4]) | (int(srch[st][5]) << 32)
+        q_l = int(srch[st][6]) | (int(srch[st][7]) << 32)
+        assert (a, b) == (table.seg_start[st], table.seg_end[st])
+        assert q_end == q[b - 1]
+        assert q_l == ((1 << 64) - 1 if st == a else q[st - 1])
+        ts = [(int(x) * q_l) >> 64 for x in rng.integers(0, 2**63, 40, dtype=np.int64) * 2]
+        ts += [q_end, max(q_l - 1, 0)]
+        for t in ts:
+            if q_end > t:
+                continue
+            i = int(guide[gbase + _guide_key(t, shift)])
+            assert i <= _first_at_or_below(q, st, b, t)
+            while q[i] > t:
+                i += 1
+            assert i == _first_at_or_below(q, st, b, t)
+            checked += 1
+    assert checked >= min(100, 10 * n_sites)
