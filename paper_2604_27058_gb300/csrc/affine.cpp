@@ -321,8 +321,25 @@ void append_affine(std::vector<uint8_t>& blob) {
   h.off_aff_rowev_off = place((uint64_t)(R + 1) * 4);
   h.off_aff_rowev = place((uint64_t)rowev.size() * 4);
   h.off_aff_rand_ev = place((uint64_t)rand_ev.size() * 4);
+  // per-site fault records: option chunk counts as nibbles, K, first chunk
+  std::vector<uint32_t> frec((size_t)h.n_sites * 4, 0);
+  for (uint32_t s = 0; s < h.n_sites; s++) {
+    const uint32_t kk = site_k(site_info[s]);
+    uint64_t nib = 0;
+    bool long_site = false;
+    for (uint32_t o = 0; o < kk; o++) {
+      const uint32_t n = col_off[(size_t)s * kRecPerSite + o + 1] - col_off[(size_t)s * kRecPerSite + o];
+      if (n > 15) long_site = true;
+      nib |= (uint64_t)(n & 15u) << (4 * o);
+    }
+    nib |= (uint64_t)kk << 60;
+    frec[4 * s] = (uint32_t)nib;
+    frec[4 * s + 1] = (uint32_t)(nib >> 32);
+    frec[4 * s + 2] = long_site ? 0xFFFFFFFFu : col_off[(size_t)s * kRecPerSite];
+  }
   h.off_aff_col_off = place((uint64_t)col_off.size() * 4);
   h.off_aff_col = place((uint64_t)chunks.size() * 2);
+  h.off_aff_frec = place((uint64_t)frec.size() * 4);
   h.total_bytes = off;
   h.aff_ok = 1;
   h.aff_rows = R;
@@ -339,6 +356,7 @@ void append_affine(std::vector<uint8_t>& blob) {
   cp(h.off_aff_rand_ev, rand_ev.data(), rand_ev.size() * 4);
   cp(h.off_aff_col_off, col_off.data(), col_off.size() * 4);
   cp(h.off_aff_col, chunks.data(), chunks.size() * 2);
+  cp(h.off_aff_frec, frec.data(), frec.size() * 4);
   std::memcpy(blob.data(), &h, sizeof(h));
 }
 

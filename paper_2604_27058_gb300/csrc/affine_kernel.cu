@@ -16,8 +16,8 @@
 //      every fault appends its column's 8-row chunks to the warp's list, and
 //      the warp applies a full list one chunk per lane: eight shared-memory
 //      atomic XORs of the shot's bit;
-//   4. the tile is written out row by row, bits of shots past the end
-//      cleared, plus the kept row.
+//   4. the tile is written out row by row (16-byte stores when the rows
+//      allow), bits of shots past the end cleared, plus the kept row.
 // The records equal those of the executors bit for bit: same draws, same
 // faults, and the tables are the executors' own frame updates propagated to
 // the records once at compile time.
@@ -59,12 +59,35 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
     atomicXor(col + (ch.w & 0xFFFFu) * STR, bit);
     atomicXor(col + (ch.w >> 16) * STR, bit);
   };
-  // the warp applies its list, one item per lane
+  // the warp applies its list (at most kAffList = 4 x 32 items): every lane
+  // first loads its up to four chunks, then does the atomics
   auto flush = [&](uint32_t n) {
     __syncwarp();
-    for (uint32_t i = lane; i < n; i += 32) {
-      const uint32_t it = LW[i];
-      apply_chunk(it >> 10, it & 1023u);
+    uint4 ch[kAffList / 32];
+    uint32_t sh[kAffList / 32];
+#pragma unroll
+    for (uint32_t k = 0; k < kAffList / 32; k++) {
+      const uint32_t i = lane + 32u * k;
+      if (i < n) {
+        const uint32_t it = LW[i];
+        ch[k] = __ldg(p.aff_chunks + (it >> 10));
+        sh[k] = it & 1023u;
+      }
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < kAffList / 32; k++) {
+      if (lane + 32u * k < n) {
+        uint32_t* col = TILE + (sh[k] >> 5);
+        const uint32_t bit = 1u << (sh[k] & 31u);
+        atomicXor(col + (ch[k].x & 0xFFFFu) * STR, bit);
+        atomicXor(col + (ch[k].x >> 16) * STR, bit);
+        atomicXor(col + (ch[k].y & 0xFFFFu) * STR, bit);
+        atomicXor(col + (ch[k].y >> 16) * STR, bit);
+        atomicXor(col + (ch[k].z & 0xFFFFu) * STR, bit);
+        atomicXor(col + (ch[k].z >> 16) * STR, bit);
+        atomicXor(col + (ch[k].w & 0xFFFFu) * STR, bit);
+        atomicXor(col + (ch[k].w >> 16) * STR, bit);
+      }
     }
     __syncwarp();
   };
@@ -118,14 +141,38 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
         uint32_t c0 = 0, nch = 0;
         bool fin = false;
         if (live) {
+          // one survival-jump draw (kernels.cuh jump_draw, with the fault
+          // record loaded beside each Q[i] of the scan)
           const uint64_t shot = L.shot_offset + pool0 + sh;
-          uint4 w;
-          const uint32_t i = jump_draw(p, key, shot, st, &w, &st);
-          if (i != kNoFault) {
-            const uint32_t kk = (__ldg(p.site_info + i) >> 4) & 15u;
-            const uint32_t c = i * kRecPerSite + __umulhi(w.z, kk);
-            c0 = __ldg(p.aff_col_off + c);
-            nch = __ldg(p.aff_col_off + c + 1) - c0;
+          const uint4 r0 = __ldg(reinterpret_cast<const uint4*>(p.srch) + 2 * st);
+          const uint4 r1 = __ldg(reinterpret_cast<const uint4*>(p.srch) + 2 * st + 1);
+          const uint4 w = philox(make_uint4((uint32_t)shot, (uint32_t)(shot >> 32), TAG_GAP, st), key);
+          const uint64_t u = (uint64_t)w.x | ((uint64_t)w.y << 32);
+          const uint64_t q_end = (uint64_t)r1.x | ((uint64_t)r1.y << 32);
+          const uint64_t tq = mulhi64(u, (uint64_t)r1.z | ((uint64_t)r1.w << 32));
+          if (q_end > tq) {
+            st = r0.y;
+          } else {
+            uint32_t i = __ldg(p.guide + r0.z + guide_key_dev(tq, r0.w));
+            uint64_t qi = __ldg(p.q + i);
+            uint4 fr = __ldg(p.aff_frec + i);
+            while (qi > tq) {
+              i++;
+              qi = __ldg(p.q + i);
+              fr = __ldg(p.aff_frec + i);
+            }
+            const uint32_t opt = __umulhi(w.z, fr.y >> 28);
+            if (fr.z != 0xFFFFFFFFu) {
+              const uint64_t nib = (uint64_t)fr.x | ((uint64_t)(fr.y & 0x0FFFFFFFu) << 32);
+              nch = (uint32_t)(nib >> (4 * opt)) & 15u;
+              uint64_t below = nib & ((1ull << (4 * opt)) - 1ull);
+              below = (below & 0x0F0F0F0F0F0F0F0Full) + ((below >> 4) & 0x0F0F0F0F0F0F0F0Full);
+              c0 = fr.z + (uint32_t)((below * 0x0101010101010101ull) >> 56);
+            } else {
+              const uint32_t c = i * kRecPerSite + opt;
+              c0 = __ldg(p.aff_col_off + c);
+              nch = __ldg(p.aff_col_off + c + 1) - c0;
+            }
             st = i + 1;
           }
           fin = st >= p.n_sites;
@@ -161,41 +208,57 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
       flush(cnt);
     }
     __syncthreads();
-    // 4. rows out (u64 pairs of words), then the kept row
-    constexpr uint32_t PR = WPT / 2;
+    // 4. rows out, then the kept row: four words per thread (16-byte stores)
+    // when rows are 16-byte aligned (row_words32 % 4 == 0), else two
     const uint64_t gw0 = (uint64_t)tile * WPT;
-    for (uint32_t i = t; i < (R + 1) * PR; i += T) {
-      const uint32_t r = i / PR, w2 = (i % PR) * 2u;
-      const uint64_t gw = gw0 + w2;
-      if (gw >= L.row_words32) continue;  // row_words32 is even: gw + 1 is in range too
-      uint32_t m[2];
-#pragma unroll
-      for (uint32_t h = 0; h < 2; h++) {
-        const uint64_t s0 = (gw + h) * 32u;
-        m[h] = s0 + 32 <= L.shots ? ~0u : s0 < L.shots ? (1u << (uint32_t)(L.shots - s0)) - 1u : 0u;
-      }
-      uint32_t* dst;
-      uint32_t a, b;
-      if (r < R) {
-        if (r < p.n_meas) {
-          if (!(L.flags & LF_OUT_MEAS)) continue;
-          dst = L.meas + (size_t)r * L.row_words32;
-        } else if (r < n_det_end) {
-          if (!(L.flags & LF_OUT_DET)) continue;
-          dst = L.det + (size_t)(r - p.n_meas) * L.row_words32;
-        } else {
-          if (!(L.flags & LF_OUT_OBS)) continue;
-          dst = L.obs + (size_t)(r - n_det_end) * L.row_words32;
-        }
-        a = TILE[r * STR + w2] & m[0];
-        b = TILE[r * STR + w2 + 1] & m[1];
-      } else {
-        if (!(L.flags & LF_OUT_KEPT)) continue;
+    auto out_row = [&](uint32_t r, uint32_t*& dst) -> bool {
+      if (r == R) {
         dst = L.kept;
-        a = m[0];
-        b = m[1];
+        return (L.flags & LF_OUT_KEPT) != 0;
       }
-      *reinterpret_cast<uint2*>(dst + gw) = make_uint2(a, b);
+      if (r < p.n_meas) {
+        dst = L.meas + (size_t)r * L.row_words32;
+        return (L.flags & LF_OUT_MEAS) != 0;
+      }
+      if (r < n_det_end) {
+        dst = L.det + (size_t)(r - p.n_meas) * L.row_words32;
+        return (L.flags & LF_OUT_DET) != 0;
+      }
+      dst = L.obs + (size_t)(r - n_det_end) * L.row_words32;
+      return (L.flags & LF_OUT_OBS) != 0;
+    };
+    auto valid = [&](uint64_t gw) -> uint32_t {
+      const uint64_t s0 = gw * 32u;
+      return s0 + 32 <= L.shots ? ~0u : s0 < L.shots ? (1u << (uint32_t)(L.shots - s0)) - 1u : 0u;
+    };
+    if ((L.row_words32 & 3u) == 0) {
+      constexpr uint32_t PR = WPT / 4;
+      for (uint32_t i = t; i < (R + 1) * PR; i += T) {
+        const uint32_t r = i / PR, w4 = (i % PR) * 4u;
+        const uint64_t gw = gw0 + w4;
+        uint32_t* dst;
+        if (gw >= L.row_words32 || !out_row(r, dst)) continue;  // gw + 3 is in range too
+        uint4 v;
+        if (r < R) {
+          const uint32_t* src = TILE + r * STR + w4;
+          v = make_uint4(src[0] & valid(gw), src[1] & valid(gw + 1), src[2] & valid(gw + 2), src[3] & valid(gw + 3));
+        } else {
+          v = make_uint4(valid(gw), valid(gw + 1), valid(gw + 2), valid(gw + 3));
+        }
+        *reinterpret_cast<uint4*>(dst + gw) = v;
+      }
+    } else {
+      constexpr uint32_t PR = WPT / 2;
+      for (uint32_t i = t; i < (R + 1) * PR; i += T) {
+        const uint32_t r = i / PR, w2 = (i % PR) * 2u;
+        const uint64_t gw = gw0 + w2;
+        uint32_t* dst;
+        if (gw >= L.row_words32 || !out_row(r, dst)) continue;  // row_words32 is even
+        uint2 v;
+        if (r < R) v = make_uint2(TILE[r * STR + w2] & valid(gw), TILE[r * STR + w2 + 1] & valid(gw + 1));
+        else v = make_uint2(valid(gw), valid(gw + 1));
+        *reinterpret_cast<uint2*>(dst + gw) = v;
+      }
     }
     if (t == 0 && (uint64_t)tile * S < L.shots) {
       const uint64_t left = L.shots - (uint64_t)tile * S;

@@ -31,6 +31,7 @@ struct DevProg {
   const uint32_t* aff_rand_ev;
   const uint32_t* aff_col_off;
   const uint4* aff_chunks;
+  const uint4* aff_frec;
   const uint32_t* srch;   // SrchRec per site (program.h)
   const uint32_t* guide;
   uint32_t n_qubits, nw, n_ops, n_sites, n_slots, k_max, kept_slot;

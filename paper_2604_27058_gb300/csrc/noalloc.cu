@@ -101,6 +101,7 @@ DevProg view(const ProgHeader& h, const uint8_t* base) {
     d.aff_rand_ev = reinterpret_cast<const uint32_t*>(base + h.off_aff_rand_ev);
     d.aff_col_off = reinterpret_cast<const uint32_t*>(base + h.off_aff_col_off);
     d.aff_chunks = reinterpret_cast<const uint4*>(base + h.off_aff_col);
+    d.aff_frec = reinterpret_cast<const uint4*>(base + h.off_aff_frec);
     d.aff_chunks_per_shot = h.aff_chunks_per_shot;
     d.aff_rows = h.aff_rows;
     d.aff_n_rand = h.aff_n_rand;

@@ -108,7 +108,7 @@ struct ProgHeader {
   uint64_t off_ops, off_masks, off_q, off_seg_start, off_seg_end, off_site_info, off_site_eff,
       off_slot_list, off_det_ref, off_obs_ref, off_site_opt, off_opt_tab, off_plist, off_orec, off_site_blk,
       off_aff_const, off_aff_rowev_off, off_aff_rowev, off_aff_rand_ev, off_aff_col_off, off_aff_col,
-      off_srch, off_guide, total_bytes;
+      off_aff_frec, off_srch, off_guide, total_bytes;
 };
 // Survival-jump search (Sec. 3.2 jump, integer form). srch[st] (32 bytes)
 // holds, for a jump starting at site st: the segment [a, b), its guide-table
@@ -145,6 +145,10 @@ inline uint32_t guide_key(uint64_t t, uint32_t shift) {
 //   rand_ev: u32 event per ordinal; col_off: n_sites * kRecPerSite + 1 u32
 //   chunk offsets; col: chunks of 8 u16 rows (16 bytes), each column's rows
 //   ascending and padded with row index `rows` (a scratch row).
+//   frec: 16 bytes per site, so that one load after the search gives a
+//   fault's chunk range: words 0-1 hold 4-bit chunk counts of options 0..14
+//   (bits 60..63: the option count K), word 2 the first chunk of option 0
+//   (0xFFFFFFFF: some option has more than 15 chunks; use col_off).
 // site_blk[site] = ordinal of the NOISE_BLOCK instruction that covers the site.
 // Option records: orec[site * 15 + option] is 16 bytes (8 x u16). Word 0 is
 // a tag: n <= 7 -> n frame-plane indices follow; kRecFlip -> the site flips

@@ -21,7 +21,8 @@ HEAD = "<17If8I"  # 17 counts, mean_faults, n_blocks, aff_ok, aff_rows, aff_n_ra
 HEAD_BYTES = struct.calcsize(HEAD)
 OFF_NAMES = ["ops", "masks", "q", "seg_start", "seg_end", "site_info", "site_eff", "slot_list", "det_ref",
              "obs_ref", "site_opt", "opt_tab", "plist", "orec", "site_blk", "aff_const", "aff_rowev_off",
-             "aff_rowev", "aff_rand_ev", "aff_col_off", "aff_col", "srch", "guide", "total_bytes"]
+             "aff_rowev", "aff_rand_ev", "aff_col_off", "aff_col", "aff_frec", "srch", "guide",
+             "total_bytes"]
 REC_PER_SITE = 15
 
 
@@ -48,6 +49,17 @@ def _tables(blob: bytes):
     n_chunks = int(col_off[-1])
     assert n_chunks == u[22]
     chunks = np.frombuffer(blob, dtype=np.uint16, count=8 * n_chunks, offset=offs["aff_col"]).reshape(-1, 8)
+    frec = np.frombuffer(blob, dtype=np.uint32, count=4 * n_sites, offset=offs["aff_frec"]).reshape(-1, 4)
+    # per-site records: 4-bit chunk counts, K, first chunk (or the long-site mark)
+    for s in range(n_sites):
+        nib = int(frec[s, 0]) | (int(frec[s, 1]) << 32)
+        kk = nib >> 60
+        counts = [int(col_off[s * REC_PER_SITE + o + 1] - col_off[s * REC_PER_SITE + o]) for o in range(kk)]
+        if int(frec[s, 2]) == 0xFFFFFFFF:
+            assert max(counts) > 15
+            continue
+        assert int(frec[s, 2]) == int(col_off[s * REC_PER_SITE])
+        assert [(nib >> (4 * o)) & 15 for o in range(kk)] == counts
     return {
         "rows": rows, "n_meas": n_meas, "n_det": n_det,
         "const": arr("aff_const", rows),
