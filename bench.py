@@ -52,7 +52,7 @@ def record_bytes_per_shot(info) -> float:
 
 def kernel_sha() -> str:
     h = hashlib.sha256()
-    for f in ("kernels.cu", "kernels.cuh", "program.h"):
+    for f in ("kernels.cu", "kernels.cuh", "program.h", "affine_kernel.cu"):
         h.update(open(os.path.join(ROOT, "paper_2604_27058_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -287,15 +287,18 @@ def run_ours(args):
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h)}
         del hb
 
-    # roofline of the dominant kernel (the batched executor): algorithmic
-    # bytes = the records it must write, per launch, over its own event time
+    # roofline of the dominant kernel (the record-tile kernel of the k_max = 0
+    # path, else the batched executor): algorithmic bytes = the records it
+    # must write, over its own summed launch time
     peaks, peak_src = measured_peaks()
     alg = record_bytes_per_shot(info) * shots
     achieved = alg / (exec_ms / 1000.0) / 1e9
     tr = ncu_traffic(wname)
+    affine = info.k_max == 0 and "a=0" not in (args.tune or "")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": (tr * shots) if tr else None,
-            "kernel": "exec_batched", "peak_source": f"{peak_src} (hbm_gbs, burst copy)",
+            "kernel": "sample_affine" if affine else "exec_batched",
+            "peak_source": f"{peak_src} (hbm_gbs, burst copy)",
             "algorithmic_bytes_per_launch": alg, "kernel_ms": exec_ms, "call_ms": call_ms}
 
     if rank == 0:

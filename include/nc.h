@@ -96,8 +96,10 @@ typedef struct {
   double kernel_ms;       /* filled: device time of the whole sampling call
                              (fault bucketing, executors), CUDA events on
                              cuda_stream */
-  double exec_ms;         /* filled: device time of this program's executor
-                             launch alone, CUDA events on cuda_stream */
+  double exec_ms;         /* filled: device time of this program's dominant
+                             kernel (the executor, or the record-tile kernel
+                             of the k_max = 0 path), summed over its
+                             launches, CUDA events on cuda_stream */
   uint32_t launches;      /* filled: kernels this call launched for this
                              program (memsets and copies not counted) */
   uint32_t reserved;

@@ -27,8 +27,101 @@
 
 namespace nc {
 
-constexpr uint32_t kAffPool = 64;   // shots per warp
+constexpr uint32_t kAffPool = 64;   // shots per warp (fused sampling)
 constexpr uint32_t kAffList = 128;  // chunk items per warp list
+
+// One survival-jump draw from site st for `shot` (Sec. 3.2, integer form;
+// kernels.cuh jump_draw with the fault record loaded beside each Q[i] of
+// the scan). On a fault: *c0 / *nch = its column's chunk range, returns the
+// next start site (fault + 1). Otherwise *nch = 0 and returns the segment
+// end.
+__device__ __forceinline__ uint32_t aff_draw(const DevProg& p, uint2 key, uint64_t shot, uint32_t st, uint32_t* c0,
+                                             uint32_t* nch) {
+  const uint4 r0 = __ldg(reinterpret_cast<const uint4*>(p.srch) + 2 * st);
+  const uint4 r1 = __ldg(reinterpret_cast<const uint4*>(p.srch) + 2 * st + 1);
+  const uint4 w = philox(make_uint4((uint32_t)shot, (uint32_t)(shot >> 32), TAG_GAP, st), key);
+  const uint64_t u = (uint64_t)w.x | ((uint64_t)w.y << 32);
+  const uint64_t q_end = (uint64_t)r1.x | ((uint64_t)r1.y << 32);
+  const uint64_t tq = mulhi64(u, (uint64_t)r1.z | ((uint64_t)r1.w << 32));
+  *nch = 0;
+  if (q_end > tq) return r0.y;
+  uint32_t i = __ldg(p.guide + r0.z + guide_key_dev(tq, r0.w));
+  uint64_t qi = __ldg(p.q + i);
+  uint4 fr = __ldg(p.aff_frec + i);
+  while (qi > tq) {
+    i++;
+    qi = __ldg(p.q + i);
+    fr = __ldg(p.aff_frec + i);
+  }
+  const uint32_t opt = __umulhi(w.z, fr.y >> 28);
+  if (fr.z != 0xFFFFFFFFu) {
+    const uint64_t nib = (uint64_t)fr.x | ((uint64_t)(fr.y & 0x0FFFFFFFu) << 32);
+    *nch = (uint32_t)(nib >> (4 * opt)) & 15u;
+    uint64_t below = nib & ((1ull << (4 * opt)) - 1ull);
+    below = (below & 0x0F0F0F0F0F0F0F0Full) + ((below >> 4) & 0x0F0F0F0F0F0F0F0Full);
+    *c0 = fr.z + (uint32_t)((below * 0x0101010101010101ull) >> 56);
+  } else {
+    const uint32_t c = i * kRecPerSite + opt;
+    *c0 = __ldg(p.aff_col_off + c);
+    *nch = __ldg(p.aff_col_off + c + 1) - *c0;
+  }
+  return i + 1;
+}
+
+// Warp-inclusive prefix sum.
+__device__ __forceinline__ uint32_t warp_incl(uint32_t v, uint32_t lane) {
+#pragma unroll
+  for (uint32_t d = 1; d < 32; d <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= d) v += x;
+  }
+  return v;
+}
+
+// affine_items: fault sampling alone, at high occupancy (no record tile).
+// One warp per tile of `pool` shots (tile g of the launch = call-local shots
+// (tile0 + g) * pool ...), lanes refilled as their shots end; every fault's
+// chunk items (chunk << 10 | shot in the tile) go to
+// the pool's list items[g * cap ...], and counts[g] receives the number of
+// items (a count above cap means the list overflowed).
+__global__ void __launch_bounds__(512, 2) affine_items(LaunchParams L, uint32_t pool0, uint32_t n_pools,
+                                                       uint32_t* items, uint32_t cap, uint32_t* counts,
+                                                       uint32_t pool) {
+  const DevProg& p = L.p;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const uint2 key = key_of(L.seed);
+  for (uint32_t g = wg; g < n_pools; g += nw) {
+    const uint64_t s0 = (uint64_t)(pool0 + g) * pool;  // call-local first shot
+    const uint64_t left = s0 < L.shots ? L.shots - s0 : 0;
+    const uint32_t n = left < pool ? (uint32_t)left : pool;
+    uint32_t* out = items + (size_t)g * cap;
+    uint32_t sh = lane, nxt = 32, st = 0, cnt = 0;
+    bool live = sh < n && p.n_sites > 0;
+    while (__any_sync(0xffffffffu, live)) {
+      uint32_t c0 = 0, nch = 0;
+      bool fin = false;
+      if (live) {
+        st = aff_draw(p, key, L.shot_offset + s0 + sh, st, &c0, &nch);
+        fin = st >= p.n_sites;
+      }
+      const uint32_t incl = warp_incl(nch, lane);
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      const uint32_t it0 = sh;
+      for (uint32_t j = 0, pos = cnt + incl - nch; j < nch; j++, pos++)
+        if (pos < cap) out[pos] = ((c0 + j) << 10) | it0;
+      cnt += total;
+      const uint32_t done = __ballot_sync(0xffffffffu, fin);
+      if (fin) {
+        sh = nxt + __popc(done & ((1u << lane) - 1u));
+        st = 0;
+        live = sh < n;
+      }
+      nxt += __popc(done);
+    }
+    if (lane == 0) counts[g] = cnt;
+  }
+}
 
 template <int WPT>
 __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
@@ -92,8 +185,16 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
     __syncwarp();
   };
 
-  for (uint32_t tile = blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
+  for (uint32_t tile = L.tile0 + blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
     const uint64_t tile_s0 = L.shot_offset + (uint64_t)tile * S;  // a multiple of 128
+    // pre-sampled chunk items of this tile (affine_items), unless its list
+    // overflowed: then the tile samples its faults itself
+    const uint32_t* titems = nullptr;
+    uint32_t tcnt = 0;
+    if (L.aff_items) {
+      tcnt = L.aff_counts[tile - L.tile0];
+      if (tcnt <= L.aff_cap) titems = L.aff_items + (size_t)(tile - L.tile0) * L.aff_cap;
+    }
     // 1. random dormant measurement words
     constexpr uint32_t GR = WPT / 4;  // 128-shot groups per tile
     for (uint32_t i = t; i < NR * GR; i += T) {
@@ -130,8 +231,40 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
       for (uint32_t w = 0; w < WPT; w++) TILE[r * STR + w] = v[w];
     }
     __syncthreads();
-    // 3. fault sampling with lane refill; chunk items through the warp list
-    if (noisy) {
+    // 3a. apply the tile's pre-sampled items, four per thread at a time
+    if (noisy && titems) {
+      const uint32_t n = tcnt;
+      for (uint32_t i0 = 0; i0 < n; i0 += 4 * T) {
+        uint4 ch[4];
+        uint32_t sh[4];
+#pragma unroll
+        for (uint32_t u = 0; u < 4; u++) {
+          const uint32_t i = i0 + u * T + t;
+          if (i < n) {
+            const uint32_t it = __ldg(titems + i);
+            ch[u] = __ldg(p.aff_chunks + (it >> 10));
+            sh[u] = it & 1023u;
+          }
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < 4; u++) {
+          if (i0 + u * T + t < n) {
+            uint32_t* col = TILE + (sh[u] >> 5);
+            const uint32_t bit = 1u << (sh[u] & 31u);
+            atomicXor(col + (ch[u].x & 0xFFFFu) * STR, bit);
+            atomicXor(col + (ch[u].x >> 16) * STR, bit);
+            atomicXor(col + (ch[u].y & 0xFFFFu) * STR, bit);
+            atomicXor(col + (ch[u].y >> 16) * STR, bit);
+            atomicXor(col + (ch[u].z & 0xFFFFu) * STR, bit);
+            atomicXor(col + (ch[u].z >> 16) * STR, bit);
+            atomicXor(col + (ch[u].w & 0xFFFFu) * STR, bit);
+            atomicXor(col + (ch[u].w >> 16) * STR, bit);
+          }
+        }
+      }
+    }
+    // 3b. otherwise fault sampling with lane refill; chunk items through the warp list
+    if (noisy && !titems) {
       const uint64_t pool0 = (uint64_t)tile * S + warp * kAffPool;  // call-local first shot of the pool
       const uint64_t left = pool0 < L.shots ? L.shots - pool0 : 0;
       const uint32_t pool_n = left < kAffPool ? (uint32_t)left : kAffPool;
@@ -141,49 +274,11 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
         uint32_t c0 = 0, nch = 0;
         bool fin = false;
         if (live) {
-          // one survival-jump draw (kernels.cuh jump_draw, with the fault
-          // record loaded beside each Q[i] of the scan)
-          const uint64_t shot = L.shot_offset + pool0 + sh;
-          const uint4 r0 = __ldg(reinterpret_cast<const uint4*>(p.srch) + 2 * st);
-          const uint4 r1 = __ldg(reinterpret_cast<const uint4*>(p.srch) + 2 * st + 1);
-          const uint4 w = philox(make_uint4((uint32_t)shot, (uint32_t)(shot >> 32), TAG_GAP, st), key);
-          const uint64_t u = (uint64_t)w.x | ((uint64_t)w.y << 32);
-          const uint64_t q_end = (uint64_t)r1.x | ((uint64_t)r1.y << 32);
-          const uint64_t tq = mulhi64(u, (uint64_t)r1.z | ((uint64_t)r1.w << 32));
-          if (q_end > tq) {
-            st = r0.y;
-          } else {
-            uint32_t i = __ldg(p.guide + r0.z + guide_key_dev(tq, r0.w));
-            uint64_t qi = __ldg(p.q + i);
-            uint4 fr = __ldg(p.aff_frec + i);
-            while (qi > tq) {
-              i++;
-              qi = __ldg(p.q + i);
-              fr = __ldg(p.aff_frec + i);
-            }
-            const uint32_t opt = __umulhi(w.z, fr.y >> 28);
-            if (fr.z != 0xFFFFFFFFu) {
-              const uint64_t nib = (uint64_t)fr.x | ((uint64_t)(fr.y & 0x0FFFFFFFu) << 32);
-              nch = (uint32_t)(nib >> (4 * opt)) & 15u;
-              uint64_t below = nib & ((1ull << (4 * opt)) - 1ull);
-              below = (below & 0x0F0F0F0F0F0F0F0Full) + ((below >> 4) & 0x0F0F0F0F0F0F0F0Full);
-              c0 = fr.z + (uint32_t)((below * 0x0101010101010101ull) >> 56);
-            } else {
-              const uint32_t c = i * kRecPerSite + opt;
-              c0 = __ldg(p.aff_col_off + c);
-              nch = __ldg(p.aff_col_off + c + 1) - c0;
-            }
-            st = i + 1;
-          }
+          st = aff_draw(p, key, L.shot_offset + pool0 + sh, st, &c0, &nch);
           fin = st >= p.n_sites;
         }
         // warp prefix of the chunk counts
-        uint32_t incl = nch;
-#pragma unroll
-        for (uint32_t d = 1; d < 32; d <<= 1) {
-          const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
-          if (lane >= d) incl += v;
-        }
+        const uint32_t incl = warp_incl(nch, lane);
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         const uint32_t s_tile = warp * kAffPool + sh;
         if (cnt + total > kAffList) {
@@ -285,6 +380,14 @@ static cudaError_t aff_one(const LaunchParams& L, uint32_t grid, size_t smem, cu
   fn<<<grid, 16 * WPT, smem, st>>>(L);
   return cudaGetLastError();
 }
+
+// Item lists for the tiles [tile0, tile0 + n_tiles) of a call.
+cudaError_t launch_affine_items(const LaunchParams& L, uint32_t tile0, uint32_t n_tiles, uint32_t* items,
+                                uint32_t cap, uint32_t* counts, uint32_t tile_shots, uint32_t grid, cudaStream_t st) {
+  affine_items<<<grid, 512, 0, st>>>(L, tile0, n_tiles, items, cap, counts, tile_shots);
+  return cudaGetLastError();
+}
+
 
 // per_sm != null: report resident CTAs per SM instead of launching.
 cudaError_t launch_affine(const LaunchParams& L, uint32_t wpt, uint32_t grid, size_t smem, cudaStream_t st,

@@ -34,6 +34,8 @@ cudaError_t launch_presample(const LaunchParams& L, cudaStream_t st);
 size_t affine_smem_bytes(const DevProg& p, uint32_t wpt);
 cudaError_t launch_affine(const LaunchParams& L, uint32_t wpt, uint32_t grid, size_t smem, cudaStream_t st,
                           int* per_sm);
+cudaError_t launch_affine_items(const LaunchParams& L, uint32_t tile0, uint32_t n_tiles, uint32_t* items,
+                                uint32_t cap, uint32_t* counts, uint32_t tile_shots, uint32_t grid, cudaStream_t st);
 cudaError_t launch_bucket(const LaunchParams& L, uint32_t n_wt, uint32_t* ents, uint32_t* offs, uint64_t cap_total,
                           unsigned long long* total, uint32_t* ovf, cudaStream_t st);
 bool plain_supported(const DevProg& p);
@@ -163,18 +165,22 @@ struct Scratch {
 // Launch shape of the batched executor: G 32-shot words per tile, W words
 // per owner thread (G / W owners), T threads per CTA; B = 0 turns the
 // bucketed noise path off. A = 0 turns the record-level propagation path
-// (programs with k_max = 0) off; AW forces its 32-shot words per tile.
+// (programs with k_max = 0) off; AW forces its 32-shot words per tile; AI = 0
+// makes it sample faults inside the tile kernel instead of in a separate
+// high-occupancy pass; AV is the shots per pass pair (0: default); AC
+// overrides the item-list capacity per tile (tiles whose list overflows
+// sample in the tile kernel).
 struct Tuning {
-  uint32_t G, T, W, B, A, AW;
+  uint32_t G, T, W, B, A, AW, AI, AV, AC;
 };
 
 Tuning choose_tuning(const DevProg& d, const char* tune) {
   Tuning t;
-  if (d.k_max == 0) t = {128, 128, 1, 1, 1, 0};
-  else if (d.k_max <= 6) t = {32, 256, 1, 1, 1, 0};
-  else if (d.k_max <= 10) t = {8, 256, 1, 1, 1, 0};
-  else if (d.k_max <= 13) t = {2, 512, 1, 1, 1, 0};
-  else t = {1, 1024, 1, 1, 1, 0};
+  if (d.k_max == 0) t = {128, 128, 1, 1, 1, 0, 1, 0, 0};
+  else if (d.k_max <= 6) t = {32, 256, 1, 1, 1, 0, 1, 0, 0};
+  else if (d.k_max <= 10) t = {8, 256, 1, 1, 1, 0, 1, 0, 0};
+  else if (d.k_max <= 13) t = {2, 512, 1, 1, 1, 0, 1, 0, 0};
+  else t = {1, 1024, 1, 1, 1, 0, 1, 0, 0};
   if (tune) {
     unsigned v = 0;
     const char* s = tune;
@@ -185,6 +191,9 @@ Tuning choose_tuning(const DevProg& d, const char* tune) {
       else if (sscanf(s, "b=%u", &v) == 1) t.B = v;
       else if (sscanf(s, "a=%u", &v) == 1) t.A = v;
       else if (sscanf(s, "aw=%u", &v) == 1) t.AW = v;
+      else if (sscanf(s, "ai=%u", &v) == 1) t.AI = v;
+      else if (sscanf(s, "av=%u", &v) == 1) t.AV = v;
+      else if (sscanf(s, "ac=%u", &v) == 1) t.AC = v;
       const char* c = strchr(s, ',');
       if (!c) break;
       s = c + 1;
@@ -201,6 +210,23 @@ Tuning choose_tuning(const DevProg& d, const char* tune) {
 
 bool pow2(uint32_t v) { return v && !(v & (v - 1)); }
 
+// Per-call scratch comes from the device's default stream-ordered pool. By
+// default the pool hands freed memory back at every synchronisation, so a
+// call would map its scratch (up to a few GB) anew each time; keeping it
+// cached in the pool makes the next call's allocation free. This changes
+// only this process's default pool, once per device.
+void keep_pool_memory(int dev) {
+  static std::mutex mu;
+  static std::vector<int> done;
+  std::lock_guard<std::mutex> g(mu);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+  done.push_back(dev);
+  cudaMemPool_t pool = nullptr;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+  uint64_t keep = ~0ull;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+}
+
 // Get (uploading once) the device copy of a program for the current device.
 nc_status device_copy(nc_program* p, DevCopy** out) {
   int dev = 0;
@@ -212,6 +238,7 @@ nc_status device_copy(nc_program* p, DevCopy** out) {
     }
   DevCopy c;
   c.device = dev;
+  keep_pool_memory(dev);
   cudaError_t e = cudaMalloc(&c.blob, p->cp.blob.size());
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaMemcpy(c.blob, p->cp.blob.data(), p->cp.blob.size(), cudaMemcpyHostToDevice);
@@ -231,8 +258,29 @@ struct CallOut {
 // Optional per-program timing: events around the executor launch and the
 // number of kernels launched.
 struct Timing {
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::vector<cudaEvent_t> ev;  // pairs around each launch of the dominant kernel
   uint32_t launches = 0;
+  cudaError_t begin(cudaStream_t s) { return mark(s); }
+  cudaError_t end(cudaStream_t s) { return mark(s); }
+  cudaError_t mark(cudaStream_t s) {
+    cudaEvent_t e = nullptr;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    ev.push_back(e);
+    return cudaEventRecord(e, s);
+  }
+  // summed device time of the bracketed launches (after the stream synced)
+  float ms() const {
+    float tot = 0.f;
+    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+      float x = 0.f;
+      if (cudaEventElapsedTime(&x, ev[i], ev[i + 1]) == cudaSuccess) tot += x;
+    }
+    return tot;
+  }
+  ~Timing() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
 };
 
 // Enqueue one sampling launch. kept_count must point to a zeroed device u64.
@@ -269,10 +317,10 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
       size_t bytes = ((size_t)1 << h.k_max) * padded * sizeof(double) * 2;
       NC_TRY(scratch.get(&L.work, bytes));
     }
-    if (tm) NC_TRY(cudaEventRecord(tm->e0, stream));
+    if (tm) NC_TRY(tm->begin(stream));
     NC_TRY(launch_plain(L, stream));
     if (tm) {
-      NC_TRY(cudaEventRecord(tm->e1, stream));
+      NC_TRY(tm->end(stream));
       tm->launches += 1;
     }
   } else {
@@ -300,13 +348,47 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
       }
       if (wpt) {
         const size_t smem = affine_smem_bytes(L.p, wpt);
-        L.n_tiles = (uint32_t)((L.row_words32 + wpt - 1) / wpt);
-        const uint64_t grid = std::min<uint64_t>(L.n_tiles, (uint64_t)best_ctas * n_sm);
-        if (tm) NC_TRY(cudaEventRecord(tm->e0, stream));
-        NC_TRY(launch_affine(L, wpt, (uint32_t)grid, smem, stream, nullptr));
-        if (tm) {
-          NC_TRY(cudaEventRecord(tm->e1, stream));
-          tm->launches += 1;
+        const uint32_t n_tiles = (uint32_t)((L.row_words32 + wpt - 1) / wpt);
+        const uint32_t tile_shots = 32 * wpt;
+        // faults sampled by affine_items in passes of `wave` tiles, each
+        // followed by the tile kernel on the same tiles
+        const bool items = tu.AI && !(lflags & LF_NOISELESS) && h.n_sites > 0;
+        uint32_t wave = n_tiles;
+        uint32_t cap = 0;
+        uint32_t *ibuf = nullptr, *cbuf = nullptr;
+        if (items) {
+          const uint64_t wave_shots = tu.AV ? tu.AV : (8ull << 20);
+          wave = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, wave_shots / tile_shots));
+          // list capacity per tile: mean + 10 sigma (a chunk count per fault
+          // of at most 15, so the variance is below 16 x the mean) + slack
+          const double mean = (double)h.aff_chunks_per_shot * tile_shots;
+          cap = (uint32_t)(mean * 1.1 + 10.0 * std::sqrt(mean * 16.0) + 64.0);
+          if (tu.AC) cap = tu.AC;
+          void *a = nullptr, *b = nullptr;
+          NC_TRY(scratch.get(&a, (size_t)wave * cap * 4));
+          NC_TRY(scratch.get(&b, (size_t)wave * 4));
+          ibuf = (uint32_t*)a;
+          cbuf = (uint32_t*)b;
+        }
+        for (uint32_t t0 = 0; t0 < n_tiles; t0 += wave) {
+          const uint32_t nt = std::min(wave, n_tiles - t0);
+          L.tile0 = t0;
+          L.n_tiles = t0 + nt;
+          if (items) {
+            const uint32_t grid = std::min<uint32_t>((nt + 15) / 16, 2 * (uint32_t)n_sm);
+            NC_TRY(launch_affine_items(L, t0, nt, ibuf, cap, cbuf, tile_shots, grid, stream));
+            L.aff_items = ibuf;
+            L.aff_counts = cbuf;
+            L.aff_cap = cap;
+            if (tm) tm->launches += 1;
+          }
+          const uint64_t grid = std::min<uint64_t>(nt, (uint64_t)best_ctas * n_sm);
+          if (tm) NC_TRY(tm->begin(stream));
+          NC_TRY(launch_affine(L, wpt, (uint32_t)grid, smem, stream, nullptr));
+          if (tm) {
+            NC_TRY(tm->end(stream));
+            tm->launches += 1;
+          }
         }
         return NC_OK;
       }
@@ -387,10 +469,10 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
         if (tm) tm->launches += 1;
       }
     }
-    if (tm) NC_TRY(cudaEventRecord(tm->e0, stream));
+    if (tm) NC_TRY(tm->begin(stream));
     NC_TRY(launch_batched(L, fp64, tu.W, bk, (uint32_t)grid, tu.T, smem, stream));
     if (tm) {
-      NC_TRY(cudaEventRecord(tm->e1, stream));
+      NC_TRY(tm->end(stream));
       tm->launches += 1;
     }
   }
@@ -514,11 +596,6 @@ nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, con
     if (ev0) cudaEventDestroy(ev0);
     return NC_E_CUDA;
   }
-  for (auto& tm : tms)
-    if (cudaEventCreate(&tm.e0) != cudaSuccess || cudaEventCreate(&tm.e1) != cudaSuccess) {
-      st = NC_E_CUDA;
-      goto done;
-    }
   {
     Scratch scratch(stream);
     void* counters = nullptr;
@@ -565,18 +642,12 @@ nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, con
     outs[i].shots_run = shots[i];
     outs[i].shots_kept = kept[i];
     outs[i].kernel_ms = kernel_ms;
-    float ems = 0.f;
-    if (shots[i] == 0 || cudaEventElapsedTime(&ems, tms[i].e0, tms[i].e1) != cudaSuccess) ems = 0.f;
-    outs[i].exec_ms = ems;
+    outs[i].exec_ms = shots[i] ? tms[i].ms() : 0.0;
     outs[i].launches = tms[i].launches;
   }
 done:
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
-  for (auto& tm : tms) {
-    if (tm.e0) cudaEventDestroy(tm.e0);
-    if (tm.e1) cudaEventDestroy(tm.e1);
-  }
   return st;
 }
 

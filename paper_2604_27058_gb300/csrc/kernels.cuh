@@ -75,6 +75,12 @@ struct LaunchParams {
   // boffs[wt*(nb+1)+k+1]); an entry is (option record << 10) | shot in tile.
   const uint32_t* bents;
   const uint32_t* boffs;
+  // record-level propagation sampler: first tile of this launch and the
+  // pre-sampled chunk items of its tiles (null: sample in the kernel)
+  uint32_t tile0;
+  const uint32_t* aff_items;
+  const uint32_t* aff_counts;
+  uint32_t aff_cap;
   uint32_t stop_event;                // debug: stop before this event (0xffffffff = never)
   uint64_t dump_shot;                 // debug: call-local shot index
   double* dump_amps;

@@ -144,12 +144,14 @@ def test_surface_code_bit_exact(nc, precision, tune):
     assert int(g["det"].sum()) > 0
 
 
-@pytest.mark.parametrize("tune", [None, "aw=8", "a=0", "a=0,g=64,t=64", "a=0,b=0"])
+@pytest.mark.parametrize("tune", [None, "aw=8", "ai=0", "ac=100", "av=2048", "a=0", "a=0,g=64,t=64", "a=0,b=0"])
 def test_surface_code_many_warp_tiles(nc, tune):
     """Several tiles and a ragged last tile: the record-level propagation
-    sampler (default for k_max = 0), the executor with bucketed noise (a=0)
-    and with per-shot noise (a=0,b=0) give the oracle's records on shots
-    spread over every tile."""
+    sampler (default for k_max = 0; faults sampled in a separate pass, or in
+    the tile kernel with ai=0, or after an item list overflows with ac=100,
+    or in passes of 2048 shots with av=2048), the executor with bucketed
+    noise (a=0) and with per-shot noise (a=0,b=0) give the oracle's records
+    on shots spread over every tile."""
     text = gc.surface_code_memory(d=5, rounds=25, p=1e-3)
     prog = nc.compile(text)
     sim = FrameSim(text)
@@ -175,8 +177,10 @@ def test_affine_sampler_equals_executor(nc, name):
     for shots, off in ((100_003, 0), (777, 128 * 5)):
         a = nc.sample(prog, shots, 99, shot_offset=off)
         b = nc.sample(prog, shots, 99, shot_offset=off, tune="a=0")
+        c = nc.sample(prog, shots, 99, shot_offset=off, tune="ai=0")
         for key, n in rows.items():
             assert torch_equal(a[key][:n], b[key][:n]), key
+            assert torch_equal(a[key][:n], c[key][:n]), key
         assert a["shots_kept"] == b["shots_kept"] == shots
 
 
