@@ -11,14 +11,17 @@
 // shot's random measurement bits and f its fault indicators. This pass finds
 // const, A and F by running the compiled program on 64 probe lanes at a time
 // (lane = "no fault, all m = 0", "only m_j = 1", or "only fault option f")
-// and XORing each lane's rows with the baseline's. The sampler then needs,
-// per shot, only its faults and its random bits; the frame work is done once
-// here instead of once per shot.
+// and XORing each lane's rows with the baseline's, then rewrites rows that
+// overlap an earlier row as differences (chains of delta rows), which makes
+// the fault columns short. The sampler then needs, per shot, only its
+// faults and its random bits; the frame work is done once here instead of
+// once per shot.
 //
 // The probe interpreter follows the bytecode as the executors run it
 // (program.h); it never runs on a program with active-array instructions.
 #include <algorithm>
 #include <cstring>
+#include <iterator>
 #include <vector>
 
 #include "compiler.h"
@@ -268,6 +271,79 @@ void append_affine(std::vector<uint8_t>& blob) {
     }
   }
 
+  // ---- delta rows ----
+  // A row that shares most of its support with an earlier row is stored as
+  // the difference: row r = delta_r ^ row parent(r). Each row is the parent
+  // of at most one row, so parents form chains that the sampler resolves
+  // with one running XOR per chain and word. In a memory experiment a
+  // stabiliser's measurement in round t then differs from round t - 1 by its
+  // detector's few faults, instead of carrying every earlier fault.
+  constexpr uint32_t kNone = 0xFFFFFFFFu;
+  std::vector<uint32_t> parent(R, kNone), child(R, kNone);
+  {
+    const uint32_t n_cols = (uint32_t)col_rows.size();
+    auto rows_of = [&](uint32_t x) -> const std::vector<uint32_t>& {
+      return x < n_cols ? col_rows[x] : rand_rows[x - n_cols];
+    };
+    std::vector<std::vector<uint32_t>> F(R);  // row -> ascending supports (faults, then random events)
+    for (uint32_t c = 0; c < n_cols; c++)
+      for (uint32_t r : col_rows[c]) F[r].push_back(c);
+    for (uint32_t j = 0; j < rand_rows.size(); j++)
+      for (uint32_t r : rand_rows[j]) F[r].push_back(n_cols + j);
+    std::vector<uint32_t> cnt(R, 0), touched;
+    for (uint32_t r = 0; r < R; r++) {
+      if (F[r].empty()) continue;
+      touched.clear();
+      for (uint32_t x : F[r])
+        for (uint32_t p : rows_of(x)) {
+          if (p >= r) break;
+          if (child[p] != kNone) continue;
+          if (!cnt[p]++) touched.push_back(p);
+        }
+      uint32_t best = kNone;
+      int64_t best_gain = 0;
+      for (uint32_t p : touched) {
+        // |F_r| - |F_r ^ F_p| = 2 |F_r & F_p| - |F_p|
+        const int64_t gain = 2 * (int64_t)cnt[p] - (int64_t)F[p].size();
+        if (gain > best_gain || (gain == best_gain && gain > 0 && p > best)) {
+          best_gain = gain;
+          best = p;
+        }
+        cnt[p] = 0;
+      }
+      if (best != kNone) {
+        parent[r] = best;
+        child[best] = r;
+      }
+    }
+    // supports in delta form, then the columns again (rows ascending)
+    for (auto& v : col_rows) v.clear();
+    for (auto& v : rand_rows) v.clear();
+    std::vector<uint32_t> d;
+    for (uint32_t r = 0; r < R; r++) {
+      d.clear();
+      if (parent[r] == kNone) d = F[r];
+      else std::set_symmetric_difference(F[r].begin(), F[r].end(), F[parent[r]].begin(), F[parent[r]].end(),
+                                         std::back_inserter(d));
+      for (uint32_t x : d) {
+        if (x < n_cols) col_rows[x].push_back(r);
+        else rand_rows[x - n_cols].push_back(r);
+      }
+    }
+    // constants in delta form (parents come first: fix from the last row down)
+    for (uint32_t r = R; r-- > 0;)
+      if (parent[r] != kNone) base.rows[r] ^= base.rows[parent[r]];
+  }
+  // chains of two or more rows, head first
+  std::vector<uint32_t> chain_off, chain;
+  for (uint32_t r = 0; r < R; r++) {
+    if (parent[r] != kNone || child[r] == kNone) continue;
+    chain_off.push_back((uint32_t)chain.size());
+    for (uint32_t x = r; x != kNone; x = child[x]) chain.push_back(x);
+  }
+  const uint32_t n_chains = (uint32_t)chain_off.size();
+  chain_off.push_back((uint32_t)chain.size());
+
   // row-major random-event lists
   std::vector<uint32_t> rowev_off(R + 1, 0), rowev;
   {
@@ -340,6 +416,10 @@ void append_affine(std::vector<uint8_t>& blob) {
   h.off_aff_col_off = place((uint64_t)col_off.size() * 4);
   h.off_aff_col = place((uint64_t)chunks.size() * 2);
   h.off_aff_frec = place((uint64_t)frec.size() * 4);
+  h.off_aff_parent = place((uint64_t)R * 4);
+  h.off_aff_chain_off = place((uint64_t)chain_off.size() * 4);
+  h.off_aff_chain = place((uint64_t)chain.size() * 4);
+  h.aff_n_chains = n_chains;
   h.total_bytes = off;
   h.aff_ok = 1;
   h.aff_rows = R;
@@ -357,6 +437,9 @@ void append_affine(std::vector<uint8_t>& blob) {
   cp(h.off_aff_col_off, col_off.data(), col_off.size() * 4);
   cp(h.off_aff_col, chunks.data(), chunks.size() * 2);
   cp(h.off_aff_frec, frec.data(), frec.size() * 4);
+  cp(h.off_aff_parent, parent.data(), parent.size() * 4);
+  cp(h.off_aff_chain_off, chain_off.data(), chain_off.size() * 4);
+  cp(h.off_aff_chain, chain.data(), chain.size() * 4);
   std::memcpy(blob.data(), &h, sizeof(h));
 }
 

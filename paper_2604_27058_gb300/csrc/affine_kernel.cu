@@ -16,7 +16,9 @@
 //      every fault appends its column's 8-row chunks to the warp's list, and
 //      the warp applies a full list one chunk per lane: eight shared-memory
 //      atomic XORs of the shot's bit;
-//   4. the tile is written out row by row (16-byte stores when the rows
+//   4. rows kept as differences from a parent row (short fault columns) are
+//      turned back into record rows by a running XOR down each chain;
+//   5. the tile is written out row by row (16-byte stores when the rows
 //      allow), bits of shots past the end cleared, plus the kept row.
 // The records equal those of the executors bit for bit: same draws, same
 // faults, and the tables are the executors' own frame updates propagated to
@@ -209,9 +211,16 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
     }
     __syncthreads();
     // 2. constants, reference parities and random-bit terms, one row per thread
+    auto ref = [&](uint32_t r) -> uint32_t {
+      return r < p.n_meas || r >= R ? 0u
+             : r < n_det_end       ? __ldg(p.det_ref + (r - p.n_meas))
+                                   : __ldg(p.obs_ref + (r - n_det_end));
+    };
     for (uint32_t r = t; r < R; r += T) {
-      uint32_t c = __ldg(p.aff_const + r);
-      if (r >= p.n_meas) c ^= r < n_det_end ? __ldg(p.det_ref + (r - p.n_meas)) : __ldg(p.obs_ref + (r - n_det_end));
+      // delta form: the reference parities of the row and of its parent
+      uint32_t c = __ldg(p.aff_const + r) ^ ref(r);
+      const uint32_t par = __ldg(p.aff_parent + r);
+      if (par != 0xFFFFFFFFu) c ^= ref(par);
       uint32_t v[WPT];
 #pragma unroll
       for (uint32_t w = 0; w < WPT; w++) v[w] = (c & 1u) ? ~0u : 0u;
@@ -301,6 +310,33 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
         nxt += __popc(done);
       }
       flush(cnt);
+    }
+    __syncthreads();
+    // delta rows to record rows: a running XOR down each chain, per word
+    for (uint32_t i = t; i < p.aff_n_chains * WPT; i += T) {
+      const uint32_t ch = i / WPT, w = i % WPT;
+      const uint32_t j0 = __ldg(p.aff_chain_off + ch), j1 = __ldg(p.aff_chain_off + ch + 1);
+      uint32_t v = 0, j = j0;
+      for (; j + 4 <= j1; j += 4) {  // four rows' loads in flight
+        uint32_t* x0 = TILE + __ldg(p.aff_chain + j) * STR + w;
+        uint32_t* x1 = TILE + __ldg(p.aff_chain + j + 1) * STR + w;
+        uint32_t* x2 = TILE + __ldg(p.aff_chain + j + 2) * STR + w;
+        uint32_t* x3 = TILE + __ldg(p.aff_chain + j + 3) * STR + w;
+        const uint32_t a0 = *x0, a1 = *x1, a2 = *x2, a3 = *x3;
+        v ^= a0;
+        *x0 = v;
+        v ^= a1;
+        *x1 = v;
+        v ^= a2;
+        *x2 = v;
+        v ^= a3;
+        *x3 = v;
+      }
+      for (; j < j1; j++) {
+        uint32_t* x = TILE + __ldg(p.aff_chain + j) * STR + w;
+        v ^= *x;
+        *x = v;
+      }
     }
     __syncthreads();
     // 4. rows out, then the kept row: four words per thread (16-byte stores)

@@ -105,6 +105,10 @@ DevProg dev_view(const ProgHeader& h, const uint8_t* base) {
     d.aff_col_off = reinterpret_cast<const uint32_t*>(base + h.off_aff_col_off);
     d.aff_chunks = reinterpret_cast<const uint4*>(base + h.off_aff_col);
     d.aff_frec = reinterpret_cast<const uint4*>(base + h.off_aff_frec);
+    d.aff_parent = reinterpret_cast<const uint32_t*>(base + h.off_aff_parent);
+    d.aff_chain_off = reinterpret_cast<const uint32_t*>(base + h.off_aff_chain_off);
+    d.aff_chain = reinterpret_cast<const uint32_t*>(base + h.off_aff_chain);
+    d.aff_n_chains = h.aff_n_chains;
     d.aff_chunks_per_shot = h.aff_chunks_per_shot;
     d.aff_rows = h.aff_rows;
     d.aff_n_rand = h.aff_n_rand;
@@ -702,7 +706,8 @@ nc_status nc_program_deserialize(const void* buf, size_t len, nc_program** out) 
                      h.off_site_eff, h.off_slot_list, h.off_det_ref, h.off_obs_ref,
                      h.off_site_opt, h.off_opt_tab, h.off_plist, h.off_orec, h.off_site_blk,
                      h.off_aff_const, h.off_aff_rowev_off, h.off_aff_rowev, h.off_aff_rand_ev,
-                     h.off_aff_col_off, h.off_aff_col, h.off_aff_frec, h.off_srch, h.off_guide};
+                     h.off_aff_col_off, h.off_aff_col, h.off_aff_frec, h.off_aff_parent, h.off_aff_chain_off,
+                     h.off_aff_chain, h.off_srch, h.off_guide};
   for (uint64_t o : offs)
     if (o > h.total_bytes || (o & 15)) return NC_E_ARG;
   if (h.off_ops + (uint64_t)h.n_ops * sizeof(Op) > h.total_bytes || h.k_max > kMaxK || h.n_qubits > kMaxQubits)

@@ -32,11 +32,14 @@ struct DevProg {
   const uint32_t* aff_col_off;
   const uint4* aff_chunks;
   const uint4* aff_frec;
+  const uint32_t* aff_parent;
+  const uint32_t* aff_chain_off;
+  const uint32_t* aff_chain;
   const uint32_t* srch;   // SrchRec per site (program.h)
   const uint32_t* guide;
   uint32_t n_qubits, nw, n_ops, n_sites, n_slots, k_max, kept_slot;
   uint32_t n_meas, n_det, n_obs, n_blocks;
-  uint32_t aff_rows, aff_n_rand;
+  uint32_t aff_rows, aff_n_rand, aff_n_chains;
   float aff_chunks_per_shot;
 };
 

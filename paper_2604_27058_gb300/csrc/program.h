@@ -104,11 +104,12 @@ struct ProgHeader {
   uint32_t aff_rows, aff_n_rand;   // rows = n_meas + n_det + n_obs; random dormant measurements
   uint32_t aff_n_chunks;           // 8-row chunks of the fault columns
   float aff_chunks_per_shot;       // expected chunks of a shot's faults
-  uint32_t n_guide, pad2;          // survival guide-table entries
+  uint32_t n_guide;                // survival guide-table entries
+  uint32_t aff_n_chains;           // delta-row chains of two or more rows
   uint64_t off_ops, off_masks, off_q, off_seg_start, off_seg_end, off_site_info, off_site_eff,
       off_slot_list, off_det_ref, off_obs_ref, off_site_opt, off_opt_tab, off_plist, off_orec, off_site_blk,
       off_aff_const, off_aff_rowev_off, off_aff_rowev, off_aff_rand_ev, off_aff_col_off, off_aff_col,
-      off_aff_frec, off_srch, off_guide, total_bytes;
+      off_aff_frec, off_aff_parent, off_aff_chain_off, off_aff_chain, off_srch, off_guide, total_bytes;
 };
 // Survival-jump search (Sec. 3.2 jump, integer form). srch[st] (32 bytes)
 // holds, for a jump starting at site st: the segment [a, b), its guide-table
@@ -145,6 +146,12 @@ inline uint32_t guide_key(uint64_t t, uint32_t shift) {
 //   rand_ev: u32 event per ordinal; col_off: n_sites * kRecPerSite + 1 u32
 //   chunk offsets; col: chunks of 8 u16 rows (16 bytes), each column's rows
 //   ascending and padded with row index `rows` (a scratch row).
+//   Rows are stored in delta form: the value above is delta_r, and the
+//   record row is delta_r ^ (record row parent[r]) (parent 0xFFFFFFFF: none);
+//   chain_off / chain list each chain of two or more rows head first, so a
+//   running XOR down a chain turns deltas into rows. Detector and
+//   observable reference parities apply to record rows, so delta_r takes
+//   ref(r) ^ ref(parent[r]).
 //   frec: 16 bytes per site, so that one load after the search gives a
 //   fault's chunk range: words 0-1 hold 4-bit chunk counts of options 0..14
 //   (bits 60..63: the option count K), word 2 the first chunk of option 0

@@ -17,12 +17,12 @@ from oracle.records import raw_parities
 from oracle.stabilizer import FrameSim
 
 HEAD = "<17If8I"  # 17 counts, mean_faults, n_blocks, aff_ok, aff_rows, aff_n_rand, aff_n_chunks,
-                  # aff_chunks_per_shot (read as u32), n_guide, pad
+                  # aff_chunks_per_shot (read as u32), n_guide, aff_n_chains
 HEAD_BYTES = struct.calcsize(HEAD)
 OFF_NAMES = ["ops", "masks", "q", "seg_start", "seg_end", "site_info", "site_eff", "slot_list", "det_ref",
              "obs_ref", "site_opt", "opt_tab", "plist", "orec", "site_blk", "aff_const", "aff_rowev_off",
-             "aff_rowev", "aff_rand_ev", "aff_col_off", "aff_col", "aff_frec", "srch", "guide",
-             "total_bytes"]
+             "aff_rowev", "aff_rand_ev", "aff_col_off", "aff_col", "aff_frec", "aff_parent", "aff_chain_off",
+             "aff_chain", "srch", "guide", "total_bytes"]
 REC_PER_SITE = 15
 
 
@@ -60,7 +60,15 @@ def _tables(blob: bytes):
             continue
         assert int(frec[s, 2]) == int(col_off[s * REC_PER_SITE])
         assert [(nib >> (4 * o)) & 15 for o in range(kk)] == counts
+    n_chains = u[25]
+    chain_off = arr("aff_chain_off", n_chains + 1)
+    chains = [arr("aff_chain", int(chain_off[-1]))[chain_off[i]:chain_off[i + 1]] for i in range(n_chains)]
+    parent = arr("aff_parent", rows)
+    for ch in chains:  # chains follow parent links, head first
+        assert parent[ch[0]] == 0xFFFFFFFF
+        assert all(parent[ch[j]] == ch[j - 1] for j in range(1, len(ch)))
     return {
+        "chains": chains,
         "rows": rows, "n_meas": n_meas, "n_det": n_det,
         "const": arr("aff_const", rows),
         "rowev_off": arr("aff_rowev_off", rows + 1),
@@ -82,6 +90,11 @@ def _rows(t, faults, m):
             for r in ch:
                 if r != t["rows"]:  # padding entries name the scratch row
                     v[r] ^= 1
+    for ch in t["chains"]:  # delta rows to record rows
+        acc = 0
+        for r in ch:
+            acc ^= int(v[r])
+            v[r] = acc
     return v
 
 
