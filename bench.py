@@ -148,11 +148,16 @@ def cpu_oracle_rate(text: str, seed: int, budget_s: float, cores: int):
     """Shots/s of the oracle on `cores` processes over a bounded sample."""
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores, initializer=_oracle_init, initargs=(text,)) as pool:
-        # warm every worker, then calibrate on 16 shots per worker
-        pool.map(_oracle_chunk, [(seed, 20_000_000 + i * 2, 2) for i in range(cores)])
+        # warm every worker on one shot (which also calibrates slow
+        # workloads), then calibrate on up to 16 shots per worker
         t0 = time.perf_counter()
-        pool.map(_oracle_chunk, [(seed, 10_000_000 + i * 16, 16) for i in range(cores)])
-        per_shot = (time.perf_counter() - t0) / 16
+        pool.map(_oracle_chunk, [(seed, 20_000_000 + i, 1) for i in range(cores)])
+        per_shot = time.perf_counter() - t0
+        n_cal = max(0, min(16, int(budget_s / 4 / max(per_shot, 1e-6))))
+        if n_cal:
+            t0 = time.perf_counter()
+            pool.map(_oracle_chunk, [(seed, 10_000_000 + i * 16, n_cal) for i in range(cores)])
+            per_shot = (time.perf_counter() - t0) / n_cal
         per_worker = max(1, int(budget_s / max(per_shot, 1e-6)))
         t0 = time.perf_counter()
         done = sum(pool.map(_oracle_chunk, [(seed, i * per_worker, per_worker) for i in range(cores)]))
@@ -218,7 +223,8 @@ def run_ours(args):
     prog = nc.compile(text)
     info = prog.info
     bufs = nc.alloc_records(prog, shots)
-    offset = rank * ((shots + 127) // 128) * 128
+    from paper_2604_27058_gb300 import shard
+    offset, shots = shard.weak(shots, rank)
     stream = torch.cuda.current_stream()
 
     def step(precision="fp32", out=None, host=False):
@@ -271,11 +277,37 @@ def run_ours(args):
 
     fp64 = None
     if not args.no_fp64:
+        # the plain form keeps one 2^k FP64 vector per shot in global memory;
+        # past k = 14 that no longer fits for a whole launch, and the FP64
+        # batched executor stands in for it
+        plain = info.k_max <= 14
         p_steps = max(1, min(args.steps, 3))
-        ms64, tk64, _, _ = timed("fp64", p_steps, 1)
+        ms64, tk64, _, _ = timed("fp64" if plain else "fp64_batched", p_steps, 1)
         fp64 = {"value": shots * world * p_steps / (ms64 / 1000.0), "unit": "shots/s",
                 "ms_per_step": ms64 / p_steps, "exec_ms": statistics.mean(tk64["exec_ms"]),
-                "executor": "exec_plain (one thread per shot, FP64)"}
+                "executor": "exec_plain (one thread per shot, FP64)" if plain
+                else "exec_batched<double> (FP64 batched; the plain form does not fit at this k)"}
+
+    # FP32 error: the batched FP32 state against the FP64 batched state of the
+    # same shots, just before the first measurement event (norm-wise relative
+    # error modulo global phase; max-abs amplitude error beside it)
+    fp32_err = None
+    if info.k_max > 0 and rank == 0 and not args.no_fp64:
+        import numpy as np
+        errs, aerr, kk = [], [], 0
+        for s in range(4):
+            _, _, p32, k32 = nc.debug_dump(prog, 2002, s, 0, precision="fp32")
+            _, _, p64, k64 = nc.debug_dump(prog, 2002, s, 0, precision="fp64_batched")
+            if k32 != k64 or k32 == 0:
+                continue
+            ov = np.vdot(p64, p32)
+            ph = ov / abs(ov) if abs(ov) > 0 else 1.0
+            errs.append(float(np.linalg.norm(p32 - ph * p64) / np.linalg.norm(p64)))
+            aerr.append(float(np.max(np.abs(p32 - ph * p64))))
+            kk = k32
+        if errs:
+            fp32_err = {"state_rel_l2_max": max(errs), "amp_abs_max": max(aerr), "k": kk, "shots": len(errs),
+                        "at": "before measurement event 0", "vs": "FP64 batched executor, same shots"}
 
     e2e = None
     if not args.no_e2e:
@@ -316,6 +348,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "fp64_plain": fp64,
+            "fp32_error": fp32_err,
             "gpu_launches": tk["launches"],
             "clocks": ck,
             "shots_kept_last_step": last["shots_kept"],

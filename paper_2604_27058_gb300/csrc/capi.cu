@@ -316,16 +316,26 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
   L.dump_k = dump_k;
   if (precision == NC_FP64_PLAIN) {
     if (!plain_supported(L.p)) return NC_E_UNSUPPORTED;
+    // one FP64 vector of 2^k amplitudes per shot: launches over shot ranges
+    // whose vectors fit in a quarter of the free memory
     const uint64_t padded = L.row_words32 * 32;
+    uint64_t chunk = padded;
     if (h.k_max > 0) {
-      size_t bytes = ((size_t)1 << h.k_max) * padded * sizeof(double) * 2;
-      NC_TRY(scratch.get(&L.work, bytes));
+      size_t free_b = 0, total_b = 0;
+      NC_TRY(cudaMemGetInfo(&free_b, &total_b));
+      const uint64_t per_shot = ((uint64_t)1 << h.k_max) * sizeof(double) * 2;
+      chunk = std::min<uint64_t>(padded, std::max<uint64_t>(128, (free_b / 4 / per_shot) & ~127ull));
+      NC_TRY(scratch.get(&L.work, per_shot * chunk));
     }
-    if (tm) NC_TRY(tm->begin(stream));
-    NC_TRY(launch_plain(L, stream));
-    if (tm) {
-      NC_TRY(tm->end(stream));
-      tm->launches += 1;
+    for (uint64_t b0 = 0; b0 < padded; b0 += chunk) {
+      L.plain_base = b0;
+      L.plain_n = std::min(chunk, padded - b0);
+      if (tm) NC_TRY(tm->begin(stream));
+      NC_TRY(launch_plain(L, stream));
+      if (tm) {
+        NC_TRY(tm->end(stream));
+        tm->launches += 1;
+      }
     }
   } else {
     Tuning tu = choose_tuning(L.p, tune);

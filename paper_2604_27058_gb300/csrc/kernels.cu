@@ -1119,9 +1119,10 @@ constexpr uint32_t kPlainMaxSlots = 2048;
 
 __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
   const DevProg& p = L.p;
-  const uint64_t sl = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // this launch covers call-local shots [plain_base, plain_base + plain_n)
+  const uint64_t sl = L.plain_base + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t padded = L.row_words32 * 32u;
-  if ((sl & ~31ull) >= padded) return;  // whole warps only
+  if ((sl & ~31ull) >= padded || sl - L.plain_base >= L.plain_n) return;  // whole warps only
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t word = sl >> 5;
   const bool valid = sl < L.shots;
@@ -1131,8 +1132,8 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
   for (uint32_t w = 0; w < kPlainMaxW; w++) x[w] = z[w] = 0;
   for (uint32_t w = 0; w < kPlainMaxSlots / 32; w++) slots[w] = 0;
   double2* A = reinterpret_cast<double2*>(L.work);
-  const uint64_t stride = padded;
-  auto amp = [&](uint32_t i) -> double2& { return A[(size_t)i * stride + sl]; };
+  const uint64_t stride = L.plain_n;
+  auto amp = [&](uint32_t i) -> double2& { return A[(size_t)i * stride + (sl - L.plain_base)]; };
   auto getb = [](const uint32_t* v, uint32_t q) -> uint32_t { return (v[q >> 5] >> (q & 31)) & 1u; };
   auto setb = [](uint32_t* v, uint32_t q, uint32_t b) {
     v[q >> 5] = (v[q >> 5] & ~(1u << (q & 31))) | (b << (q & 31));
@@ -1471,9 +1472,8 @@ cudaError_t batched_occupancy(bool fp64, uint32_t W, bool bk, uint32_t threads, 
 }
 
 cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st) {
-  const uint64_t padded = L.row_words32 * 32u;
   const uint32_t threads = 128;
-  const uint64_t blocks = (padded + threads - 1) / threads;
+  const uint64_t blocks = (L.plain_n + threads - 1) / threads;
   exec_plain<<<(uint32_t)blocks, threads, 0, st>>>(L);
   return cudaGetLastError();
 }

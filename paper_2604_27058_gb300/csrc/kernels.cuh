@@ -81,6 +81,8 @@ struct LaunchParams {
   // record-level propagation sampler: first tile of this launch and the
   // pre-sampled chunk items of its tiles (null: sample in the kernel)
   uint32_t tile0;
+  // plain executor: this launch's call-local shots [plain_base, plain_base + plain_n)
+  uint64_t plain_base, plain_n;
   const uint32_t* aff_items;
   const uint32_t* aff_counts;
   uint32_t aff_cap;

@@ -1,0 +1,87 @@
+"""The multi-GPU path is replicas with disjoint shot ranges. Two gloo ranks on
+CPU take their ranges from paper_2604_27058_gb300.shard, compute their shots'
+records with the oracle at the global shot indices, and the gathered records
+must equal a single run over the union; the max-over-ranks reduction the
+benchmark uses is checked on the same group."""
+
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+from paper_2604_27058_gb300 import shard
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, mode, q):
+    import torch
+    import torch.distributed as dist
+    from gen import circuits as gc
+    from oracle.stabilizer import FrameSim
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sim = FrameSim(gc.surface_code_memory(d=3, rounds=3, p=0.02))
+    if mode == "weak":
+        off, n = shard.weak(150, rank)
+    else:
+        off, n = shard.strong(300, rank, world)
+    recs = [(off + s, tuple(r.det), tuple(r.obs)) for s in range(n)
+            for r in [sim.sample(5, off + s)]]
+    out = [None] * world
+    dist.all_gather_object(out, recs)
+    t = torch.tensor([float(rank + 1)])
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    if rank == 0:
+        q.put((out, float(t.item())))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("mode", ["weak", "strong"])
+def test_two_rank_shards_equal_single_run(mode):
+    from gen import circuits as gc
+    from oracle.stabilizer import FrameSim
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, mode, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    gathered, tmax = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert tmax == 2.0
+    flat = [x for part in gathered for x in part]
+    idx = [x[0] for x in flat]
+    assert len(set(idx)) == len(idx)  # disjoint ranges
+    assert all(off % shard.ALIGN == 0 for off in
+               ([shard.weak(150, r)[0] for r in range(2)] if mode == "weak" else
+                [shard.strong(300, r, 2)[0] for r in range(2)]))
+    if mode == "strong":
+        assert sorted(idx) == list(range(300))
+    sim = FrameSim(gc.surface_code_memory(d=3, rounds=3, p=0.02))
+    for s, det, obs in flat:
+        r = sim.sample(5, s)
+        assert (tuple(r.det), tuple(r.obs)) == (det, obs)
+
+
+def test_strong_split_covers_exactly():
+    for total in (0, 1, 127, 128, 129, 10_000, 10**8 + 3):
+        for world in (1, 2, 3, 8):
+            parts = [shard.strong(total, r, world) for r in range(world)]
+            assert sum(n for _, n in parts) == total
+            assert all(off % 128 == 0 for off, _ in parts)
+            end = 0
+            for off, n in parts:
+                if n:
+                    assert off == end
+                    end = off + n
