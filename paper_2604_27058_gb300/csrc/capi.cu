@@ -175,16 +175,18 @@ struct Scratch {
 // overrides the item-list capacity per tile (tiles whose list overflows
 // sample in the tile kernel).
 struct Tuning {
-  uint32_t G, T, W, B, A, AW, AI, AV, AC;
+  uint32_t G, T, W, B, A, AW, AI, AV, AC, PS;  // PS = 1: pre-sample faults even for small calls
 };
 
-Tuning choose_tuning(const DevProg& d, const char* tune) {
+Tuning choose_tuning(const DevProg& d, const char* tune, uint64_t shots, int n_sm) {
   Tuning t;
-  if (d.k_max == 0) t = {128, 128, 1, 1, 1, 0, 1, 0, 0};
-  else if (d.k_max <= 6) t = {32, 256, 1, 1, 1, 0, 1, 0, 0};
-  else if (d.k_max <= 10) t = {8, 256, 1, 1, 1, 0, 1, 0, 0};
-  else if (d.k_max <= 13) t = {2, 512, 1, 1, 1, 0, 1, 0, 0};
-  else t = {1, 1024, 1, 1, 1, 0, 1, 0, 0};
+  if (d.k_max == 0) t = {128, 128, 1, 1, 1, 0, 1, 0, 0, 0};
+  else if (d.k_max <= 6) t = {64, 512, 1, 1, 1, 0, 1, 0, 0, 0};
+  else if (d.k_max <= 10) t = {8, 512, 1, 1, 1, 0, 1, 0, 0, 0};
+  else if (d.k_max <= 13) t = {2, 512, 1, 1, 1, 0, 1, 0, 0, 0};
+  else t = {1, 1024, 1, 1, 1, 0, 1, 0, 0, 0};
+  // small calls: smaller tiles, so that every SM gets one
+  while (t.G > 1 && (shots + 32 * t.G - 1) / (32 * t.G) < (uint64_t)n_sm) t.G >>= 1;
   if (tune) {
     unsigned v = 0;
     const char* s = tune;
@@ -198,6 +200,7 @@ Tuning choose_tuning(const DevProg& d, const char* tune) {
       else if (sscanf(s, "ai=%u", &v) == 1) t.AI = v;
       else if (sscanf(s, "av=%u", &v) == 1) t.AV = v;
       else if (sscanf(s, "ac=%u", &v) == 1) t.AC = v;
+      else if (sscanf(s, "ps=%u", &v) == 1) t.PS = v;
       const char* c = strchr(s, ',');
       if (!c) break;
       s = c + 1;
@@ -338,7 +341,10 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
       }
     }
   } else {
-    Tuning tu = choose_tuning(L.p, tune);
+    int n_sm_dev = 0, dev_id = 0;
+    NC_TRY(cudaGetDevice(&dev_id));
+    NC_TRY(cudaDeviceGetAttribute(&n_sm_dev, cudaDevAttrMultiProcessorCount, dev_id));
+    Tuning tu = choose_tuning(L.p, tune, shots, n_sm_dev);
     if (h.aff_ok && tu.A && !(lflags & (LF_POSTSELECT | LF_REFERENCE)) && stop_event == 0xffffffffu) {
       // record-level propagation sampler: tile of 32 * wpt shots per CTA of
       // 16 * wpt threads; the shape with the most resident warps wins
@@ -414,7 +420,10 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
     L.qc_n = coarse_count(h.n_sites);
     const uint64_t S = 32ull * tu.G;
     L.n_tiles = (uint32_t)((L.row_words32 + tu.G - 1) / tu.G);
-    const bool noisy = !(lflags & LF_NOISELESS) && h.n_sites && stop_event == 0xffffffffu;
+    // fault pre-sampling (bucketed or per-shot lists) pays off only for
+    // large calls; small ones sample faults inside the executor
+    const bool noisy =
+        !(lflags & LF_NOISELESS) && h.n_sites && stop_event == 0xffffffffu && (shots >= (1u << 20) || tu.PS);
     const double mean = (double)h.mean_faults;
     const double per_shot_cap = std::ceil(mean + 6.0 * std::sqrt(mean) + 4.0);
     // Bucketed noise: every shot's faults sampled up front and sorted by

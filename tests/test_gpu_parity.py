@@ -130,7 +130,7 @@ def test_tiny_workload_full_size_sampled(nc):
 # workload 2: surface-code memory d=5, 25 rounds (k_max = 0): bit-exact
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("precision,tune", [("fp32", "a=0,g=4,t=128"), ("fp32", None), ("fp64", None),
-                                            ("fp32", "a=0"), ("fp32", "a=0,b=0"), ("fp32", "a=0,g=32,t=32"),
+                                            ("fp32", "a=0"), ("fp32", "a=0,b=0,ps=1"), ("fp32", "a=0,g=32,t=32,ps=1"),
                                             ("fp32", "aw=4"), ("fp32", "aw=32"), ("fp64", "a=0")])
 def test_surface_code_bit_exact(nc, precision, tune):
     text = gc.surface_code_memory(d=5, rounds=25, p=1e-3)
@@ -144,14 +144,17 @@ def test_surface_code_bit_exact(nc, precision, tune):
     assert int(g["det"].sum()) > 0
 
 
-@pytest.mark.parametrize("tune", [None, "aw=8", "ai=0", "ac=100", "av=2048", "a=0", "a=0,g=64,t=64", "a=0,b=0"])
+@pytest.mark.parametrize("tune", [None, "aw=8", "ai=0", "ac=100", "av=2048", "a=0", "a=0,ps=1",
+                                  "a=0,g=64,t=64,ps=1", "a=0,b=0,ps=1"])
 def test_surface_code_many_warp_tiles(nc, tune):
     """Several tiles and a ragged last tile: the record-level propagation
     sampler (default for k_max = 0; faults sampled in a separate pass, or in
     the tile kernel with ai=0, or after an item list overflows with ac=100,
     or in passes of 2048 shots with av=2048), the executor with bucketed
-    noise (a=0) and with per-shot noise (a=0,b=0) give the oracle's records
-    on shots spread over every tile."""
+    noise (a=0,ps=1), with per-shot fault lists (a=0,b=0,ps=1) and with
+    faults sampled inside the executor (a=0: calls this small skip the
+    pre-sampling passes unless ps=1) give the oracle's records on shots
+    spread over every tile."""
     text = gc.surface_code_memory(d=5, rounds=25, p=1e-3)
     prog = nc.compile(text)
     sim = FrameSim(text)
@@ -406,7 +409,8 @@ def test_tuning_variants_agree(nc):
     text = gc.tiny_random(seed=6)
     prog = nc.compile(text)
     base = gpu_records(prog, 1000, 12, precision="fp32")
-    for tune in ("g=1,t=32", "g=1,t=1024", "g=8,t=256", "g=4,t=64", "b=0", "g=64,t=64"):
+    for tune in ("g=1,t=32", "g=1,t=1024", "g=8,t=256", "g=4,t=64", "b=0", "g=64,t=64", "g=32,t=256,ps=1",
+                 "ps=1,b=0", "g=8,t=512,ps=1"):
         g = gpu_records(prog, 1000, 12, precision="fp32", tune=tune)
         assert (g["meas"] == base["meas"]).mean() > 0.999
 
