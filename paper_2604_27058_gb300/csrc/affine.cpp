@@ -420,6 +420,7 @@ void append_affine(std::vector<uint8_t>& blob) {
   h.off_aff_chain_off = place((uint64_t)chain_off.size() * 4);
   h.off_aff_chain = place((uint64_t)chain.size() * 4);
   h.aff_n_chains = n_chains;
+  h.aff_n_chain_rows = (uint32_t)chain.size();
   h.total_bytes = off;
   h.aff_ok = 1;
   h.aff_rows = R;

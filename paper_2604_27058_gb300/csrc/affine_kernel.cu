@@ -136,6 +136,12 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
   uint32_t* TILE = sm;                                // (R + 1) rows; row R is scratch
   uint32_t* MW = sm + o_mw;                           // random bits [NR][WPT]
   uint32_t* LW = MW + NR * WPT + warp * kAffList;     // this warp's chunk list
+  // per-launch tables staged once: row info (bit 0: constant ^ reference
+  // parities of the row and its parent; bits 1..: first random-event entry)
+  // and the chains as u16 rows
+  uint32_t* RI = MW + NR * WPT + (T / 32) * kAffList;  // [R + 1]
+  uint16_t* CH = reinterpret_cast<uint16_t*>(RI + R + 1);                    // [n_chain_rows]
+  uint16_t* CHOFF = CH + ((p.aff_n_chain_rows + 1) & ~1u);                  // [n_chains + 1]
   const bool noisy = !(L.flags & LF_NOISELESS) && p.n_sites > 0;
   const uint2 key = key_of(L.seed);
   const uint32_t n_det_end = p.n_meas + p.n_det;
@@ -187,6 +193,26 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
     __syncwarp();
   };
 
+  {
+    auto ref = [&](uint32_t r) -> uint32_t {
+      return r < p.n_meas || r >= R ? 0u
+             : r < n_det_end       ? __ldg(p.det_ref + (r - p.n_meas))
+                                   : __ldg(p.obs_ref + (r - n_det_end));
+    };
+    for (uint32_t r = t; r <= R; r += T) {
+      uint32_t c = 0;
+      if (r < R) {
+        c = __ldg(p.aff_const + r) ^ ref(r);
+        const uint32_t par = __ldg(p.aff_parent + r);
+        if (par != 0xFFFFFFFFu) c ^= ref(par);
+      }
+      RI[r] = (__ldg(p.aff_rowev_off + r) << 1) | (c & 1u);
+    }
+    for (uint32_t j = t; j < p.aff_n_chain_rows; j += T) CH[j] = (uint16_t)__ldg(p.aff_chain + j);
+    for (uint32_t j = t; j <= p.aff_n_chains; j += T) CHOFF[j] = (uint16_t)__ldg(p.aff_chain_off + j);
+    __syncthreads();
+  }
+
   for (uint32_t tile = L.tile0 + blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
     const uint64_t tile_s0 = L.shot_offset + (uint64_t)tile * S;  // a multiple of 128
     // pre-sampled chunk items of this tile (affine_items), unless its list
@@ -211,20 +237,13 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
     }
     __syncthreads();
     // 2. constants, reference parities and random-bit terms, one row per thread
-    auto ref = [&](uint32_t r) -> uint32_t {
-      return r < p.n_meas || r >= R ? 0u
-             : r < n_det_end       ? __ldg(p.det_ref + (r - p.n_meas))
-                                   : __ldg(p.obs_ref + (r - n_det_end));
-    };
     for (uint32_t r = t; r < R; r += T) {
-      // delta form: the reference parities of the row and of its parent
-      uint32_t c = __ldg(p.aff_const + r) ^ ref(r);
-      const uint32_t par = __ldg(p.aff_parent + r);
-      if (par != 0xFFFFFFFFu) c ^= ref(par);
+      const uint32_t ri = RI[r];
+      const uint32_t c = ri & 1u;
+      const uint32_t e0 = ri >> 1, e1 = RI[r + 1] >> 1;
       uint32_t v[WPT];
 #pragma unroll
-      for (uint32_t w = 0; w < WPT; w++) v[w] = (c & 1u) ? ~0u : 0u;
-      const uint32_t e0 = __ldg(p.aff_rowev_off + r), e1 = __ldg(p.aff_rowev_off + r + 1);
+      for (uint32_t w = 0; w < WPT; w++) v[w] = c ? ~0u : 0u;
       for (uint32_t e = e0; e < e1; e++) {
         const uint4* mw = reinterpret_cast<const uint4*>(MW + __ldg(p.aff_rowev + e) * WPT);
 #pragma unroll
@@ -315,13 +334,13 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
     // delta rows to record rows: a running XOR down each chain, per word
     for (uint32_t i = t; i < p.aff_n_chains * WPT; i += T) {
       const uint32_t ch = i / WPT, w = i % WPT;
-      const uint32_t j0 = __ldg(p.aff_chain_off + ch), j1 = __ldg(p.aff_chain_off + ch + 1);
+      const uint32_t j0 = CHOFF[ch], j1 = CHOFF[ch + 1];
       uint32_t v = 0, j = j0;
       for (; j + 4 <= j1; j += 4) {  // four rows' loads in flight
-        uint32_t* x0 = TILE + __ldg(p.aff_chain + j) * STR + w;
-        uint32_t* x1 = TILE + __ldg(p.aff_chain + j + 1) * STR + w;
-        uint32_t* x2 = TILE + __ldg(p.aff_chain + j + 2) * STR + w;
-        uint32_t* x3 = TILE + __ldg(p.aff_chain + j + 3) * STR + w;
+        uint32_t* x0 = TILE + CH[j] * STR + w;
+        uint32_t* x1 = TILE + CH[j + 1] * STR + w;
+        uint32_t* x2 = TILE + CH[j + 2] * STR + w;
+        uint32_t* x3 = TILE + CH[j + 3] * STR + w;
         const uint32_t a0 = *x0, a1 = *x1, a2 = *x2, a3 = *x3;
         v ^= a0;
         *x0 = v;
@@ -333,7 +352,7 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
         *x3 = v;
       }
       for (; j < j1; j++) {
-        uint32_t* x = TILE + __ldg(p.aff_chain + j) * STR + w;
+        uint32_t* x = TILE + CH[j] * STR + w;
         v ^= *x;
         *x = v;
       }
@@ -404,7 +423,8 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
 // chunk list per warp.
 size_t affine_smem_bytes(const DevProg& p, uint32_t wpt) {
   const size_t o_mw = ((size_t)(wpt + 1) * (p.aff_rows + 1) + 3) & ~(size_t)3;
-  return 4 * (o_mw + (size_t)wpt * p.aff_n_rand + (size_t)(wpt / 2) * kAffList);
+  const size_t staged = (size_t)p.aff_rows + 1 + ((size_t)p.aff_n_chain_rows + 1) / 2 + ((size_t)p.aff_n_chains + 2) / 2;
+  return 4 * (o_mw + (size_t)wpt * p.aff_n_rand + (size_t)(wpt / 2) * kAffList + staged);
 }
 
 template <int WPT>

@@ -39,7 +39,7 @@ struct DevProg {
   const uint32_t* guide;
   uint32_t n_qubits, nw, n_ops, n_sites, n_slots, k_max, kept_slot;
   uint32_t n_meas, n_det, n_obs, n_blocks;
-  uint32_t aff_rows, aff_n_rand, aff_n_chains;
+  uint32_t aff_rows, aff_n_rand, aff_n_chains, aff_n_chain_rows;
   float aff_chunks_per_shot;
 };
 

@@ -106,6 +106,7 @@ DevProg view(const ProgHeader& h, const uint8_t* base) {
     d.aff_chain_off = reinterpret_cast<const uint32_t*>(base + h.off_aff_chain_off);
     d.aff_chain = reinterpret_cast<const uint32_t*>(base + h.off_aff_chain);
     d.aff_n_chains = h.aff_n_chains;
+    d.aff_n_chain_rows = h.aff_n_chain_rows;
     d.aff_chunks_per_shot = h.aff_chunks_per_shot;
     d.aff_rows = h.aff_rows;
     d.aff_n_rand = h.aff_n_rand;

@@ -106,6 +106,7 @@ struct ProgHeader {
   float aff_chunks_per_shot;       // expected chunks of a shot's faults
   uint32_t n_guide;                // survival guide-table entries
   uint32_t aff_n_chains;           // delta-row chains of two or more rows
+  uint32_t aff_n_chain_rows, pad3; // rows on those chains
   uint64_t off_ops, off_masks, off_q, off_seg_start, off_seg_end, off_site_info, off_site_eff,
       off_slot_list, off_det_ref, off_obs_ref, off_site_opt, off_opt_tab, off_plist, off_orec, off_site_blk,
       off_aff_const, off_aff_rowev_off, off_aff_rowev, off_aff_rand_ev, off_aff_col_off, off_aff_col,

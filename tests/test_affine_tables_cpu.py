@@ -16,8 +16,8 @@ from oracle.philox import meas_u
 from oracle.records import raw_parities
 from oracle.stabilizer import FrameSim
 
-HEAD = "<17If8I"  # 17 counts, mean_faults, n_blocks, aff_ok, aff_rows, aff_n_rand, aff_n_chunks,
-                  # aff_chunks_per_shot (read as u32), n_guide, aff_n_chains
+HEAD = "<17If10I"  # 17 counts, mean_faults, n_blocks, aff_ok, aff_rows, aff_n_rand, aff_n_chunks,
+                   # aff_chunks_per_shot (read as u32), n_guide, aff_n_chains, aff_n_chain_rows, pad
 HEAD_BYTES = struct.calcsize(HEAD)
 OFF_NAMES = ["ops", "masks", "q", "seg_start", "seg_end", "site_info", "site_eff", "slot_list", "det_ref",
              "obs_ref", "site_opt", "opt_tab", "plist", "orec", "site_blk", "aff_const", "aff_rowev_off",
@@ -62,6 +62,7 @@ def _tables(blob: bytes):
         assert [(nib >> (4 * o)) & 15 for o in range(kk)] == counts
     n_chains = u[25]
     chain_off = arr("aff_chain_off", n_chains + 1)
+    assert u[26] == int(chain_off[-1])
     chains = [arr("aff_chain", int(chain_off[-1]))[chain_off[i]:chain_off[i + 1]] for i in range(n_chains)]
     parent = arr("aff_parent", rows)
     for ch in chains:  # chains follow parent links, head first
