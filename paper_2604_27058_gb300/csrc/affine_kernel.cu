@@ -70,6 +70,17 @@ __device__ __forceinline__ uint32_t aff_draw(const DevProg& p, uint2 key, uint64
   return i + 1;
 }
 
+// XOR `bit` into the tile column `col` at the (up to) eight rows of a chunk;
+// padding entries (row index R, the scratch row) are skipped.
+template <uint32_t STR>
+__device__ __forceinline__ void xor_chunk(uint32_t* col, uint4 ch, uint32_t bit, uint32_t R) {
+  const uint32_t r[8] = {ch.x & 0xFFFFu, ch.x >> 16, ch.y & 0xFFFFu, ch.y >> 16,
+                         ch.z & 0xFFFFu, ch.z >> 16, ch.w & 0xFFFFu, ch.w >> 16};
+#pragma unroll
+  for (uint32_t e = 0; e < 8; e++)
+    if (r[e] < R) atomicXor(col + r[e] * STR, bit);
+}
+
 // Warp-inclusive prefix sum.
 __device__ __forceinline__ uint32_t warp_incl(uint32_t v, uint32_t lane) {
 #pragma unroll
@@ -151,14 +162,7 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
     const uint4 ch = __ldg(p.aff_chunks + chunk);
     uint32_t* col = TILE + (s >> 5);
     const uint32_t bit = 1u << (s & 31u);
-    atomicXor(col + (ch.x & 0xFFFFu) * STR, bit);
-    atomicXor(col + (ch.x >> 16) * STR, bit);
-    atomicXor(col + (ch.y & 0xFFFFu) * STR, bit);
-    atomicXor(col + (ch.y >> 16) * STR, bit);
-    atomicXor(col + (ch.z & 0xFFFFu) * STR, bit);
-    atomicXor(col + (ch.z >> 16) * STR, bit);
-    atomicXor(col + (ch.w & 0xFFFFu) * STR, bit);
-    atomicXor(col + (ch.w >> 16) * STR, bit);
+    xor_chunk<STR>(col, ch, bit, R);
   };
   // the warp applies its list (at most kAffList = 4 x 32 items): every lane
   // first loads its up to four chunks, then does the atomics
@@ -180,14 +184,7 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
       if (lane + 32u * k < n) {
         uint32_t* col = TILE + (sh[k] >> 5);
         const uint32_t bit = 1u << (sh[k] & 31u);
-        atomicXor(col + (ch[k].x & 0xFFFFu) * STR, bit);
-        atomicXor(col + (ch[k].x >> 16) * STR, bit);
-        atomicXor(col + (ch[k].y & 0xFFFFu) * STR, bit);
-        atomicXor(col + (ch[k].y >> 16) * STR, bit);
-        atomicXor(col + (ch[k].z & 0xFFFFu) * STR, bit);
-        atomicXor(col + (ch[k].z >> 16) * STR, bit);
-        atomicXor(col + (ch[k].w & 0xFFFFu) * STR, bit);
-        atomicXor(col + (ch[k].w >> 16) * STR, bit);
+        xor_chunk<STR>(col, ch[k], bit, R);
       }
     }
     __syncwarp();
@@ -279,14 +276,7 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
           if (i0 + u * T + t < n) {
             uint32_t* col = TILE + (sh[u] >> 5);
             const uint32_t bit = 1u << (sh[u] & 31u);
-            atomicXor(col + (ch[u].x & 0xFFFFu) * STR, bit);
-            atomicXor(col + (ch[u].x >> 16) * STR, bit);
-            atomicXor(col + (ch[u].y & 0xFFFFu) * STR, bit);
-            atomicXor(col + (ch[u].y >> 16) * STR, bit);
-            atomicXor(col + (ch[u].z & 0xFFFFu) * STR, bit);
-            atomicXor(col + (ch[u].z >> 16) * STR, bit);
-            atomicXor(col + (ch[u].w & 0xFFFFu) * STR, bit);
-            atomicXor(col + (ch[u].w >> 16) * STR, bit);
+            xor_chunk<STR>(col, ch[u], bit, R);
           }
         }
       }
