@@ -2,7 +2,7 @@
 // (k_max = 0), through the record-level propagation tables that affine.cpp
 // derives from the bytecode (program.h).
 //
-// sample_affine<WPT>: one CTA of 16*WPT threads runs tiles of 32*WPT shots.
+// sample_affine<WPT>: one CTA of 32*WPT threads runs tiles of 32*WPT shots.
 // A tile's records live in shared memory as rows x WPT words (bit j of word
 // w of a row = shot 32 w + j of the tile; rows padded to WPT + 1 words so
 // that different rows of one word fall in different banks):
@@ -10,9 +10,10 @@
 //      the 128-shot block draw), one Philox call per event and 128 shots;
 //   2. every row starts at its constant, the detector / observable reference
 //      parity and the XOR of the random bits it depends on (thread per row);
-//   3. fault sampling: each warp owns 64 shots and keeps its 32 lanes busy
-//      by handing a finished lane the next shot, one survival-jump draw per
-//      lane per step (Sec. 3.2; guide-table search of the survival table);
+//   3. faults: the tile's chunk items from affine_items, applied with
+//      shared-memory atomic XORs; or (when no item list is available) fault
+//      sampling in the tile kernel, one warp per 32 shots, one survival-jump
+//      draw per lane per step (Sec. 3.2; guide-table search);
 //      every fault appends its column's 8-row chunks to the warp's list, and
 //      the warp applies a full list one chunk per lane: eight shared-memory
 //      atomic XORs of the shot's bit;
@@ -29,7 +30,8 @@
 
 namespace nc {
 
-constexpr uint32_t kAffPool = 64;   // shots per warp (fused sampling)
+constexpr uint32_t kAffTpw = 32;    // threads per 32-shot word of the tile: one warp per word
+constexpr uint32_t kAffPool = 32;   // shots per warp (fused sampling): S / warps
 constexpr uint32_t kAffList = 128;  // chunk items per warp list
 
 // One survival-jump draw from site st for `shot` (Sec. 3.2, integer form;
@@ -137,10 +139,11 @@ __global__ void __launch_bounds__(512, 2) affine_items(LaunchParams L, uint32_t 
 }
 
 template <int WPT>
-__global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
+__global__ void __launch_bounds__(kAffTpw * WPT, 65536 / (kAffTpw * WPT * 64)) sample_affine(LaunchParams L) {
   extern __shared__ __align__(16) uint32_t sm[];
   const DevProg& p = L.p;
-  constexpr uint32_t S = 32u * WPT, T = 16u * WPT, STR = WPT + 1;
+  constexpr uint32_t S = 32u * WPT, T = kAffTpw * WPT, STR = WPT + 1;
+  static_assert(S / (T / 32) == kAffPool, "one fused-sampling pool per warp");
   const uint32_t R = p.aff_rows, NR = p.aff_n_rand, t = threadIdx.x, lane = t & 31u, warp = t >> 5;
   // word offsets, each region 16-byte aligned (MW rows are read as uint4)
   const uint32_t o_mw = ((R + 1) * STR + 3u) & ~3u;
@@ -164,31 +167,30 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
     const uint32_t bit = 1u << (s & 31u);
     xor_chunk<STR>(col, ch, bit, R);
   };
-  // the warp applies its list (at most kAffList = 4 x 32 items): every lane
-  // first loads its up to four chunks, then does the atomics
+  // the warp applies its list (at most kAffList = 4 x 32 items), two chunk
+  // loads per lane in flight before their atomics
   auto flush = [&](uint32_t n) {
     __syncwarp();
-    uint4 ch[kAffList / 32];
-    uint32_t sh[kAffList / 32];
 #pragma unroll
-    for (uint32_t k = 0; k < kAffList / 32; k++) {
-      const uint32_t i = lane + 32u * k;
-      if (i < n) {
-        const uint32_t it = LW[i];
-        ch[k] = __ldg(p.aff_chunks + (it >> 10));
-        sh[k] = it & 1023u;
-      }
-    }
+    for (uint32_t k0 = 0; k0 < kAffList / 32; k0 += 2) {
+      uint4 ch[2];
+      uint32_t sh[2];
 #pragma unroll
-    for (uint32_t k = 0; k < kAffList / 32; k++) {
-      if (lane + 32u * k < n) {
-        uint32_t* col = TILE + (sh[k] >> 5);
-        const uint32_t bit = 1u << (sh[k] & 31u);
-        xor_chunk<STR>(col, ch[k], bit, R);
+      for (uint32_t u = 0; u < 2; u++) {
+        const uint32_t i = lane + 32u * (k0 + u);
+        if (i < n) {
+          const uint32_t it = LW[i];
+          ch[u] = __ldg(p.aff_chunks + (it >> 10));
+          sh[u] = it & 1023u;
+        }
       }
+#pragma unroll
+      for (uint32_t u = 0; u < 2; u++)
+        if (lane + 32u * (k0 + u) < n) xor_chunk<STR>(TILE + (sh[u] >> 5), ch[u], 1u << (sh[u] & 31u), R);
     }
     __syncwarp();
   };
+
 
   {
     auto ref = [&](uint32_t r) -> uint32_t {
@@ -233,37 +235,36 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
       dst[3] = ~tb.w;
     }
     __syncthreads();
-    // 2. constants, reference parities and random-bit terms, one row per thread
-    for (uint32_t r = t; r < R; r += T) {
+    // 2. constants, reference parities and random-bit terms, four words per thread
+    constexpr uint32_t QPR = WPT / 4;  // 4-word quarters per row
+    for (uint32_t i = t; i < R * QPR; i += T) {
+      const uint32_t r = i / QPR, q = (i % QPR) * 4u;
       const uint32_t ri = RI[r];
-      const uint32_t c = ri & 1u;
+      const uint32_t c = (ri & 1u) ? ~0u : 0u;
       const uint32_t e0 = ri >> 1, e1 = RI[r + 1] >> 1;
-      uint32_t v[WPT];
-#pragma unroll
-      for (uint32_t w = 0; w < WPT; w++) v[w] = c ? ~0u : 0u;
+      uint4 v = make_uint4(c, c, c, c);
       for (uint32_t e = e0; e < e1; e++) {
-        const uint4* mw = reinterpret_cast<const uint4*>(MW + __ldg(p.aff_rowev + e) * WPT);
-#pragma unroll
-        for (uint32_t w4 = 0; w4 < WPT / 4; w4++) {
-          const uint4 x = mw[w4];
-          v[4 * w4] ^= x.x;
-          v[4 * w4 + 1] ^= x.y;
-          v[4 * w4 + 2] ^= x.z;
-          v[4 * w4 + 3] ^= x.w;
-        }
+        const uint4 x = *reinterpret_cast<const uint4*>(MW + __ldg(p.aff_rowev + e) * WPT + q);
+        v.x ^= x.x;
+        v.y ^= x.y;
+        v.z ^= x.z;
+        v.w ^= x.w;
       }
-#pragma unroll
-      for (uint32_t w = 0; w < WPT; w++) TILE[r * STR + w] = v[w];
+      uint32_t* dst = TILE + r * STR + q;
+      dst[0] = v.x;
+      dst[1] = v.y;
+      dst[2] = v.z;
+      dst[3] = v.w;
     }
     __syncthreads();
-    // 3a. apply the tile's pre-sampled items, four per thread at a time
+    // 3a. apply the tile's pre-sampled items, two per thread at a time
     if (noisy && titems) {
       const uint32_t n = tcnt;
-      for (uint32_t i0 = 0; i0 < n; i0 += 4 * T) {
-        uint4 ch[4];
-        uint32_t sh[4];
+      for (uint32_t i0 = 0; i0 < n; i0 += 2 * T) {
+        uint4 ch[2];
+        uint32_t sh[2];
 #pragma unroll
-        for (uint32_t u = 0; u < 4; u++) {
+        for (uint32_t u = 0; u < 2; u++) {
           const uint32_t i = i0 + u * T + t;
           if (i < n) {
             const uint32_t it = __ldg(titems + i);
@@ -272,13 +273,8 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
           }
         }
 #pragma unroll
-        for (uint32_t u = 0; u < 4; u++) {
-          if (i0 + u * T + t < n) {
-            uint32_t* col = TILE + (sh[u] >> 5);
-            const uint32_t bit = 1u << (sh[u] & 31u);
-            xor_chunk<STR>(col, ch[u], bit, R);
-          }
-        }
+        for (uint32_t u = 0; u < 2; u++)
+          if (i0 + u * T + t < n) xor_chunk<STR>(TILE + (sh[u] >> 5), ch[u], 1u << (sh[u] & 31u), R);
       }
     }
     // 3b. otherwise fault sampling with lane refill; chunk items through the warp list
@@ -321,7 +317,7 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
       flush(cnt);
     }
     __syncthreads();
-    // delta rows to record rows: a running XOR down each chain, per word
+    // 4. delta rows to record rows: a running XOR down each chain, per word
     for (uint32_t i = t; i < p.aff_n_chains * WPT; i += T) {
       const uint32_t ch = i / WPT, w = i % WPT;
       const uint32_t j0 = CHOFF[ch], j1 = CHOFF[ch + 1];
@@ -348,58 +344,56 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
       }
     }
     __syncthreads();
-    // 4. rows out, then the kept row: four words per thread (16-byte stores)
-    // when rows are 16-byte aligned (row_words32 % 4 == 0), else two
+    // 5. rows out, then the kept row: four words per thread (16-byte stores)
+    // when rows are 16-byte aligned (row_words32 % 4 == 0), else two. Shot
+    // masks and the row-end check only in the last tile.
     const uint64_t gw0 = (uint64_t)tile * WPT;
-    auto out_row = [&](uint32_t r, uint32_t*& dst) -> bool {
-      if (r == R) {
-        dst = L.kept;
-        return (L.flags & LF_OUT_KEPT) != 0;
-      }
-      if (r < p.n_meas) {
-        dst = L.meas + (size_t)r * L.row_words32;
-        return (L.flags & LF_OUT_MEAS) != 0;
-      }
-      if (r < n_det_end) {
-        dst = L.det + (size_t)(r - p.n_meas) * L.row_words32;
-        return (L.flags & LF_OUT_DET) != 0;
-      }
-      dst = L.obs + (size_t)(r - n_det_end) * L.row_words32;
-      return (L.flags & LF_OUT_OBS) != 0;
-    };
+    const bool full = (uint64_t)(tile + 1) * S <= L.shots && gw0 + WPT <= L.row_words32;
     auto valid = [&](uint64_t gw) -> uint32_t {
       const uint64_t s0 = gw * 32u;
       return s0 + 32 <= L.shots ? ~0u : s0 < L.shots ? (1u << (uint32_t)(L.shots - s0)) - 1u : 0u;
     };
-    if ((L.row_words32 & 3u) == 0) {
-      constexpr uint32_t PR = WPT / 4;
-      for (uint32_t i = t; i < (R + 1) * PR; i += T) {
-        const uint32_t r = i / PR, w4 = (i % PR) * 4u;
-        const uint64_t gw = gw0 + w4;
-        uint32_t* dst;
-        if (gw >= L.row_words32 || !out_row(r, dst)) continue;  // gw + 3 is in range too
-        uint4 v;
-        if (r < R) {
-          const uint32_t* src = TILE + r * STR + w4;
-          v = make_uint4(src[0] & valid(gw), src[1] & valid(gw + 1), src[2] & valid(gw + 2), src[3] & valid(gw + 3));
-        } else {
-          v = make_uint4(valid(gw), valid(gw + 1), valid(gw + 2), valid(gw + 3));
+    // rows [r0, r0 + nr) of the tile to base (kept row: r0 = R, constant)
+    auto write_rows = [&](uint32_t* base, uint32_t r0, uint32_t nr) {
+      if ((L.row_words32 & 3u) == 0) {
+        constexpr uint32_t PR = WPT / 4;
+        for (uint32_t i = t; i < nr * PR; i += T) {
+          const uint32_t rr = i / PR, w4 = (i % PR) * 4u;
+          const uint64_t gw = gw0 + w4;
+          uint4 v;
+          if (r0 < R) {
+            const uint32_t* src = TILE + (r0 + rr) * STR + w4;
+            v = make_uint4(src[0], src[1], src[2], src[3]);
+          } else {
+            v = make_uint4(~0u, ~0u, ~0u, ~0u);
+          }
+          if (!full) {
+            if (gw >= L.row_words32) continue;  // gw + 3 is in range too
+            v.x &= valid(gw);
+            v.y &= valid(gw + 1);
+            v.z &= valid(gw + 2);
+            v.w &= valid(gw + 3);
+          }
+          *reinterpret_cast<uint4*>(base + (size_t)rr * L.row_words32 + gw) = v;
         }
-        *reinterpret_cast<uint4*>(dst + gw) = v;
+      } else {
+        constexpr uint32_t PR = WPT / 2;
+        for (uint32_t i = t; i < nr * PR; i += T) {
+          const uint32_t rr = i / PR, w2 = (i % PR) * 2u;
+          const uint64_t gw = gw0 + w2;
+          if (gw >= L.row_words32) continue;  // row_words32 is even
+          uint2 v = r0 < R ? make_uint2(TILE[(r0 + rr) * STR + w2], TILE[(r0 + rr) * STR + w2 + 1])
+                           : make_uint2(~0u, ~0u);
+          v.x &= valid(gw);
+          v.y &= valid(gw + 1);
+          *reinterpret_cast<uint2*>(base + (size_t)rr * L.row_words32 + gw) = v;
+        }
       }
-    } else {
-      constexpr uint32_t PR = WPT / 2;
-      for (uint32_t i = t; i < (R + 1) * PR; i += T) {
-        const uint32_t r = i / PR, w2 = (i % PR) * 2u;
-        const uint64_t gw = gw0 + w2;
-        uint32_t* dst;
-        if (gw >= L.row_words32 || !out_row(r, dst)) continue;  // row_words32 is even
-        uint2 v;
-        if (r < R) v = make_uint2(TILE[r * STR + w2] & valid(gw), TILE[r * STR + w2 + 1] & valid(gw + 1));
-        else v = make_uint2(valid(gw), valid(gw + 1));
-        *reinterpret_cast<uint2*>(dst + gw) = v;
-      }
-    }
+    };
+    if (L.flags & LF_OUT_MEAS) write_rows(L.meas, 0, p.n_meas);
+    if (L.flags & LF_OUT_DET) write_rows(L.det, p.n_meas, p.n_det);
+    if (L.flags & LF_OUT_OBS) write_rows(L.obs, n_det_end, p.n_obs);
+    if (L.flags & LF_OUT_KEPT) write_rows(L.kept, R, 1);
     if (t == 0 && (uint64_t)tile * S < L.shots) {
       const uint64_t left = L.shots - (uint64_t)tile * S;
       atomicAdd(L.kept_count, (unsigned long long)(left < S ? left : S));
@@ -414,7 +408,7 @@ __global__ void __launch_bounds__(16 * WPT) sample_affine(LaunchParams L) {
 size_t affine_smem_bytes(const DevProg& p, uint32_t wpt) {
   const size_t o_mw = ((size_t)(wpt + 1) * (p.aff_rows + 1) + 3) & ~(size_t)3;
   const size_t staged = (size_t)p.aff_rows + 1 + ((size_t)p.aff_n_chain_rows + 1) / 2 + ((size_t)p.aff_n_chains + 2) / 2;
-  return 4 * (o_mw + (size_t)wpt * p.aff_n_rand + (size_t)(wpt / 2) * kAffList + staged);
+  return 4 * (o_mw + (size_t)wpt * p.aff_n_rand + (size_t)(wpt * kAffTpw / 32) * kAffList + staged);
 }
 
 template <int WPT>
@@ -422,8 +416,8 @@ static cudaError_t aff_one(const LaunchParams& L, uint32_t grid, size_t smem, cu
   auto fn = sample_affine<WPT>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (per_sm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, 16 * WPT, smem);
-  fn<<<grid, 16 * WPT, smem, st>>>(L);
+  if (per_sm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, kAffTpw * WPT, smem);
+  fn<<<grid, kAffTpw * WPT, smem, st>>>(L);
   return cudaGetLastError();
 }
 

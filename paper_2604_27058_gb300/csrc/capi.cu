@@ -348,19 +348,19 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
     Tuning tu = choose_tuning(L.p, tune, shots, n_sm_dev);
     if (h.aff_ok && tu.A && !(lflags & (LF_POSTSELECT | LF_REFERENCE)) && stop_event == 0xffffffffu) {
       // record-level propagation sampler: tile of 32 * wpt shots per CTA of
-      // 16 * wpt threads; the shape with the most resident warps wins
+      // 32 * wpt threads; the shape with the most resident warps wins
       int n_sm = 0, dev = 0;
       NC_TRY(cudaGetDevice(&dev));
       NC_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
       uint32_t wpt = 0;
       int best_warps = 0, best_ctas = 0;
-      for (uint32_t c : {16u, 32u, 8u}) {
+      for (uint32_t c : {32u, 16u, 8u}) {
         if (tu.AW && tu.AW != c) continue;
         const size_t smem = affine_smem_bytes(L.p, c);
         if (smem > 227 * 1024) continue;
         int per_sm = 0;
         NC_TRY(launch_affine(L, c, 0, smem, stream, &per_sm));
-        const int warps = per_sm * (int)(c / 2);
+        const int warps = per_sm * (int)c;
         if (per_sm > 0 && warps > best_warps) {
           best_warps = warps;
           best_ctas = per_sm;
