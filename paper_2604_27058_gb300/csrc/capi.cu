@@ -174,18 +174,20 @@ struct Scratch {
 // makes it sample faults inside the tile kernel instead of in a separate
 // high-occupancy pass; AV is the shots per pass pair (0: default); AC
 // overrides the item-list capacity per tile (tiles whose list overflows
-// sample in the tile kernel).
+// sample in the tile kernel); AO = 1 overlaps the item passes (side stream,
+// two item buffers) with the tile kernel, which then keeps one CTA per SM
+// (slower on GB300 for the surface-code workload, so off by default).
 struct Tuning {
-  uint32_t G, T, W, B, A, AW, AI, AV, AC, PS;  // PS = 1: pre-sample faults even for small calls
+  uint32_t G, T, W, B, A, AW, AI, AV, AC, PS, AO;  // PS = 1: pre-sample faults even for small calls
 };
 
 Tuning choose_tuning(const DevProg& d, const char* tune, uint64_t shots, int n_sm) {
   Tuning t;
-  if (d.k_max == 0) t = {128, 128, 1, 1, 1, 0, 1, 0, 0, 0};
-  else if (d.k_max <= 6) t = {64, 512, 1, 1, 1, 0, 1, 0, 0, 0};
-  else if (d.k_max <= 10) t = {8, 512, 1, 1, 1, 0, 1, 0, 0, 0};
-  else if (d.k_max <= 13) t = {2, 512, 1, 1, 1, 0, 1, 0, 0, 0};
-  else t = {1, 1024, 1, 1, 1, 0, 1, 0, 0, 0};
+  if (d.k_max == 0) t = {128, 128, 1, 1, 1, 0, 1, 0, 0, 0, 0};
+  else if (d.k_max <= 6) t = {64, 512, 1, 1, 1, 0, 1, 0, 0, 0, 0};
+  else if (d.k_max <= 10) t = {8, 512, 1, 1, 1, 0, 1, 0, 0, 0, 0};
+  else if (d.k_max <= 13) t = {2, 512, 1, 1, 1, 0, 1, 0, 0, 0, 0};
+  else t = {1, 1024, 1, 1, 1, 0, 1, 0, 0, 0, 0};
   // small calls: smaller tiles, so that every SM gets one
   while (t.G > 1 && (shots + 32 * t.G - 1) / (32 * t.G) < (uint64_t)n_sm) t.G >>= 1;
   if (tune) {
@@ -202,6 +204,7 @@ Tuning choose_tuning(const DevProg& d, const char* tune, uint64_t shots, int n_s
       else if (sscanf(s, "av=%u", &v) == 1) t.AV = v;
       else if (sscanf(s, "ac=%u", &v) == 1) t.AC = v;
       else if (sscanf(s, "ps=%u", &v) == 1) t.PS = v;
+      else if (sscanf(s, "ao=%u", &v) == 1) t.AO = v;
       const char* c = strchr(s, ',');
       if (!c) break;
       s = c + 1;
@@ -217,6 +220,62 @@ Tuning choose_tuning(const DevProg& d, const char* tune, uint64_t shots, int n_s
 }
 
 bool pow2(uint32_t v) { return v && !(v & (v - 1)); }
+
+// Internal side streams (one per concurrent call and device), kept for
+// reuse. A call orders its side-stream work after the caller's stream and
+// makes the caller's stream wait for it before anything that depends on it.
+struct SideStream {
+  int dev = -1;
+  cudaStream_t s = nullptr;
+  SideStream() = default;
+  SideStream(const SideStream&) = delete;
+  SideStream& operator=(const SideStream&) = delete;
+  static std::mutex& mu() {
+    static std::mutex m;
+    return m;
+  }
+  static std::vector<std::pair<int, cudaStream_t>>& pool() {
+    static std::vector<std::pair<int, cudaStream_t>> v;
+    return v;
+  }
+  cudaError_t acquire(int device) {
+    dev = device;
+    {
+      std::lock_guard<std::mutex> g(mu());
+      auto& v = pool();
+      for (size_t i = 0; i < v.size(); i++)
+        if (v[i].first == device) {
+          s = v[i].second;
+          v.erase(v.begin() + i);
+          return cudaSuccess;
+        }
+    }
+    return cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  }
+  ~SideStream() {
+    if (!s) return;
+    std::lock_guard<std::mutex> g(mu());
+    pool().push_back({dev, s});
+  }
+};
+
+// A few events for ordering work between the caller's stream and a side
+// stream (timing disabled), destroyed with the holder.
+struct Events {
+  std::vector<cudaEvent_t> ev;
+  cudaError_t make(size_t n) {
+    for (size_t i = 0; i < n; i++) {
+      cudaEvent_t e = nullptr;
+      cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+      if (r != cudaSuccess) return r;
+      ev.push_back(e);
+    }
+    return cudaSuccess;
+  }
+  ~Events() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
 
 // Per-call scratch comes from the device's default stream-ordered pool. By
 // default the pool hands freed memory back at every synchronisation, so a
@@ -352,10 +411,15 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
       int n_sm = 0, dev = 0;
       NC_TRY(cudaGetDevice(&dev));
       NC_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+      // with the item passes overlapped, the tile kernel keeps one CTA of
+      // 512 threads per SM so that an item-pass CTA fits beside it
+      const bool items = tu.AI && !(lflags & LF_NOISELESS) && h.n_sites > 0;
+      const bool overlap = items && tu.AO;
       uint32_t wpt = 0;
       int best_warps = 0, best_ctas = 0;
       for (uint32_t c : {32u, 16u, 8u}) {
         if (tu.AW && tu.AW != c) continue;
+        if (overlap && !tu.AW && c != 16) continue;
         const size_t smem = affine_smem_bytes(L.p, c);
         if (smem > 227 * 1024) continue;
         int per_sm = 0;
@@ -371,9 +435,9 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
         const size_t smem = affine_smem_bytes(L.p, wpt);
         const uint32_t n_tiles = (uint32_t)((L.row_words32 + wpt - 1) / wpt);
         const uint32_t tile_shots = 32 * wpt;
+        if (overlap) best_ctas = 1;
         // faults sampled by affine_items in passes of `wave` tiles, each
         // followed by the tile kernel on the same tiles
-        const bool items = tu.AI && !(lflags & LF_NOISELESS) && h.n_sites > 0;
         uint32_t wave = n_tiles;
         uint32_t cap = 0;
         uint32_t *ibuf = nullptr, *cbuf = nullptr;
@@ -385,21 +449,43 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
           const double mean = (double)h.aff_chunks_per_shot * tile_shots;
           cap = (uint32_t)(mean * 1.1 + 10.0 * std::sqrt(mean * 16.0) + 64.0);
           if (tu.AC) cap = tu.AC;
+          // two buffers when the passes overlap: pass j + 1 fills one while
+          // the tile kernel of pass j reads the other
+          const size_t nbuf = overlap ? 2 : 1;
           void *a = nullptr, *b = nullptr;
-          NC_TRY(scratch.get(&a, (size_t)wave * cap * 4));
-          NC_TRY(scratch.get(&b, (size_t)wave * 4));
+          NC_TRY(scratch.get(&a, nbuf * wave * cap * 4));
+          NC_TRY(scratch.get(&b, nbuf * wave * 4));
           ibuf = (uint32_t*)a;
           cbuf = (uint32_t*)b;
         }
-        for (uint32_t t0 = 0; t0 < n_tiles; t0 += wave) {
+        SideStream side;
+        Events ev;  // [0] start, [1..2] items ready, [3..4] tile kernel done with a buffer
+        cudaStream_t istream = stream;
+        if (overlap) {
+          NC_TRY(side.acquire(dev));
+          NC_TRY(ev.make(5));
+          istream = side.s;
+          NC_TRY(cudaEventRecord(ev.ev[0], stream));
+          NC_TRY(cudaStreamWaitEvent(istream, ev.ev[0], 0));
+        }
+        uint32_t pass = 0;
+        for (uint32_t t0 = 0; t0 < n_tiles; t0 += wave, pass++) {
           const uint32_t nt = std::min(wave, n_tiles - t0);
+          const uint32_t bsel = overlap ? (pass & 1u) : 0u;
           L.tile0 = t0;
           L.n_tiles = t0 + nt;
           if (items) {
+            uint32_t* ib = ibuf + (size_t)bsel * wave * cap;
+            uint32_t* cb = cbuf + (size_t)bsel * wave;
+            if (overlap && pass >= 2) NC_TRY(cudaStreamWaitEvent(istream, ev.ev[3 + bsel], 0));
             const uint32_t grid = std::min<uint32_t>((nt + 15) / 16, 2 * (uint32_t)n_sm);
-            NC_TRY(launch_affine_items(L, t0, nt, ibuf, cap, cbuf, tile_shots, grid, stream));
-            L.aff_items = ibuf;
-            L.aff_counts = cbuf;
+            NC_TRY(launch_affine_items(L, t0, nt, ib, cap, cb, tile_shots, grid, istream));
+            if (overlap) {
+              NC_TRY(cudaEventRecord(ev.ev[1 + bsel], istream));
+              NC_TRY(cudaStreamWaitEvent(stream, ev.ev[1 + bsel], 0));
+            }
+            L.aff_items = ib;
+            L.aff_counts = cb;
             L.aff_cap = cap;
             if (tm) tm->launches += 1;
           }
@@ -410,6 +496,7 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
             NC_TRY(tm->end(stream));
             tm->launches += 1;
           }
+          if (overlap) NC_TRY(cudaEventRecord(ev.ev[3 + bsel], stream));
         }
         return NC_OK;
       }

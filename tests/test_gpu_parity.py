@@ -144,13 +144,14 @@ def test_surface_code_bit_exact(nc, precision, tune):
     assert int(g["det"].sum()) > 0
 
 
-@pytest.mark.parametrize("tune", [None, "aw=8", "ai=0", "ac=100", "av=2048", "a=0", "a=0,ps=1",
+@pytest.mark.parametrize("tune", [None, "aw=8", "ai=0", "ao=1", "ac=100", "av=2048", "a=0", "a=0,ps=1",
                                   "a=0,g=64,t=64,ps=1", "a=0,b=0,ps=1"])
 def test_surface_code_many_warp_tiles(nc, tune):
     """Several tiles and a ragged last tile: the record-level propagation
     sampler (default for k_max = 0; faults sampled in a separate pass, or in
     the tile kernel with ai=0, or after an item list overflows with ac=100,
-    or in passes of 2048 shots with av=2048), the executor with bucketed
+    or in passes of 2048 shots with av=2048, or overlapped with the tile
+    kernel on a side stream with ao=1), the executor with bucketed
     noise (a=0,ps=1), with per-shot fault lists (a=0,b=0,ps=1) and with
     faults sampled inside the executor (a=0: calls this small skip the
     pre-sampling passes unless ps=1) give the oracle's records on shots
