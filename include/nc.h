@@ -134,6 +134,35 @@ nc_status nc_sample_batch(const nc_program* const* progs, const uint64_t* shots,
                           const uint64_t* seeds, uint32_t n, const nc_sample_opts* opts,
                           nc_records* outs, void* cuda_stream);
 
+/* Upload a program to the current device and run its 64-shot noiseless
+ * reference launch (Sec. 3.2 records: detector / observable references);
+ * synchronises cuda_stream. nc_sample does this on first use; call it
+ * explicitly before nc_sample_batch_async. */
+nc_status nc_program_prepare(const nc_program* prog, void* cuda_stream);
+
+/* nc_sample_batch for stream capture (a CUDA graph of many circuits, the
+ * batching row of Sec. 3.2): only enqueues work on cuda_stream and never
+ * synchronises the host. Requirements: every program prepared on the
+ * current device (else NC_E_ARG); device outputs only (NC_OUT_HOST is
+ * NC_E_ARG). kept_dev (n device u64) and err_dev (one device u32) are
+ * caller-owned and zeroed by the caller: kept_dev[i] accumulates program
+ * i's kept shots and err_dev receives a nonzero value if a kernel reported
+ * an internal error. outs[i].shots_run is set; shots_kept, kernel_ms,
+ * exec_ms and launches are 0. Scratch comes from the stream-ordered pool. */
+nc_status nc_sample_batch_async(const nc_program* const* progs, const uint64_t* shots,
+                                const uint64_t* seeds, uint32_t n, const nc_sample_opts* opts,
+                                nc_records* outs, unsigned long long* kept_dev, uint32_t* err_dev,
+                                void* cuda_stream);
+
+/* Launch-shape autotuner (shots per CTA, CTA size, warp- or word-per-shot
+ * layout of the record tile, fault pre-sampling): times the candidates for
+ * this program on min(shots, 2^22) shots with opts' outputs and keeps the
+ * fastest for later calls on this device whose opts->tune is NULL. best
+ * (if best_len > 0) receives the chosen shape as a tune string. The
+ * program must not be sampled concurrently while it is tuned. */
+nc_status nc_autotune(nc_program* prog, uint64_t shots, const nc_sample_opts* opts, void* cuda_stream,
+                      char* best, size_t best_len);
+
 /*
  * Allocation-free sampling. Some callers cannot allocate device memory once
  * they are running: an application whose device memory is owned entirely by

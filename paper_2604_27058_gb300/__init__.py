@@ -201,6 +201,40 @@ def sample_batch(progs, shots, seeds, precision="fp32", outputs=NC_OUT_ALL, post
     return res
 
 
+def prepare(prog: Program, stream=None) -> None:
+    """nc_program_prepare: upload and reference launch (synchronises)."""
+    _nc.check(_nc.lib().nc_program_prepare(prog.handle, ctypes.c_void_p(_stream_ptr(stream))))
+
+
+def sample_batch_async(progs, shots, seeds, outs, kept_dev, err_dev, precision="fp32", outputs=NC_OUT_ALL,
+                       postselect=False, tune=None, stream=None):
+    """nc_sample_batch_async: enqueue only (capturable in a CUDA graph).
+    outs: record buffers from alloc_records; kept_dev: int64 device tensor
+    of len(progs) and err_dev: int32 device tensor of 1, both zeroed by the
+    caller."""
+    n = len(progs)
+    handles = (ctypes.c_void_p * n)(*[p.handle for p in progs])
+    sh = (ctypes.c_uint64 * n)(*shots)
+    sd = (ctypes.c_uint64 * n)(*seeds)
+    recs = (_nc.Records * n)(*[_records_struct(b, (s + 63) // 64) for b, s in zip(outs, shots)])
+    opts = _opts(precision, outputs, postselect, 0, tune, False)
+    _nc.check(_nc.lib().nc_sample_batch_async(handles, sh, sd, n, ctypes.byref(opts), recs,
+                                              ctypes.c_void_p(kept_dev.data_ptr()),
+                                              ctypes.c_void_p(err_dev.data_ptr()),
+                                              ctypes.c_void_p(_stream_ptr(stream))))
+
+
+def autotune(prog: Program, shots: int, precision="fp32", outputs=NC_OUT_ALL, postselect=False,
+             stream=None) -> str:
+    """nc_autotune: returns the chosen launch shape (used by later calls
+    with tune=None on this device)."""
+    opts = _opts(precision, outputs, postselect, 0, None, False)
+    buf = ctypes.create_string_buffer(128)
+    _nc.check(_nc.lib().nc_autotune(prog.handle, shots, ctypes.byref(opts), ctypes.c_void_p(_stream_ptr(stream)),
+                                    buf, 128))
+    return buf.value.decode()
+
+
 def debug_dump(prog: Program, seed: int, shot: int, event: int, precision="fp32", stream=None):
     """(frame x bits, frame z bits, amplitudes (complex128), k) just before
     measurement event ``event`` of global shot ``shot``."""

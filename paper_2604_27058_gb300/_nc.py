@@ -33,7 +33,8 @@ STATUS = {0: "NC_OK", 1: "NC_E_PARSE", 2: "NC_E_UNSUPPORTED", 3: "NC_E_KMAX",
 
 EXPORTS = ["nc_compile", "nc_program_info", "nc_program_serialize", "nc_program_deserialize",
            "nc_sample", "nc_sample_batch", "nc_program_free", "nc_status_str", "nc_debug_dump",
-           "nc_abi_version", "nc_sample_noalloc"]
+           "nc_abi_version", "nc_sample_noalloc", "nc_program_prepare", "nc_sample_batch_async",
+           "nc_autotune"]
 
 
 class NcError(RuntimeError):
@@ -90,10 +91,15 @@ def lib() -> ctypes.CDLL:
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32), vp]
     L.nc_sample_noalloc.argtypes = [vp, u64, u64, ctypes.POINTER(SampleOpts), ctypes.POINTER(Records), vp]
     L.nc_sample_noalloc.restype = ctypes.c_int
+    L.nc_program_prepare.argtypes = [vp, vp]
+    L.nc_sample_batch_async.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(u64), ctypes.POINTER(u64), u32,
+                                        ctypes.POINTER(SampleOpts), ctypes.POINTER(Records), vp, vp, vp]
+    L.nc_autotune.argtypes = [vp, u64, ctypes.POINTER(SampleOpts), vp, ctypes.c_char_p, sz]
     L.nc_abi_version.argtypes = []
     L.nc_abi_version.restype = u32
     for name in ("nc_compile", "nc_program_info", "nc_program_serialize", "nc_program_deserialize",
-                 "nc_sample", "nc_sample_batch", "nc_debug_dump"):
+                 "nc_sample", "nc_sample_batch", "nc_debug_dump", "nc_program_prepare", "nc_sample_batch_async",
+                 "nc_autotune"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L

@@ -50,6 +50,7 @@ struct DevCopy {
   uint8_t* blob = nullptr;
   bool ref_ready = false;
   nc_status ref_status = NC_OK;
+  std::string tuned;  // launch shape chosen by nc_autotune ("" = heuristic)
 };
 
 }  // namespace
@@ -221,6 +222,23 @@ Tuning choose_tuning(const DevProg& d, const char* tune, uint64_t shots, int n_s
 
 bool pow2(uint32_t v) { return v && !(v & (v - 1)); }
 
+// Free device memory for sizing scratch. Under LF_ASYNC (possibly inside a
+// stream capture) the device's total memory stands in, and an allocation
+// that does not fit fails as NC_E_OOM.
+cudaError_t free_memory(uint32_t lflags, size_t* free_b) {
+  size_t total_b = 0;
+  if (lflags & LF_ASYNC) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaDeviceProp pr;
+    e = cudaGetDeviceProperties(&pr, dev);
+    *free_b = pr.totalGlobalMem / 2;
+    return e;
+  }
+  return cudaMemGetInfo(free_b, &total_b);
+}
+
 // Internal side streams (one per concurrent call and device), kept for
 // reuse. A call orders its side-stream work after the caller's stream and
 // makes the caller's stream wait for it before anything that depends on it.
@@ -384,8 +402,8 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
     const uint64_t padded = L.row_words32 * 32;
     uint64_t chunk = padded;
     if (h.k_max > 0) {
-      size_t free_b = 0, total_b = 0;
-      NC_TRY(cudaMemGetInfo(&free_b, &total_b));
+      size_t free_b = 0;
+      NC_TRY(free_memory(lflags, &free_b));
       const uint64_t per_shot = ((uint64_t)1 << h.k_max) * sizeof(double) * 2;
       chunk = std::min<uint64_t>(padded, std::max<uint64_t>(128, (free_b / 4 / per_shot) & ~127ull));
       NC_TRY(scratch.get(&L.work, per_shot * chunk));
@@ -517,14 +535,14 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
     // Bucketed noise: every shot's faults sampled up front and sorted by
     // noise block per 1024-shot warp-tile (one owner word per lane).
     bool bk = false;
-    if (noisy && tu.B && tu.W == 1 && tu.T <= 256 && tu.G >= 32 && h.n_blocks <= 8192 &&
+    if (noisy && tu.B && !(lflags & LF_ASYNC) && tu.W == 1 && tu.T <= 256 && tu.G >= 32 && h.n_blocks <= 8192 &&
         (uint64_t)h.n_sites * kRecPerSite < (1ull << 22) && per_shot_cap <= 32.0) {
       const uint32_t n_wt = L.n_tiles * (tu.G / 32);
       const double lam = mean * (double)shots;
       const uint64_t cap_total = (uint64_t)(lam * 1.02 + 12.0 * std::sqrt(lam) + 65536.0);
       const size_t ents_b = cap_total * 4, offs_b = (size_t)n_wt * (h.n_blocks + 1) * 4;
-      size_t free_b = 0, total_b = 0;
-      NC_TRY(cudaMemGetInfo(&free_b, &total_b));
+      size_t free_b = 0;
+      NC_TRY(free_memory(lflags, &free_b));
       if (cap_total < (1ull << 32) && ents_b + offs_b < free_b / 2) {
         void *ents = nullptr, *offs = nullptr, *ctr = nullptr;
         NC_TRY(scratch.get(&ents, ents_b));
@@ -556,8 +574,8 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
     if (h.k_max > 0) {
       L.work_stride = ((size_t)1 << h.k_max) * S;
       size_t per_cta = L.work_stride * (fp64 ? sizeof(double) : sizeof(float)) * 2;
-      size_t free_b = 0, total_b = 0;
-      NC_TRY(cudaMemGetInfo(&free_b, &total_b));
+      size_t free_b = 0;
+      NC_TRY(free_memory(lflags, &free_b));
       uint64_t cap = std::max<uint64_t>(1, (uint64_t)(free_b * 0.6) / per_cta);
       grid = std::min(grid, cap);
       NC_TRY(scratch.get(&L.work, per_cta * grid));
@@ -567,8 +585,8 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
       const uint32_t cap = (uint32_t)std::min(127.0, per_shot_cap);
       const uint64_t padded = L.row_words32 * 32;
       const size_t bytes = (size_t)cap * padded * 4 + padded;
-      size_t free_b = 0, total_b = 0;
-      NC_TRY(cudaMemGetInfo(&free_b, &total_b));
+      size_t free_b = 0;
+      NC_TRY(free_memory(lflags, &free_b));
       if (bytes < free_b / 2) {
         void* buf = nullptr;
         NC_TRY(scratch.get(&buf, bytes));
@@ -729,7 +747,8 @@ nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, con
         if ((o.outputs & NC_OUT_OBS) && h.n_obs) { NC_TRY(scratch.get(&d, row_bytes * h.n_obs)); co.obs = (uint32_t*)d; }
         if (o.outputs & NC_OUT_KEPT) { NC_TRY(scratch.get(&d, row_bytes)); co.kept = (uint32_t*)d; }
       }
-      st = enqueue(progs[i], *dcs[i], shots[i], seeds[i], o.shot_offset, o.precision, launch_flags(o), o.tune, co,
+      const char* tn = o.tune ? o.tune : (dcs[i]->tuned.empty() ? nullptr : dcs[i]->tuned.c_str());
+      st = enqueue(progs[i], *dcs[i], shots[i], seeds[i], o.shot_offset, o.precision, launch_flags(o), tn, co,
                    (unsigned long long*)counters + i, (uint32_t*)err, scratch, stream, 0xffffffffu, 0, nullptr,
                    nullptr, nullptr, &tms[i]);
       if (st != NC_OK) goto done;
@@ -843,6 +862,129 @@ nc_status nc_sample_batch(const nc_program* const* progs, const uint64_t* shots,
   return sample_many(progs, shots, seeds, n, opts, outs, (cudaStream_t)cuda_stream);
 }
 
+nc_status nc_program_prepare(const nc_program* prog, void* cuda_stream) {
+  if (!prog) return NC_E_ARG;
+  DevCopy* dc = nullptr;
+  return prepare(prog, &dc, (cudaStream_t)cuda_stream);
+}
+
+nc_status nc_sample_batch_async(const nc_program* const* progs, const uint64_t* shots, const uint64_t* seeds,
+                                uint32_t n, const nc_sample_opts* opts_in, nc_records* outs,
+                                unsigned long long* kept_dev, uint32_t* err_dev, void* cuda_stream) {
+  if (n == 0) return NC_OK;
+  if (!progs || !shots || !seeds || !outs || !kept_dev || !err_dev) return NC_E_ARG;
+  nc_sample_opts o = opts_in ? *opts_in : default_opts();
+  if (o.precision != NC_FP32_BATCHED && o.precision != NC_FP64_PLAIN && o.precision != NC_FP64_BATCHED)
+    return NC_E_ARG;
+  if (o.shot_offset % 128 || (o.outputs & NC_OUT_HOST)) return NC_E_ARG;
+  if (o.postselect != NC_PS_NONE && o.postselect != NC_PS_ALL_DETECTORS) return NC_E_ARG;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return NC_E_CUDA;
+  std::vector<DevCopy*> dcs(n, nullptr);
+  for (uint32_t i = 0; i < n; i++) {
+    if (!progs[i]) return NC_E_ARG;
+    const ProgHeader& h = header(progs[i]);
+    if (outs[i].words_per_record != (shots[i] + 63) / 64) return NC_E_ARG;
+    if ((o.outputs & NC_OUT_MEAS) && h.n_meas && !outs[i].meas) return NC_E_ARG;
+    if ((o.outputs & NC_OUT_DET) && h.n_det && !outs[i].det) return NC_E_ARG;
+    if ((o.outputs & NC_OUT_OBS) && h.n_obs && !outs[i].obs) return NC_E_ARG;
+    if ((o.outputs & NC_OUT_KEPT) && !outs[i].kept) return NC_E_ARG;
+    nc_program* p = const_cast<nc_program*>(progs[i]);
+    std::lock_guard<std::mutex> lock(p->mu);
+    for (auto& c : p->devs)
+      if (c.device == dev && c.ref_ready) dcs[i] = &c;
+    if (!dcs[i]) return NC_E_ARG;  // not prepared on this device
+    if (dcs[i]->ref_status != NC_OK) return dcs[i]->ref_status;
+  }
+  nc_status st = NC_OK;
+  {
+    Scratch scratch(stream);
+    for (uint32_t i = 0; i < n; i++) {
+      outs[i].shots_run = shots[i];
+      outs[i].shots_kept = 0;
+      outs[i].kernel_ms = outs[i].exec_ms = 0.0;
+      outs[i].launches = 0;
+      if (shots[i] == 0) continue;
+      CallOut co{(uint32_t*)outs[i].meas, (uint32_t*)outs[i].det, (uint32_t*)outs[i].obs, (uint32_t*)outs[i].kept};
+      const char* tn = o.tune ? o.tune : (dcs[i]->tuned.empty() ? nullptr : dcs[i]->tuned.c_str());
+      st = enqueue(progs[i], *dcs[i], shots[i], seeds[i], o.shot_offset, o.precision, launch_flags(o) | LF_ASYNC,
+                   tn, co, kept_dev + i, err_dev, scratch, stream);
+      if (st != NC_OK) break;
+    }
+  }
+  return st;
+}
+
+nc_status nc_autotune(nc_program* prog, uint64_t shots, const nc_sample_opts* opts_in, void* cuda_stream,
+                      char* best, size_t best_len) {
+  if (!prog || shots == 0) return NC_E_ARG;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  DevCopy* dc = nullptr;
+  nc_status st = prepare(prog, &dc, stream);
+  if (st != NC_OK) return st;
+  nc_sample_opts o = opts_in ? *opts_in : default_opts();
+  o.outputs &= ~(uint32_t)NC_OUT_HOST;
+  const ProgHeader& h = header(prog);
+  const uint64_t n = std::min<uint64_t>(std::max<uint64_t>(shots, 128), 4ull << 20);
+  const uint64_t wpr = (n + 63) / 64;
+  // candidate launch shapes
+  std::vector<std::string> cand;
+  if (h.k_max == 0 && h.aff_ok) {
+    for (const char* c : {"aw=32", "aw=16", "aw=8", "aw=32,ai=0", "a=0"}) cand.push_back(c);
+  } else {
+    const uint32_t gs[] = {1, 2, 4, 8, 16, 32, 64, 128};
+    const uint32_t ts[] = {256, 512, 1024};
+    const DevProg d = dev_view(h, dc->blob);
+    for (uint32_t g : gs)
+      for (uint32_t t : ts) {
+        if (batched_smem_bytes(d, g, 1, false) > 220 * 1024 || g > 1024u * 1024u / (1u << std::min(h.k_max, 20u)))
+          continue;
+        cand.push_back("g=" + std::to_string(g) + ",t=" + std::to_string(t));
+      }
+  }
+  Scratch scratch(stream);
+  void *meas = nullptr, *det = nullptr, *obs = nullptr, *kept = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (h.n_meas) e = scratch.get(&meas, (size_t)h.n_meas * wpr * 8);
+  if (e == cudaSuccess && h.n_det) e = scratch.get(&det, (size_t)h.n_det * wpr * 8);
+  if (e == cudaSuccess && h.n_obs) e = scratch.get(&obs, (size_t)h.n_obs * wpr * 8);
+  if (e == cudaSuccess) e = scratch.get(&kept, wpr * 8);
+  if (e != cudaSuccess) return cuda_status(e);
+  nc_records r;
+  std::memset(&r, 0, sizeof(r));
+  r.meas = (uint64_t*)meas;
+  r.det = (uint64_t*)det;
+  r.obs = (uint64_t*)obs;
+  r.kept = (uint64_t*)kept;
+  r.words_per_record = wpr;
+  std::string win;
+  double win_ms = 1e30;
+  const uint64_t seed = 1;
+  for (const auto& c : cand) {
+    nc_sample_opts oc = o;
+    oc.tune = c.c_str();
+    const nc_program* cp = prog;
+    if (sample_many(&cp, &n, &seed, 1, &oc, &r, stream) != NC_OK) continue;  // warm-up; skips unusable shapes
+    double ms = 1e30;
+    for (int rep = 0; rep < 2; rep++) {
+      if (sample_many(&cp, &n, &seed, 1, &oc, &r, stream) != NC_OK) break;
+      ms = std::min(ms, r.kernel_ms);
+    }
+    if (ms < win_ms) {
+      win_ms = ms;
+      win = c;
+    }
+  }
+  if (win.empty()) return NC_E_UNSUPPORTED;
+  {
+    std::lock_guard<std::mutex> lock(prog->mu);
+    dc->tuned = win;
+  }
+  if (best && best_len) snprintf(best, best_len, "%s", win.c_str());
+  return NC_OK;
+}
+
 void nc_program_free(nc_program* prog) {
   if (!prog) return;
   int cur = 0;
@@ -915,7 +1057,7 @@ done:
   return st;
 }
 
-uint32_t nc_abi_version(void) { return (kVersion << 16) | 2u; }
+uint32_t nc_abi_version(void) { return (kVersion << 16) | 3u; }
 
 }  // extern "C"
 

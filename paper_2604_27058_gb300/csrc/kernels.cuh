@@ -51,6 +51,7 @@ enum : uint32_t {
   LF_OUT_DET = 16,
   LF_OUT_OBS = 32,
   LF_OUT_KEPT = 64,
+  LF_ASYNC = 128,     // host side only: no host synchronisation (stream capture)
 };
 
 struct LaunchParams {

@@ -424,3 +424,48 @@ def test_closed_form_t_on_plus_statistics(nc, precision):
     p1 = float(g["meas"][0].mean())
     exp = 1 - math.cos(math.pi / 8) ** 2
     assert abs(p1 - exp) <= 5 * math.sqrt(exp * (1 - exp) / shots)
+
+
+# ---------------------------------------------------------------------------
+# batching: many circuits in one captured CUDA graph; the autotuner
+# ---------------------------------------------------------------------------
+def test_graph_captured_batch_equals_batch(nc):
+    """nc_sample_batch_async captured in a CUDA graph (the uneven sweep mix,
+    k_max 0..14) gives the records of nc_sample_batch, on two replays."""
+    import torch
+    sweep = gc.sweep_batch(64)
+    picks = sorted(range(64), key=lambda i: (gc.sweep_mirror(i).n, i))[:6]
+    progs = [nc.compile(sweep[i].text) for i in picks]
+    shots = [5_000 + 1_000 * j for j in range(len(progs))]
+    seeds = [5005 + i for i in picks]
+    ref = nc.sample_batch(progs, shots, seeds)
+    for p in progs:
+        nc.prepare(p)
+    outs = [nc.alloc_records(p, s) for p, s in zip(progs, shots)]
+    kept = torch.zeros(len(progs), dtype=torch.int64, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        nc.sample_batch_async(progs, shots, seeds, outs, kept, err)
+    for _ in range(2):
+        kept.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
+        for p, o, r, s in zip(progs, outs, ref, shots):
+            info = p.info
+            for key, n in (("meas", info.n_meas), ("det", info.n_det), ("obs", info.n_obs), ("kept", 1)):
+                assert torch_equal(o[key][:n], r[key][:n]), key
+        assert [int(x) for x in kept.cpu()] == shots
+
+
+def test_autotune_keeps_records(nc):
+    for text in (gc.surface_code_memory(d=3, rounds=3, p=0.01), gc.tiny_random(seed=2)):
+        prog = nc.compile(text)
+        before = nc.sample(prog, 20_000, 77)
+        best = nc.autotune(prog, 200_000)
+        assert best
+        after = nc.sample(prog, 20_000, 77)
+        info = prog.info
+        for key, n in (("meas", info.n_meas), ("det", info.n_det), ("obs", info.n_obs), ("kept", 1)):
+            assert torch_equal(before[key][:n], after[key][:n]), (best, key)
