@@ -97,6 +97,13 @@ DevProg dev_view(const ProgHeader& h, const uint8_t* base) {
   d.n_obs = h.n_obs;
   d.n_blocks = h.n_blocks;
   d.srch = reinterpret_cast<const uint32_t*>(base + h.off_srch);
+  if (h.n_fops) {
+    d.fops = reinterpret_cast<const Op*>(base + h.off_fops);
+    d.fterm = reinterpret_cast<const FTerm*>(base + h.off_fterm);
+    d.fperm = reinterpret_cast<const uint32_t*>(base + h.off_fperm);
+    d.n_fops = h.n_fops;
+    d.f_perm = h.f_perm;
+  }
   d.guide = reinterpret_cast<const uint32_t*>(base + h.off_guide);
   if (h.aff_ok) {
     d.aff_const = reinterpret_cast<const uint32_t*>(base + h.off_aff_const);
@@ -573,7 +580,10 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
     uint64_t grid = std::min<uint64_t>(L.n_tiles, (uint64_t)per_sm * n_sm);
     if (h.k_max > 0) {
       L.work_stride = ((size_t)1 << h.k_max) * S;
-      size_t per_cta = L.work_stride * (fp64 ? sizeof(double) : sizeof(float)) * 2;
+      // two buffers per CTA when the fused list gathers (debug stops use the
+      // original list)
+      const bool two = h.n_fops && h.f_perm && stop_event == 0xffffffffu;
+      size_t per_cta = L.work_stride * (fp64 ? sizeof(double) : sizeof(float)) * 2 * (two ? 2 : 1);
       size_t free_b = 0;
       NC_TRY(free_memory(lflags, &free_b));
       uint64_t cap = std::max<uint64_t>(1, (uint64_t)(free_b * 0.6) / per_cta);
@@ -833,7 +843,7 @@ nc_status nc_program_deserialize(const void* buf, size_t len, nc_program** out) 
                      h.off_site_opt, h.off_opt_tab, h.off_plist, h.off_orec, h.off_site_blk,
                      h.off_aff_const, h.off_aff_rowev_off, h.off_aff_rowev, h.off_aff_rand_ev,
                      h.off_aff_col_off, h.off_aff_col, h.off_aff_frec, h.off_aff_parent, h.off_aff_chain_off,
-                     h.off_aff_chain, h.off_srch, h.off_guide};
+                     h.off_aff_chain, h.off_srch, h.off_guide, h.off_fops, h.off_fterm, h.off_fperm};
   for (uint64_t o : offs)
     if (o > h.total_bytes || (o & 15)) return NC_E_ARG;
   if (h.off_ops + (uint64_t)h.n_ops * sizeof(Op) > h.total_bytes || h.k_max > kMaxK || h.n_qubits > kMaxQubits)

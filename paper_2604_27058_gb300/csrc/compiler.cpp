@@ -1376,6 +1376,7 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     cp(h.off_srch, srch.data(), S * sizeof(SrchRec));
     cp(h.off_guide, guide.data(), guide.size() * 4);
     append_affine(out.blob);
+    append_fused(out.blob);
     out.counts = c.counts;
     return 0;
   } catch (CompileError& e) {

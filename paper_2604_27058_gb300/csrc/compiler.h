@@ -25,4 +25,8 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
 // program with k_max = 0 (affine.cpp).
 void append_affine(std::vector<uint8_t>& blob);
 
+// Appends the fused array-pass instruction list (program.h OP_DIAGF /
+// OP_MIXF / OP_PERMF) for the batched executor (fuse.cpp).
+void append_fused(std::vector<uint8_t>& blob);
+
 }  // namespace nc

@@ -91,8 +91,9 @@ __device__ __forceinline__ bool is_meas(uint8_t c) {
 constexpr uint32_t kQueue = 256;
 
 struct SmemLayout {
-  size_t pl, sl, nf, cur, tmp, qu, ops, qc, red, bytes;
+  size_t pl, sl, nf, cur, tmp, qu, ops, qc, red, ft, bytes;
 };
+constexpr uint32_t kFTermSmem = 64;  // terms of a fused pass staged in shared memory
 
 __host__ __device__ inline SmemLayout smem_layout(uint32_t n_qubits, uint32_t n_slots, uint32_t k_max, uint32_t G,
                                                   uint32_t W, uint32_t qc_n, bool bk = false) {
@@ -121,6 +122,9 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t n_qubits, uint32_t n_
   w = (w + 3) & ~(size_t)3;
   L.red = w;
   if (k_max > 0) w += (size_t)2 * 2 * 32 * G;  // 2 doubles per shot
+  w = (w + 7) & ~(size_t)7;
+  L.ft = w;
+  if (k_max > 0) w += (size_t)kFTermSmem * (sizeof(FTerm) / 4);
   L.bytes = w * 4;
   return L;
 }
@@ -206,7 +210,14 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
   const uint32_t lane = t & 31u, warp = t >> 5;
   uint16_t* QU = reinterpret_cast<uint16_t*>(smem + lay.qu) + (size_t)warp * kQueue;
   double* RED = reinterpret_cast<double*>(smem + lay.red);
-  C* work = reinterpret_cast<C*>(L.work) + (size_t)blockIdx.x * L.work_stride;
+  // the fused array-pass list (fuse.cpp) unless a debug stop needs the
+  // original one; with gather passes each CTA owns two vector buffers
+  const bool fused = p.n_fops > 0 && L.stop_event == 0xffffffffu;
+  const Op* OPS = fused ? p.fops : p.ops;
+  const uint32_t n_ops = fused ? p.n_fops : p.n_ops;
+  C* const work_base = reinterpret_cast<C*>(L.work) + (size_t)blockIdx.x * L.work_stride * (fused && p.f_perm ? 2 : 1);
+  C* work = work_base;
+  C* work2 = work_base + L.work_stride;
   Op* OPB = reinterpret_cast<Op*>(smem + lay.ops);
   uint64_t* QC = reinterpret_cast<uint64_t*>(smem + lay.qc);
 
@@ -218,11 +229,11 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
   const uint32_t sub = T >= S ? t / S : 0u;
   const bool noisy = !(L.flags & LF_NOISELESS) && p.n_sites > 0;
   const uint32_t kept_off = p.kept_slot * G;
-  const uint32_t n_chunks = (p.n_ops + kChunk - 1) / kChunk;
+  const uint32_t n_chunks = (n_ops + kChunk - 1) / kChunk;
 
   auto load_chunk = [&](uint32_t c) {
-    const uint32_t first = c * kChunk, cnt = min(kChunk, p.n_ops - first);
-    const uint4* src = reinterpret_cast<const uint4*>(p.ops + first);
+    const uint32_t first = c * kChunk, cnt = min(kChunk, n_ops - first);
+    const uint4* src = reinterpret_cast<const uint4*>(OPS + first);
     uint4* dst = reinterpret_cast<uint4*>(OPB + (c & 1u) * kChunk);
     for (uint32_t i = t; i < 2 * cnt; i += T) cp_async16(dst + i, src + i);
     cp_async_commit();
@@ -271,6 +282,8 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
         }
       }
     }
+    work = work_base;
+    work2 = work_base + L.work_stride;
     if (p.k_max > 0) {
       for (uint32_t s = t; s < S; s += T) {
         C one;
@@ -299,7 +312,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
     for (uint32_t ch = 0; ch < n_chunks; ch++) {
       if (ch + 1 < n_chunks) load_chunk(ch + 1);
       const Op* ops = OPB + (ch & 1u) * kChunk;
-      const uint32_t n_here = min(kChunk, p.n_ops - ch * kChunk);
+      const uint32_t n_here = min(kChunk, n_ops - ch * kChunk);
       Op nxt = ops[0];
       uint32_t skip = 0;  // payload instructions consumed by a batch
       for (uint32_t pi = 0; pi < n_here; pi += 1 + skip) {
@@ -707,6 +720,124 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
               if (c) atomicAdd(L.kept_count, (unsigned long long)c);
             }
             break;
+          case OP_DIAGF:
+          case OP_MIXF:
+          case OP_PERMF: {
+            // ---- fused array passes (fuse.cpp): amplitude i at p = A i ^ c ----
+            __syncthreads();
+            const FTerm* TG = p.fterm + op.i2 + (op.code == OP_MIXF ? 1u : 0u);
+            const uint32_t nt = op.i3, ns = min(nt, kFTermSmem);
+            FTerm* FT = reinterpret_cast<FTerm*>(smem + lay.ft);
+            for (uint32_t e = t; e < 2 * ns; e += T)
+              reinterpret_cast<uint4*>(FT)[e] = __ldg(reinterpret_cast<const uint4*>(TG) + e);
+            __syncthreads();
+            // product of the deferred diagonal phases at physical indices q0 and
+            // q1 (a pair, or the same index twice): quarter turns from CZ / S,
+            // complex factors from ROTZ
+            auto phase2 = [&](C& v0, C& v1, uint32_t q0, uint32_t q1, uint32_t s, bool pair) {
+              uint32_t qt0 = 0, qt1 = 0;
+              for (uint32_t e = 0; e < nt; e++) {
+                const FTerm& tm = e < ns ? FT[e] : TG[e];
+                const uint32_t kind = tm.kind & 255u;
+                const uint32_t a0 = (__popc(q0 & tm.r1) ^ (tm.kind >> 8)) & 1u;
+                const uint32_t a1 = pair ? (__popc(q1 & tm.r1) ^ (tm.kind >> 8)) & 1u : 0u;
+                if (!(a0 | a1)) continue;
+                if (kind == FT_CZ) {
+                  qt0 += (a0 & (__popc(q0 & tm.r2) ^ (tm.kind >> 9))) << 1;
+                  if (pair) qt1 += (a1 & (__popc(q1 & tm.r2) ^ (tm.kind >> 9))) << 1;
+                } else if (kind == FT_S) {
+                  qt0 += a0;
+                  qt1 += a1;
+                } else {
+                  C ph;
+                  ph.x = (real)tm.cs;
+                  ph.y = (real)(fbit(PL + tm.plane * G, s) ? -tm.sn : tm.sn);
+                  if (a0) v0 = cmul(v0, ph);
+                  if (a1) v1 = cmul(v1, ph);
+                }
+              }
+              auto turn = [](C v, uint32_t q) {
+                C r = v;
+                switch (q & 3u) {
+                  case 1: r.x = -v.y; r.y = v.x; break;
+                  case 2: r.x = -v.x; r.y = -v.y; break;
+                  case 3: r.x = v.y; r.y = -v.x; break;
+                  default: break;
+                }
+                return r;
+              };
+              v0 = turn(v0, qt0);
+              if (pair) v1 = turn(v1, qt1);
+            };
+            const uint32_t dim = 1u << k;
+            if (op.code == OP_DIAGF) {
+              for (uint32_t s = t % S; s < S; s += T)
+                for (uint32_t j = sub; j < dim; j += R) {
+                  C v = work[(size_t)j * S + s], dummy = v;
+                  phase2(v, dummy, j, j, s, false);
+                  work[(size_t)j * S + s] = v;
+                }
+            } else if (op.code == OP_MIXF) {
+              const FTerm lead = p.fterm[op.i2];
+              const uint32_t m = op.i0, r = op.i1 & 0x7FFFFFFFu, rc = op.i1 >> 31, piv = op.pa;
+              const real rs = (real)0.70710678118654752440;
+              for (uint32_t s = t % S; s < S; s += T) {
+                const real cr = (real)lead.cs, sr = (real)(fbit(PL + lead.plane * G, s) ? -lead.sn : lead.sn);
+                for (uint32_t j = sub; j < dim / 2; j += R) {
+                  uint32_t q0 = insert0(j, piv), q1 = q0 ^ m;
+                  if ((__popc(q0 & r) ^ rc) & 1u) {
+                    const uint32_t x = q0;
+                    q0 = q1;
+                    q1 = x;
+                  }
+                  if ((q0 | q1) >= dim) {  // cannot happen for a well-formed list
+                    atomicOr(L.err, 2u);
+                    continue;
+                  }
+                  const size_t i0 = (size_t)q0 * S + s, i1 = (size_t)q1 * S + s;
+                  C a = work[i0], b = work[i1];
+                  phase2(a, b, q0, q1, s, true);
+                  C na, nb;
+                  if (op.pb == 0) {
+                    na = cscale(cadd(a, b), rs);
+                    nb = cscale(csub(a, b), rs);
+                  } else {
+                    na.x = cr * a.x + sr * b.y;
+                    na.y = cr * a.y - sr * b.x;
+                    nb.x = sr * a.y + cr * b.x;
+                    nb.y = -sr * a.x + cr * b.y;
+                  }
+                  work[i0] = na;
+                  work[i1] = nb;
+                }
+              }
+            } else {
+              // gather into logical order: new[i] = phase(q) old[q], q = A i ^ c
+              const uint32_t* cols = p.fperm + op.i0;
+              const uint32_t kk = op.i1, c0 = __ldg(cols + kk);
+              for (uint32_t s = t % S; s < S; s += T)
+                for (uint32_t j = sub; j < dim; j += R) {
+                  uint32_t q = c0, bits = j;
+                  while (bits) {
+                    q ^= __ldg(cols + (__ffs(bits) - 1));
+                    bits &= bits - 1;
+                  }
+                  if (q >= dim) {  // cannot happen for a well-formed list
+                    atomicOr(L.err, 2u);
+                    continue;
+                  }
+                  C v = work[(size_t)q * S + s], dummy = v;
+                  phase2(v, dummy, q, q, s, false);
+                  work2[(size_t)j * S + s] = v;
+                }
+              __syncthreads();
+              C* const x = work;
+              work = work2;
+              work2 = x;
+            }
+            __syncthreads();
+            break;
+          }
           default: {
             // ---- instructions on the active array (all threads) ----
             if (is_meas(op.code) && L.stop_event != 0xffffffffu && op.i1 == L.stop_event) goto dump;

@@ -37,6 +37,11 @@ struct DevProg {
   const uint32_t* aff_chain;
   const uint32_t* srch;   // SrchRec per site (program.h)
   const uint32_t* guide;
+  // fused array-pass list (fuse.cpp; n_fops = 0: none)
+  const Op* fops;
+  const FTerm* fterm;
+  const uint32_t* fperm;
+  uint32_t n_fops, f_perm;
   uint32_t n_qubits, nw, n_ops, n_sites, n_slots, k_max, kept_slot;
   uint32_t n_meas, n_det, n_obs, n_blocks;
   uint32_t aff_rows, aff_n_rand, aff_n_chains, aff_n_chain_rows;

@@ -93,6 +93,13 @@ DevProg view(const ProgHeader& h, const uint8_t* base) {
   d.n_obs = h.n_obs;
   d.n_blocks = h.n_blocks;
   d.srch = reinterpret_cast<const uint32_t*>(base + h.off_srch);
+  if (h.n_fops) {
+    d.fops = reinterpret_cast<const Op*>(base + h.off_fops);
+    d.fterm = reinterpret_cast<const FTerm*>(base + h.off_fterm);
+    d.fperm = reinterpret_cast<const uint32_t*>(base + h.off_fperm);
+    d.n_fops = h.n_fops;
+    d.f_perm = h.f_perm;
+  }
   d.guide = reinterpret_cast<const uint32_t*>(base + h.off_guide);
   if (h.aff_ok) {
     d.aff_const = reinterpret_cast<const uint32_t*>(base + h.off_aff_const);
@@ -161,7 +168,7 @@ nc_status launch(const DevProg& d, uint64_t shots, uint64_t seed, uint64_t shot_
   uint64_t grid = std::min<uint64_t>(L.n_tiles, (uint64_t)per_sm * n_sm);
   if (d.k_max > 0) {
     L.work_stride = ((uint64_t)1 << d.k_max) * 32ull * G;
-    const uint64_t per_cta = L.work_stride * sizeof(float) * 2;
+    const uint64_t per_cta = L.work_stride * sizeof(float) * 2 * (d.n_fops && d.f_perm ? 2 : 1);
     const uint64_t fit = work_bytes / per_cta;
     if (fit == 0) return NC_E_ARG;  // one tile's amplitudes exceed the fixed scratch
     grid = std::min<uint64_t>(grid, fit);

@@ -40,8 +40,26 @@ enum OpCode : uint8_t {
   // all inside one staging chunk) may run together. An executor may also
   // ignore the header and run them one by one.
   OP_BATCH,
+  // Fused array passes (second instruction list, batched executor only;
+  // fuse.cpp). Amplitude i of the active vector sits at p = A i ^ c.
+  OP_DIAGF,  // i2 = first term, i3 = term count: apply the diagonal terms to every amplitude
+  OP_MIXF,   // pair pass: partner mask i0, orientation mask i1 (bit 31: its constant), pivot
+             // bit pa, pb = 0 H / 1 ROT_X; i2 = lead record (ROT_X angle, sign plane), then i3 terms
+  OP_PERMF,  // gather into logical order: perm table at i0 (i1 column masks, then c), i2 / i3 terms
   OP_COUNT
 };
+
+// Terms of fused passes (32 bytes). kind bits 0..7: FT_*; bit 8 / bit 9: the
+// constants of the two parities. A parity is parity(r & p) ^ constant for
+// physical index p. CZ: -1 if both parities are 1; S: i if the parity is 1;
+// ROTZ: (cs, sn) with sn negated when frame plane `plane` is set, if the
+// parity is 1; MIX: the lead record of OP_MIXF (cs, sn and the sign plane).
+enum : uint32_t { FT_CZ = 1, FT_S = 2, FT_ROTZ = 3, FT_MIX = 4 };
+struct FTerm {
+  uint32_t kind, plane, r1, r2;
+  double cs, sn;
+};
+static_assert(sizeof(FTerm) == 32, "FTerm must be 32 bytes");
 
 // FLAG_REF (DETECTOR, OBS_OUT): the noiseless reference parity is 1. It is
 // set on the device copy after the reference launch (patch_ref_flags).
@@ -107,10 +125,13 @@ struct ProgHeader {
   uint32_t n_guide;                // survival guide-table entries
   uint32_t aff_n_chains;           // delta-row chains of two or more rows
   uint32_t aff_n_chain_rows, pad3; // rows on those chains
+  uint32_t n_fops, n_fterms;       // fused instruction list and its terms (0: none)
+  uint32_t n_fperm, f_perm;        // permutation-table words; 1 if the list has OP_PERMF
   uint64_t off_ops, off_masks, off_q, off_seg_start, off_seg_end, off_site_info, off_site_eff,
       off_slot_list, off_det_ref, off_obs_ref, off_site_opt, off_opt_tab, off_plist, off_orec, off_site_blk,
       off_aff_const, off_aff_rowev_off, off_aff_rowev, off_aff_rand_ev, off_aff_col_off, off_aff_col,
-      off_aff_frec, off_aff_parent, off_aff_chain_off, off_aff_chain, off_srch, off_guide, total_bytes;
+      off_aff_frec, off_aff_parent, off_aff_chain_off, off_aff_chain, off_srch, off_guide, off_fops, off_fterm,
+      off_fperm, total_bytes;
 };
 // Survival-jump search (Sec. 3.2 jump, integer form). srch[st] (32 bytes)
 // holds, for a jump starting at site st: the segment [a, b), its guide-table
@@ -170,7 +191,7 @@ constexpr uint32_t kRecPerSite = 15;
 // row): its fault flips the slot and, if the shot is kept, the output bit.
 
 constexpr uint32_t kMagic = 0x4E435047u;  // "NCPG"
-constexpr uint32_t kVersion = 8;
+constexpr uint32_t kVersion = 9;
 constexpr uint32_t kMaxK = 30;
 constexpr uint32_t kMaxQubits = 4096;
 

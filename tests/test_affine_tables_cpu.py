@@ -16,13 +16,14 @@ from oracle.philox import meas_u
 from oracle.records import raw_parities
 from oracle.stabilizer import FrameSim
 
-HEAD = "<17If10I"  # 17 counts, mean_faults, n_blocks, aff_ok, aff_rows, aff_n_rand, aff_n_chunks,
-                   # aff_chunks_per_shot (read as u32), n_guide, aff_n_chains, aff_n_chain_rows, pad
+HEAD = "<17If14I"  # 17 counts, mean_faults, n_blocks, aff_ok, aff_rows, aff_n_rand, aff_n_chunks,
+                   # aff_chunks_per_shot (read as u32), n_guide, aff_n_chains, aff_n_chain_rows, pad,
+                   # n_fops, n_fterms, n_fperm, f_perm
 HEAD_BYTES = struct.calcsize(HEAD)
 OFF_NAMES = ["ops", "masks", "q", "seg_start", "seg_end", "site_info", "site_eff", "slot_list", "det_ref",
              "obs_ref", "site_opt", "opt_tab", "plist", "orec", "site_blk", "aff_const", "aff_rowev_off",
              "aff_rowev", "aff_rand_ev", "aff_col_off", "aff_col", "aff_frec", "aff_parent", "aff_chain_off",
-             "aff_chain", "srch", "guide", "total_bytes"]
+             "aff_chain", "srch", "guide", "fops", "fterm", "fperm", "total_bytes"]
 REC_PER_SITE = 15
 
 
