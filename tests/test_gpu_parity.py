@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
 
-Tolerances (see DESIGN.md): records bit-exact (integer paths without any
+Tolerances: records bit-exact (integer paths without any
 exclusion; paths with active amplitudes excluding flagged near-ties with
 |u - P| < 1e-6); amplitudes norm-wise relative error modulo global phase
 <= 1e-5 for the FP32 batched form and <= 1e-10 for the FP64 plain form;
