@@ -469,3 +469,51 @@ def test_autotune_keeps_records(nc):
         info = prog.info
         for key, n in (("meas", info.n_meas), ("det", info.n_det), ("obs", info.n_obs), ("kept", 1)):
             assert torch_equal(before[key][:n], after[key][:n]), (best, key)
+
+
+# ---------------------------------------------------------------------------
+# degenerate and large programs
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("text", ["", "H 0\n", "X_ERROR(0.5) 0 1 2\n", "DEPOLARIZE1(0.2) 0\nH 1\nT 1\n"])
+def test_programs_without_records(nc, text):
+    """No measurements at all: nothing but the kept row is written, every
+    shot is kept."""
+    prog = nc.compile(text)
+    assert prog.info.n_meas == 0
+    res = nc.sample(prog, 1000, 5)
+    assert res["shots_kept"] == 1000
+    kept = nc.unpack_rows(res["kept"][:1], 1000)
+    assert kept.all()
+
+
+def test_wide_clifford_circuit_bit_exact(nc):
+    """1000 qubits (2002 frame planes), noisy CX layers, measurements with
+    record flips and detectors: records equal the oracle's frame simulator,
+    through the record-level path and through the bytecode executor."""
+    import random
+    rng = random.Random(9)
+    n = 1000
+    lines = []
+    for layer in range(4):
+        q = list(range(n))
+        rng.shuffle(q)
+        pairs = [q[i:i + 2] for i in range(0, n - 1, 2)]
+        lines.append("H " + " ".join(str(x) for x in range(0, n, 3)))
+        lines.append("CX " + " ".join(f"{a} {b}" for a, b in pairs))
+        lines.append("DEPOLARIZE2(0.002) " + " ".join(f"{a} {b}" for a, b in pairs))
+        lines.append("H " + " ".join(str(x) for x in range(0, n, 3)))
+    sel = list(range(0, n, 7))
+    lines.append("M(0.01) " + " ".join(str(x) for x in sel))
+    lines.append("M " + " ".join(str(x) for x in sel))
+    for j in range(len(sel)):
+        lines.append(f"DETECTOR rec[-{len(sel) - j}] rec[-{2 * len(sel) - j}]")
+    text = "\n".join(lines) + "\n"
+    prog = nc.compile(text)
+    assert prog.info.k_max == 0 and prog.info.n_qubits == n
+    sim = FrameSim(text)
+    shots = 3000
+    idx = sorted(set(range(0, shots, 97)) | {shots - 1})
+    for tune in (None, "a=0"):
+        g = gpu_records(prog, shots, 4242, tune=tune)
+        n_ok, _ = _check(_frame_run(sim, 4242), sim.ref_det, sim.ref_obs, sim.flat, g, 4242, idx, exact=True)
+        assert n_ok == len(idx)
