@@ -21,7 +21,7 @@
 #include "kernels.cuh"
 
 namespace nc {
-size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W, bool bk);
+size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W, bool bk, uint32_t work_words = 0);
 uint32_t coarse_stride(uint32_t n_sites);
 uint32_t coarse_count(uint32_t n_sites);
 cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, bool bk, uint32_t grid, uint32_t threads,
@@ -187,13 +187,14 @@ struct Scratch {
 // (slower on GB300 for the surface-code workload, so off by default).
 struct Tuning {
   uint32_t G, T, W, B, A, AW, AI, AV, AC, PS, AO;  // PS = 1: pre-sample faults even for small calls
+  uint32_t SW = 1;                                 // SW = 0: active vectors never in shared memory
 };
 
 Tuning choose_tuning(const DevProg& d, const char* tune, uint64_t shots, int n_sm) {
   Tuning t;
   if (d.k_max == 0) t = {128, 128, 1, 1, 1, 0, 1, 0, 0, 0, 0};
   else if (d.k_max <= 6) t = {64, 512, 1, 1, 1, 0, 1, 0, 0, 0, 0};
-  else if (d.k_max <= 10) t = {8, 512, 1, 1, 1, 0, 1, 0, 0, 0, 0};
+  else if (d.k_max <= 10) t = {16, 512, 1, 1, 1, 0, 1, 0, 0, 0, 0};
   else if (d.k_max <= 13) t = {2, 512, 1, 1, 1, 0, 1, 0, 0, 0, 0};
   else t = {1, 1024, 1, 1, 1, 0, 1, 0, 0, 0, 0};
   // small calls: smaller tiles, so that every SM gets one
@@ -213,6 +214,7 @@ Tuning choose_tuning(const DevProg& d, const char* tune, uint64_t shots, int n_s
       else if (sscanf(s, "ac=%u", &v) == 1) t.AC = v;
       else if (sscanf(s, "ps=%u", &v) == 1) t.PS = v;
       else if (sscanf(s, "ao=%u", &v) == 1) t.AO = v;
+      else if (sscanf(s, "sw=%u", &v) == 1) t.SW = v;
       const char* c = strchr(s, ',');
       if (!c) break;
       s = c + 1;
@@ -570,20 +572,27 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
         }
       }
     }
-    const size_t smem = batched_smem_bytes(L.p, tu.G, tu.W, bk);
+    const bool fp64 = precision == NC_FP64_BATCHED;
+    // the tile's active vectors: shared memory when they fit beside the
+    // planes (small tiles: latency-bound calls), else the global workspace;
+    // two buffers per CTA when the fused list gathers (debug stops use the
+    // original list)
+    const bool two = h.n_fops && h.f_perm && stop_event == 0xffffffffu;
+    size_t per_cta = 0;
+    if (h.k_max > 0) {
+      L.work_stride = ((size_t)1 << h.k_max) * S;
+      per_cta = L.work_stride * (fp64 ? sizeof(double) : sizeof(float)) * 2 * (two ? 2 : 1);
+      if (tu.SW && per_cta <= 64 * 1024 && batched_smem_bytes(L.p, tu.G, tu.W, bk, 0) + per_cta <= 200 * 1024)
+        L.smem_work_words = (uint32_t)(per_cta / 4);
+    }
+    const size_t smem = batched_smem_bytes(L.p, tu.G, tu.W, bk, L.smem_work_words);
     int per_sm = 0, n_sm = 0, dev = 0;
     NC_TRY(cudaGetDevice(&dev));
     NC_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-    const bool fp64 = precision == NC_FP64_BATCHED;
     NC_TRY(batched_occupancy(fp64, tu.W, bk, tu.T, smem, &per_sm));
     if (per_sm < 1) return NC_E_UNSUPPORTED;
     uint64_t grid = std::min<uint64_t>(L.n_tiles, (uint64_t)per_sm * n_sm);
-    if (h.k_max > 0) {
-      L.work_stride = ((size_t)1 << h.k_max) * S;
-      // two buffers per CTA when the fused list gathers (debug stops use the
-      // original list)
-      const bool two = h.n_fops && h.f_perm && stop_event == 0xffffffffu;
-      size_t per_cta = L.work_stride * (fp64 ? sizeof(double) : sizeof(float)) * 2 * (two ? 2 : 1);
+    if (h.k_max > 0 && !L.smem_work_words) {
       size_t free_b = 0;
       NC_TRY(free_memory(lflags, &free_b));
       uint64_t cap = std::max<uint64_t>(1, (uint64_t)(free_b * 0.6) / per_cta);

@@ -91,12 +91,13 @@ __device__ __forceinline__ bool is_meas(uint8_t c) {
 constexpr uint32_t kQueue = 256;
 
 struct SmemLayout {
-  size_t pl, sl, nf, cur, tmp, qu, ops, qc, red, ft, bytes;
+  size_t pl, sl, nf, cur, tmp, qu, ops, qc, red, ft, work, bytes;
 };
 constexpr uint32_t kFTermSmem = 64;  // terms of a fused pass staged in shared memory
 
 __host__ __device__ inline SmemLayout smem_layout(uint32_t n_qubits, uint32_t n_slots, uint32_t k_max, uint32_t G,
-                                                  uint32_t W, uint32_t qc_n, bool bk = false) {
+                                                  uint32_t W, uint32_t qc_n, bool bk = false,
+                                                  uint32_t work_words = 0) {
   // the bucketed executor keeps no per-shot noise state (NF, CUR, QU, QC)
   if (bk) qc_n = 0;
   SmemLayout L;
@@ -125,6 +126,10 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t n_qubits, uint32_t n_
   w = (w + 7) & ~(size_t)7;
   L.ft = w;
   if (k_max > 0) w += (size_t)kFTermSmem * (sizeof(FTerm) / 4);
+  // active vectors of the tile, when they are kept in shared memory
+  w = (w + 3) & ~(size_t)3;
+  L.work = w;
+  w += work_words;
   L.bytes = w * 4;
   return L;
 }
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
   extern __shared__ __align__(16) uint32_t smem[];
   const DevProg& p = L.p;
   const uint32_t G = L.G, S = 32u * G, N = p.n_qubits, T = blockDim.x, t = threadIdx.x;
-  const SmemLayout lay = smem_layout(N, p.n_slots, p.k_max, G, W, L.qc_n, BK);
+  const SmemLayout lay = smem_layout(N, p.n_slots, p.k_max, G, W, L.qc_n, BK, L.smem_work_words);
   uint32_t* PL = smem + lay.pl;
   uint32_t* X = PL;
   uint32_t* Z = PL + (size_t)N * G;
@@ -215,7 +220,11 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
   const bool fused = p.n_fops > 0 && L.stop_event == 0xffffffffu;
   const Op* OPS = fused ? p.fops : p.ops;
   const uint32_t n_ops = fused ? p.n_fops : p.n_ops;
-  C* const work_base = reinterpret_cast<C*>(L.work) + (size_t)blockIdx.x * L.work_stride * (fused && p.f_perm ? 2 : 1);
+  // active vectors: in shared memory when they fit (small tiles), else in
+  // this CTA's slice of the global workspace
+  C* const work_base = L.smem_work_words
+                           ? reinterpret_cast<C*>(smem + lay.work)
+                           : reinterpret_cast<C*>(L.work) + (size_t)blockIdx.x * L.work_stride * (fused && p.f_perm ? 2 : 1);
   C* work = work_base;
   C* work2 = work_base + L.work_stride;
   Op* OPB = reinterpret_cast<Op*>(smem + lay.ops);
@@ -1549,8 +1558,8 @@ uint32_t coarse_count(uint32_t n_sites) {
   return n_sites ? (n_sites + s - 1) / s : 0;
 }
 
-size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W, bool bk) {
-  return smem_layout(p.n_qubits, p.n_slots, p.k_max, G, W, coarse_count(p.n_sites), bk).bytes;
+size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W, bool bk, uint32_t work_words) {
+  return smem_layout(p.n_qubits, p.n_slots, p.k_max, G, W, coarse_count(p.n_sites), bk, work_words).bytes;
 }
 
 template <typename real, int W, bool BIG, bool BK>

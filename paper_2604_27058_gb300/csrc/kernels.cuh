@@ -68,6 +68,7 @@ struct LaunchParams {
   uint32_t G;                         // 32-shot words per tile (batched executor)
   uint32_t n_tiles;
   uint64_t work_stride;               // amplitudes per CTA workspace (batched) / per shot (plain)
+  uint32_t smem_work_words;           // batched: > 0 = the CTA's vectors live in shared memory (words)
   void* work;                         // amplitude workspace
   unsigned long long* kept_count;
   uint32_t* err;

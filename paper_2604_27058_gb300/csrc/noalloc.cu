@@ -25,7 +25,7 @@
 #include "kernels.cuh"
 
 namespace nc {
-size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W, bool bk);
+size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W, bool bk, uint32_t work_words = 0);
 uint32_t coarse_stride(uint32_t n_sites);
 uint32_t coarse_count(uint32_t n_sites);
 cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, bool bk, uint32_t grid, uint32_t threads,

@@ -84,7 +84,8 @@ def _frame_run(sim, seed):
 # ---------------------------------------------------------------------------
 # random small circuits: every instruction kind, both forms, several tiles
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("precision,tune", [("fp32", "g=2,t=64"), ("fp32", None), ("fp64", None)])
+@pytest.mark.parametrize("precision,tune", [("fp32", "g=2,t=64"), ("fp32", None), ("fp64", None),
+                                            ("fp32", "sw=0")])
 @pytest.mark.parametrize("seed", range(10))
 def test_random_small_vs_dense(nc, seed, precision, tune):
     n = 3 + seed % 5
@@ -411,7 +412,7 @@ def test_tuning_variants_agree(nc):
     prog = nc.compile(text)
     base = gpu_records(prog, 1000, 12, precision="fp32")
     for tune in ("g=1,t=32", "g=1,t=1024", "g=8,t=256", "g=4,t=64", "b=0", "g=64,t=64", "g=32,t=256,ps=1",
-                 "ps=1,b=0", "g=8,t=512,ps=1"):
+                 "ps=1,b=0", "g=8,t=512,ps=1", "sw=0", "g=2,t=256,sw=0"):
         g = gpu_records(prog, 1000, 12, precision="fp32", tune=tune)
         assert (g["meas"] == base["meas"]).mean() > 0.999
 
