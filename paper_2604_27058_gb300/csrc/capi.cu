@@ -22,8 +22,6 @@
 
 namespace nc {
 size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W, bool bk, uint32_t work_words = 0);
-uint32_t coarse_stride(uint32_t n_sites);
-uint32_t coarse_count(uint32_t n_sites);
 cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, bool bk, uint32_t grid, uint32_t threads,
                            size_t smem, cudaStream_t st);
 cudaError_t batched_occupancy(bool fp64, uint32_t W, bool bk, uint32_t threads, size_t smem, int* blocks_per_sm);
@@ -531,8 +529,6 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
     if (!pow2(tu.G) || !pow2(tu.T) || !pow2(tu.W) || tu.T > (tu.W == 1 ? 1024u : 256u) || tu.T < 32)
       return NC_E_ARG;
     L.G = tu.G;
-    L.qc_stride = coarse_stride(h.n_sites);
-    L.qc_n = coarse_count(h.n_sites);
     const uint64_t S = 32ull * tu.G;
     L.n_tiles = (uint32_t)((L.row_words32 + tu.G - 1) / tu.G);
     // fault pre-sampling (bucketed or per-shot lists) pays off only for

@@ -7,17 +7,22 @@
 //   the G word-owner threads, one 32-shot word each, with no synchronisation.
 //   Active-array instructions (expand, rotations, array Cliffords, active
 //   measurements) run on all threads over (amplitude, shot) pairs of the
-//   tile's amplitude block in global memory, laid out amplitude-major /
-//   shot-minor so that consecutive threads touch consecutive shots.
-//   Measurement probabilities are accumulated in FP64; amplitudes are
-//   stored in `real` (float for the batched form).
+//   tile's amplitude block (global memory, or shared memory for small
+//   tiles), laid out amplitude-major / shot-minor so that consecutive
+//   threads touch consecutive shots. Measurement probabilities are
+//   accumulated in FP64; amplitudes are stored in `real` (float for the
+//   batched form). When the program carries a fused array-pass list
+//   (fuse.cpp) the executor runs that list: pair, diagonal and gather passes
+//   over an index-mapped vector.
 //
 // exec_plain: the baseline form — one thread per shot, frame and record bits
 //   in thread-local arrays, FP64 amplitudes in global memory, instructions
 //   read straight from global memory.
 //
-// Both interpret the same bytecode (program.h) and follow the same random-
-// draw contract (kernels.cuh), so they produce identical records.
+// bucket_faults / presample_faults: fault sampling ahead of the executor.
+//
+// The executors follow the same random-draw contract (kernels.cuh) and
+// produce identical records.
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
@@ -79,7 +84,6 @@ __device__ __forceinline__ bool is_meas(uint8_t c) {
 // A tile is G 32-shot words; thread t < G / W owns words t*W .. t*W+W-1.
 // Shared-memory layout of one CTA (u32 words unless noted):
 //   OPS Op [2][kChunk] double-buffered instruction chunks (cp.async)
-//   QC  u64 [qc_n] coarse survival index
 //   PL  [2N+2][G] frame planes (x bits of virtual qubit q at plane q, z bits at N + q),
 //                 an all-zero plane 2N and a scratch plane 2N + 1 (padding targets)
 //   SL  [n_slots+1][G] record slots and an all-zero slot n_slots
@@ -88,24 +92,22 @@ __device__ __forceinline__ bool is_meas(uint8_t c) {
 //   TMP [G]      per-word scratch (virtual outcomes of an active measurement)
 //   QU  u16 [owner warps][kQueue] warp queues of due (word, bit) noise entries
 //   RED f64 [2][S] measurement sums / scales (k_max > 0 only)
+//   FT  FTerm [kFTermSmem] terms of the current fused pass (k_max > 0 only)
+//   WORK the tile's active vectors, when they fit here (else global memory)
 constexpr uint32_t kQueue = 256;
 
 struct SmemLayout {
-  size_t pl, sl, nf, cur, tmp, qu, ops, qc, red, ft, work, bytes;
+  size_t pl, sl, nf, cur, tmp, qu, ops, red, ft, work, bytes;
 };
 constexpr uint32_t kFTermSmem = 64;  // terms of a fused pass staged in shared memory
 
 __host__ __device__ inline SmemLayout smem_layout(uint32_t n_qubits, uint32_t n_slots, uint32_t k_max, uint32_t G,
-                                                  uint32_t W, uint32_t qc_n, bool bk = false,
-                                                  uint32_t work_words = 0) {
-  // the bucketed executor keeps no per-shot noise state (NF, CUR, QU, QC)
-  if (bk) qc_n = 0;
+                                                  uint32_t W, bool bk = false, uint32_t work_words = 0) {
+  // the bucketed executor keeps no per-shot noise state (NF, CUR, QU)
   SmemLayout L;
   size_t w = 0;
   L.ops = w;
   w += (size_t)2 * kChunk * (sizeof(Op) / 4);
-  L.qc = w;
-  w += (size_t)2 * qc_n;
   L.pl = w;
   w += (size_t)(2 * n_qubits + 2) * G;  // + zero plane (2N) and scratch plane (2N + 1)
   L.sl = w;
@@ -204,7 +206,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
   extern __shared__ __align__(16) uint32_t smem[];
   const DevProg& p = L.p;
   const uint32_t G = L.G, S = 32u * G, N = p.n_qubits, T = blockDim.x, t = threadIdx.x;
-  const SmemLayout lay = smem_layout(N, p.n_slots, p.k_max, G, W, L.qc_n, BK, L.smem_work_words);
+  const SmemLayout lay = smem_layout(N, p.n_slots, p.k_max, G, W, BK, L.smem_work_words);
   uint32_t* PL = smem + lay.pl;
   uint32_t* X = PL;
   uint32_t* Z = PL + (size_t)N * G;
@@ -228,7 +230,6 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
   C* work = work_base;
   C* work2 = work_base + L.work_stride;
   Op* OPB = reinterpret_cast<Op*>(smem + lay.ops);
-  uint64_t* QC = reinterpret_cast<uint64_t*>(smem + lay.qc);
 
   const uint32_t n_owners = G / W;
   const bool owner = t < n_owners;
@@ -247,8 +248,6 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
     for (uint32_t i = t; i < 2 * cnt; i += T) cp_async16(dst + i, src + i);
     cp_async_commit();
   };
-  if (!BK)
-    for (uint32_t c = t; c < L.qc_n; c += T) QC[c] = __ldg(p.q + (size_t)c * L.qc_stride);
   __syncthreads();
 
   for (uint32_t tile = blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
@@ -280,9 +279,9 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
             if (L.flist) {
               const uint32_t c = L.fcount[sl0 + j];
               if (c & 127u) f = L.flist[sl0 + j];
-              else if (c & 128u) f = next_fault_coarse(p, L.seed, s0 + (uint64_t)i * 32u + j, 0, QC, L.qc_stride);
+              else if (c & 128u) f = next_fault(p, L.seed, s0 + (uint64_t)i * 32u + j, 0);
             } else {
-              f = next_fault_coarse(p, L.seed, s0 + (uint64_t)i * 32u + j, 0, QC, L.qc_stride);
+              f = next_fault(p, L.seed, s0 + (uint64_t)i * 32u + j, 0);
             }
           }
           NF[j * G + tw + i] = f;
@@ -623,7 +622,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
                       for (uint32_t q = 0; q < 7; q++)
                         if (q < tag) atomicXor(&PL[ent7[q] * G + w], bit);
                     }
-                    if (search) fn = next_fault_coarse(p, L.seed, shot, site + 1, QC, L.qc_stride);
+                    if (search) fn = next_fault(p, L.seed, shot, site + 1);
                     f = fn;
                   } while ((f >> 4) < op.i1);
                   NF[j * G + w] = f;
@@ -1552,14 +1551,8 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
 // ---------------------------------------------------------------------------
 // Host-side launchers (called from capi.cu)
 // ---------------------------------------------------------------------------
-uint32_t coarse_stride(uint32_t n_sites) { return n_sites <= 512 ? 1u : (n_sites + 511) / 512; }
-uint32_t coarse_count(uint32_t n_sites) {
-  uint32_t s = coarse_stride(n_sites);
-  return n_sites ? (n_sites + s - 1) / s : 0;
-}
-
 size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W, bool bk, uint32_t work_words) {
-  return smem_layout(p.n_qubits, p.n_slots, p.k_max, G, W, coarse_count(p.n_sites), bk, work_words).bytes;
+  return smem_layout(p.n_qubits, p.n_slots, p.k_max, G, W, bk, work_words).bytes;
 }
 
 template <typename real, int W, bool BIG, bool BK>

@@ -72,7 +72,6 @@ struct LaunchParams {
   void* work;                         // amplitude workspace
   unsigned long long* kept_count;
   uint32_t* err;
-  uint32_t qc_stride, qc_n;            // coarse survival index: every qc_stride-th Q, qc_n entries
   // pre-sampled faults (batched executor; null = sample inline): fault j of
   // call-local shot s at flist[j * fstride + s] for j < fcount[s] & 127;
   // bit 7 of fcount marks a list truncated at fcap entries.
@@ -193,13 +192,6 @@ __device__ __forceinline__ uint32_t next_fault(const DevProg& p, uint64_t seed, 
     st = nx;
   }
   return kNoFault;
-}
-
-// Older call form with a shared-memory coarse index; the guide table makes
-// the index unnecessary.
-__device__ __forceinline__ uint32_t next_fault_coarse(const DevProg& p, uint64_t seed, uint64_t shot,
-                                                      uint32_t st, const uint64_t*, uint32_t) {
-  return next_fault(p, seed, shot, st);
 }
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {

@@ -26,8 +26,6 @@
 
 namespace nc {
 size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W, bool bk, uint32_t work_words = 0);
-uint32_t coarse_stride(uint32_t n_sites);
-uint32_t coarse_count(uint32_t n_sites);
 cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, bool bk, uint32_t grid, uint32_t threads,
                            size_t smem, cudaStream_t st);
 cudaError_t batched_occupancy(bool fp64, uint32_t W, bool bk, uint32_t threads, size_t smem, int* blocks_per_sm);
@@ -156,8 +154,6 @@ nc_status launch(const DevProg& d, uint64_t shots, uint64_t seed, uint64_t shot_
   while (G > 1 && batched_smem_bytes(d, G, 1, false) > 220 * 1024) G >>= 1;
   if (T < G) T = G;
   L.G = G;
-  L.qc_stride = coarse_stride(d.n_sites);
-  L.qc_n = coarse_count(d.n_sites);
   L.n_tiles = (uint32_t)((L.row_words32 + G - 1) / G);
   const size_t smem = batched_smem_bytes(d, G, 1, false);
   int per_sm = 0, n_sm = 0, dev = 0;
