@@ -110,3 +110,13 @@ def test_repeat_and_aliases(nc):
     a = nc.compile("REPEAT 3 {\nCNOT 0 1\nMZ 1\n}\n")
     b = nc.compile("CX 0 1\nM 1\nCX 0 1\nM 1\nCX 0 1\nM 1\n")
     assert a.info == b.info
+
+
+def test_missing_library_fails_loudly(nc, monkeypatch):
+    """No CPU fallback: without libnc.so the binding raises instead of
+    sampling some other way."""
+    from paper_2604_27058_gb300 import _nc
+    monkeypatch.setattr(_nc, "LIB_PATH", "/nonexistent/libnc.so")
+    monkeypatch.setattr(_nc, "_lib", None, raising=False)
+    with pytest.raises(RuntimeError):
+        _nc.lib()
