@@ -78,7 +78,11 @@ def ncu_traffic(workload_name: str):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (every 100 ms) around the timed region. A reader
+    thread stamps each sample on arrival; start() returns once the sampler
+    is producing lines, and only samples stamped inside [start(), stop()]
+    are summarised (the first later one if the region was shorter than the
+    sampling period)."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -87,27 +91,44 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.monotonic(), line))
 
     def start(self):
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+        deadline = time.monotonic() + 3.0
+        while not self.lines and time.monotonic() < deadline:
+            time.sleep(0.01)
+        self.t0 = time.monotonic()
 
     def stop(self):
         if not self.proc:
             return None
+        self.t1 = time.monotonic()
+        time.sleep(0.25)  # one more sample after the region
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-            return None
+        inside = [ln for t, ln in self.lines if self.t0 <= t <= self.t1]
+        if not inside:
+            inside = [ln for t, ln in self.lines if t > self.t1][:1]
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        for line in inside:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -450,7 +471,7 @@ def run_sweep(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="surface")
