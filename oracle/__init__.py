@@ -13,6 +13,9 @@ Everything here is plain, slow and FP64, written from the paper:
                  and assigns physical event / site / record indices.
 * ``noise``      the cumulative-hazard jump sampler of Sec. 3.2 in its
                  integer survival form.
+* ``strata``     stratified importance sampling (Sec. 3.2): Poisson-binomial
+                 stratum weights and exactly-K fault sets drawn from the
+                 conditional distribution.
 * ``dense``      O-B: a dense 2^N state vector of the physical circuit. The
                  plain definition of what the sampler computes, for N <= ~14.
 * ``stabilizer`` O-D: CHP tableau reference + physical Pauli-frame
@@ -25,6 +28,9 @@ Everything here is plain, slow and FP64, written from the paper:
 Pins (tests/test_oracle_*.py): Philox known-answer vectors; closed forms
 (cos^2(pi/8), sin^2(theta/2), GHZ parity, T^8 = I, the Fig. 4 example);
 noise marginals and a brute-force Bernoulli comparison of the sampler;
+stratum weights against the binomial closed form and enumeration, the
+stratified sampler's path probabilities against the enumerated conditional
+distribution;
 O-D == O-B and O-A == O-B record-for-record (and P(m=1) to 1e-12) on random
 small circuits; O-A == O-D on the d=5 surface-code memory; mirror circuits.
 
