@@ -12,6 +12,9 @@ collective on the data path.
 
 --impl reference times the CPU oracle (the frame-factored FP64 oracle) on
 the host cores on a bounded sample of the same workload.
+
+--stratum K runs the same workload in stratified importance sampling
+(exactly K faults per shot); the line then names the stratum and its weight.
 """
 
 from __future__ import annotations
@@ -31,6 +34,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "shots/sec at stated peak active dim (FP32 batched vs FP64 plain); % HBM roofline"
+
+
+def workload_name(args) -> str:
+    name = workload(args.workload)[0]
+    return name if args.stratum is None else f"{name}_stratum{args.stratum}"
 
 
 def workload(name: str):
@@ -152,23 +160,35 @@ class Clocks:
 _ORACLE = None
 
 
-def _oracle_init(text):
-    global _ORACLE
+_STRATA = None
+
+
+def _oracle_init(text, stratum=None):
+    global _ORACLE, _STRATA
     from oracle.factored import FactoredSim
     _ORACLE = FactoredSim(text, k_limit=22)
+    if stratum is not None:
+        from oracle.strata import build_strata
+        _STRATA = (build_strata(_ORACLE.flat.site_p, _ORACLE.flat.site_kind, max(stratum, 1)), stratum)
 
 
 def _oracle_chunk(args):
     seed, start, count = args
     for s in range(start, start + count):
-        _ORACLE.sample(seed, s)
+        if _STRATA is None:
+            _ORACLE.sample(seed, s)
+        else:
+            from oracle.records import assemble
+            from oracle.strata import sample_stratum_faults
+            f = sample_stratum_faults(_STRATA[0], seed, s, _STRATA[1])
+            assemble(_ORACLE.flat, _ORACLE.run_raw(seed, s, faults=f)[0], _ORACLE.ref_det, _ORACLE.ref_obs, False)
     return count
 
 
-def cpu_oracle_rate(text: str, seed: int, budget_s: float, cores: int):
+def cpu_oracle_rate(text: str, seed: int, budget_s: float, cores: int, stratum=None):
     """Shots/s of the oracle on `cores` processes over a bounded sample."""
     ctx = mp.get_context("spawn")
-    with ctx.Pool(cores, initializer=_oracle_init, initargs=(text,)) as pool:
+    with ctx.Pool(cores, initializer=_oracle_init, initargs=(text, stratum)) as pool:
         # warm every worker on one shot (which also calibrates slow
         # workloads), then calibrate on up to 16 shots per worker
         t0 = time.perf_counter()
@@ -191,14 +211,15 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wname, text, shots = workload(args.workload)
+    _, text, shots = workload(args.workload)
+    wname = workload_name(args)
     cores = os.cpu_count() or 1
     rates = []
     total = 0
     for _ in range(args.warmup):
-        cpu_oracle_rate(text, 2002, args.ref_budget / 4, cores)
+        cpu_oracle_rate(text, 2002, args.ref_budget / 4, cores, args.stratum)
     for _ in range(args.steps):
-        r, n, dt = cpu_oracle_rate(text, 2002, args.ref_budget, cores)
+        r, n, dt = cpu_oracle_rate(text, 2002, args.ref_budget, cores, args.stratum)
         rates.append(r)
         total += n
     value = statistics.median(rates)
@@ -221,14 +242,15 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    wname, text, shots = workload(args.workload)
+    _, text, shots = workload(args.workload)
+    wname = workload_name(args)
     if args.shots:
         shots = args.shots
 
     cpu = None
     if rank == 0 and not args.no_cpu:
         cores = os.cpu_count() or 1
-        r, n, dt = cpu_oracle_rate(text, 2002, args.cpu_budget, cores)
+        r, n, dt = cpu_oracle_rate(text, 2002, args.cpu_budget, cores, args.stratum)
         cpu = {"value": r, "unit": "shots/s", "cores": cores, "kind": "oracle",
                "sample": f"{n} shots of {wname} in {dt:.1f} s (frame-factored FP64 oracle, "
                          f"{cores} spawn processes)"}
@@ -251,9 +273,9 @@ def run_ours(args):
     def step(precision="fp32", out=None, host=False):
         if host:
             return nc.sample_host(prog, shots, 2002, precision=precision, shot_offset=offset, out=out,
-                                  tune=args.tune)
+                                  tune=args.tune, stratum=args.stratum)
         return nc.sample(prog, shots, 2002, precision=precision, shot_offset=offset, out=out or bufs,
-                         tune=args.tune)
+                         tune=args.tune, stratum=args.stratum)
 
     def barrier():
         if world > 1:
@@ -365,6 +387,11 @@ def run_ours(args):
                        "record_bits_per_shot": info.n_meas + info.n_det + info.n_obs + 1,
                        "precision": "fp32_batched", "l2": "records per step >> L2 (no flush needed)",
                        "parallelism": f"replicas{world}"},
+            **({} if args.stratum is None else
+               {"stratum": {"faults_per_shot": args.stratum,
+                            "weight": nc.stratum_weights(prog, args.stratum)[0][args.stratum],
+                            "sampler": "exactly K faults per shot, conditional jumps (stratified importance "
+                                       "sampling)"}}),
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -484,6 +511,8 @@ def main():
     ap.add_argument("--tune", default=None, help="executor tuning override, e.g. g=64,t=64")
     ap.add_argument("--sweep-scale", type=float, default=0.01, help="sweep workload: shots per circuit scale")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--stratum", type=int, default=None,
+                    help="stratified importance sampling: exactly K faults per shot")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not os.environ.get("NC_BENCH_ALLOW_SHORT"):
         args.warmup = 3

@@ -76,6 +76,11 @@ typedef struct {
   uint64_t shot_offset;   /* global index of this call's first shot */
   const char* tune;       /* NULL = built-in heuristic; "w=<1|2|4>,g=<words>" */
   int noiseless;          /* 1 = disable every noise site (reference runs) */
+  uint32_t stratified;    /* 0 = independent noise sites (default);
+                             1 = stratified importance sampling: every shot
+                             has exactly `stratum` faults (see
+                             nc_stratum_weights) */
+  uint32_t stratum;       /* faults per shot when stratified (K <= 127) */
 } nc_sample_opts;
 
 /*
@@ -153,6 +158,36 @@ nc_status nc_sample_batch_async(const nc_program* const* progs, const uint64_t* 
                                 const uint64_t* seeds, uint32_t n, const nc_sample_opts* opts,
                                 nc_records* outs, unsigned long long* kept_dev, uint32_t* err_dev,
                                 void* cuda_stream);
+
+/*
+ * Stratified importance sampling (Sec. 3.2, the rare-event mode used for
+ * Sec. 4.2.1): a call with opts->stratified = 1 runs stratum K =
+ * opts->stratum, whose shots each have exactly K realised faults drawn from
+ * the independent-site distribution conditioned on K faults,
+ *   P(F | |F| = K) = prod_{i in F} p_i prod_{i not in F} (1 - p_i) / P(K).
+ * An estimate over strata weights the stratum-K mean by P(K), the
+ * Poisson-binomial mass that nc_stratum_weights returns. Each fault's Pauli
+ * option is drawn as for independent noise; everything else is unchanged.
+ * Draw contract: shot s holding r faults at site index st draws
+ * Philox(key, (s lo, s hi, 4, st)); u = ((w0 | w1 << 32) >> 11) * 2^-53; the
+ * fault is the first j >= st with G_r(j + 1) <= u * G_r(st) (FP64), where
+ * G_r(j) = prod_{l<j}(1 - p_l) * P(r faults among sites j..) as a running
+ * minimum over j; its option is floor(w2 * K_j / 2^32).
+ * A stratum is refused (NC_E_ARG) if some site has p >= 1, if K exceeds the
+ * number of sites with p > 0, or if the tables underflow the FP64 normal
+ * range. K = 0 is the noiseless run. nc_sample_noalloc does not support it
+ * (NC_E_UNSUPPORTED).
+ */
+
+/* weights[K] = P(exactly K faults) for K = 0..k_max (k_max + 1 doubles, host
+ * memory); valid (optional, k_max + 1 bytes) receives 1 for every stratum
+ * that can be sampled. Host computation only. */
+nc_status nc_stratum_weights(const nc_program* prog, uint32_t k_max, double* weights, uint8_t* valid);
+
+/* Upload the stratified tables for strata up to k_max to the current device
+ * (and prepare the program as nc_program_prepare does). nc_sample does this
+ * on demand; nc_sample_batch_async requires it (NC_E_ARG otherwise). */
+nc_status nc_strata_prepare(const nc_program* prog, uint32_t k_max, void* cuda_stream);
 
 /* Launch-shape autotuner (shots per CTA, CTA size, warp- or word-per-shot
  * layout of the record tile, fault pre-sampling): times the candidates for

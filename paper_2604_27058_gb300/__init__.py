@@ -5,6 +5,8 @@ one GPU.
     prog = compile(text)                       # nc_compile
     rec = sample(prog, shots, seed)            # nc_sample into torch tensors
     rec = sample_host(prog, shots, seed)       # nc_sample with host buffers
+    rec = sample(prog, shots, seed, stratum=K) # exactly K faults per shot
+    w, ok = stratum_weights(prog, k_max)       # P(K faults), K = 0..k_max
 
 Record tensors are int64 views of the bit-packed uint64 rows of include/nc.h:
 bit (s % 64) of word [r, s // 64] is record r of shot s.
@@ -22,7 +24,7 @@ from ._nc import (NC_FP32_BATCHED, NC_FP64_BATCHED, NC_FP64_PLAIN, NC_OUT_ALL, N
                   NcError, ProgramInfo)
 
 __all__ = ["Program", "compile", "sample", "sample_host", "sample_batch", "debug_dump",
-           "unpack_rows", "NcError", "NC_FP32_BATCHED", "NC_FP64_PLAIN"]
+           "stratum_weights", "strata_prepare", "unpack_rows", "NcError", "NC_FP32_BATCHED", "NC_FP64_PLAIN"]
 
 PRECISION = {"fp32": NC_FP32_BATCHED, "fp64": NC_FP64_PLAIN, "fp64_batched": NC_FP64_BATCHED,
              NC_FP32_BATCHED: NC_FP32_BATCHED, NC_FP64_PLAIN: NC_FP64_PLAIN,
@@ -75,7 +77,7 @@ def compile(text: str) -> Program:  # noqa: A001 - mirrors nc_compile
     return Program(h.value)
 
 
-def _opts(precision, outputs, postselect, shot_offset, tune, noiseless):
+def _opts(precision, outputs, postselect, shot_offset, tune, noiseless, stratum=None):
     o = _nc.SampleOpts()
     o.precision = PRECISION[precision]
     o.outputs = outputs
@@ -83,6 +85,8 @@ def _opts(precision, outputs, postselect, shot_offset, tune, noiseless):
     o.shot_offset = shot_offset
     o.tune = tune.encode() if tune else None
     o.noiseless = 1 if noiseless else 0
+    o.stratified = 0 if stratum is None else 1
+    o.stratum = 0 if stratum is None else int(stratum)
     return o
 
 
@@ -123,12 +127,14 @@ def _records_struct(bufs, wpr, host=False):
 
 
 def sample(prog: Program, shots: int, seed: int, precision="fp32", outputs=NC_OUT_ALL,
-           postselect=False, shot_offset=0, tune=None, stream=None, out=None, noiseless=False):
-    """nc_sample into device tensors; returns the buffer dict plus counts."""
+           postselect=False, shot_offset=0, tune=None, stream=None, out=None, noiseless=False, stratum=None):
+    """nc_sample into device tensors; returns the buffer dict plus counts.
+    stratum=K runs stratified importance sampling: exactly K faults per shot
+    (weights from stratum_weights)."""
     bufs = out if out is not None else alloc_records(prog, shots, outputs=outputs)
     wpr = (shots + 63) // 64
     rec = _records_struct(bufs, wpr)
-    opts = _opts(precision, outputs, postselect, shot_offset, tune, noiseless)
+    opts = _opts(precision, outputs, postselect, shot_offset, tune, noiseless, stratum)
     _nc.check(_nc.lib().nc_sample(prog.handle, shots, seed, ctypes.byref(opts), ctypes.byref(rec),
                                   ctypes.c_void_p(_stream_ptr(stream))))
     res = dict(bufs)
@@ -161,12 +167,13 @@ def alloc_host_records(prog: Program, shots: int, outputs=NC_OUT_ALL, pinned=Tru
 
 
 def sample_host(prog: Program, shots: int, seed: int, precision="fp32", outputs=NC_OUT_ALL,
-                postselect=False, shot_offset=0, tune=None, stream=None, out=None, noiseless=False):
+                postselect=False, shot_offset=0, tune=None, stream=None, out=None, noiseless=False,
+                stratum=None):
     """nc_sample with NC_OUT_HOST: records land in host (numpy) arrays."""
     bufs = out if out is not None else alloc_host_records(prog, shots, outputs)
     wpr = (shots + 63) // 64
     rec = _records_struct(bufs, wpr, host=True)
-    opts = _opts(precision, outputs | NC_OUT_HOST, postselect, shot_offset, tune, noiseless)
+    opts = _opts(precision, outputs | NC_OUT_HOST, postselect, shot_offset, tune, noiseless, stratum)
     _nc.check(_nc.lib().nc_sample(prog.handle, shots, seed, ctypes.byref(opts), ctypes.byref(rec),
                                   ctypes.c_void_p(_stream_ptr(stream))))
     res = dict(bufs)
@@ -179,14 +186,14 @@ def sample_host(prog: Program, shots: int, seed: int, precision="fp32", outputs=
 
 
 def sample_batch(progs, shots, seeds, precision="fp32", outputs=NC_OUT_ALL, postselect=False,
-                 tune=None, stream=None, outs=None):
+                 tune=None, stream=None, outs=None, stratum=None):
     n = len(progs)
     outs = outs if outs is not None else [alloc_records(p, s, outputs=outputs) for p, s in zip(progs, shots)]
     handles = (ctypes.c_void_p * n)(*[p.handle for p in progs])
     sh = (ctypes.c_uint64 * n)(*shots)
     sd = (ctypes.c_uint64 * n)(*seeds)
     recs = (_nc.Records * n)(*[_records_struct(b, (s + 63) // 64) for b, s in zip(outs, shots)])
-    opts = _opts(precision, outputs, postselect, 0, tune, False)
+    opts = _opts(precision, outputs, postselect, 0, tune, False, stratum)
     _nc.check(_nc.lib().nc_sample_batch(handles, sh, sd, n, ctypes.byref(opts), recs,
                                         ctypes.c_void_p(_stream_ptr(stream))))
     res = []
@@ -207,7 +214,7 @@ def prepare(prog: Program, stream=None) -> None:
 
 
 def sample_batch_async(progs, shots, seeds, outs, kept_dev, err_dev, precision="fp32", outputs=NC_OUT_ALL,
-                       postselect=False, tune=None, stream=None):
+                       postselect=False, tune=None, stream=None, stratum=None):
     """nc_sample_batch_async: enqueue only (capturable in a CUDA graph).
     outs: record buffers from alloc_records; kept_dev: int64 device tensor
     of len(progs) and err_dev: int32 device tensor of 1, both zeroed by the
@@ -217,7 +224,7 @@ def sample_batch_async(progs, shots, seeds, outs, kept_dev, err_dev, precision="
     sh = (ctypes.c_uint64 * n)(*shots)
     sd = (ctypes.c_uint64 * n)(*seeds)
     recs = (_nc.Records * n)(*[_records_struct(b, (s + 63) // 64) for b, s in zip(outs, shots)])
-    opts = _opts(precision, outputs, postselect, 0, tune, False)
+    opts = _opts(precision, outputs, postselect, 0, tune, False, stratum)
     _nc.check(_nc.lib().nc_sample_batch_async(handles, sh, sd, n, ctypes.byref(opts), recs,
                                               ctypes.c_void_p(kept_dev.data_ptr()),
                                               ctypes.c_void_p(err_dev.data_ptr()),
@@ -225,14 +232,29 @@ def sample_batch_async(progs, shots, seeds, outs, kept_dev, err_dev, precision="
 
 
 def autotune(prog: Program, shots: int, precision="fp32", outputs=NC_OUT_ALL, postselect=False,
-             stream=None) -> str:
+             stream=None, stratum=None) -> str:
     """nc_autotune: returns the chosen launch shape (used by later calls
     with tune=None on this device)."""
-    opts = _opts(precision, outputs, postselect, 0, None, False)
+    opts = _opts(precision, outputs, postselect, 0, None, False, stratum)
     buf = ctypes.create_string_buffer(128)
     _nc.check(_nc.lib().nc_autotune(prog.handle, shots, ctypes.byref(opts), ctypes.c_void_p(_stream_ptr(stream)),
                                     buf, 128))
     return buf.value.decode()
+
+
+def stratum_weights(prog: Program, k_max: int):
+    """nc_stratum_weights: (P(exactly K faults) for K = 0..k_max, and
+    whether each stratum can be sampled). Host computation."""
+    w = (ctypes.c_double * (k_max + 1))()
+    v = (ctypes.c_uint8 * (k_max + 1))()
+    _nc.check(_nc.lib().nc_stratum_weights(prog.handle, k_max, w, v))
+    return list(w), [bool(x) for x in v]
+
+
+def strata_prepare(prog: Program, k_max: int, stream=None) -> None:
+    """nc_strata_prepare: upload the stratified tables up to k_max (needed
+    before sample_batch_async with a stratum)."""
+    _nc.check(_nc.lib().nc_strata_prepare(prog.handle, k_max, ctypes.c_void_p(_stream_ptr(stream))))
 
 
 def debug_dump(prog: Program, seed: int, shot: int, event: int, precision="fp32", stream=None):

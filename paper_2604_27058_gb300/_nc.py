@@ -34,7 +34,7 @@ STATUS = {0: "NC_OK", 1: "NC_E_PARSE", 2: "NC_E_UNSUPPORTED", 3: "NC_E_KMAX",
 EXPORTS = ["nc_compile", "nc_program_info", "nc_program_serialize", "nc_program_deserialize",
            "nc_sample", "nc_sample_batch", "nc_program_free", "nc_status_str", "nc_debug_dump",
            "nc_abi_version", "nc_sample_noalloc", "nc_program_prepare", "nc_sample_batch_async",
-           "nc_autotune"]
+           "nc_autotune", "nc_stratum_weights", "nc_strata_prepare"]
 
 
 class NcError(RuntimeError):
@@ -53,7 +53,8 @@ class Info(ctypes.Structure):
 class SampleOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("outputs", ctypes.c_uint32),
                 ("postselect", ctypes.c_int), ("shot_offset", ctypes.c_uint64),
-                ("tune", ctypes.c_char_p), ("noiseless", ctypes.c_int)]
+                ("tune", ctypes.c_char_p), ("noiseless", ctypes.c_int),
+                ("stratified", ctypes.c_uint32), ("stratum", ctypes.c_uint32)]
 
 
 class Records(ctypes.Structure):
@@ -95,11 +96,13 @@ def lib() -> ctypes.CDLL:
     L.nc_sample_batch_async.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(u64), ctypes.POINTER(u64), u32,
                                         ctypes.POINTER(SampleOpts), ctypes.POINTER(Records), vp, vp, vp]
     L.nc_autotune.argtypes = [vp, u64, ctypes.POINTER(SampleOpts), vp, ctypes.c_char_p, sz]
+    L.nc_stratum_weights.argtypes = [vp, u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint8)]
+    L.nc_strata_prepare.argtypes = [vp, u32, vp]
     L.nc_abi_version.argtypes = []
     L.nc_abi_version.restype = u32
     for name in ("nc_compile", "nc_program_info", "nc_program_serialize", "nc_program_deserialize",
                  "nc_sample", "nc_sample_batch", "nc_debug_dump", "nc_program_prepare", "nc_sample_batch_async",
-                 "nc_autotune"):
+                 "nc_autotune", "nc_stratum_weights", "nc_strata_prepare"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L

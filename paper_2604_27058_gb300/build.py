@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnc.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["compiler.cpp", "affine.cpp", "fuse.cpp", "kernels.cu", "affine_kernel.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["compiler.cpp", "affine.cpp", "fuse.cpp", "strata.cpp", "kernels.cu", "affine_kernel.cu", "capi.cu", "noalloc.cu"]
 HEADERS = ["program.h", "compiler.h", "kernels.cuh"]
 
 
@@ -51,7 +51,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(BUILD, src + ".o")
         objs.append(obj)
         if src.endswith(".cpp"):
-            cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", "-c", path, "-o", obj] + inc
+            cmd = ["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", "-ffp-contract=off", "-c", path, "-o", obj] + inc
         else:
             cmd = [nvcc, ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
                    "-Xptxas", "-O3", "-c", path, "-o", obj] + inc

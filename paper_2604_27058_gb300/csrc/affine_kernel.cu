@@ -13,7 +13,8 @@
 //   3. faults: the tile's chunk items from affine_items, applied with
 //      shared-memory atomic XORs; or (when no item list is available) fault
 //      sampling in the tile kernel, one warp per 32 shots, one survival-jump
-//      draw per lane per step (Sec. 3.2; guide-table search);
+//      draw per lane per step (Sec. 3.2; guide-table search), or one
+//      conditional jump per fault for a stratified call (exactly K faults);
 //      every fault appends its column's 8-row chunks to the warp's list, and
 //      the warp applies a full list one chunk per lane: eight shared-memory
 //      atomic XORs of the shot's bit;
@@ -33,6 +34,24 @@ namespace nc {
 constexpr uint32_t kAffTpw = 32;    // threads per 32-shot word of the tile: one warp per word
 constexpr uint32_t kAffPool = 32;   // shots per warp (fused sampling): S / warps
 constexpr uint32_t kAffList = 128;  // chunk items per warp list
+
+// Chunk range of the fault column of site i with the option that option
+// word wz picks (fault record fr = aff_frec[i]).
+__device__ __forceinline__ void fault_chunks(const DevProg& p, uint32_t i, uint4 fr, uint32_t wz, uint32_t* c0,
+                                             uint32_t* nch) {
+  const uint32_t opt = __umulhi(wz, fr.y >> 28);
+  if (fr.z != 0xFFFFFFFFu) {
+    const uint64_t nib = (uint64_t)fr.x | ((uint64_t)(fr.y & 0x0FFFFFFFu) << 32);
+    *nch = (uint32_t)(nib >> (4 * opt)) & 15u;
+    uint64_t below = nib & ((1ull << (4 * opt)) - 1ull);
+    below = (below & 0x0F0F0F0F0F0F0F0Full) + ((below >> 4) & 0x0F0F0F0F0F0F0F0Full);
+    *c0 = fr.z + (uint32_t)((below * 0x0101010101010101ull) >> 56);
+  } else {
+    const uint32_t c = i * kRecPerSite + opt;
+    *c0 = __ldg(p.aff_col_off + c);
+    *nch = __ldg(p.aff_col_off + c + 1) - *c0;
+  }
+}
 
 // One survival-jump draw from site st for `shot` (Sec. 3.2, integer form;
 // kernels.cuh jump_draw with the fault record loaded beside each Q[i] of
@@ -57,18 +76,17 @@ __device__ __forceinline__ uint32_t aff_draw(const DevProg& p, uint2 key, uint64
     qi = __ldg(p.q + i);
     fr = __ldg(p.aff_frec + i);
   }
-  const uint32_t opt = __umulhi(w.z, fr.y >> 28);
-  if (fr.z != 0xFFFFFFFFu) {
-    const uint64_t nib = (uint64_t)fr.x | ((uint64_t)(fr.y & 0x0FFFFFFFu) << 32);
-    *nch = (uint32_t)(nib >> (4 * opt)) & 15u;
-    uint64_t below = nib & ((1ull << (4 * opt)) - 1ull);
-    below = (below & 0x0F0F0F0F0F0F0F0Full) + ((below >> 4) & 0x0F0F0F0F0F0F0F0Full);
-    *c0 = fr.z + (uint32_t)((below * 0x0101010101010101ull) >> 56);
-  } else {
-    const uint32_t c = i * kRecPerSite + opt;
-    *c0 = __ldg(p.aff_col_off + c);
-    *nch = __ldg(p.aff_col_off + c + 1) - *c0;
-  }
+  fault_chunks(p, i, fr, w.z, c0, nch);
+  return i + 1;
+}
+
+// The same for a stratified shot holding r >= 1 faults (kernels.cuh
+// strat_jump): always a fault; returns the next start site (fault + 1).
+__device__ __forceinline__ uint32_t aff_draw_strat(const DevProg& p, uint2 key, uint64_t shot, uint32_t st,
+                                                   uint32_t r, uint32_t* c0, uint32_t* nch) {
+  uint32_t wz;
+  const uint32_t i = strat_jump(p, key, shot, st, r, &wz);
+  fault_chunks(p, i, __ldg(p.aff_frec + i), wz, c0, nch);
   return i + 1;
 }
 
@@ -111,14 +129,20 @@ __global__ void __launch_bounds__(512, 2) affine_items(LaunchParams L, uint32_t 
     const uint64_t left = s0 < L.shots ? L.shots - s0 : 0;
     const uint32_t n = left < pool ? (uint32_t)left : pool;
     uint32_t* out = items + (size_t)g * cap;
-    uint32_t sh = lane, nxt = 32, st = 0, cnt = 0;
-    bool live = sh < n && p.n_sites > 0;
+    uint32_t sh = lane, nxt = 32, st = 0, cnt = 0, r = p.sg_k;
+    const bool any = p.n_sites > 0 && (!p.sg || p.sg_k > 0);
+    bool live = sh < n && any;
     while (__any_sync(0xffffffffu, live)) {
       uint32_t c0 = 0, nch = 0;
       bool fin = false;
       if (live) {
-        st = aff_draw(p, key, L.shot_offset + s0 + sh, st, &c0, &nch);
-        fin = st >= p.n_sites;
+        if (p.sg) {
+          st = aff_draw_strat(p, key, L.shot_offset + s0 + sh, st, r, &c0, &nch);
+          fin = --r == 0 || st >= p.n_sites;
+        } else {
+          st = aff_draw(p, key, L.shot_offset + s0 + sh, st, &c0, &nch);
+          fin = st >= p.n_sites;
+        }
       }
       const uint32_t incl = warp_incl(nch, lane);
       const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
@@ -130,6 +154,7 @@ __global__ void __launch_bounds__(512, 2) affine_items(LaunchParams L, uint32_t 
       if (fin) {
         sh = nxt + __popc(done & ((1u << lane) - 1u));
         st = 0;
+        r = p.sg_k;
         live = sh < n;
       }
       nxt += __popc(done);
@@ -282,14 +307,19 @@ __global__ void __launch_bounds__(kAffTpw * WPT, 65536 / (kAffTpw * WPT * 64)) s
       const uint64_t pool0 = (uint64_t)tile * S + warp * kAffPool;  // call-local first shot of the pool
       const uint64_t left = pool0 < L.shots ? L.shots - pool0 : 0;
       const uint32_t pool_n = left < kAffPool ? (uint32_t)left : kAffPool;
-      uint32_t sh = lane, nxt = 32, st = 0, cnt = 0;
-      bool live = sh < pool_n;
+      uint32_t sh = lane, nxt = 32, st = 0, cnt = 0, r = p.sg_k;
+      bool live = sh < pool_n && (!p.sg || p.sg_k > 0);
       while (__any_sync(0xffffffffu, live)) {
         uint32_t c0 = 0, nch = 0;
         bool fin = false;
         if (live) {
-          st = aff_draw(p, key, L.shot_offset + pool0 + sh, st, &c0, &nch);
-          fin = st >= p.n_sites;
+          if (p.sg) {
+            st = aff_draw_strat(p, key, L.shot_offset + pool0 + sh, st, r, &c0, &nch);
+            fin = --r == 0 || st >= p.n_sites;
+          } else {
+            st = aff_draw(p, key, L.shot_offset + pool0 + sh, st, &c0, &nch);
+            fin = st >= p.n_sites;
+          }
         }
         // warp prefix of the chunk counts
         const uint32_t incl = warp_incl(nch, lane);
@@ -310,6 +340,7 @@ __global__ void __launch_bounds__(kAffTpw * WPT, 65536 / (kAffTpw * WPT * 64)) s
         if (fin) {
           sh = nxt + __popc(done & ((1u << lane) - 1u));
           st = 0;
+          r = p.sg_k;
           live = sh < pool_n;
         }
         nxt += __popc(done);

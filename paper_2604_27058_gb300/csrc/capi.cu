@@ -49,6 +49,8 @@ struct DevCopy {
   bool ref_ready = false;
   nc_status ref_status = NC_OK;
   std::string tuned;  // launch shape chosen by nc_autotune ("" = heuristic)
+  double* sg = nullptr;  // stratified tables G_r, rows r = 1..sg_rows (strata.cpp)
+  uint32_t sg_rows = 0;
 };
 
 }  // namespace
@@ -58,6 +60,7 @@ struct nc_program {
   nc_info info{};
   std::mutex mu;
   std::vector<DevCopy> devs;
+  StrataTables strata;  // host stratified tables, built on first use (under mu)
 };
 
 namespace {
@@ -375,17 +378,31 @@ struct Timing {
   }
 };
 
+constexpr uint32_t kNoStratum = 0xffffffffu;
+constexpr uint32_t kMaxStratum = 127;  // per-shot fault lists hold up to 127 entries
+
 // Enqueue one sampling launch. kept_count must point to a zeroed device u64.
 nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uint64_t seed,
                   uint64_t shot_offset, int precision, uint32_t lflags, const char* tune, CallOut o,
                   unsigned long long* kept_count, uint32_t* err, Scratch& scratch, cudaStream_t stream,
                   uint32_t stop_event = 0xffffffffu, uint64_t dump_shot = 0, double* dump_amps = nullptr,
-                  uint32_t* dump_frame = nullptr, uint32_t* dump_k = nullptr, Timing* tm = nullptr) {
+                  uint32_t* dump_frame = nullptr, uint32_t* dump_k = nullptr, Timing* tm = nullptr,
+                  uint32_t stratum = kNoStratum) {
   nc_status st = NC_OK;
   const ProgHeader& h = header(prog);
   LaunchParams L;
   std::memset(&L, 0, sizeof(L));
   L.p = dev_view(h, dc.blob);
+  // stratified call (stratum K >= 1; K = 0 runs as noiseless): exactly K
+  // faults per shot from the device tables
+  const bool strat = stratum != kNoStratum && stratum > 0 && !(lflags & LF_NOISELESS);
+  if (stratum == 0) lflags |= LF_NOISELESS;
+  if (strat) {
+    if (!dc.sg || dc.sg_rows < stratum || stop_event != 0xffffffffu) return NC_E_INTERNAL;
+    L.p.sg = dc.sg;
+    L.p.sg_k = stratum;
+    L.p.sg_n = h.n_sites + 1;
+  }
   L.seed = seed;
   L.shot_offset = shot_offset;
   L.shots = shots;
@@ -471,7 +488,11 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
           wave = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, wave_shots / tile_shots));
           // list capacity per tile: mean + 10 sigma (a chunk count per fault
           // of at most 15, so the variance is below 16 x the mean) + slack
-          const double mean = (double)h.aff_chunks_per_shot * tile_shots;
+          // (stratified: K faults of the average chunk count per fault)
+          const double per_shot = strat && h.mean_faults > 0.f
+                                      ? (double)h.aff_chunks_per_shot / h.mean_faults * stratum
+                                      : (double)h.aff_chunks_per_shot;
+          const double mean = per_shot * tile_shots;
           cap = (uint32_t)(mean * 1.1 + 10.0 * std::sqrt(mean * 16.0) + 64.0);
           if (tu.AC) cap = tu.AC;
           // two buffers when the passes overlap: pass j + 1 fills one while
@@ -533,10 +554,11 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
     L.n_tiles = (uint32_t)((L.row_words32 + tu.G - 1) / tu.G);
     // fault pre-sampling (bucketed or per-shot lists) pays off only for
     // large calls; small ones sample faults inside the executor
-    const bool noisy =
-        !(lflags & LF_NOISELESS) && h.n_sites && stop_event == 0xffffffffu && (shots >= (1u << 20) || tu.PS);
-    const double mean = (double)h.mean_faults;
-    const double per_shot_cap = std::ceil(mean + 6.0 * std::sqrt(mean) + 4.0);
+    // (stratified shots are always pre-sampled: exactly K faults each)
+    const bool noisy = !(lflags & LF_NOISELESS) && h.n_sites && stop_event == 0xffffffffu &&
+                       (shots >= (1u << 20) || tu.PS || strat);
+    const double mean = strat ? (double)stratum : (double)h.mean_faults;
+    const double per_shot_cap = strat ? mean : std::ceil(mean + 6.0 * std::sqrt(mean) + 4.0);
     // Bucketed noise: every shot's faults sampled up front and sorted by
     // noise block per 1024-shot warp-tile (one owner word per lane).
     bool bk = false;
@@ -544,7 +566,8 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
         (uint64_t)h.n_sites * kRecPerSite < (1ull << 22) && per_shot_cap <= 32.0) {
       const uint32_t n_wt = L.n_tiles * (tu.G / 32);
       const double lam = mean * (double)shots;
-      const uint64_t cap_total = (uint64_t)(lam * 1.02 + 12.0 * std::sqrt(lam) + 65536.0);
+      const uint64_t cap_total =
+          strat ? (uint64_t)lam + 65536 : (uint64_t)(lam * 1.02 + 12.0 * std::sqrt(lam) + 65536.0);
       const size_t ents_b = cap_total * 4, offs_b = (size_t)n_wt * (h.n_blocks + 1) * 4;
       size_t free_b = 0;
       NC_TRY(free_memory(lflags, &free_b));
@@ -613,6 +636,7 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
         if (tm) tm->launches += 1;
       }
     }
+    if (strat && !bk && !L.flist) return NC_E_OOM;  // stratified shots need their fault lists
     if (tm) NC_TRY(tm->begin(stream));
     NC_TRY(launch_batched(L, fp64, tu.W, bk, (uint32_t)grid, tu.T, smem, stream));
     if (tm) {
@@ -688,6 +712,45 @@ nc_status prepare(const nc_program* cprog, DevCopy** dc_out, cudaStream_t stream
   return NC_OK;
 }
 
+// Host stratified tables covering strata 0..k: built on first use, grown on
+// demand (rows of smaller strata do not change). Caller holds p->mu.
+nc_status host_strata(nc_program* p, uint32_t k) {
+  if (p->strata.valid.size() >= (size_t)k + 1) return NC_OK;
+  const ProgHeader& h = header(p);
+  try {
+    build_strata(reinterpret_cast<const double*>(p->cp.blob.data() + h.off_site_p), h.n_sites,
+                 std::max<uint32_t>(k, 16), p->strata);
+  } catch (std::bad_alloc&) {
+    return NC_E_OOM;
+  }
+  return NC_OK;
+}
+
+// The tables for stratum k and, with dc, their copy on dc's device.
+// NC_E_ARG for a stratum that cannot be sampled.
+nc_status strata_tables(nc_program* p, uint32_t k, DevCopy* dc) {
+  std::lock_guard<std::mutex> lock(p->mu);
+  if (k > kMaxStratum) return NC_E_ARG;
+  nc_status st = host_strata(p, k);
+  if (st != NC_OK) return st;
+  if (!p->strata.valid[k]) return NC_E_ARG;
+  if (dc && k > 0 && dc->sg_rows < k) {
+    const size_t bytes = p->strata.g.size() * sizeof(double);
+    double* g = nullptr;
+    cudaError_t e = cudaMalloc(&g, bytes);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaMemcpy(g, p->strata.g.data(), bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(g);
+      return cuda_status(e);
+    }
+    if (dc->sg) cudaFree(dc->sg);  // synchronises the device: no launch still reads it
+    dc->sg = g;
+    dc->sg_rows = p->strata.k_max;
+  }
+  return NC_OK;
+}
+
 uint32_t launch_flags(const nc_sample_opts& o) {
   uint32_t f = 0;
   if (o.outputs & NC_OUT_MEAS) f |= LF_OUT_MEAS;
@@ -716,6 +779,8 @@ nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, con
     return NC_E_ARG;
   if (o.shot_offset % 128) return NC_E_ARG;
   if (o.postselect != NC_PS_NONE && o.postselect != NC_PS_ALL_DETECTORS) return NC_E_ARG;
+  if (o.stratified > 1 || (o.stratified && o.stratum > kMaxStratum)) return NC_E_ARG;
+  const uint32_t stratum = o.stratified ? o.stratum : kNoStratum;
   const bool host = (o.outputs & NC_OUT_HOST) != 0;
   nc_status st = NC_OK;
   std::vector<DevCopy*> dcs(n, nullptr);
@@ -731,6 +796,10 @@ nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, con
     if (h.n_sites >= (1u << 28) - 1) return NC_E_UNSUPPORTED;
     st = prepare(progs[i], &dcs[i], stream);
     if (st != NC_OK) return st;
+    if (o.stratified) {
+      st = strata_tables(const_cast<nc_program*>(progs[i]), o.stratum, dcs[i]);
+      if (st != NC_OK) return st;
+    }
   }
   std::vector<unsigned long long> kept(n, 0);
   float kernel_ms = 0.f;
@@ -765,7 +834,7 @@ nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, con
       const char* tn = o.tune ? o.tune : (dcs[i]->tuned.empty() ? nullptr : dcs[i]->tuned.c_str());
       st = enqueue(progs[i], *dcs[i], shots[i], seeds[i], o.shot_offset, o.precision, launch_flags(o), tn, co,
                    (unsigned long long*)counters + i, (uint32_t*)err, scratch, stream, 0xffffffffu, 0, nullptr,
-                   nullptr, nullptr, &tms[i]);
+                   nullptr, nullptr, &tms[i], stratum);
       if (st != NC_OK) goto done;
       if (i + 1 == n) NC_TRY(cudaEventRecord(ev1, stream));
       if (host) {
@@ -848,7 +917,8 @@ nc_status nc_program_deserialize(const void* buf, size_t len, nc_program** out) 
                      h.off_site_opt, h.off_opt_tab, h.off_plist, h.off_orec, h.off_site_blk,
                      h.off_aff_const, h.off_aff_rowev_off, h.off_aff_rowev, h.off_aff_rand_ev,
                      h.off_aff_col_off, h.off_aff_col, h.off_aff_frec, h.off_aff_parent, h.off_aff_chain_off,
-                     h.off_aff_chain, h.off_srch, h.off_guide, h.off_fops, h.off_fterm, h.off_fperm};
+                     h.off_aff_chain, h.off_srch, h.off_guide, h.off_fops, h.off_fterm, h.off_fperm,
+                     h.off_site_p};
   for (uint64_t o : offs)
     if (o > h.total_bytes || (o & 15)) return NC_E_ARG;
   if (h.off_ops + (uint64_t)h.n_ops * sizeof(Op) > h.total_bytes || h.k_max > kMaxK || h.n_qubits > kMaxQubits)
@@ -883,6 +953,36 @@ nc_status nc_program_prepare(const nc_program* prog, void* cuda_stream) {
   return prepare(prog, &dc, (cudaStream_t)cuda_stream);
 }
 
+nc_status nc_stratum_weights(const nc_program* prog, uint32_t k_max, double* weights, uint8_t* valid) {
+  if (!prog || !weights || k_max > kMaxStratum) return NC_E_ARG;
+  nc_program* p = const_cast<nc_program*>(prog);
+  std::lock_guard<std::mutex> lock(p->mu);
+  nc_status st = host_strata(p, k_max);
+  if (st != NC_OK) return st;
+  for (uint32_t k = 0; k <= k_max; k++) {
+    weights[k] = p->strata.weight[k];
+    if (valid) valid[k] = p->strata.valid[k];
+  }
+  return NC_OK;
+}
+
+nc_status nc_strata_prepare(const nc_program* prog, uint32_t k_max, void* cuda_stream) {
+  if (!prog || k_max > kMaxStratum) return NC_E_ARG;
+  DevCopy* dc = nullptr;
+  nc_status st = prepare(prog, &dc, (cudaStream_t)cuda_stream);
+  if (st != NC_OK) return st;
+  nc_program* p = const_cast<nc_program*>(prog);
+  uint32_t top = 0;  // largest stratum <= k_max that can be sampled
+  {
+    std::lock_guard<std::mutex> lock(p->mu);
+    st = host_strata(p, k_max);
+    if (st != NC_OK) return st;
+    for (uint32_t k = 1; k <= k_max; k++)
+      if (p->strata.valid[k]) top = k;
+  }
+  return top ? strata_tables(p, top, dc) : NC_OK;
+}
+
 nc_status nc_sample_batch_async(const nc_program* const* progs, const uint64_t* shots, const uint64_t* seeds,
                                 uint32_t n, const nc_sample_opts* opts_in, nc_records* outs,
                                 unsigned long long* kept_dev, uint32_t* err_dev, void* cuda_stream) {
@@ -893,6 +993,8 @@ nc_status nc_sample_batch_async(const nc_program* const* progs, const uint64_t* 
     return NC_E_ARG;
   if (o.shot_offset % 128 || (o.outputs & NC_OUT_HOST)) return NC_E_ARG;
   if (o.postselect != NC_PS_NONE && o.postselect != NC_PS_ALL_DETECTORS) return NC_E_ARG;
+  if (o.stratified > 1 || (o.stratified && o.stratum > kMaxStratum)) return NC_E_ARG;
+  const uint32_t stratum = o.stratified ? o.stratum : kNoStratum;
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return NC_E_CUDA;
@@ -911,6 +1013,10 @@ nc_status nc_sample_batch_async(const nc_program* const* progs, const uint64_t* 
       if (c.device == dev && c.ref_ready) dcs[i] = &c;
     if (!dcs[i]) return NC_E_ARG;  // not prepared on this device
     if (dcs[i]->ref_status != NC_OK) return dcs[i]->ref_status;
+    // stratified: tables uploaded by nc_strata_prepare, stratum checked
+    if (o.stratified && o.stratum > 0 &&
+        (dcs[i]->sg_rows < o.stratum || p->strata.valid.size() <= o.stratum || !p->strata.valid[o.stratum]))
+      return NC_E_ARG;
   }
   nc_status st = NC_OK;
   {
@@ -924,7 +1030,8 @@ nc_status nc_sample_batch_async(const nc_program* const* progs, const uint64_t* 
       CallOut co{(uint32_t*)outs[i].meas, (uint32_t*)outs[i].det, (uint32_t*)outs[i].obs, (uint32_t*)outs[i].kept};
       const char* tn = o.tune ? o.tune : (dcs[i]->tuned.empty() ? nullptr : dcs[i]->tuned.c_str());
       st = enqueue(progs[i], *dcs[i], shots[i], seeds[i], o.shot_offset, o.precision, launch_flags(o) | LF_ASYNC,
-                   tn, co, kept_dev + i, err_dev, scratch, stream);
+                   tn, co, kept_dev + i, err_dev, scratch, stream, 0xffffffffu, 0, nullptr, nullptr, nullptr,
+                   nullptr, stratum);
       if (st != NC_OK) break;
     }
   }
@@ -1005,9 +1112,10 @@ void nc_program_free(nc_program* prog) {
   int cur = 0;
   bool have = cudaGetDevice(&cur) == cudaSuccess;
   for (auto& c : prog->devs) {
-    if (c.blob) {
+    if (c.blob || c.sg) {
       cudaSetDevice(c.device);
-      cudaFree(c.blob);
+      if (c.blob) cudaFree(c.blob);
+      if (c.sg) cudaFree(c.sg);
     }
   }
   if (have) cudaSetDevice(cur);
@@ -1072,7 +1180,7 @@ done:
   return st;
 }
 
-uint32_t nc_abi_version(void) { return (kVersion << 16) | 3u; }
+uint32_t nc_abi_version(void) { return (kVersion << 16) | 4u; }
 
 }  // extern "C"
 

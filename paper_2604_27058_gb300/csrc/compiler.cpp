@@ -1354,6 +1354,7 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     h.off_site_blk = place(site_blk.size() * 4);
     h.off_srch = place(S * sizeof(SrchRec));
     h.off_guide = place(guide.size() * 4);
+    h.off_site_p = place(S * 8);
     h.total_bytes = off;
     out.blob.assign(off, 0);
     std::memcpy(out.blob.data(), &h, sizeof(h));
@@ -1375,6 +1376,7 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     cp(h.off_site_blk, site_blk.data(), site_blk.size() * 4);
     cp(h.off_srch, srch.data(), S * sizeof(SrchRec));
     cp(h.off_guide, guide.data(), guide.size() * 4);
+    cp(h.off_site_p, c.site_p.data(), S * 8);
     append_affine(out.blob);
     append_fused(out.blob);
     out.counts = c.counts;

@@ -29,4 +29,15 @@ void append_affine(std::vector<uint8_t>& blob);
 // OP_MIXF / OP_PERMF) for the batched executor (fuse.cpp).
 void append_fused(std::vector<uint8_t>& blob);
 
+// Stratified importance sampling tables (Sec. 3.2; strata.cpp): for the
+// site probabilities p[0..S), g = G_r(j) for r = 1..k_max (row r - 1, n =
+// S + 1 entries per row), weight[K] = P(exactly K faults) and valid[K] = 1 if
+// stratum K can be sampled (every p < 1, K live sites, no table underflow).
+struct StrataTables {
+  uint32_t k_max = 0, n = 0;
+  std::vector<double> g, weight;
+  std::vector<uint8_t> valid;
+};
+void build_strata(const double* p, uint32_t S, uint32_t k_max, StrataTables& out);
+
 }  // namespace nc

@@ -283,6 +283,8 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
             } else {
               f = next_fault(p, L.seed, s0 + (uint64_t)i * 32u + j, 0);
             }
+            // stratified shots come only from complete pre-sampled lists
+            if (p.sg && (!L.flist || (L.fcount[sl0 + j] & 128u))) atomicOr(L.err, 4u);
           }
           NF[j * G + tw + i] = f;
           CUR[j * G + tw + i] = 1;
@@ -1144,7 +1146,8 @@ __global__ void __launch_bounds__(1024) bucket_faults(LaunchParams L, uint32_t* 
   uint32_t n = 0;
   if (sl < L.shots) {
     const uint64_t shot = L.shot_offset + sl;
-    uint32_t f = next_fault(L.p, L.seed, shot, 0);
+    uint32_t r = L.p.sg_k;
+    uint32_t f = next_fault_r(L.p, L.seed, shot, 0, r);
     while (f != kNoFault) {
       if (n == kBucketCap) {
         atomicOr(ovf, 1u);
@@ -1153,7 +1156,7 @@ __global__ void __launch_bounds__(1024) bucket_faults(LaunchParams L, uint32_t* 
       const uint32_t site = f >> 4;
       loc[n++] = f;
       atomicAdd(&cnt[__ldg(L.p.site_blk + site)], 1u);
-      f = next_fault(L.p, L.seed, shot, site + 1);
+      f = next_fault_r(L.p, L.seed, shot, site + 1, r);
     }
   }
   __syncthreads();
@@ -1228,7 +1231,8 @@ __global__ void __launch_bounds__(256) presample_faults(LaunchParams L) {
   bool ovf = false;
   if (s < L.shots) {
     const uint64_t shot = L.shot_offset + s;
-    uint32_t f = next_fault(L.p, L.seed, shot, 0);
+    uint32_t r = L.p.sg_k;
+    uint32_t f = next_fault_r(L.p, L.seed, shot, 0, r);
     uint32_t* dst = const_cast<uint32_t*>(L.flist);
     while (f != kNoFault) {
       if (n == L.fcap) {
@@ -1237,7 +1241,7 @@ __global__ void __launch_bounds__(256) presample_faults(LaunchParams L) {
       }
       dst[(uint64_t)n * L.fstride + s] = f;
       n++;
-      f = next_fault(L.p, L.seed, shot, (f >> 4) + 1);
+      f = next_fault_r(L.p, L.seed, shot, (f >> 4) + 1, r);
     }
   }
   const_cast<uint8_t*>(L.fcount)[s] = (uint8_t)(n | (ovf ? 128u : 0u));
@@ -1283,7 +1287,8 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
     if (lane == 0) base[(size_t)row * L.row_words32 + word] = w;
   };
   setb(slots, p.kept_slot, valid ? 1u : 0u);
-  uint32_t nf = (valid && !(L.flags & LF_NOISELESS) && p.n_sites) ? next_fault(p, L.seed, s, 0) : kNoFault;
+  uint32_t nr = p.sg_k;  // stratified: faults this shot still holds
+  uint32_t nf = (valid && !(L.flags & LF_NOISELESS) && p.n_sites) ? next_fault_r(p, L.seed, s, 0, nr) : kNoFault;
   uint32_t k = 0;
   if (p.k_max > 0) amp(0) = make_double2(1.0, 0.0);
   const double rs = 0.70710678118654752440;
@@ -1502,7 +1507,7 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
               z[w] ^= __ldg(mk + p.nw + w);
             }
           }
-          nf = next_fault(p, L.seed, s, site + 1);
+          nf = next_fault_r(p, L.seed, s, site + 1, nr);
         }
         break;
       case OP_FEEDFORWARD:

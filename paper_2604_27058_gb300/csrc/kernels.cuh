@@ -46,6 +46,10 @@ struct DevProg {
   uint32_t n_meas, n_det, n_obs, n_blocks;
   uint32_t aff_rows, aff_n_rand, aff_n_chains, aff_n_chain_rows;
   float aff_chunks_per_shot;
+  // stratified noise (strata.cpp tables; set per call, null = independent
+  // sites): G_r(j) at sg[(r - 1) * sg_n + j], exactly sg_k faults per shot
+  const double* sg;
+  uint32_t sg_k, sg_n;
 };
 
 enum : uint32_t {
@@ -100,7 +104,7 @@ struct LaunchParams {
 };
 
 constexpr uint32_t kNoFault = 0xffffffffu;
-constexpr uint32_t TAG_MT = 1, TAG_ML = 2, TAG_GAP = 3;
+constexpr uint32_t TAG_MT = 1, TAG_ML = 2, TAG_GAP = 3, TAG_STRAT = 4;
 
 // Philox4x32-10 (Salmon et al., SC'11).
 __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
@@ -192,6 +196,42 @@ __device__ __forceinline__ uint32_t next_fault(const DevProg& p, uint64_t seed, 
     st = nx;
   }
   return kNoFault;
+}
+
+// Stratified noise (Sec. 3.2 rare-event strata): a shot holding r >= 1
+// faults at site st draws u on the 53-bit grid from
+// Philox(shot, TAG_STRAT, st) and puts its next fault at the first j >= st
+// with G_r(j + 1) <= u * G_r(st) (one rounded FP64 product; G_r never
+// increases, so a bisection finds it). Returns j and the option word.
+__device__ __forceinline__ uint32_t strat_jump(const DevProg& p, uint2 key, uint64_t shot, uint32_t st, uint32_t r,
+                                               uint32_t* wz) {
+  const uint4 w = philox(make_uint4((uint32_t)shot, (uint32_t)(shot >> 32), TAG_STRAT, st), key);
+  const uint64_t u53 = ((uint64_t)w.x | ((uint64_t)w.y << 32)) >> 11;
+  const double* g = p.sg + (size_t)(r - 1) * p.sg_n;
+  const double thr = __dmul_rn((double)u53 * 0x1p-53, __ldg(g + st));
+  uint32_t lo = st, hi = p.n_sites - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(g + mid + 1) <= thr)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  *wz = w.z;
+  return lo;
+}
+
+// Next fault at or after site st under either noise model; r counts the
+// faults a stratified shot still holds (start at p.sg_k; ignored otherwise).
+__device__ __forceinline__ uint32_t next_fault_r(const DevProg& p, uint64_t seed, uint64_t shot, uint32_t st,
+                                                 uint32_t& r) {
+  if (!p.sg) return next_fault(p, seed, shot, st);
+  if (r == 0 || st >= p.n_sites) return kNoFault;
+  uint32_t wz;
+  const uint32_t i = strat_jump(p, key_of(seed), shot, st, r, &wz);
+  r--;
+  const uint32_t k = (__ldg(p.site_info + i) >> 4) & 15u;
+  return (i << 4) | __umulhi(wz, k);
 }
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {

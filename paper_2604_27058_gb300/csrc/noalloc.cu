@@ -187,6 +187,7 @@ extern "C" nc_status nc_sample_noalloc(const nc_program* prog, uint64_t shots, u
   if (opts) o = *opts;
   if (o.precision != NC_FP32_BATCHED || (o.outputs & NC_OUT_HOST) || o.shot_offset % 128) return NC_E_ARG;
   if (o.postselect != NC_PS_NONE && o.postselect != NC_PS_ALL_DETECTORS) return NC_E_ARG;
+  if (o.stratified) return NC_E_UNSUPPORTED;  // its tables are allocated on demand
   const std::vector<uint8_t>& blob = program_blob(prog);
   ProgHeader h;
   std::memcpy(&h, blob.data(), sizeof(h));

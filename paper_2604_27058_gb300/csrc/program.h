@@ -131,8 +131,10 @@ struct ProgHeader {
       off_slot_list, off_det_ref, off_obs_ref, off_site_opt, off_opt_tab, off_plist, off_orec, off_site_blk,
       off_aff_const, off_aff_rowev_off, off_aff_rowev, off_aff_rand_ev, off_aff_col_off, off_aff_col,
       off_aff_frec, off_aff_parent, off_aff_chain_off, off_aff_chain, off_srch, off_guide, off_fops, off_fterm,
-      off_fperm, total_bytes;
+      off_fperm, off_site_p, total_bytes;
 };
+// site_p: the fault probability of every noise site (FP64, site order), from
+// which the host builds the stratified-sampling tables (strata.cpp).
 // Survival-jump search (Sec. 3.2 jump, integer form). srch[st] (32 bytes)
 // holds, for a jump starting at site st: the segment [a, b), its guide-table
 // base and shift, Q[b - 1] and Q_L (Q[st - 1], or 2^64 - 1 at a segment
@@ -191,7 +193,7 @@ constexpr uint32_t kRecPerSite = 15;
 // row): its fault flips the slot and, if the shot is kept, the output bit.
 
 constexpr uint32_t kMagic = 0x4E435047u;  // "NCPG"
-constexpr uint32_t kVersion = 9;
+constexpr uint32_t kVersion = 10;
 constexpr uint32_t kMaxK = 30;
 constexpr uint32_t kMaxQubits = 4096;
 

@@ -22,10 +22,10 @@ def unpack(rows, shots):
     return nc.unpack_rows(rows, shots)
 
 
-def gpu_records(prog, shots, seed, precision="fp32", postselect=False, shot_offset=0, tune=None):
+def gpu_records(prog, shots, seed, precision="fp32", postselect=False, shot_offset=0, tune=None, stratum=None):
     import paper_2604_27058_gb300 as nc
     res = nc.sample(prog, shots, seed, precision=precision, postselect=postselect,
-                    shot_offset=shot_offset, tune=tune)
+                    shot_offset=shot_offset, tune=tune, stratum=stratum)
     i = prog.info
     out = {
         "meas": unpack(res["meas"], shots)[: i.n_meas],
@@ -46,19 +46,21 @@ def near_tie(p1: dict, seed: int, shot: int) -> bool:
 
 
 def compare(oracle, gpu, shots_idx, seed, global_offset=0, postselect=False, exact=False,
-            local_idx=None):
+            local_idx=None, faults=None):
     """Compare oracle shots (global indices) against the GPU record columns
-    (local indices). Returns (n_compared, n_flagged)."""
+    (local indices). faults(s), if given, supplies the fault set of global
+    shot s (stratified sampling). Returns (n_compared, n_flagged)."""
     from oracle.records import assemble
     flagged = 0
     n = 0
     for j, s in enumerate(shots_idx):
         col = local_idx[j] if local_idx is not None else s - global_offset
         tr = {}
+        kw = {} if faults is None else {"faults": faults(s)}
         if hasattr(oracle, "steps"):
-            meas = oracle.run_raw(seed, s, trace=tr)[0]
+            meas = oracle.run_raw(seed, s, trace=tr, **kw)[0]
         else:
-            meas = oracle.run_raw(seed, s)[0]
+            meas = oracle.run_raw(seed, s, **kw)[0]
         if not exact and tr and near_tie(tr.get("p1", {}), seed, s):
             flagged += 1
             continue

@@ -23,7 +23,8 @@ HEAD_BYTES = struct.calcsize(HEAD)
 OFF_NAMES = ["ops", "masks", "q", "seg_start", "seg_end", "site_info", "site_eff", "slot_list", "det_ref",
              "obs_ref", "site_opt", "opt_tab", "plist", "orec", "site_blk", "aff_const", "aff_rowev_off",
              "aff_rowev", "aff_rand_ev", "aff_col_off", "aff_col", "aff_frec", "aff_parent", "aff_chain_off",
-             "aff_chain", "srch", "guide", "fops", "fterm", "fperm", "total_bytes"]
+             "aff_chain", "srch", "guide", "fops", "fterm", "fperm", "site_p",
+             "total_bytes"]
 REC_PER_SITE = 15
 
 
