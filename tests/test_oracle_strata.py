@@ -150,3 +150,48 @@ def test_records_carry_exactly_k_flips():
             f = sample_stratum_faults(t, 9, s, kk)
             raw = sim.run_raw(9, s, faults=f)[0]
             assert sum(raw) == kk
+
+
+def _bad_first_quiet_end(t, r, st, thr):
+    lo, hi = st, len(t.live) - 2
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if g_value(t, r, mid) <= thr:  # planted: G_r(j) instead of G_r(j + 1)
+            hi = mid
+        else:
+            lo = mid + 1
+    return lo
+
+
+def _bad_suffix_counts(site_p, k_max):
+    s = len(site_p)
+    r = [[0.0] * (k_max + 1) for _ in range(s + 1)]
+    r[s][0] = 1.0
+    for j in range(s - 1, -1, -1):
+        p = site_p[j]
+        r[j][0] = (1.0 - p) * r[j + 1][0]
+        for c in range(1, k_max + 1):
+            r[j][c] = r[j + 1][c] + p * r[j + 1][c - 1]  # planted: (1 - p) dropped
+    return r
+
+
+def _bad_prefix_survival(site_p):
+    return [1.0] * (len(site_p) + 1)  # planted: W dropped
+
+
+@pytest.mark.parametrize("name,target,pin", [
+    ("first_quiet_end", _bad_first_quiet_end, "test_sampler_counts_and_subset_frequencies"),
+    ("suffix_counts", _bad_suffix_counts, "test_weights_brute_force_and_total_mass"),
+    ("prefix_survival", _bad_prefix_survival, "test_path_probabilities_are_the_conditional_distribution"),
+])
+def test_planted_mistakes_fail_a_pin(monkeypatch, name, target, pin):
+    """A mistake planted in the oracle (on the CPU) makes its pin fail (an
+    assertion, or the sampler running past the last site)."""
+    import oracle.strata as st
+    monkeypatch.setattr(st, name, target)
+    fn = globals()[pin]
+    with pytest.raises((AssertionError, IndexError)):
+        if pin == "test_path_probabilities_are_the_conditional_distribution":
+            fn(3)
+        else:
+            fn()
