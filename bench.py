@@ -51,6 +51,9 @@ def workload(name: str):
         return ("dense_n20_l40", gc.dense_random(seed=3, n=20, layers=40), 4096)
     if name == "lowmagic":
         return ("low_magic_n50_k10_p5e-4", gc.low_magic_gadgets(), 100_000_000)
+    if name == "coherent":
+        return ("coherent_surface_d3_r3_p1e-3_theta0.02",
+                gc.surface_code_memory(d=3, rounds=3, p=1e-3, theta=0.02), 10_000_000)
     raise SystemExit(f"unknown workload {name}")
 
 

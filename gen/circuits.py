@@ -147,7 +147,10 @@ _X_ORDER = [0, 1, 2, 3]   # NW, SW, NE, SE
 _Z_ORDER = [0, 2, 1, 3]   # NW, NE, SW, SE
 
 
-def surface_code_memory(d: int = 5, rounds: int = 25, p: float = 1e-3) -> str:
+def surface_code_memory(d: int = 5, rounds: int = 25, p: float = 1e-3, theta: float = 0.0) -> str:
+    """Rotated surface-code memory (Z basis). theta > 0 adds the coherent
+    over-rotation R_Z(theta) on the targets of every depolarising channel
+    (the coherent-noise family of the paper's Table 1)."""
     lay = surface_layout(d)
     anc = [a for _, a, _, _ in lay.plaquettes]
     xanc = [a for k, a, _, _ in lay.plaquettes if k == "X"]
@@ -159,6 +162,8 @@ def surface_code_memory(d: int = 5, rounds: int = 25, p: float = 1e-3) -> str:
         c.op("X_ERROR", anc, p)
         c.op("H", xanc)
         c.op("DEPOLARIZE1", xanc, p)
+        if theta:
+            c.op("R_Z", xanc, theta)
         for step in range(4):
             pairs = []
             for kind, a, touched, _ in lay.plaquettes:
@@ -170,8 +175,12 @@ def surface_code_memory(d: int = 5, rounds: int = 25, p: float = 1e-3) -> str:
             flat = [t for pr in pairs for t in pr]
             c.op("CX", flat)
             c.op("DEPOLARIZE2", flat, p)
+            if theta:
+                c.op("R_Z", flat, theta)
         c.op("H", xanc)
         c.op("DEPOLARIZE1", xanc, p)
+        if theta:
+            c.op("R_Z", xanc, theta)
         c.op("M", anc, p)
         # detectors
         for idx, (kind, a, _, _) in enumerate(lay.plaquettes):

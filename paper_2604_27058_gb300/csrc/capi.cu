@@ -49,7 +49,11 @@ struct DevCopy {
   bool ref_ready = false;
   nc_status ref_status = NC_OK;
   std::string tuned;  // launch shape chosen by nc_autotune ("" = heuristic)
-  double* sg = nullptr;  // stratified tables G_r, rows r = 1..sg_rows (strata.cpp)
+  // stratified tables (strata.cpp) in one allocation: G_r rows r = 1..sg_rows,
+  // then the guide parameters (3 u64 per row), then the guide entries
+  double* sg = nullptr;
+  const unsigned long long* sgr = nullptr;
+  const uint32_t* sgg = nullptr;
   uint32_t sg_rows = 0;
 };
 
@@ -400,6 +404,8 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
   if (strat) {
     if (!dc.sg || dc.sg_rows < stratum || stop_event != 0xffffffffu) return NC_E_INTERNAL;
     L.p.sg = dc.sg;
+    L.p.sgr = dc.sgr;
+    L.p.sgg = dc.sgg;
     L.p.sg_k = stratum;
     L.p.sg_n = h.n_sites + 1;
   }
@@ -735,18 +741,26 @@ nc_status strata_tables(nc_program* p, uint32_t k, DevCopy* dc) {
   if (st != NC_OK) return st;
   if (!p->strata.valid[k]) return NC_E_ARG;
   if (dc && k > 0 && dc->sg_rows < k) {
-    const size_t bytes = p->strata.g.size() * sizeof(double);
-    double* g = nullptr;
-    cudaError_t e = cudaMalloc(&g, bytes);
+    const StrataTables& t = p->strata;
+    const size_t bg = t.g.size() * sizeof(double), br = t.rows.size() * sizeof(StrataRow),
+                 bu = t.guide.size() * 4;
+    const size_t og = 0, orow = (bg + 15) & ~(size_t)15, ogd = (orow + br + 15) & ~(size_t)15;
+    static_assert(sizeof(StrataRow) == 3 * sizeof(unsigned long long), "row = 3 u64 on the device");
+    uint8_t* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, ogd + bu);
     if (e != cudaSuccess) return cuda_status(e);
-    e = cudaMemcpy(g, p->strata.g.data(), bytes, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(base + og, t.g.data(), bg, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + orow, t.rows.data(), br, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(base + ogd, t.guide.data(), bu, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-      cudaFree(g);
+      cudaFree(base);
       return cuda_status(e);
     }
     if (dc->sg) cudaFree(dc->sg);  // synchronises the device: no launch still reads it
-    dc->sg = g;
-    dc->sg_rows = p->strata.k_max;
+    dc->sg = reinterpret_cast<double*>(base + og);
+    dc->sgr = reinterpret_cast<const unsigned long long*>(base + orow);
+    dc->sgg = reinterpret_cast<const uint32_t*>(base + ogd);
+    dc->sg_rows = t.k_max;
   }
   return NC_OK;
 }

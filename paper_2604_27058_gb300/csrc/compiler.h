@@ -33,10 +33,20 @@ void append_fused(std::vector<uint8_t>& blob);
 // site probabilities p[0..S), g = G_r(j) for r = 1..k_max (row r - 1, n =
 // S + 1 entries per row), weight[K] = P(exactly K faults) and valid[K] = 1 if
 // stratum K can be sampled (every p < 1, K live sites, no table underflow).
+// rows[r - 1] / guide: the guide table of row r (strata.cpp), searched on
+// the device by strat_jump (kernels.cuh).
+struct StrataRow {
+  uint64_t b;           // bit pattern of G_r(0)
+  uint32_t shift, kmax;  // key = min(kmax, (b - bits(t)) >> shift)
+  uint32_t goff, pad;    // first guide entry of the row
+};
+static_assert(sizeof(StrataRow) == 24, "StrataRow layout");
 struct StrataTables {
   uint32_t k_max = 0, n = 0;
   std::vector<double> g, weight;
   std::vector<uint8_t> valid;
+  std::vector<StrataRow> rows;
+  std::vector<uint32_t> guide;
 };
 void build_strata(const double* p, uint32_t S, uint32_t k_max, StrataTables& out);
 

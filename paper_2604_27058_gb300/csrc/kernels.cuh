@@ -47,8 +47,12 @@ struct DevProg {
   uint32_t aff_rows, aff_n_rand, aff_n_chains, aff_n_chain_rows;
   float aff_chunks_per_shot;
   // stratified noise (strata.cpp tables; set per call, null = independent
-  // sites): G_r(j) at sg[(r - 1) * sg_n + j], exactly sg_k faults per shot
+  // sites): G_r(j) at sg[(r - 1) * sg_n + j], exactly sg_k faults per shot;
+  // row r's guide parameters at sgr[3 (r - 1) ..] (bits of G_r(0), shift |
+  // kmax << 32, first guide entry) and its guide entries in sgg
   const double* sg;
+  const unsigned long long* sgr;
+  const uint32_t* sgg;
   uint32_t sg_k, sg_n;
 };
 
@@ -201,24 +205,25 @@ __device__ __forceinline__ uint32_t next_fault(const DevProg& p, uint64_t seed, 
 // Stratified noise (Sec. 3.2 rare-event strata): a shot holding r >= 1
 // faults at site st draws u on the 53-bit grid from
 // Philox(shot, TAG_STRAT, st) and puts its next fault at the first j >= st
-// with G_r(j + 1) <= u * G_r(st) (one rounded FP64 product; G_r never
-// increases, so a bisection finds it). Returns j and the option word.
+// with G_r(j + 1) <= t, t = u * G_r(st) (one rounded FP64 product). G_r
+// never increases: the row's guide entry for t is a site at or before the
+// answer, and a forward scan (G_r(S) = 0 ends it) finds it exactly.
+// Returns j and the option word.
 __device__ __forceinline__ uint32_t strat_jump(const DevProg& p, uint2 key, uint64_t shot, uint32_t st, uint32_t r,
                                                uint32_t* wz) {
   const uint4 w = philox(make_uint4((uint32_t)shot, (uint32_t)(shot >> 32), TAG_STRAT, st), key);
   const uint64_t u53 = ((uint64_t)w.x | ((uint64_t)w.y << 32)) >> 11;
   const double* g = p.sg + (size_t)(r - 1) * p.sg_n;
   const double thr = __dmul_rn((double)u53 * 0x1p-53, __ldg(g + st));
-  uint32_t lo = st, hi = p.n_sites - 1;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (__ldg(g + mid + 1) <= thr)
-      hi = mid;
-    else
-      lo = mid + 1;
-  }
+  const unsigned long long* row = p.sgr + 3 * (size_t)(r - 1);
+  const unsigned long long b = __ldg(row), sk = __ldg(row + 1), go = __ldg(row + 2);
+  const unsigned long long d = (b - (unsigned long long)__double_as_longlong(thr)) >> (uint32_t)sk;
+  const uint32_t kmax = (uint32_t)(sk >> 32);
+  uint32_t j = __ldg(p.sgg + (uint32_t)go + (d < kmax ? (uint32_t)d : kmax));
+  j = j > st ? j : st;
+  while (__ldg(g + j + 1) > thr) j++;
   *wz = w.z;
-  return lo;
+  return j;
 }
 
 // Next fault at or after site st under either noise model; r counts the

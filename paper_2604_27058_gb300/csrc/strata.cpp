@@ -19,7 +19,9 @@
 // Every value is one IEEE operation in a fixed order (products rounded, then
 // sums; this file is built without floating-point contraction), so the
 // tables are reproducible bit for bit.
+#include <algorithm>
 #include <cfloat>
+#include <cstring>
 #include <vector>
 
 #include "compiler.h"
@@ -70,6 +72,42 @@ void build_strata(const double* p, uint32_t S, uint32_t k_max, StrataTables& out
     }
   }
   for (uint32_t K = 0; K < K1; K++) out.valid[K] = (!certain && K <= live[0] && K < bad_from) ? 1 : 0;
+
+  // Guide tables for the jump search. The bit patterns of non-negative
+  // doubles increase with their values, so key(t) = (bits(G_r(0)) - bits(t))
+  // >> shift is a piecewise-linear log of t that grows as t falls (capped
+  // at kmax, reached at the smallest positive value of the row). guide[key]
+  // = the answer for the largest t of the key's bucket, a lower bound for
+  // every t of the bucket; a forward scan from max(st, guide[key]) finds the
+  // first j with G_r(j + 1) <= t exactly.
+  out.rows.assign(k_max, StrataRow{});
+  out.guide.clear();
+  const uint64_t target = std::max<uint64_t>(16, 2 * (uint64_t)(S + 1));
+  for (uint32_t r = 1; r < K1 && S > 0; r++) {
+    const double* g = &out.g[(size_t)(r - 1) * (S + 1)];
+    StrataRow& row = out.rows[r - 1];
+    row.goff = (uint32_t)out.guide.size();
+    uint64_t b0 = 0, bmin = 0;
+    std::memcpy(&b0, &g[0], 8);
+    bmin = b0;
+    for (uint32_t j = 0; j < S; j++)
+      if (g[j] > 0.0) std::memcpy(&bmin, &g[j], 8);
+    const uint64_t range = b0 - bmin;
+    uint32_t shift = 0;
+    while ((range >> shift) + 1 > target) shift++;
+    const uint64_t kmax = range >> shift;
+    row.b = b0;
+    row.shift = shift;
+    row.kmax = (uint32_t)kmax;
+    uint32_t j = 0;
+    for (uint64_t k = 0; k <= kmax; k++) {
+      const uint64_t vb = b0 - (k << shift);
+      double v;
+      std::memcpy(&v, &vb, 8);
+      while (j < S - 1 && g[j + 1] > v) j++;
+      out.guide.push_back(j);
+    }
+  }
 }
 
 }  // namespace nc

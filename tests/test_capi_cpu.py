@@ -49,6 +49,8 @@ def test_status_strings(nc):
     ("surface", gc.surface_code_memory(), 0),
     ("dense", gc.dense_random(), 20),
     ("lowmagic", gc.low_magic_gadgets(), 10),
+    ("coherent_d3_r3", gc.surface_code_memory(d=3, rounds=3, p=1e-3, theta=0.02), 8),
+    ("coherent_d5_r1", gc.surface_code_memory(d=5, rounds=1, p=1e-3, theta=0.02), 24),
 ])
 def test_compile_matches_oracle_schedule(nc, name, text, kmax):
     from oracle.circuit import flatten
@@ -66,6 +68,9 @@ def test_k_schedule_matches_oracle_plan(nc):
     for seed in range(10):
         text = gc.random_small(900 + seed, n=6, n_ops=80, t_frac=0.3)
         assert nc.compile(text).info.k_max == FactoredSim(text).k_max
+    for d, r in ((3, 1), (3, 3), (5, 1)):
+        text = gc.surface_code_memory(d=d, rounds=r, p=1e-3, theta=0.02)
+        assert nc.compile(text).info.k_max == FactoredSim(text, k_limit=24).k_max
 
 
 def test_serialize_roundtrip(nc):

@@ -518,3 +518,39 @@ def test_wide_clifford_circuit_bit_exact(nc):
         g = gpu_records(prog, shots, 4242, tune=tune)
         n_ok, _ = _check(_frame_run(sim, 4242), sim.ref_det, sim.ref_obs, sim.flat, g, 4242, idx, exact=True)
         assert n_ok == len(idx)
+
+
+# ---------------------------------------------------------------------------
+# coherent-noise surface code (R_Z(theta) beside every depolarising channel)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,tune", [("fp32", None), ("fp64", None), ("fp32", "g=4,t=128"),
+                                            ("fp64_batched", None)])
+def test_coherent_surface_code(nc, precision, tune):
+    """d = 3, 3 rounds, theta = 0.02: every over-rotation is an active
+    rotation (k_max = 8); records equal the oracle's shot by shot except
+    flagged near-ties."""
+    text = gc.surface_code_memory(d=3, rounds=3, p=1e-3, theta=0.02)
+    prog = nc.compile(text)
+    assert prog.info.k_max == 8
+    sim = FactoredSim(text)
+    shots = 400
+    g = gpu_records(prog, shots, 6006, precision=precision, tune=tune)
+    n_ok, flagged = _check(_factored_run(sim, 6006), sim.ref_det, sim.ref_obs, sim.flat, g, 6006, range(shots))
+    assert flagged <= 2
+    assert n_ok + flagged == shots
+
+
+def test_coherent_surface_code_amplitudes(nc):
+    """The FP32 and FP64 active vectors of the coherent circuit equal the
+    oracle's just before several measurement events."""
+    text = gc.surface_code_memory(d=3, rounds=1, p=1e-3, theta=0.02)
+    prog = nc.compile(text)
+    sim = FactoredSim(text)
+    for ev in (8, 12, 16, 20):
+        for s in (0, 5):
+            _, (ox, oz), phi_ref, act = sim.run_raw(7, s, stop_event=ev)
+            for precision, tol in (("fp32", FP32_AMP_TOL), ("fp64", FP64_AMP_TOL)):
+                fx, fz, amps, k = nc.debug_dump(prog, 7, s, ev, precision=precision)
+                assert k == len(act), (ev, s, precision)
+                assert (fx, fz) == (ox, oz)
+                assert state_error(amps, phi_ref) <= tol, (ev, s, precision)
