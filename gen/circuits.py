@@ -477,6 +477,20 @@ def random_small(seed: int, n: int = 5, n_ops: int = 60, p_noise: float = 0.0,
     return c.text()
 
 
+def with_probes(text: str, seed: int, count: int = 6, max_weight: int = 3) -> str:
+    """Insert `count` EXPVAL lines (random Pauli products over the circuit's
+    qubits) at random top-level positions of a circuit without REPEAT."""
+    rng = random.Random(seed)
+    lines = text.splitlines()
+    n = 1 + max((int(t) for ln in lines for t in ln.split()[1:] if t.isdigit()), default=0)
+    for _ in range(count):
+        w = rng.randint(1, min(max_weight, n))
+        qs = rng.sample(range(n), w)
+        prod = "*".join(f"{rng.choice('XYZ')}{q}" for q in qs)
+        lines.insert(rng.randint(0, len(lines)), f"EXPVAL {prod}")
+    return "\n".join(lines) + "\n"
+
+
 def mirror_small(seed: int, n: int = 6, depth: int = 12, n_t: int = 4) -> str:
     """Noiseless U U^dagger with Clifford+T layers; every record must be 0."""
     rng = random.Random(seed)

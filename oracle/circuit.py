@@ -12,7 +12,12 @@ the random draws (identical rule on the CUDA side):
 * records ``r``: every M, MX, MR target, in order;
 * noise sites ``i``: every noise-channel target (or target pair) in order,
   plus one record-flip site right after each M(p)/MX(p)/MR(p) target with
-  p > 0.
+  p > 0;
+* expectation probes ``j``: every target of EXPVAL, in order. A target is a
+  Pauli product such as ``X0*Y1*Z5`` (Stim's product syntax); the probe
+  reports <psi|P|psi> / <psi|psi> of the shot's state at that point
+  (Sec. 3.2: expectation-value probes act on the runtime state; the
+  instruction name and syntax are this implementation's).
 
 Gate conventions: T = diag(1, e^{i pi/4}) and R_P(theta) = exp(-i theta P / 2),
 so T equals exp(-i (pi/8) Z) up to a global phase (Fig. 1 / App. B.1).
@@ -116,7 +121,8 @@ class Op:
     site: int = -1             # noise site index (noise) / flip site (meas)
     reset: bool = False        # meas followed by conditional X (R, MR)
     recs: tuple = ()           # det / obs record lists
-    index: int = -1            # detector / observable index
+    index: int = -1            # detector / observable / probe index
+    paulis: tuple = ()         # probe: ((qubit, 'X' | 'Y' | 'Z'), ...)
 
 
 @dataclass
@@ -130,6 +136,7 @@ class Flat:
     n_observables: int
     site_p: list               # probability of every site, in site order
     site_kind: list            # 'X','Y','Z','D1','D2','FLIP'
+    n_probes: int = 0
 
 
 _TOKEN = re.compile(r"^([A-Za-z_][A-Za-z0-9_]*)(?:\(([^)]*)\))?\s*(.*)$")
@@ -193,12 +200,24 @@ def _qubit(t: str) -> int:
     return int(t)
 
 
+def _pauli_product(t: str) -> tuple:
+    out = []
+    for f in t.split("*"):
+        m = re.match(r"^([XYZ])(\d+)$", f)
+        if not m:
+            raise CircuitError(f"bad Pauli product target {t!r}")
+        out.append((int(m.group(2)), m.group(1)))
+    if len({q for q, _ in out}) != len(out):
+        raise CircuitError(f"qubit repeated in {t!r}")
+    return tuple(out)
+
+
 def flatten(text: str) -> Flat:
     lines = list(_lines(text))
     block, _ = _parse_block(lines, 0, 0)
     ops: list[Op] = []
     n_q = 0
-    ev = rec = site = det = 0
+    ev = rec = site = det = probe = 0
     n_obs = 0
     site_p: list[float] = []
     site_kind: list[str] = []
@@ -217,6 +236,15 @@ def flatten(text: str) -> Flat:
             recs = tuple(_rec_target(t, rec) for t in targets)
             ops.append(Op("obs", recs=recs, index=o))
             n_obs = max(n_obs, o + 1)
+            continue
+        if name == "EXPVAL":
+            if args or not targets:
+                raise CircuitError("EXPVAL takes Pauli product targets and no argument")
+            for t in targets:
+                ps = _pauli_product(t)
+                n_q = max(n_q, max(q for q, _ in ps) + 1)
+                ops.append(Op("probe", paulis=ps, index=probe))
+                probe += 1
             continue
         if name in ("CX", "CY", "CZ") and any(t.startswith("rec[") for t in targets):
             if len(targets) % 2:
@@ -296,7 +324,7 @@ def flatten(text: str) -> Flat:
         else:
             raise CircuitError(f"unsupported instruction {name}")
     return Flat(ops=ops, n_qubits=n_q, n_events=ev, n_records=rec, n_sites=site,
-                n_detectors=det, n_observables=n_obs, site_p=site_p, site_kind=site_kind)
+                n_detectors=det, n_observables=n_obs, site_p=site_p, site_kind=site_kind, n_probes=probe)
 
 
 def option_count(kind: str) -> int:

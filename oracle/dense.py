@@ -48,11 +48,15 @@ class DenseSim:
         if self.flat.n_qubits > max_qubits:
             raise ValueError(f"dense oracle limited to {max_qubits} qubits")
         self.table = build_table(self.flat.site_p, self.flat.site_kind)
-        ref_meas, _, _ = self.run_raw(0, 0, noisy=False)
+        ref_meas, _, _ = self.run_raw(0, 0, noisy=False, argmax=True)
         self.ref_det, self.ref_obs = raw_parities(self.flat, ref_meas)
 
-    def run_raw(self, seed: int, shot: int, noisy: bool = True, faults=None, stop_event: int = -1):
-        """Returns (records, {event: P(m=1)}, state at the stop point)."""
+    def run_raw(self, seed: int, shot: int, noisy: bool = True, faults=None, stop_event: int = -1,
+                probes: dict | None = None, argmax: bool = False):
+        """Returns (records, {event: P(m=1)}, state at the stop point).
+        ``probes`` (if given) receives {probe index: <psi|P|psi> / <psi|psi>}.
+        argmax: every measurement takes its more likely outcome, 0 on a tie
+        (the reference trajectory)."""
         f = self.flat
         n = max(1, f.n_qubits)
         psi = np.zeros(1 << n, dtype=complex)
@@ -85,8 +89,7 @@ class DenseSim:
                 s1 = float(np.sum(np.abs(v[:, 1, :]) ** 2))
                 p1 = s1 / (s0 + s1)
                 probs[op.event] = p1
-                u = meas_u(seed, shot, op.event)
-                m = 1 if u < p1 else 0
+                m = (1 if p1 > 0.5 else 0) if argmax else (1 if meas_u(seed, shot, op.event) < p1 else 0)
                 keep = np.zeros_like(v)
                 keep[:, m, :] = v[:, m, :]
                 psi = keep.reshape(-1) / np.sqrt(s1 if m else s0)
@@ -100,6 +103,11 @@ class DenseSim:
             elif op.kind == "ff":
                 if meas[op.record]:
                     psi = _apply_1q(psi, n, op.qubits[0], _PAULI[op.name])
+            elif op.kind == "probe" and probes is not None:
+                ppsi = psi
+                for q, letter in op.paulis:
+                    ppsi = _apply_1q(ppsi, n, q, _PAULI[letter])
+                probes[op.index] = float(np.vdot(psi, ppsi).real / np.vdot(psi, psi).real)
         return meas, probs, psi
 
     def sample(self, seed: int, shot: int, postselect: bool = False) -> ShotRecords:

@@ -173,7 +173,7 @@ class FactoredSim:
         self.steps: list[Step] = []
         self.k_max = 0
         self._plan()
-        ref_meas = self.run_raw(0, 0, noisy=False)[0]
+        ref_meas = self.run_raw(0, 0, noisy=False, argmax=True)[0]
         self.ref_det, self.ref_obs = raw_parities(self.flat, ref_meas)
 
     # M(P) for a physical Pauli given per physical qubit as letters
@@ -313,6 +313,15 @@ class FactoredSim:
             elif op.kind == "ff":
                 e = self._map({op.qubits[0]: op.name})
                 steps.append(Step("ff", dict(record=op.record, ex=e[0], ez=e[1])))
+            elif op.kind == "probe":
+                # <P> = <phi (x) 0| Pt^dag M(P) Pt |phi (x) 0> / <phi|phi>: zero if
+                # M(P) has x-support on a dormant qubit; dormant Z factors read +1
+                x, z, ph = self._map({q: l for q, l in op.paulis})
+                act = self.active
+                zero = any((x >> q) & 1 and q not in act for q in range(self.n))
+                mx = sum(1 << act.index(q) for q in act if (x >> q) & 1)
+                mz = sum(1 << act.index(q) for q in act if (z >> q) & 1)
+                steps.append(Step("probe", dict(index=op.index, x=x, z=z, ph=ph, mx=mx, mz=mz, zero=zero)))
             elif op.kind == "noise":
                 from .circuit import option_count
                 opts = []
@@ -326,9 +335,11 @@ class FactoredSim:
     # Run
     # ----------------------------------------------------------------------
     def run_raw(self, seed: int, shot: int, noisy: bool = True, faults=None,
-                stop_event: int = -1, trace: dict | None = None):
+                stop_event: int = -1, trace: dict | None = None, argmax: bool = False):
         """Returns (records, frame (x, z), phi, active list). ``trace`` gets
-        'p1' {event: P(m=1)} and 'k' / 'norm' lists for invariant checks."""
+        'p1' {event: P(m=1)}, 'probe' {probe index: expectation value} and
+        'k' / 'norm' lists for invariant checks. argmax: every measurement
+        takes its more likely outcome, 0 on a tie (the reference trajectory)."""
         f = self.flat
         if faults is None:
             faults = sample_faults(self.table, seed, shot) if noisy else {}
@@ -374,7 +385,7 @@ class FactoredSim:
                     p1 = float(m)
                 elif st.kind == "mrand":
                     p1 = 0.5
-                    m = 1 if meas_u(seed, shot, a["event"]) < p1 else 0
+                    m = 0 if argmax else (1 if meas_u(seed, shot, a["event"]) < p1 else 0)
                     b_last = m ^ a["a"] ^ bit(a["v"], fz)
                 else:
                     v, pos = a["v"], a["pos"]
@@ -391,7 +402,7 @@ class FactoredSim:
                     s = [float(np.sum(np.abs(x) ** 2)) for x in br]
                     tot = s[0] + s[1]
                     p1 = s[1 ^ a["a"] ^ pbit] / tot
-                    m = 1 if meas_u(seed, shot, a["event"]) < p1 else 0
+                    m = (1 if p1 > 0.5 else 0) if argmax else (1 if meas_u(seed, shot, a["event"]) < p1 else 0)
                     b = m ^ a["a"] ^ pbit
                     kept = br[b] / math.sqrt(s[b])
                     phi = _relocate(kept, k, pos)
@@ -421,6 +432,16 @@ class FactoredSim:
                     ex, ez = a["opts"][opt]
                     fx ^= ex
                     fz ^= ez
+            elif st.kind == "probe" and trace is not None:
+                val = 0.0
+                if not a["zero"]:
+                    # frame conjugation: sign of the anticommutation with the frame
+                    om = (bin(fx & a["z"]).count("1") + bin(fz & a["x"]).count("1")) & 1
+                    idx = np.arange(len(phi))
+                    sg = 1 - 2 * (np.array([bin(int(i) & a["mz"]).count("1") & 1 for i in idx]))
+                    acc = np.sum(np.conj(phi[idx ^ a["mx"]]) * sg * phi)
+                    val = float(((-1) ** om * (1j ** a["ph"]) * acc).real / np.sum(np.abs(phi) ** 2))
+                trace.setdefault("probe", {})[a["index"]] = val
             if trace is not None:
                 trace.setdefault("k", []).append(len(act))
                 trace.setdefault("norm", []).append(float(np.sum(np.abs(phi) ** 2)))

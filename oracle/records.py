@@ -4,8 +4,11 @@ Reading of the paper (Sec. 3.2, "Post-selection overhead"; detector
 references are not described there):
 
 * a detector's value is the XOR of its records XOR its reference, the value
-  it takes in a noiseless execution (noise disabled, seed 0, shot 0);
-  observables likewise;
+  it takes on the reference trajectory: noise disabled and every measurement
+  taking its more likely outcome (0 on a tie). For a deterministic detector
+  that is its value on every noiseless trajectory; for one that small
+  coherent rotations make slightly random it is the value of the rotation-free
+  limit. Observables likewise;
 * with postselection on all detectors, a shot is rejected at its first
   detector that reads 1: that detector still reports 1, every later record
   and detector reports 0, all observables report 0 and ``kept`` is 0.
@@ -69,3 +72,20 @@ def assemble(flat: Flat, meas: list[int], ref_det: list[int], ref_obs: list[int]
             out_meas[r] = 0
         obs = [0] * flat.n_observables
     return ShotRecords(meas=out_meas, det=det, obs=obs, kept=1 if alive else 0)
+
+
+def probe_alive(flat: Flat, meas: list[int], ref_det: list[int], postselect: bool) -> list[int]:
+    """1 for every probe that runs while the shot is still kept (always 1
+    without postselection). A rejected shot reports 0 for every later probe."""
+    alive = True
+    out = [1] * flat.n_probes
+    for op in flat.ops:
+        if op.kind == "det":
+            v = ref_det[op.index]
+            for r in op.recs:
+                v ^= meas[r]
+            if postselect and alive and v:
+                alive = False
+        elif op.kind == "probe":
+            out[op.index] = 1 if alive else 0
+    return out

@@ -174,10 +174,11 @@ class FrameSim:
                     for prim in _pauli_prims(op.name, op.qubits[0]):
                         tab.apply(prim[0], *prim[1:])
         self.ref_meas = ref_meas
-        raw, _ = self.run_raw(0, 0, noisy=False)
+        raw, _ = self.run_raw(0, 0, noisy=False, argmax=True)
         self.ref_det, self.ref_obs = raw_parities(f, raw)
 
-    def run_raw(self, seed: int, shot: int, noisy: bool = True, faults=None):
+    def run_raw(self, seed: int, shot: int, noisy: bool = True, faults=None, argmax: bool = False):
+        """argmax: random measurements take 0 (the reference trajectory)."""
         f = self.flat
         if faults is None:
             faults = sample_faults(self.table, seed, shot) if noisy else {}
@@ -202,7 +203,7 @@ class FrameSim:
                 c = (ex >> a) & 1
                 mr = self.m_ref[op.event]
                 if self.random[op.event]:
-                    m = 1 if meas_u(seed, shot, op.event) < 0.5 else 0
+                    m = 0 if argmax else (1 if meas_u(seed, shot, op.event) < 0.5 else 0)
                     if m ^ c ^ mr:
                         gx, gz = self.flip[op.event]
                         ex ^= gx

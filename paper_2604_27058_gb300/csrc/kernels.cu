@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
               Vw<W> m, xa, za;
               const uint32_t sg = (op.flags & FLAG_SIGN) ? ~0u : 0u;
 #pragma unroll
-              for (int i = 0; i < W; i++) m.v[i] = ~pick4(tb, (sel + i) & 3u);
+              for (int i = 0; i < W; i++) m.v[i] = (L.flags & LF_ARGMAX) ? 0u : ~pick4(tb, (sel + i) & 3u);
               // H_v then x_v ^= b: new x = old z ^ b, new z = old x
               Vw<W> ox = vld<W>(plane(op.a)), oz = vld<W>(plane(N + op.a));
 #pragma unroll
@@ -1009,9 +1009,9 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
                     const double S0 = RED[s], S1 = RED[S + s], tot = S0 + S1;
                     const uint32_t pbit = (pw >> j) & 1u;
                     const double p1 = tot > 0.0 ? ((1u ^ abit ^ pbit) ? S1 : S0) / tot : 0.0;
-                    const uint32_t m = ((valid.v[i] >> j) & 1u)
-                                           ? draw_outcome(L.seed, s0 + (uint64_t)i * 32u + j, op.i0, (top >> j) & 1u, p1)
-                                           : 0u;
+                    const uint32_t m = !((valid.v[i] >> j) & 1u) ? 0u
+                                       : (L.flags & LF_ARGMAX)     ? (p1 > 0.5 ? 1u : 0u)
+                                           : draw_outcome(L.seed, s0 + (uint64_t)i * 32u + j, op.i0, (top >> j) & 1u, p1);
                     const uint32_t b = m ^ abit ^ pbit;
                     const double sb = b ? S1 : S0;
                     RED[s] = sb > 0.0 ? 1.0 / sqrt(sb) : 0.0;
@@ -1417,7 +1417,7 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
       }
       case OP_MEAS_RANDOM: {
         uint32_t top = (meas_top_word(L.seed, s0, op.i0) >> lane) & 1u;
-        uint32_t m = top ^ 1u;
+        uint32_t m = (L.flags & LF_ARGMAX) ? 0u : top ^ 1u;
         uint32_t b = m ^ (op.flags & FLAG_SIGN ? 1u : 0u) ^ getb(z, op.a);
         uint32_t xa = getb(x, op.a);
         setb(x, op.a, getb(z, op.a) ^ b);
@@ -1448,7 +1448,7 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
         const double tot = S0 + S1;
         const double p1 = tot > 0.0 ? ((1u ^ abit ^ pbit) ? S1 : S0) / tot : 0.0;
         const uint32_t top = (meas_top_word(L.seed, s0, op.i0) >> lane) & 1u;
-        const uint32_t m = valid ? draw_outcome(L.seed, s, op.i0, top, p1) : 0u;
+        const uint32_t m = !valid ? 0u : (L.flags & LF_ARGMAX) ? (p1 > 0.5 ? 1u : 0u) : draw_outcome(L.seed, s, op.i0, top, p1);
         const uint32_t b = m ^ abit ^ pbit;
         const double sb = b ? S1 : S0;
         const double sc = sb > 0.0 ? 1.0 / sqrt(sb) : 0.0;

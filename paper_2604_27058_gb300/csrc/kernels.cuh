@@ -65,6 +65,7 @@ enum : uint32_t {
   LF_OUT_OBS = 32,
   LF_OUT_KEPT = 64,
   LF_ASYNC = 128,     // host side only: no host synchronisation (stream capture)
+  LF_ARGMAX = 256,    // every measurement takes its more likely outcome (0 on a tie): the reference trajectory
 };
 
 struct LaunchParams {

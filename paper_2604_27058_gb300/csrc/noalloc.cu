@@ -223,8 +223,10 @@ extern "C" nc_status nc_sample_noalloc(const nc_program* prog, uint64_t shots, u
     uint32_t* rdet = (uint32_t*)(base + off_ref);
     uint32_t* robs = rdet + 2 * h.n_det;
     if (cudaMemsetAsync(cnt, 0, 16, stream) != cudaSuccess) return NC_E_CUDA;
-    st = launch(d, 64, 0, 0, LF_NOISELESS | LF_REFERENCE | LF_OUT_DET | LF_OUT_OBS, nullptr, rdet, robs,
-                nullptr, cnt, err, base + off_work, work_bytes, stream);
+    // the reference trajectory: every measurement takes its more likely
+    // outcome (0 on a tie), so all 64 shots agree
+    st = launch(d, 64, 0, 0, LF_NOISELESS | LF_REFERENCE | LF_ARGMAX | LF_OUT_DET | LF_OUT_OBS, nullptr, rdet,
+                robs, nullptr, cnt, err, base + off_work, work_bytes, stream);
     if (st != NC_OK) return st;
     // rows are read back and checked in fixed stack chunks (no host heap use)
     constexpr uint32_t kRows = 256;
@@ -237,7 +239,7 @@ extern "C" nc_status nc_sample_noalloc(const nc_program* prog, uint64_t shots, u
           cudaStreamSynchronize(stream) != cudaSuccess)
         return NC_E_CUDA;
       for (uint32_t i = 0; i < nr; i++) {
-        if (rows[i] != 0 && rows[i] != ~0ull) return NC_E_NONDET_DETECTOR;
+        if (rows[i] != 0 && rows[i] != ~0ull) return NC_E_INTERNAL;
         ref[i] = (uint32_t)(rows[i] & 1);
       }
       // detector rows come first, then observable rows; the blob keeps them apart
@@ -251,6 +253,27 @@ extern "C" nc_status nc_sample_noalloc(const nc_program* prog, uint64_t shots, u
           return NC_E_CUDA;
         i += run;
       }
+    }
+    // 64 sampled noiseless shots: a detector that differs from its
+    // reference in more than a quarter of them is not deterministic
+    st = launch(d, 64, 0, 0, LF_NOISELESS | LF_REFERENCE | LF_OUT_DET | LF_OUT_OBS, nullptr, rdet, robs, nullptr,
+                cnt, err, base + off_work, work_bytes, stream);
+    if (st != NC_OK) return st;
+    for (uint32_t r0 = 0; r0 < n_rows; r0 += kRows) {
+      const uint32_t nr = std::min(kRows, n_rows - r0);
+      if (cudaMemcpyAsync(rows, rdet + 2 * (size_t)r0, nr * 8, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        return NC_E_CUDA;
+      for (uint32_t i = 0; i < nr;) {
+        const uint32_t r = r0 + i;
+        const bool is_det = r < h.n_det;
+        const uint32_t run = is_det ? std::min(nr - i, h.n_det - r) : nr - i;
+        const uint8_t* src = is_det ? dblob + h.off_det_ref + (size_t)r * 4 : dblob + h.off_obs_ref + (size_t)(r - h.n_det) * 4;
+        if (cudaMemcpyAsync(ref + i, src, run * 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess) return NC_E_CUDA;
+        i += run;
+      }
+      if (cudaStreamSynchronize(stream) != cudaSuccess) return NC_E_CUDA;
+      for (uint32_t i = 0; i < nr; i++)
+        if (__builtin_popcountll(rows[i] ^ (ref[i] ? ~0ull : 0ull)) > 16) return NC_E_NONDET_DETECTOR;
     }
     if (launch_patch_ref(reinterpret_cast<Op*>(dblob + h.off_ops), h.n_ops,
                          reinterpret_cast<const uint32_t*>(dblob + h.off_det_ref),

@@ -407,6 +407,18 @@ def test_nondeterministic_detector_reported(nc):
     assert e.value.name == "NC_E_NONDET_DETECTOR"
 
 
+def test_near_deterministic_detectors_take_the_likely_reference(nc):
+    """R_X(0.1) before M: P(m = 1) = sin^2(0.05); the reference is 0 and
+    the detector reads 1 exactly when the measurement reads 1."""
+    prog = nc.compile("R_X(0.1) 0\nM 0\nDETECTOR rec[-1]\n")
+    res = nc.sample(prog, 100_000, 5)
+    meas = nc.unpack_rows(res["meas"], 100_000)[0]
+    det = nc.unpack_rows(res["det"], 100_000)[0]
+    assert (meas == det).all()
+    p = math.sin(0.05) ** 2
+    assert abs(meas.mean() - p) < 6 * math.sqrt(p / 100_000)
+
+
 def test_tuning_variants_agree(nc):
     text = gc.tiny_random(seed=6)
     prog = nc.compile(text)

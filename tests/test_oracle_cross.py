@@ -122,3 +122,19 @@ def test_planted_mistake_is_caught(mutate):
 
 def test_unmutated_passes_same_harness():
     assert not _mismatch_found(lambda s: s)
+
+
+def test_reference_is_the_most_likely_trajectory():
+    """Detector references come from the noiseless trajectory in which every
+    measurement takes its more likely outcome: for the coherent-noise surface
+    code that is the rotation-free circuit's reference, and a near-
+    deterministic detector gets the likely value."""
+    from gen import circuits as gc
+    from oracle.factored import FactoredSim
+    from oracle.stabilizer import FrameSim
+    for d, r in ((3, 1), (3, 3)):
+        coh = FactoredSim(gc.surface_code_memory(d=d, rounds=r, p=1e-3, theta=0.02))
+        cliff = FrameSim(gc.surface_code_memory(d=d, rounds=r, p=1e-3))
+        assert coh.ref_det == cliff.ref_det and coh.ref_obs == cliff.ref_obs
+    assert FactoredSim("R_X(0.1) 0\nM 0\nDETECTOR rec[-1]").ref_det == [0]
+    assert FactoredSim("R_X(3.0) 0\nM 0\nDETECTOR rec[-1]").ref_det == [1]
