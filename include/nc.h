@@ -51,6 +51,7 @@ typedef struct nc_program nc_program;
 typedef struct {
   uint32_t n_qubits, n_meas, n_det, n_obs, k_max, n_noise_sites, n_ops;
   uint32_t n_events, n_slots, n_static, n_random, n_active_meas, n_array_ops;
+  uint32_t n_probes;  /* EXPVAL probes (rows of nc_records.expval) */
 } nc_info;
 
 /* precision */
@@ -64,6 +65,7 @@ typedef struct {
 #define NC_OUT_OBS 4u
 #define NC_OUT_KEPT 8u
 #define NC_OUT_HOST 16u    /* record pointers are host memory (copied back) */
+#define NC_OUT_EXPVAL 32u  /* expectation-value probes (nc_records.expval) */
 
 /* postselect */
 #define NC_PS_NONE 0
@@ -89,6 +91,9 @@ typedef struct {
  *   holds record r of shot s. words_per_record = ceil(shots / 64); bits of
  *   the last word beyond `shots` are written as 0.
  *   meas: n_meas rows, det: n_det rows, obs: n_obs rows, kept: 1 row.
+ * Circuit text: the extended Stim subset of Sec. 3.1 plus EXPVAL, whose
+ * targets are Pauli products (Stim's product syntax, e.g. "EXPVAL X0*Y1 Z2":
+ * two probes).
  * A rejected (postselected-out) shot reports its failing detector as 1,
  * every later record and detector as 0, all observables 0 and kept = 0.
  * shots_run, shots_kept, kernel_ms, exec_ms and launches are filled by
@@ -108,6 +113,13 @@ typedef struct {
   uint32_t launches;      /* filled: kernels this call launched for this
                              program (memsets and copies not counted) */
   uint32_t reserved;
+  double* expval;         /* NC_OUT_EXPVAL: n_probes rows of `shots` FP64
+                             values, probe j of shot s at expval[j * shots + s]:
+                             <psi|P|psi> / <psi|psi> of the shot's state where
+                             the EXPVAL target P stands (Sec. 3.2, expectation
+                             probes on the runtime state); 0 for a shot already
+                             rejected by postselection there. NULL is allowed
+                             when the program has no probes. */
 } nc_records;
 
 /* Compile extended-Stim text (Sec. 3.1). On failure *out is NULL and a

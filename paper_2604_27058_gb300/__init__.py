@@ -19,8 +19,8 @@ import ctypes
 import numpy as np
 
 from . import _nc
-from ._nc import (NC_FP32_BATCHED, NC_FP64_BATCHED, NC_FP64_PLAIN, NC_OUT_ALL, NC_OUT_DET, NC_OUT_HOST,
-                  NC_OUT_KEPT, NC_OUT_MEAS, NC_OUT_OBS, NC_PS_ALL_DETECTORS, NC_PS_NONE,
+from ._nc import (NC_FP32_BATCHED, NC_FP64_BATCHED, NC_FP64_PLAIN, NC_OUT_ALL, NC_OUT_DET, NC_OUT_EXPVAL,
+                  NC_OUT_HOST, NC_OUT_KEPT, NC_OUT_MEAS, NC_OUT_OBS, NC_PS_ALL_DETECTORS, NC_PS_NONE,
                   NcError, ProgramInfo)
 
 __all__ = ["Program", "compile", "sample", "sample_host", "sample_batch", "debug_dump",
@@ -98,23 +98,26 @@ def _stream_ptr(stream) -> int:
 
 
 def alloc_records(prog: Program, shots: int, device="cuda", outputs=NC_OUT_ALL):
-    """Device record tensors (torch, int64 view of uint64 words)."""
+    """Device record tensors (torch, int64 view of uint64 words) and, for a
+    program with probes, an FP64 [n_probes, shots] expectation tensor."""
     import torch
     wpr = (shots + 63) // 64
     i = prog.info
     mk = lambda rows: torch.empty((max(rows, 1), max(wpr, 1)), dtype=torch.int64, device=device)
+    ev = (outputs & NC_OUT_EXPVAL) and i.n_probes
     return {
         "meas": mk(i.n_meas) if outputs & NC_OUT_MEAS else None,
         "det": mk(i.n_det) if outputs & NC_OUT_DET else None,
         "obs": mk(i.n_obs) if outputs & NC_OUT_OBS else None,
         "kept": mk(1) if outputs & NC_OUT_KEPT else None,
+        "expval": torch.empty((i.n_probes, max(shots, 1)), dtype=torch.float64, device=device) if ev else None,
         "words_per_record": wpr,
     }
 
 
 def _records_struct(bufs, wpr, host=False):
     r = _nc.Records()
-    for key in ("meas", "det", "obs", "kept"):
+    for key in ("meas", "det", "obs", "kept", "expval"):
         t = bufs.get(key)
         if t is None:
             setattr(r, key, None)
@@ -157,13 +160,22 @@ def alloc_host_records(prog: Program, shots: int, outputs=NC_OUT_ALL, pinned=Tru
     else:
         def mk(rows):
             return np.empty((max(rows, 1), max(wpr, 1)), dtype=np.int64)
+    ev = (outputs & NC_OUT_EXPVAL) and i.n_probes
     return {
         "meas": mk(i.n_meas) if outputs & NC_OUT_MEAS else None,
         "det": mk(i.n_det) if outputs & NC_OUT_DET else None,
         "obs": mk(i.n_obs) if outputs & NC_OUT_OBS else None,
         "kept": mk(1) if outputs & NC_OUT_KEPT else None,
+        "expval": _host_f64((i.n_probes, max(shots, 1)), pinned) if ev else None,
         "words_per_record": wpr,
     }
+
+
+def _host_f64(shape, pinned):
+    if pinned:
+        import torch
+        return torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    return np.empty(shape, dtype=np.float64)
 
 
 def sample_host(prog: Program, shots: int, seed: int, precision="fp32", outputs=NC_OUT_ALL,

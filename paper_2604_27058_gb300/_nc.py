@@ -22,8 +22,9 @@ NC_OUT_DET = 2
 NC_OUT_OBS = 4
 NC_OUT_KEPT = 8
 NC_OUT_HOST = 16
+NC_OUT_EXPVAL = 32
 NC_NOALLOC_SCRATCH_BYTES = 64 << 20
-NC_OUT_ALL = NC_OUT_MEAS | NC_OUT_DET | NC_OUT_OBS | NC_OUT_KEPT
+NC_OUT_ALL = NC_OUT_MEAS | NC_OUT_DET | NC_OUT_OBS | NC_OUT_KEPT | NC_OUT_EXPVAL
 NC_PS_NONE = 0
 NC_PS_ALL_DETECTORS = 1
 
@@ -47,7 +48,7 @@ class NcError(RuntimeError):
 class Info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in (
         "n_qubits", "n_meas", "n_det", "n_obs", "k_max", "n_noise_sites", "n_ops",
-        "n_events", "n_slots", "n_static", "n_random", "n_active_meas", "n_array_ops")]
+        "n_events", "n_slots", "n_static", "n_random", "n_active_meas", "n_array_ops", "n_probes")]
 
 
 class SampleOpts(ctypes.Structure):
@@ -62,7 +63,8 @@ class Records(ctypes.Structure):
                 ("kept", ctypes.c_void_p), ("words_per_record", ctypes.c_uint64),
                 ("shots_run", ctypes.c_uint64), ("shots_kept", ctypes.c_uint64),
                 ("kernel_ms", ctypes.c_double), ("exec_ms", ctypes.c_double),
-                ("launches", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("launches", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("expval", ctypes.c_void_p)]
 
 
 _lib = None
@@ -128,3 +130,4 @@ class ProgramInfo:
     n_random: int
     n_active_meas: int
     n_array_ops: int
+    n_probes: int

@@ -142,6 +142,7 @@ void fill_info(nc_program* p) {
   i.n_ops = h.n_ops;
   i.n_events = h.n_events;
   i.n_slots = h.n_slots;
+  i.n_probes = h.n_probes;
   i.n_static = p->cp.counts.n_static;
   i.n_random = p->cp.counts.n_random;
   i.n_active_meas = p->cp.counts.n_active;
@@ -352,6 +353,7 @@ nc_status device_copy(nc_program* p, DevCopy** out) {
 
 struct CallOut {
   uint32_t *meas, *det, *obs, *kept;
+  double* expval = nullptr;
 };
 
 // Optional per-program timing: events around the executor launch and the
@@ -413,6 +415,8 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
   L.shot_offset = shot_offset;
   L.shots = shots;
   L.meas = o.meas;
+  L.expval = o.expval;
+  if (!o.expval || !h.n_probes) lflags &= ~(uint32_t)LF_OUT_EXPVAL;
   L.det = o.det;
   L.obs = o.obs;
   L.kept = o.kept;
@@ -785,6 +789,7 @@ uint32_t launch_flags(const nc_sample_opts& o) {
   if (o.outputs & NC_OUT_KEPT) f |= LF_OUT_KEPT;
   if (o.postselect == NC_PS_ALL_DETECTORS) f |= LF_POSTSELECT;
   if (o.noiseless) f |= LF_NOISELESS;
+  if (o.outputs & NC_OUT_EXPVAL) f |= LF_OUT_EXPVAL;
   return f;
 }
 
@@ -819,6 +824,7 @@ nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, con
     if ((o.outputs & NC_OUT_DET) && h.n_det && !outs[i].det) return NC_E_ARG;
     if ((o.outputs & NC_OUT_OBS) && h.n_obs && !outs[i].obs) return NC_E_ARG;
     if ((o.outputs & NC_OUT_KEPT) && !outs[i].kept) return NC_E_ARG;
+    if ((o.outputs & NC_OUT_EXPVAL) && h.n_probes && !outs[i].expval) return NC_E_ARG;
     if (h.n_sites >= (1u << 28) - 1) return NC_E_UNSUPPORTED;
     st = prepare(progs[i], &dcs[i], stream);
     if (st != NC_OK) return st;
@@ -849,13 +855,15 @@ nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, con
       const ProgHeader& h = header(progs[i]);
       uint64_t row_bytes = outs[i].words_per_record * 8;
       CallOut co{(uint32_t*)outs[i].meas, (uint32_t*)outs[i].det, (uint32_t*)outs[i].obs,
-                 (uint32_t*)outs[i].kept};
+                 (uint32_t*)outs[i].kept, (o.outputs & NC_OUT_EXPVAL) ? outs[i].expval : nullptr};
+      const size_t ev_bytes = (size_t)h.n_probes * shots[i] * sizeof(double);
       if (host) {
         void* d = nullptr;
         if ((o.outputs & NC_OUT_MEAS) && h.n_meas) { NC_TRY(scratch.get(&d, row_bytes * h.n_meas)); co.meas = (uint32_t*)d; }
         if ((o.outputs & NC_OUT_DET) && h.n_det) { NC_TRY(scratch.get(&d, row_bytes * h.n_det)); co.det = (uint32_t*)d; }
         if ((o.outputs & NC_OUT_OBS) && h.n_obs) { NC_TRY(scratch.get(&d, row_bytes * h.n_obs)); co.obs = (uint32_t*)d; }
         if (o.outputs & NC_OUT_KEPT) { NC_TRY(scratch.get(&d, row_bytes)); co.kept = (uint32_t*)d; }
+        if (co.expval && h.n_probes) { NC_TRY(scratch.get(&d, ev_bytes)); co.expval = (double*)d; }
       }
       const char* tn = o.tune ? o.tune : (dcs[i]->tuned.empty() ? nullptr : dcs[i]->tuned.c_str());
       st = enqueue(progs[i], *dcs[i], shots[i], seeds[i], o.shot_offset, o.precision, launch_flags(o), tn, co,
@@ -868,6 +876,7 @@ nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, con
         if (co.det && outs[i].det) NC_TRY(cudaMemcpyAsync(outs[i].det, co.det, row_bytes * h.n_det, cudaMemcpyDeviceToHost, stream));
         if (co.obs && outs[i].obs) NC_TRY(cudaMemcpyAsync(outs[i].obs, co.obs, row_bytes * h.n_obs, cudaMemcpyDeviceToHost, stream));
         if (co.kept && outs[i].kept) NC_TRY(cudaMemcpyAsync(outs[i].kept, co.kept, row_bytes, cudaMemcpyDeviceToHost, stream));
+        if (co.expval && h.n_probes) NC_TRY(cudaMemcpyAsync(outs[i].expval, co.expval, ev_bytes, cudaMemcpyDeviceToHost, stream));
       }
     }
     NC_TRY(cudaMemcpyAsync(kept.data(), counters, 8 * (size_t)n, cudaMemcpyDeviceToHost, stream));
@@ -1033,6 +1042,7 @@ nc_status nc_sample_batch_async(const nc_program* const* progs, const uint64_t* 
     if ((o.outputs & NC_OUT_DET) && h.n_det && !outs[i].det) return NC_E_ARG;
     if ((o.outputs & NC_OUT_OBS) && h.n_obs && !outs[i].obs) return NC_E_ARG;
     if ((o.outputs & NC_OUT_KEPT) && !outs[i].kept) return NC_E_ARG;
+    if ((o.outputs & NC_OUT_EXPVAL) && h.n_probes && !outs[i].expval) return NC_E_ARG;
     nc_program* p = const_cast<nc_program*>(progs[i]);
     std::lock_guard<std::mutex> lock(p->mu);
     for (auto& c : p->devs)
@@ -1053,7 +1063,8 @@ nc_status nc_sample_batch_async(const nc_program* const* progs, const uint64_t* 
       outs[i].kernel_ms = outs[i].exec_ms = 0.0;
       outs[i].launches = 0;
       if (shots[i] == 0) continue;
-      CallOut co{(uint32_t*)outs[i].meas, (uint32_t*)outs[i].det, (uint32_t*)outs[i].obs, (uint32_t*)outs[i].kept};
+      CallOut co{(uint32_t*)outs[i].meas, (uint32_t*)outs[i].det, (uint32_t*)outs[i].obs, (uint32_t*)outs[i].kept,
+                 (o.outputs & NC_OUT_EXPVAL) ? outs[i].expval : nullptr};
       const char* tn = o.tune ? o.tune : (dcs[i]->tuned.empty() ? nullptr : dcs[i]->tuned.c_str());
       st = enqueue(progs[i], *dcs[i], shots[i], seeds[i], o.shot_offset, o.precision, launch_flags(o) | LF_ASYNC,
                    tn, co, kept_dev + i, err_dev, scratch, stream, 0xffffffffu, 0, nullptr, nullptr, nullptr,
@@ -1206,7 +1217,7 @@ done:
   return st;
 }
 
-uint32_t nc_abi_version(void) { return (kVersion << 16) | 4u; }
+uint32_t nc_abi_version(void) { return (kVersion << 16) | 5u; }
 
 }  // extern "C"
 

@@ -36,7 +36,7 @@ struct CompileError : std::runtime_error {
 
 [[noreturn]] void fail(int code, const std::string& msg) { throw CompileError(code, msg); }
 
-enum Kind { K_GATE, K_ROT, K_MEAS, K_NOISE, K_FF, K_DET, K_OBS };
+enum Kind { K_GATE, K_ROT, K_MEAS, K_NOISE, K_FF, K_DET, K_OBS, K_PROBE };
 
 struct PhysOp {
   Kind kind = K_GATE;
@@ -46,8 +46,8 @@ struct PhysOp {
   int64_t event = -1, record = -1, site = -1;
   bool reset = false;
   bool xbasis = false;
-  std::vector<int64_t> recs;  // det / obs records; ff: recs[0]
-  int64_t index = -1;
+  std::vector<int64_t> recs;  // det / obs records; ff: recs[0]; probe: its qubits
+  int64_t index = -1;         // detector / observable / probe index
   int instr = -1;     // source instruction ordinal (groups targets of one line)
 };
 
@@ -163,7 +163,7 @@ bool is_2q_clifford(const std::string& n) {
 
 struct Flattener {
   std::vector<PhysOp> ops;
-  int64_t n_q = 0, ev = 0, rec = 0, site = 0, det = 0, n_obs = 0;
+  int64_t n_q = 0, ev = 0, rec = 0, site = 0, det = 0, n_obs = 0, probe = 0;
   int instr = 0;
   std::vector<double> site_p;
   std::vector<uint8_t> site_kind;
@@ -207,6 +207,30 @@ struct Flattener {
       for (auto& t : l.targets) o.recs.push_back(rec_target(t));
       o.index = det++;
       ops.push_back(o);
+      return;
+    }
+    if (name == "EXPVAL") {
+      // one probe per Pauli-product target, e.g. X0*Y1*Z5 (letters in name)
+      if (!l.args.empty() || l.targets.empty()) fail(1, "EXPVAL takes Pauli product targets and no argument");
+      for (auto& t : l.targets) {
+        PhysOp o; o.kind = K_PROBE;
+        size_t s0 = 0;
+        while (s0 <= t.size()) {
+          size_t c = t.find('*', s0);
+          std::string f = t.substr(s0, c == std::string::npos ? std::string::npos : c - s0);
+          if (f.size() < 2 || (f[0] != 'X' && f[0] != 'Y' && f[0] != 'Z')) fail(1, "bad Pauli product target '" + t + "'");
+          int q = qubit(f.substr(1));
+          for (auto r : o.recs)
+            if (r == q) fail(1, "qubit repeated in '" + t + "'");
+          o.recs.push_back(q);
+          o.name.push_back(f[0]);
+          if (c == std::string::npos) break;
+          s0 = c + 1;
+        }
+        o.index = probe++;
+        o.instr = instr;
+        ops.push_back(o);
+      }
       return;
     }
     if (name == "OBSERVABLE_INCLUDE") {
@@ -786,6 +810,27 @@ struct Compiler {
     }
   }
 
+  // Expectation-value probe (Sec. 3.2): M(P) for the product P; the frame
+  // sign and the active-vector reduction are per shot (OP_EXPVAL).
+  void probe(const PhysOp& o) {
+    Pauli p(nw64);
+    for (size_t j = 0; j < o.recs.size(); j++) pmul_inplace(p, map_letter((int)o.recs[j], o.name[j]));
+    Op e = mk(OP_EXPVAL);
+    e.i0 = add_mask(p, true, true);
+    e.i3 = (uint32_t)o.index;
+    e.pa = (uint8_t)(p.ph & 3);
+    for (int q = 0; q < n; q++) {
+      if (pos_of[q] < 0) {
+        if (p.xb(q)) e.pb = 1;  // x-support on a dormant qubit: <0|X|0> = 0
+        continue;
+      }
+      if (p.xb(q)) e.i1 |= 1u << pos_of[q];
+      if (p.zb(q)) e.i2 |= 1u << pos_of[q];
+    }
+    if (e.pb) e.i1 = e.i2 = 0;
+    emit(e);
+  }
+
   void measure(const PhysOp& o, std::vector<int64_t>& flips_of_instr) {
     Pauli p = map_letter(o.q0, o.xbasis ? 'X' : 'Z');
     int64_t id = next_id++;
@@ -976,6 +1021,9 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
           c.emit(d, u, -1);
           break;
         }
+        case K_PROBE:
+          c.probe(po);
+          break;
         case K_OBS: {
           if (obs_id[po.index] < 0) obs_id[po.index] = c.next_id++;
           Op d = c.mk(OP_OBS_INCLUDE);
@@ -1326,6 +1374,7 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     h.n_plist = (uint32_t)plist.size();
     h.n_blocks = n_blocks;
     h.n_guide = (uint32_t)guide.size();
+    h.n_probes = (uint32_t)fl.probe;
     {
       double mean = 0.0;
       for (double sp : c.site_p) mean += sp;

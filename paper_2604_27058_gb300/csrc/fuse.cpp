@@ -13,9 +13,10 @@
 //     vector anyway.
 //   * ROT_X and ARRAY_H mix amplitude pairs (i, i ^ e_v), stored at p and
 //     p ^ (A e_v): one pass that first applies the pending phases.
-//   * Before an active measurement the map is materialised (one gather pass
-//     with the pending phases), so measurement, demotion and every record
-//     stay exactly those of the plain bytecode.
+//   * Before an active measurement or an expectation probe the map is
+//     materialised (one gather pass with the pending phases), so
+//     measurement, demotion, probes and every record stay exactly those of
+//     the plain bytecode.
 // The frame parts of the array Cliffords stay as frame instructions at
 // their original places. A pending ROT_Z reads its frame sign bit when the
 // phases are applied, so pending phases are applied first whenever a later
@@ -198,8 +199,10 @@ void append_fused(std::vector<uint8_t>& blob) {
         out.push_back(o);
         break;
       }
+      case OP_EXPVAL:
       case OP_MEAS_ACTIVE_Z:
       case OP_MEAS_ACTIVE_X: {
+        // the vector in logical order with every pending phase applied
         if (!s.identity()) {
           Op m{};
           m.code = OP_PERMF;
@@ -216,7 +219,7 @@ void append_fused(std::vector<uint8_t>& blob) {
           flush_diag();
         }
         out.push_back(o);
-        s.k--;
+        if (o.code != OP_EXPVAL) s.k--;  // a probe keeps every axis
         for (uint32_t t = 0; t < s.k; t++) s.col[t] = s.rinv[t] = 1u << t;
         break;
       }

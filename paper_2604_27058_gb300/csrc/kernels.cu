@@ -730,6 +730,68 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
               if (c) atomicAdd(L.kept_count, (unsigned long long)c);
             }
             break;
+          case OP_EXPVAL: {
+            // ---- expectation probe (Sec. 3.2): <P> = (-1)^(frame sign) Re(i^pa
+            // <phi| X^i1 Z^i2 |phi>) / <phi|phi>, FP64 sums per shot ----
+            if (!(L.flags & LF_OUT_EXPVAL)) break;
+            __syncthreads();
+            const bool odd = (op.pa & 1u) != 0;
+            if (!op.pb && k > 0) {
+              for (uint32_t s = t; s < S; s += T) {
+                RED[s] = 0.0;
+                RED[S + s] = 0.0;
+              }
+              __syncthreads();
+              const uint32_t dim = 1u << k, mx = op.i1, mz = op.i2;
+              for (uint32_t s = t % S; s < S; s += T) {
+                double acc = 0.0, nrm = 0.0;
+                for (uint32_t j = sub; j < dim; j += R) {
+                  const C a = work[(size_t)j * S + s], b = work[(size_t)(j ^ mx) * S + s];
+                  const double ax = a.x, ay = a.y, bx = b.x, by = b.y;
+                  const double v = odd ? bx * ay - by * ax : bx * ax + by * ay;  // conj(b) a
+                  acc += (__popc(j & mz) & 1u) ? -v : v;
+                  nrm += ax * ax + ay * ay;
+                }
+                atomicAdd(&RED[s], acc);
+                atomicAdd(&RED[S + s], nrm);
+              }
+              __syncthreads();
+            }
+            if (owner) {
+              // frame sign: parity(fx & z) ^ parity(fz & x) of the image M(P)
+              const uint32_t* mk = p.masks + op.i0;
+              Vw<W> om = vfill<W>(0u);
+              for (uint32_t w = 0; w < p.nw; w++) {
+                uint32_t bx = __ldg(mk + w), bz = __ldg(mk + p.nw + w);
+                while (bz) {
+                  vxor<W>(om, vld<W>(plane(w * 32u + (__ffs(bz) - 1))));
+                  bz &= bz - 1;
+                }
+                while (bx) {
+                  vxor<W>(om, vld<W>(plane(N + w * 32u + (__ffs(bx) - 1))));
+                  bx &= bx - 1;
+                }
+              }
+              const Vw<W> kept = vld<W>(slot(p.kept_slot));
+              const double sg = (op.pa == 1 || op.pa == 2) ? -1.0 : 1.0;
+#pragma unroll
+              for (int i = 0; i < W; i++)
+                for (uint32_t j = 0; j < 32; j++) {
+                  const uint64_t sl = (word0 + i) * 32u + j;  // call-local shot
+                  if (sl >= L.shots) break;
+                  const uint32_t s = (tw + i) * 32u + j;      // shot in the tile
+                  double v = 0.0;
+                  if (!op.pb && ((kept.v[i] >> j) & 1u)) {
+                    double part = odd ? 0.0 : 1.0;
+                    if (k > 0) part = RED[S + s] > 0.0 ? RED[s] / RED[S + s] : 0.0;
+                    v = ((om.v[i] >> j) & 1u) ? -sg * part : sg * part;
+                  }
+                  L.expval[(size_t)op.i3 * L.shots + sl] = v;
+                }
+            }
+            __syncthreads();
+            break;
+          }
           case OP_DIAGF:
           case OP_MIXF:
           case OP_PERMF: {
@@ -1510,6 +1572,32 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
           nf = next_fault_r(p, L.seed, s, site + 1, nr);
         }
         break;
+      case OP_EXPVAL: {
+        // expectation probe: (-1)^(frame sign) Re(i^pa <phi| X^i1 Z^i2 |phi>) / <phi|phi>
+        if (!(L.flags & LF_OUT_EXPVAL) || !valid) break;
+        double v = 0.0;
+        if (!op.pb && getb(slots, p.kept_slot)) {
+          const bool odd = (op.pa & 1u) != 0;
+          double part = odd ? 0.0 : 1.0;
+          if (k > 0) {
+            double acc = 0.0, nrm = 0.0;
+            for (uint32_t j = 0; j < (1u << k); j++) {
+              const double2 a = amp(j), b = amp(j ^ op.i1);
+              const double t1 = odd ? b.x * a.y - b.y * a.x : b.x * a.x + b.y * a.y;
+              acc += (__popc(j & op.i2) & 1u) ? -t1 : t1;
+              nrm += a.x * a.x + a.y * a.y;
+            }
+            part = nrm > 0.0 ? acc / nrm : 0.0;
+          }
+          uint32_t om = 0;
+          for (uint32_t w = 0; w < p.nw; w++)
+            om ^= __popc(x[w] & __ldg(p.masks + op.i0 + p.nw + w)) ^ __popc(z[w] & __ldg(p.masks + op.i0 + w));
+          const double sg = (op.pa == 1 || op.pa == 2) ? -1.0 : 1.0;
+          v = (om & 1u) ? -sg * part : sg * part;
+        }
+        L.expval[(size_t)op.i3 * L.shots + sl] = v;
+        break;
+      }
       case OP_FEEDFORWARD:
         if (getb(slots, op.i2))
           for (uint32_t w = 0; w < p.nw; w++) {

@@ -66,12 +66,14 @@ enum : uint32_t {
   LF_OUT_KEPT = 64,
   LF_ASYNC = 128,     // host side only: no host synchronisation (stream capture)
   LF_ARGMAX = 256,    // every measurement takes its more likely outcome (0 on a tie): the reference trajectory
+  LF_OUT_EXPVAL = 512,  // write the expectation probes (OP_EXPVAL) to expval
 };
 
 struct LaunchParams {
   DevProg p;
   uint64_t seed, shot_offset, shots;
   uint32_t *meas, *det, *obs, *kept;  // u32 views of the u64 record rows
+  double* expval;                     // probe j of call-local shot s at expval[j * shots + s]
   uint64_t row_words32;               // u32 words per record row
   uint32_t flags;
   uint32_t G;                         // 32-shot words per tile (batched executor)

@@ -191,6 +191,7 @@ extern "C" nc_status nc_sample_noalloc(const nc_program* prog, uint64_t shots, u
   const std::vector<uint8_t>& blob = program_blob(prog);
   ProgHeader h;
   std::memcpy(&h, blob.data(), sizeof(h));
+  if ((o.outputs & NC_OUT_EXPVAL) && h.n_probes) return NC_E_UNSUPPORTED;  // probes: nc_sample
   if (out->words_per_record != (shots + 63) / 64) return NC_E_ARG;
   if ((o.outputs & NC_OUT_MEAS) && h.n_meas && !out->meas) return NC_E_ARG;
   if ((o.outputs & NC_OUT_DET) && h.n_det && !out->det) return NC_E_ARG;

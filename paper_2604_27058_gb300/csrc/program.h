@@ -46,6 +46,12 @@ enum OpCode : uint8_t {
   OP_MIXF,   // pair pass: partner mask i0, orientation mask i1 (bit 31: its constant), pivot
              // bit pa, pb = 0 H / 1 ROT_X; i2 = lead record (ROT_X angle, sign plane), then i3 terms
   OP_PERMF,  // gather into logical order: perm table at i0 (i1 column masks, then c), i2 / i3 terms
+  // Expectation-value probe (Sec. 3.2): <P> of the shot's state into probe row i3.
+  // M(P) = i^pa X^x Z^z (mask i0: x words then z words); the frame contributes
+  // (-1)^{parity(fx & z) ^ parity(fz & x)}; pb = 1: x-support on a dormant
+  // qubit (the value is 0); else <phi| X^i1 Z^i2 |phi> / <phi|phi> over the
+  // active positions.
+  OP_EXPVAL,
   OP_COUNT
 };
 
@@ -124,7 +130,8 @@ struct ProgHeader {
   float aff_chunks_per_shot;       // expected chunks of a shot's faults
   uint32_t n_guide;                // survival guide-table entries
   uint32_t aff_n_chains;           // delta-row chains of two or more rows
-  uint32_t aff_n_chain_rows, pad3; // rows on those chains
+  uint32_t aff_n_chain_rows;       // rows on those chains
+  uint32_t n_probes;               // expectation-value probes (OP_EXPVAL rows)
   uint32_t n_fops, n_fterms;       // fused instruction list and its terms (0: none)
   uint32_t n_fperm, f_perm;        // permutation-table words; 1 if the list has OP_PERMF
   uint64_t off_ops, off_masks, off_q, off_seg_start, off_seg_end, off_site_info, off_site_eff,
@@ -193,7 +200,7 @@ constexpr uint32_t kRecPerSite = 15;
 // row): its fault flips the slot and, if the shot is kept, the output bit.
 
 constexpr uint32_t kMagic = 0x4E435047u;  // "NCPG"
-constexpr uint32_t kVersion = 10;
+constexpr uint32_t kVersion = 11;
 constexpr uint32_t kMaxK = 30;
 constexpr uint32_t kMaxQubits = 4096;
 
