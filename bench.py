@@ -367,9 +367,11 @@ def run_ours(args):
 
     # roofline of the dominant kernel (the record-tile kernel of the k_max = 0
     # path, else the batched executor): algorithmic bytes = the records it
-    # must write, over its own summed launch time
+    # must write and the active-vector traversals of the instruction list
+    # (before fusion), over its own summed launch time
     peaks, peak_src = measured_peaks()
-    alg = record_bytes_per_shot(info) * shots
+    # records, plus the active-vector traversals of a program with active axes
+    alg = (record_bytes_per_shot(info) + info.array_bytes_fp32) * shots
     achieved = alg / (exec_ms / 1000.0) / 1e9
     tr = ncu_traffic(wname)
     affine = info.k_max == 0 and "a=0" not in (args.tune or "")

@@ -52,6 +52,10 @@ typedef struct {
   uint32_t n_qubits, n_meas, n_det, n_obs, k_max, n_noise_sites, n_ops;
   uint32_t n_events, n_slots, n_static, n_random, n_active_meas, n_array_ops;
   uint32_t n_probes;  /* EXPVAL probes (rows of nc_records.expval) */
+  double array_bytes_fp32;  /* active-vector bytes one shot's array traversals
+                               (Sec. 2.6) move at FP32, counted as: expansion
+                               3 * 2^k amplitudes, a 1- or 2-axis pass 2 * 2^k,
+                               an active measurement 2.5 * 2^k; 8 bytes each */
 } nc_info;
 
 /* precision */

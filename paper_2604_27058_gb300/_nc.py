@@ -48,7 +48,8 @@ class NcError(RuntimeError):
 class Info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in (
         "n_qubits", "n_meas", "n_det", "n_obs", "k_max", "n_noise_sites", "n_ops",
-        "n_events", "n_slots", "n_static", "n_random", "n_active_meas", "n_array_ops", "n_probes")]
+        "n_events", "n_slots", "n_static", "n_random", "n_active_meas", "n_array_ops", "n_probes")] + [
+        ("array_bytes_fp32", ctypes.c_double)]
 
 
 class SampleOpts(ctypes.Structure):
@@ -131,3 +132,4 @@ class ProgramInfo:
     n_active_meas: int
     n_array_ops: int
     n_probes: int
+    array_bytes_fp32: float

@@ -143,6 +143,7 @@ void fill_info(nc_program* p) {
   i.n_events = h.n_events;
   i.n_slots = h.n_slots;
   i.n_probes = h.n_probes;
+  i.array_bytes_fp32 = p->cp.counts.array_bytes;
   i.n_static = p->cp.counts.n_static;
   i.n_random = p->cp.counts.n_random;
   i.n_active_meas = p->cp.counts.n_active;

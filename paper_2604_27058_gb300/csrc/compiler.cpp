@@ -1428,6 +1428,23 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     cp(h.off_site_p, c.site_p.data(), S * 8);
     append_affine(out.blob);
     append_fused(out.blob);
+    {
+      // array traffic of one shot through the (unfused) instruction list
+      double bytes = 0.0;
+      uint32_t k = 0;
+      for (const Op& o : ops) {
+        const double dim = std::ldexp(1.0, (int)k);
+        switch (o.code) {
+          case OP_EXPAND_ROT: bytes += 8.0 * 3.0 * dim; k++; break;
+          case OP_ARRAY_H: case OP_ARRAY_S: case OP_ARRAY_CX: case OP_ARRAY_CZ: case OP_ROT_Z: case OP_ROT_X:
+            bytes += 8.0 * 2.0 * dim;
+            break;
+          case OP_MEAS_ACTIVE_Z: case OP_MEAS_ACTIVE_X: bytes += 8.0 * 2.5 * dim; k--; break;
+          default: break;
+        }
+      }
+      c.counts.array_bytes = bytes;
+    }
     out.counts = c.counts;
     return 0;
   } catch (CompileError& e) {

@@ -11,6 +11,11 @@ namespace nc {
 
 struct nc_info_counts {
   uint32_t n_static, n_random, n_active, array_ops;
+  // bytes per shot the array traversals of Sec. 2.6 move at FP32 (8-byte
+  // amplitudes), counted as: an expansion reads 2^k and writes 2^(k+1)
+  // amplitudes, a diagonal, 2x2 or permutation pass reads and writes 2^k, an
+  // active measurement reads 2^k twice and writes 2^(k-1)
+  double array_bytes;
 };
 
 struct CompiledProgram {

@@ -125,3 +125,30 @@ def test_missing_library_fails_loudly(nc, monkeypatch):
     monkeypatch.setattr(_nc, "_lib", None, raising=False)
     with pytest.raises(RuntimeError):
         _nc.lib()
+
+
+def _plan_array_bytes(sim):
+    """Array bytes per shot at FP32 from the oracle's plan (the same
+    traversal count: expand 3 * 2^k, passes 2 * 2^k, active measurement
+    2.5 * 2^k amplitudes of 8 bytes)."""
+    k, b = 0, 0.0
+    for st in sim.steps:
+        if st.kind == "expand":
+            b += 8 * 3 * 2 ** k
+            k += 1
+        elif st.kind == "rot" or (st.kind == "vg" and st.a["pos"] is not None):
+            b += 8 * 2 * 2 ** k
+        elif st.kind == "mact":
+            b += 8 * 2.5 * 2 ** k
+            k -= 1
+    return b
+
+
+@pytest.mark.parametrize("name", ["tiny", "lowmagic", "coherent", "small"])
+def test_array_bytes_match_the_oracle_plan(nc, name):
+    from oracle.factored import FactoredSim
+    text = {"tiny": gc.tiny_random(), "lowmagic": gc.low_magic_gadgets(),
+            "coherent": gc.surface_code_memory(d=3, rounds=3, p=1e-3, theta=0.02),
+            "small": gc.random_small(77, n=6, n_ops=100, t_frac=0.3)}[name]
+    assert nc.compile(text).info.array_bytes_fp32 == pytest.approx(_plan_array_bytes(FactoredSim(text)), rel=1e-12)
+    assert nc.compile(gc.surface_code_memory(d=3, rounds=2)).info.array_bytes_fp32 == 0.0
