@@ -118,7 +118,10 @@ def test_host_and_graph_paths_equal_device(nc):
     prog = nc.compile(text)
     a = nc.sample(prog, 3000, 8)
     h = nc.sample_host(prog, 3000, 8)
-    assert np.array_equal(a["expval"].cpu().numpy(), h["expval"])
+    # the per-shot FP64 sums are shared-memory atomic adds: equal up to the
+    # order of the additions
+    d = float(np.max(np.abs(a["expval"].cpu().numpy() - h["expval"])))
+    assert d <= 1e-12, d
     nc.prepare(prog)
     outs = [nc.alloc_records(prog, 3000)]
     kept = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -129,7 +132,8 @@ def test_host_and_graph_paths_equal_device(nc):
     g.replay()
     torch.cuda.synchronize()
     assert int(err.item()) == 0
-    assert torch.equal(outs[0]["expval"], a["expval"])
+    d = float((outs[0]["expval"] - a["expval"]).abs().max())
+    assert d <= 1e-12, d
 
 
 def test_probe_outputs_optional(nc):
