@@ -379,7 +379,10 @@ def run_ours(args):
             "frac": achieved / peaks["hbm_gbs"], "traffic": (tr * shots) if tr else None,
             "kernel": "sample_affine" if affine else "exec_batched",
             "peak_source": f"{peak_src} (hbm_gbs, burst copy)",
-            "algorithmic_bytes_per_launch": alg, "kernel_ms": exec_ms, "call_ms": call_ms}
+            "algorithmic_bytes_per_launch": alg, "kernel_ms": exec_ms, "call_ms": call_ms,
+            "bytes_model": "records written + active-vector traversals of the unfused instruction list "
+                           "(Sec. 2.6 traversal count, 8 B per FP32 amplitude); fused passes, vectors kept in "
+                           "shared memory and a shared prefix read as effective bandwidth above the copy peak"}
 
     if rank == 0:
         line = {

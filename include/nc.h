@@ -56,6 +56,12 @@ typedef struct {
                                (Sec. 2.6) move at FP32, counted as: expansion
                                3 * 2^k amplitudes, a 1- or 2-axis pass 2 * 2^k,
                                an active measurement 2.5 * 2^k; 8 bytes each */
+  uint32_t prefix_ops, prefix_k;  /* shared prefix: the first prefix_ops
+                               instructions hold no noise, measurement or
+                               record, so every shot leaves them with the same
+                               state (prefix_k active axes, zero frame); the
+                               batched forms compute that state once per call */
+  double prefix_bytes_fp32;  /* the part of array_bytes_fp32 spent in it */
 } nc_info;
 
 /* precision */
@@ -116,7 +122,8 @@ typedef struct {
                              launches, CUDA events on cuda_stream */
   uint32_t launches;      /* filled: kernels this call launched for this
                              program (memsets and copies not counted) */
-  uint32_t reserved;
+  uint32_t path;          /* filled: bit 0 = the shared prefix was computed
+                             once for the call (nc_info.prefix_ops) */
   double* expval;         /* NC_OUT_EXPVAL: n_probes rows of `shots` FP64
                              values, probe j of shot s at expval[j * shots + s]:
                              <psi|P|psi> / <psi|psi> of the shot's state where

@@ -146,6 +146,7 @@ def sample(prog: Program, shots: int, seed: int, precision="fp32", outputs=NC_OU
     res["kernel_ms"] = rec.kernel_ms
     res["exec_ms"] = rec.exec_ms
     res["launches"] = rec.launches
+    res["path"] = rec.path
     return res
 
 
@@ -194,6 +195,7 @@ def sample_host(prog: Program, shots: int, seed: int, precision="fp32", outputs=
     res["kernel_ms"] = rec.kernel_ms
     res["exec_ms"] = rec.exec_ms
     res["launches"] = rec.launches
+    res["path"] = rec.path
     return res
 
 
@@ -216,6 +218,7 @@ def sample_batch(progs, shots, seeds, precision="fp32", outputs=NC_OUT_ALL, post
         d["kernel_ms"] = r.kernel_ms
         d["exec_ms"] = r.exec_ms
         d["launches"] = r.launches
+        d["path"] = r.path
         res.append(d)
     return res
 

@@ -49,7 +49,8 @@ class Info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in (
         "n_qubits", "n_meas", "n_det", "n_obs", "k_max", "n_noise_sites", "n_ops",
         "n_events", "n_slots", "n_static", "n_random", "n_active_meas", "n_array_ops", "n_probes")] + [
-        ("array_bytes_fp32", ctypes.c_double)]
+        ("array_bytes_fp32", ctypes.c_double), ("prefix_ops", ctypes.c_uint32), ("prefix_k", ctypes.c_uint32),
+        ("prefix_bytes_fp32", ctypes.c_double)]
 
 
 class SampleOpts(ctypes.Structure):
@@ -64,7 +65,7 @@ class Records(ctypes.Structure):
                 ("kept", ctypes.c_void_p), ("words_per_record", ctypes.c_uint64),
                 ("shots_run", ctypes.c_uint64), ("shots_kept", ctypes.c_uint64),
                 ("kernel_ms", ctypes.c_double), ("exec_ms", ctypes.c_double),
-                ("launches", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("launches", ctypes.c_uint32), ("path", ctypes.c_uint32),
                 ("expval", ctypes.c_void_p)]
 
 
@@ -133,3 +134,6 @@ class ProgramInfo:
     n_array_ops: int
     n_probes: int
     array_bytes_fp32: float
+    prefix_ops: int
+    prefix_k: int
+    prefix_bytes_fp32: float

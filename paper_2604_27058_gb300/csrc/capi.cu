@@ -29,6 +29,8 @@ cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st);
 cudaError_t launch_patch_ref(Op* ops, uint32_t n_ops, const uint32_t* det_ref, const uint32_t* obs_ref,
                              cudaStream_t st);
 cudaError_t launch_presample(const LaunchParams& L, cudaStream_t st);
+cudaError_t launch_prefix(const Op* host_ops, uint32_t n, bool fp64, void* vec, int n_sm, cudaStream_t st,
+                          uint32_t* launches);
 size_t affine_smem_bytes(const DevProg& p, uint32_t wpt);
 cudaError_t launch_affine(const LaunchParams& L, uint32_t wpt, uint32_t grid, size_t smem, cudaStream_t st,
                           int* per_sm);
@@ -144,6 +146,9 @@ void fill_info(nc_program* p) {
   i.n_slots = h.n_slots;
   i.n_probes = h.n_probes;
   i.array_bytes_fp32 = p->cp.counts.array_bytes;
+  i.prefix_ops = h.prefix_end;
+  i.prefix_k = h.prefix_k;
+  i.prefix_bytes_fp32 = p->cp.counts.prefix_bytes;
   i.n_static = p->cp.counts.n_static;
   i.n_random = p->cp.counts.n_random;
   i.n_active_meas = p->cp.counts.n_active;
@@ -195,6 +200,7 @@ struct Scratch {
 struct Tuning {
   uint32_t G, T, W, B, A, AW, AI, AV, AC, PS, AO;  // PS = 1: pre-sample faults even for small calls
   uint32_t SW = 1;                                 // SW = 0: active vectors never in shared memory
+  uint32_t PX = 1;  // shared prefix: 0 off, 1 when it saves enough traffic, 2 whenever it has array work
 };
 
 Tuning choose_tuning(const DevProg& d, const char* tune, uint64_t shots, int n_sm) {
@@ -222,6 +228,7 @@ Tuning choose_tuning(const DevProg& d, const char* tune, uint64_t shots, int n_s
       else if (sscanf(s, "ps=%u", &v) == 1) t.PS = v;
       else if (sscanf(s, "ao=%u", &v) == 1) t.AO = v;
       else if (sscanf(s, "sw=%u", &v) == 1) t.SW = v;
+      else if (sscanf(s, "px=%u", &v) == 1) t.PX = v;
       const char* c = strchr(s, ',');
       if (!c) break;
       s = c + 1;
@@ -362,6 +369,7 @@ struct CallOut {
 struct Timing {
   std::vector<cudaEvent_t> ev;  // pairs around each launch of the dominant kernel
   uint32_t launches = 0;
+  uint32_t path = 0;  // bit 0: the shared prefix ran once for the call
   cudaError_t begin(cudaStream_t s) { return mark(s); }
   cudaError_t end(cudaStream_t s) { return mark(s); }
   cudaError_t mark(cudaStream_t s) {
@@ -648,6 +656,25 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
       }
     }
     if (strat && !bk && !L.flist) return NC_E_OOM;  // stratified shots need their fault lists
+    // the shared prefix (program.h prefix_end) once for the whole call, when
+    // its traffic over all shots outweighs one launch per instruction
+    if (h.prefix_end > 0 && h.prefix_k > 0 && tu.PX && stop_event == 0xffffffffu) {
+      const double saved = (double)prog->cp.counts.prefix_bytes * (fp64 ? 2.0 : 1.0) * (double)shots;
+      if (tu.PX == 2 || (h.prefix_k >= 6 && saved > 64.0 * 1024 * 1024)) {
+        void* vec = nullptr;
+        NC_TRY(scratch.get(&vec, ((size_t)1 << h.prefix_k) * (fp64 ? 16 : 8)));
+        uint32_t nl = 0;
+        NC_TRY(launch_prefix(reinterpret_cast<const Op*>(prog->cp.blob.data() + h.off_ops), h.prefix_end, fp64, vec,
+                             n_sm, stream, &nl));
+        L.init_vec = vec;
+        L.start_op = h.n_fops ? h.f_start : h.prefix_end;  // the executor runs the fused list when there is one
+        L.start_k = h.prefix_k;
+        if (tm) {
+          tm->launches += nl;
+          tm->path |= 1u;
+        }
+      }
+    }
     if (tm) NC_TRY(tm->begin(stream));
     NC_TRY(launch_batched(L, fp64, tu.W, bk, (uint32_t)grid, tu.T, smem, stream));
     if (tm) {
@@ -894,6 +921,7 @@ nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, con
     outs[i].kernel_ms = kernel_ms;
     outs[i].exec_ms = shots[i] ? tms[i].ms() : 0.0;
     outs[i].launches = tms[i].launches;
+    outs[i].path = tms[i].path;
   }
 done:
   cudaEventDestroy(ev0);
@@ -1063,6 +1091,7 @@ nc_status nc_sample_batch_async(const nc_program* const* progs, const uint64_t* 
       outs[i].shots_kept = 0;
       outs[i].kernel_ms = outs[i].exec_ms = 0.0;
       outs[i].launches = 0;
+      outs[i].path = 0;
       if (shots[i] == 0) continue;
       CallOut co{(uint32_t*)outs[i].meas, (uint32_t*)outs[i].det, (uint32_t*)outs[i].obs, (uint32_t*)outs[i].kept,
                  (o.outputs & NC_OUT_EXPVAL) ? outs[i].expval : nullptr};

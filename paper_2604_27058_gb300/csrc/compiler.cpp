@@ -1376,6 +1376,17 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     h.n_guide = (uint32_t)guide.size();
     h.n_probes = (uint32_t)fl.probe;
     {
+      // shared prefix: frame, array and rotation instructions from the start
+      uint32_t k = 0, pe = 0;
+      for (; pe < ops.size(); pe++) {
+        const uint8_t cd = ops[pe].code;
+        if (!(cd >= OP_FRAME_H && cd <= OP_ROT_X)) break;
+        if (cd == OP_EXPAND_ROT) k++;
+      }
+      h.prefix_end = pe;
+      h.prefix_k = k;
+    }
+    {
       double mean = 0.0;
       for (double sp : c.site_p) mean += sp;
       h.mean_faults = (float)mean;
@@ -1432,7 +1443,11 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
       // array traffic of one shot through the (unfused) instruction list
       double bytes = 0.0;
       uint32_t k = 0;
-      for (const Op& o : ops) {
+      ProgHeader hh;
+      std::memcpy(&hh, out.blob.data(), sizeof(hh));
+      for (size_t pc = 0; pc < ops.size(); pc++) {
+        if (pc == hh.prefix_end) c.counts.prefix_bytes = bytes;
+        const Op& o = ops[pc];
         const double dim = std::ldexp(1.0, (int)k);
         switch (o.code) {
           case OP_EXPAND_ROT: bytes += 8.0 * 3.0 * dim; k++; break;

@@ -16,6 +16,8 @@ struct nc_info_counts {
   // amplitudes, a diagonal, 2x2 or permutation pass reads and writes 2^k, an
   // active measurement reads 2^k twice and writes 2^(k-1)
   double array_bytes;
+  // the part of array_bytes spent in the shared prefix (program.h prefix_end)
+  double prefix_bytes;
 };
 
 struct CompiledProgram {

@@ -150,6 +150,26 @@ void append_fused(std::vector<uint8_t>& blob) {
 
   for (uint32_t pc = 0; pc < h.n_ops; pc++) {
     const Op& o = ops[pc];
+    if (pc == h.prefix_end && h.prefix_k > 0) {
+      // end of the shared prefix: logical order, no pending term, so shots
+      // can resume here from the prefix's vector
+      if (!s.identity()) {
+        Op m{};
+        m.code = OP_PERMF;
+        m.i0 = (uint32_t)perm.size();
+        m.i1 = s.k;
+        for (uint32_t t = 0; t < s.k; t++) perm.push_back(s.col[t]);
+        perm.push_back(s.c);
+        take_terms(m, nullptr);
+        out.push_back(m);
+        any_perm = true;
+        for (uint32_t t = 0; t < s.k; t++) s.col[t] = s.rinv[t] = 1u << t;
+        s.c = 0;
+      } else {
+        flush_diag();
+      }
+      h.f_start = (uint32_t)out.size();
+    }
     switch (o.code) {
       case OP_BATCH:
         break;  // the payloads follow as single instructions

@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
     }
     work = work_base;
     work2 = work_base + L.work_stride;
-    if (p.k_max > 0) {
+    if (p.k_max > 0 && !L.init_vec) {
       for (uint32_t s = t; s < S; s += T) {
         C one;
         one.x = (real)1;
@@ -303,6 +303,14 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
       }
     }
     uint32_t k = 0;
+    if (L.init_vec) {
+      // the shared prefix's state (frame zero, no record): every shot's copy
+      const C* iv = reinterpret_cast<const C*>(L.init_vec);
+      const uint32_t dim = 1u << L.start_k;
+      for (uint32_t s = t % S; s < S; s += T)
+        for (uint32_t j = sub; j < dim; j += R) work[(size_t)j * S + s] = iv[j];
+      k = L.start_k;
+    }
 
     auto store = [&](uint32_t* base, uint32_t row, const Vw<W>& v) {
       uint32_t* dst = base + (size_t)row * L.row_words32 + word0;
@@ -316,16 +324,18 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
     auto plane = [&](uint32_t q) -> uint32_t* { return PL + q * G + tw; };
     auto slot = [&](uint32_t s) -> uint32_t* { return SL + s * G + tw; };
 
-    load_chunk(0);
+    const uint32_t op0 = L.init_vec ? L.start_op : 0u;  // past the shared prefix
+    load_chunk(op0 / kChunk);
     cp_async_wait_all();
     __syncthreads();
-    for (uint32_t ch = 0; ch < n_chunks; ch++) {
+    for (uint32_t ch = op0 / kChunk; ch < n_chunks; ch++) {
       if (ch + 1 < n_chunks) load_chunk(ch + 1);
       const Op* ops = OPB + (ch & 1u) * kChunk;
       const uint32_t n_here = min(kChunk, n_ops - ch * kChunk);
-      Op nxt = ops[0];
+      const uint32_t pi0 = ch == op0 / kChunk ? op0 % kChunk : 0u;
+      Op nxt = ops[pi0];
       uint32_t skip = 0;  // payload instructions consumed by a batch
-      for (uint32_t pi = 0; pi < n_here; pi += 1 + skip) {
+      for (uint32_t pi = pi0; pi < n_here; pi += 1 + skip) {
         const Op op = nxt;
         skip = 0;
         if (op.code == OP_BATCH && L.stop_event == 0xffffffffu) skip = op.pa;
@@ -1695,6 +1705,138 @@ cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, bool bk
 
 cudaError_t batched_occupancy(bool fp64, uint32_t W, bool bk, uint32_t threads, size_t smem, int* per_sm) {
   return fp64 ? occ_t<double>(W, bk, threads, smem, per_sm) : occ_t<float>(W, bk, threads, smem, per_sm);
+}
+
+// ---------------------------------------------------------------------------
+// Shared prefix: the frame, array and rotation instructions before the first
+// noise, measurement or record instruction act alike on every shot (the frame
+// stays zero, so every rotation takes its unsigned angle). They run once per
+// call on one vector spread over the whole grid, one launch per instruction,
+// with the executor's own update formulas; the executor then starts every
+// shot from that vector.
+// ---------------------------------------------------------------------------
+template <typename real>
+__global__ void __launch_bounds__(256) prefix_init(typename Cx<real>::T* v) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    v[0].x = (real)1;
+    v[0].y = (real)0;
+  }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) prefix_pass(const Op op, typename Cx<real>::T* v, uint32_t k) {
+  using C = typename Cx<real>::T;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  const real rs = (real)0.70710678118654752440;
+  const uint32_t pa = op.pa;
+  switch (op.code) {
+    case OP_EXPAND_ROT: {
+      const uint32_t n = 1u << k;
+      C ph;
+      ph.x = (real)op.cs * rs;
+      ph.y = (real)op.sn * rs;
+      for (uint32_t j = tid; j < n; j += nt) {
+        const C a = v[j];
+        v[j] = cscale(a, rs);
+        v[j + n] = cmul(a, ph);
+      }
+      break;
+    }
+    case OP_ROT_Z: {
+      C ph;
+      ph.x = (real)op.cs;
+      ph.y = (real)op.sn;
+      for (uint32_t j = tid; j < (1u << (k - 1)); j += nt) {
+        const uint32_t i1 = insert0(j, pa) | (1u << pa);
+        v[i1] = cmul(v[i1], ph);
+      }
+      break;
+    }
+    case OP_ROT_X: {
+      const real cr = (real)op.cs, sr = (real)op.sn;
+      for (uint32_t j = tid; j < (1u << (k - 1)); j += nt) {
+        const uint32_t i0 = insert0(j, pa), i1 = i0 | (1u << pa);
+        const C a = v[i0], b = v[i1];
+        C na, nb;
+        na.x = cr * a.x + sr * b.y;
+        na.y = cr * a.y - sr * b.x;
+        nb.x = sr * a.y + cr * b.x;
+        nb.y = -sr * a.x + cr * b.y;
+        v[i0] = na;
+        v[i1] = nb;
+      }
+      break;
+    }
+    case OP_ARRAY_H:
+      for (uint32_t j = tid; j < (1u << (k - 1)); j += nt) {
+        const uint32_t i0 = insert0(j, pa), i1 = i0 | (1u << pa);
+        const C a = v[i0], b = v[i1];
+        v[i0] = cscale(cadd(a, b), rs);
+        v[i1] = cscale(csub(a, b), rs);
+      }
+      break;
+    case OP_ARRAY_S:
+      for (uint32_t j = tid; j < (1u << (k - 1)); j += nt) {
+        const uint32_t i1 = insert0(j, pa) | (1u << pa);
+        const C a = v[i1];
+        C r;
+        r.x = -a.y;
+        r.y = a.x;
+        v[i1] = r;
+      }
+      break;
+    case OP_ARRAY_CX:
+    case OP_ARRAY_CZ: {
+      const uint32_t pb = op.pb, lo = min(pa, pb), hi = max(pa, pb);
+      for (uint32_t j = tid; j < (1u << (k - 2)); j += nt) {
+        const uint32_t base = insert0(insert0(j, lo), hi);
+        if (op.code == OP_ARRAY_CX) {
+          const uint32_t i0 = base | (1u << pa), i1 = i0 | (1u << pb);
+          const C a = v[i0];
+          v[i0] = v[i1];
+          v[i1] = a;
+        } else {
+          const uint32_t i = base | (1u << pa) | (1u << pb);
+          C a = v[i];
+          a.x = -a.x;
+          a.y = -a.y;
+          v[i] = a;
+        }
+      }
+      break;
+    }
+    default:
+      break;  // frame instructions: the frame stays zero
+  }
+}
+
+// Runs ops [0, p.prefix_end) of the program on vec (2^k_max amplitudes of the
+// given precision); returns the launches made.
+cudaError_t launch_prefix(const Op* host_ops, uint32_t n, bool fp64, void* vec, int n_sm, cudaStream_t st,
+                          uint32_t* launches) {
+  *launches = 0;
+  if (fp64) prefix_init<double><<<1, 32, 0, st>>>(reinterpret_cast<double2*>(vec));
+  else prefix_init<float><<<1, 32, 0, st>>>(reinterpret_cast<float2*>(vec));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  (*launches)++;
+  uint32_t k = 0;
+  for (uint32_t pc = 0; pc < n; pc++) {
+    const Op& o = host_ops[pc];
+    if (o.code < OP_ARRAY_H || o.code > OP_ROT_X) continue;  // frame instructions
+    const uint32_t work = o.code == OP_EXPAND_ROT ? (1u << k)
+                          : (o.code == OP_ARRAY_CX || o.code == OP_ARRAY_CZ) ? (1u << (k - 2)) : (1u << (k - 1));
+    uint32_t grid = (work + 255) / 256;
+    if (grid > 8u * (uint32_t)n_sm) grid = 8u * (uint32_t)n_sm;
+    if (grid < 1) grid = 1;
+    if (fp64) prefix_pass<double><<<grid, 256, 0, st>>>(o, reinterpret_cast<double2*>(vec), k);
+    else prefix_pass<float><<<grid, 256, 0, st>>>(o, reinterpret_cast<float2*>(vec), k);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    (*launches)++;
+    if (o.code == OP_EXPAND_ROT) k++;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st) {

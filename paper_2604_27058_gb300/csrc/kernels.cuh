@@ -103,6 +103,13 @@ struct LaunchParams {
   const uint32_t* aff_items;
   const uint32_t* aff_counts;
   uint32_t aff_cap;
+  // shared prefix (batched executor): every shot starts at instruction
+  // start_op of the list it runs (the fused list's f_start, or prefix_end of
+  // the plain list) with the active vector init_vec (2^start_k amplitudes,
+  // the executor's precision) and a zero frame; null = start at instruction
+  // 0 with phi = [1]
+  const void* init_vec;
+  uint32_t start_op, start_k;
   uint32_t stop_event;                // debug: stop before this event (0xffffffff = never)
   uint64_t dump_shot;                 // debug: call-local shot index
   double* dump_amps;

@@ -132,6 +132,14 @@ struct ProgHeader {
   uint32_t aff_n_chains;           // delta-row chains of two or more rows
   uint32_t aff_n_chain_rows;       // rows on those chains
   uint32_t n_probes;               // expectation-value probes (OP_EXPVAL rows)
+  // shared prefix: ops [0, prefix_end) are frame / array / rotation
+  // instructions only (no noise, measurement or record), so every shot
+  // reaches ops[prefix_end] with the same active vector (prefix_k axes) and
+  // a zero frame
+  uint32_t prefix_end, prefix_k;
+  // the fused list's instruction where the shots resume after the shared
+  // prefix, in logical order with no pending term (fuse.cpp)
+  uint32_t f_start, pad4;
   uint32_t n_fops, n_fterms;       // fused instruction list and its terms (0: none)
   uint32_t n_fperm, f_perm;        // permutation-table words; 1 if the list has OP_PERMF
   uint64_t off_ops, off_masks, off_q, off_seg_start, off_seg_end, off_site_info, off_site_eff,
@@ -200,7 +208,7 @@ constexpr uint32_t kRecPerSite = 15;
 // row): its fault flips the slot and, if the shot is kept, the output bit.
 
 constexpr uint32_t kMagic = 0x4E435047u;  // "NCPG"
-constexpr uint32_t kVersion = 11;
+constexpr uint32_t kVersion = 13;
 constexpr uint32_t kMaxK = 30;
 constexpr uint32_t kMaxQubits = 4096;
 

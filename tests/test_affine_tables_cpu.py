@@ -16,7 +16,7 @@ from oracle.philox import meas_u
 from oracle.records import raw_parities
 from oracle.stabilizer import FrameSim
 
-HEAD = "<17If14I"  # 17 counts, mean_faults, n_blocks, aff_ok, aff_rows, aff_n_rand, aff_n_chunks,
+HEAD = "<17If18I"  # 17 counts, mean_faults, n_blocks, aff_ok, aff_rows, aff_n_rand, aff_n_chunks,
                    # aff_chunks_per_shot (read as u32), n_guide, aff_n_chains, aff_n_chain_rows, pad,
                    # n_fops, n_fterms, n_fperm, f_perm
 HEAD_BYTES = struct.calcsize(HEAD)

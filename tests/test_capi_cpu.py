@@ -152,3 +152,25 @@ def test_array_bytes_match_the_oracle_plan(nc, name):
             "small": gc.random_small(77, n=6, n_ops=100, t_frac=0.3)}[name]
     assert nc.compile(text).info.array_bytes_fp32 == pytest.approx(_plan_array_bytes(FactoredSim(text)), rel=1e-12)
     assert nc.compile(gc.surface_code_memory(d=3, rounds=2)).info.array_bytes_fp32 == 0.0
+
+
+@pytest.mark.parametrize("name", ["dense", "dense_small", "tiny", "surface"])
+def test_shared_prefix_matches_the_oracle_plan(nc, name):
+    """The shared prefix ends at the first noise, measurement or record
+    instruction; its active dimension is the number of expansions the
+    oracle's plan makes before its first such step."""
+    from oracle.factored import FactoredSim
+    text = {"dense": gc.dense_random(), "dense_small": gc.dense_random(seed=33, n=10, layers=12),
+            "tiny": gc.tiny_random(), "surface": gc.surface_code_memory(d=3, rounds=2)}[name]
+    info = nc.compile(text).info
+    sim = FactoredSim(text)
+    k = 0
+    for st in sim.steps:
+        if st.kind == "expand":
+            k += 1
+        elif st.kind not in ("vg", "rot"):
+            break
+    assert info.prefix_k == k
+    assert 0.0 <= info.prefix_bytes_fp32 <= info.array_bytes_fp32
+    if name == "dense":
+        assert info.prefix_k == 20 and info.prefix_bytes_fp32 > 0.99 * info.array_bytes_fp32 - 6e7

@@ -13,7 +13,7 @@ import pytest
 
 from gen import circuits as gc
 
-HEAD = "<17If14I"
+HEAD = "<17If18I"
 HEAD_BYTES = struct.calcsize(HEAD)
 OFF_NAMES = ["ops", "masks", "q", "seg_start", "seg_end", "site_info", "site_eff", "slot_list", "det_ref",
              "obs_ref", "site_opt", "opt_tab", "plist", "orec", "site_blk", "aff_const", "aff_rowev_off",
@@ -146,7 +146,7 @@ def test_fused_list_builds_the_same_vector(nc, seed, n, layers):
     blob = nc.compile(gc.dense_random(seed=seed, n=n, layers=layers)).serialize()
     u = struct.unpack_from(HEAD, blob, 0)
     n_ops = u[4]
-    n_fops, n_fterms, n_fperm = u[28], u[29], u[30]
+    n_fops, n_fterms, n_fperm = u[32], u[33], u[34]
     offs = dict(zip(OFF_NAMES, struct.unpack_from(f"<{len(OFF_NAMES)}Q", blob, HEAD_BYTES)))
     assert n_fops > 0
     ops = _ops(blob, offs["ops"], n_ops)
@@ -172,7 +172,7 @@ def test_dense_workload_passes_shrink(nc):
     u = struct.unpack_from(HEAD, blob, 0)
     offs = dict(zip(OFF_NAMES, struct.unpack_from(f"<{len(OFF_NAMES)}Q", blob, HEAD_BYTES)))
     ops = _ops(blob, offs["ops"], u[4])
-    fops = _ops(blob, offs["fops"], u[28])
+    fops = _ops(blob, offs["fops"], u[32])
     passes = sum(o["code"] in ("ARRAY_H", "ARRAY_S", "ARRAY_CX", "ARRAY_CZ", "ROT_Z", "ROT_X", "EXPAND_ROT")
                  for o in ops)
     fpasses = sum(o["code"] in ("DIAGF", "MIXF", "PERMF", "EXPAND_ROT") for o in fops)

@@ -566,3 +566,34 @@ def test_coherent_surface_code_amplitudes(nc):
                 assert k == len(act), (ev, s, precision)
                 assert (fx, fz) == (ox, oz)
                 assert state_error(amps, phi_ref) <= tol, (ev, s, precision)
+
+
+# ---------------------------------------------------------------------------
+# shared noiseless prefix (computed once per call, then every shot resumes)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp32", "fp64_batched"])
+def test_shared_prefix_equals_per_shot_execution(nc, precision):
+    """A dense circuit whose gates all precede its measurements: with the
+    prefix computed once (px=2) the records equal the oracle's and the
+    per-shot execution (px=0), near-ties aside."""
+    text = gc.dense_random(seed=33, n=10, layers=12)
+    prog = nc.compile(text)
+    assert prog.info.prefix_k == prog.info.k_max >= 8
+    sim = FactoredSim(text)
+    shots = 256
+    shared = gpu_records(prog, shots, 19, precision=precision, tune="px=2")
+    assert shared["raw"]["path"] & 1
+    plain = gpu_records(prog, shots, 19, precision=precision, tune="px=0")
+    assert not plain["raw"]["path"] & 1
+    n_ok, flagged = _check(_factored_run(sim, 19), sim.ref_det, sim.ref_obs, sim.flat, shared, 19, range(shots))
+    assert flagged <= 3 and n_ok + flagged == shots
+    differ = int((shared["meas"] != plain["meas"]).any(axis=0).sum())
+    assert differ <= flagged
+
+
+def test_shared_prefix_k20_mirror_returns_to_zero(nc):
+    """The k = 20 mirror circuit through the shared prefix: every record 0."""
+    prog = nc.compile(gc.dense_random(seed=3, n=20, layers=12, mirror=True))
+    res = nc.sample(prog, 256, 3)
+    assert res["path"] & 1
+    assert int(res["meas"][: prog.info.n_meas].count_nonzero()) == 0

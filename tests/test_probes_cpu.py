@@ -10,7 +10,7 @@ import pytest
 from gen import circuits as gc
 from oracle.factored import FactoredSim
 
-HEAD = "<17If14I"
+HEAD = "<17If18I"
 HEAD_BYTES = struct.calcsize(HEAD)
 OFF_NAMES = ["ops", "masks", "q", "seg_start", "seg_end", "site_info", "site_eff", "slot_list", "det_ref",
              "obs_ref", "site_opt", "opt_tab", "plist", "orec", "site_blk", "aff_const", "aff_rowev_off",

@@ -11,7 +11,7 @@ from gen import circuits as gc
 from oracle.circuit import flatten
 from oracle.strata import build_strata, stratum_valid, stratum_weights
 
-HEAD = "<17If14I"
+HEAD = "<17If18I"
 HEAD_BYTES = struct.calcsize(HEAD)
 OFF_NAMES = ["ops", "masks", "q", "seg_start", "seg_end", "site_info", "site_eff", "slot_list", "det_ref",
              "obs_ref", "site_opt", "opt_tab", "plist", "orec", "site_blk", "aff_const", "aff_rowev_off",
