@@ -370,8 +370,13 @@ def run_ours(args):
     # must write and the active-vector traversals of the instruction list
     # (before fusion), over its own summed launch time
     peaks, peak_src = measured_peaks()
-    # records, plus the active-vector traversals of a program with active axes
-    alg = (record_bytes_per_shot(info) + info.array_bytes_fp32) * shots
+    # records, plus the active-vector traversals of a program with active axes;
+    # with the shared prefix the executor starts every shot from the prefix's
+    # vector (one write of it per shot) and runs only the rest of the list
+    per_shot = record_bytes_per_shot(info) + info.array_bytes_fp32
+    if last.get("path", 0) & 1:
+        per_shot += 8.0 * 2 ** info.prefix_k - info.prefix_bytes_fp32
+    alg = per_shot * shots
     achieved = alg / (exec_ms / 1000.0) / 1e9
     tr = ncu_traffic(wname)
     affine = info.k_max == 0 and "a=0" not in (args.tune or "")
