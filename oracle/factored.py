@@ -433,15 +433,7 @@ class FactoredSim:
                     fx ^= ex
                     fz ^= ez
             elif st.kind == "probe" and trace is not None:
-                val = 0.0
-                if not a["zero"]:
-                    # frame conjugation: sign of the anticommutation with the frame
-                    om = (bin(fx & a["z"]).count("1") + bin(fz & a["x"]).count("1")) & 1
-                    idx = np.arange(len(phi))
-                    sg = 1 - 2 * (np.array([bin(int(i) & a["mz"]).count("1") & 1 for i in idx]))
-                    acc = np.sum(np.conj(phi[idx ^ a["mx"]]) * sg * phi)
-                    val = float(((-1) ** om * (1j ** a["ph"]) * acc).real / np.sum(np.abs(phi) ** 2))
-                trace.setdefault("probe", {})[a["index"]] = val
+                trace.setdefault("probe", {})[a["index"]] = probe_value(a, fx, fz, phi)
             if trace is not None:
                 trace.setdefault("k", []).append(len(act))
                 trace.setdefault("norm", []).append(float(np.sum(np.abs(phi) ** 2)))
@@ -450,6 +442,19 @@ class FactoredSim:
     def sample(self, seed: int, shot: int, postselect: bool = False) -> ShotRecords:
         meas = self.run_raw(seed, shot)[0]
         return assemble(self.flat, meas, self.ref_det, self.ref_obs, postselect)
+
+
+def probe_value(a: dict, fx: int, fz: int, phi: np.ndarray) -> float:
+    """<P> of the factored state for a probe step (image i^ph X^x Z^z, active
+    position masks mx / mz, dormant-x flag zero) under the frame (fx, fz)."""
+    if a["zero"]:
+        return 0.0
+    # frame conjugation: sign of the anticommutation with the frame
+    om = (bin(fx & a["z"]).count("1") + bin(fz & a["x"]).count("1")) & 1
+    idx = np.arange(len(phi))
+    sg = 1 - 2 * (np.array([bin(int(i) & a["mz"]).count("1") & 1 for i in idx]))
+    acc = np.sum(np.conj(phi[idx ^ a["mx"]]) * sg * phi)
+    return float(((-1) ** om * (1j ** a["ph"]) * acc).real / np.sum(np.abs(phi) ** 2))
 
 
 def _frame_conj(name: str, vq: tuple, fx: int, fz: int):

@@ -23,7 +23,7 @@ OFF_NAMES = ["ops", "masks", "q", "seg_start", "seg_end", "site_info", "site_eff
 CODES = ["END", "FRAME_H", "FRAME_S", "FRAME_CX", "FRAME_CZ", "ARRAY_H", "ARRAY_S", "ARRAY_CX", "ARRAY_CZ",
          "EXPAND_ROT", "ROT_Z", "ROT_X", "MEAS_STATIC", "MEAS_RANDOM", "MEAS_ACTIVE_Z", "MEAS_ACTIVE_X",
          "NOISE_BLOCK", "FEEDFORWARD", "REC_OUT", "DETECTOR", "OBS_INCLUDE", "OBS_OUT", "KEPT_OUT", "BATCH",
-         "DIAGF", "MIXF", "PERMF"]
+         "DIAGF", "MIXF", "PERMF", "EXPVAL"]
 RS = 1 / np.sqrt(2)
 
 
@@ -64,10 +64,12 @@ def _phase(p, terms):
     return ph
 
 
-def _run_original(ops):
+def _run_original(ops, probes=None):
     v = np.ones(1, dtype=complex)
     for o in ops:
         c = o["code"]
+        if c == "EXPVAL" and probes is not None:
+            probes.append(v.copy())
         k = int(np.log2(len(v)))
         idx = np.arange(len(v))
         if c == "EXPAND_ROT":
@@ -95,10 +97,12 @@ def _run_original(ops):
     raise AssertionError("no active measurement")
 
 
-def _run_fused(ops, terms, perm):
+def _run_fused(ops, terms, perm, probes=None):
     w = np.ones(1, dtype=complex)
     for o in ops:
         c = o["code"]
+        if c == "EXPVAL" and probes is not None:
+            probes.append(w.copy())
         k = int(np.log2(len(w)))
         if c == "EXPAND_ROT":
             w = np.concatenate([w * RS, w * RS * (o["cs"] + 1j * o["sn"])])
@@ -177,3 +181,29 @@ def test_dense_workload_passes_shrink(nc):
                  for o in ops)
     fpasses = sum(o["code"] in ("DIAGF", "MIXF", "PERMF", "EXPAND_ROT") for o in fops)
     assert fpasses * 5 <= passes, (fpasses, passes)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_fused_list_in_logical_order_at_every_probe(nc, seed):
+    """Probes (OP_EXPVAL) read the vector in logical order: at every probe the
+    fused list's vector equals the original list's."""
+    text = gc.with_probes(gc.dense_random(seed=seed, n=9, layers=10), seed, count=6, max_weight=3)
+    # keep the probes before the final measurements
+    lines = text.splitlines()
+    body = [ln for ln in lines if not ln.startswith("M ")] + [ln for ln in lines if ln.startswith("M ")]
+    blob = nc.compile("\n".join(body)).serialize()
+    u = struct.unpack_from(HEAD, blob, 0)
+    offs = dict(zip(OFF_NAMES, struct.unpack_from(f"<{len(OFF_NAMES)}Q", blob, HEAD_BYTES)))
+    n_fops, n_fterms, n_fperm = u[32], u[33], u[34]
+    assert n_fops > 0
+    ops = _ops(blob, offs["ops"], u[4])
+    fops = _ops(blob, offs["fops"], n_fops)
+    terms = [struct.unpack_from("<4I2d", blob, offs["fterm"] + 32 * i) for i in range(n_fterms)]
+    terms = [(t[0], t[2], t[3], t[4], t[5]) for t in terms]
+    perm = list(struct.unpack_from(f"<{n_fperm}I", blob, offs["fperm"])) if n_fperm else []
+    pa, pb = [], []
+    _run_original(ops, pa)
+    _run_fused(fops, terms, perm, pb)
+    assert len(pa) == len(pb) == 6
+    for a, b in zip(pa, pb):
+        assert np.allclose(a, b, atol=1e-12)

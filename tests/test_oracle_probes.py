@@ -77,3 +77,43 @@ def test_parse_errors():
         with pytest.raises(CircuitError):
             flatten(bad)
     assert flatten("EXPVAL X3*Z1 Y0").n_probes == 2
+
+
+def _planted(kind):
+    import numpy as np
+    from oracle import factored
+
+    def bad(a, fx, fz, phi):
+        if a["zero"]:
+            return 0.0 if kind != "no_zero" else 1.0
+        om = (bin(fx & a["z"]).count("1") + bin(fz & a["x"]).count("1")) & 1
+        if kind == "no_frame_sign":
+            om = 0
+        if kind == "half_frame_sign":
+            om = bin(fx & a["z"]).count("1") & 1
+        idx = np.arange(len(phi))
+        sg = 1 - 2 * (np.array([bin(int(i) & a["mz"]).count("1") & 1 for i in idx]))
+        acc = np.sum(np.conj(phi[idx ^ a["mx"]]) * sg * phi)
+        ph = 1 if kind == "no_phase" else 1j ** a["ph"]
+        return float(((-1) ** om * ph * acc).real / np.sum(np.abs(phi) ** 2))
+    return factored, bad
+
+
+@pytest.mark.parametrize("kind", ["no_frame_sign", "half_frame_sign", "no_phase", "no_zero"])
+def test_planted_mistakes_fail_a_pin(monkeypatch, kind):
+    """A mistake planted in the oracle's probe (on the CPU) fails a pin."""
+    mod, bad = _planted(kind)
+    monkeypatch.setattr(mod, "probe_value", bad)
+    failed = False
+    for fn, args in ((test_closed_forms, None), (test_factored_equals_dense_on_random_noisy_circuits, None)):
+        try:
+            if fn is test_closed_forms:
+                for text, want in [("H 0\nT 0\nEXPVAL X0 Y0 Z0", [math.cos(math.pi / 4), math.sin(math.pi / 4), 0.0]),
+                                   ("H 0\nCX 0 1\nCX 1 2\nEXPVAL X0*X1*X2 Z0*Z1 Z0 Y0*Y1*X2", [1.0, 1.0, 0.0, -1.0])]:
+                    fn(text, want)
+            else:
+                for seed in range(12):
+                    fn(seed)
+        except AssertionError:
+            failed = True
+    assert failed
