@@ -984,9 +984,37 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
       flips.clear();
     };
 
+    // HIR peephole: a Z rotation (T, T_DAG, R_Z) whose qubit's next
+    // instruction, other Z rotations aside, is a Z measurement or reset, or
+    // an R_X followed likewise by MX, only multiplies each outcome branch by
+    // a phase (the instructions in between act on other qubits and commute
+    // with it): it is dropped, with no change to any probability or state.
+    std::vector<char> dropped(fl.ops.size(), 0);
+    {
+      auto touches = [](const PhysOp& o, int q) {
+        if (o.kind == K_PROBE) return std::find(o.recs.begin(), o.recs.end(), (int64_t)q) != o.recs.end();
+        return o.q0 == q || o.q1 == q;
+      };
+      auto z_rot = [](const PhysOp& o) { return o.name == "T" || o.name == "T_DAG" || o.name == "R_Z"; };
+      for (size_t i = 0; i < fl.ops.size(); i++) {
+        const PhysOp& r = fl.ops[i];
+        if (r.kind != K_ROT || (!z_rot(r) && r.name != "R_X")) continue;
+        const bool z = z_rot(r);
+        for (size_t j = i + 1; j < fl.ops.size(); j++) {
+          const PhysOp& o = fl.ops[j];
+          if (o.kind == K_DET || o.kind == K_OBS || !touches(o, r.q0)) continue;
+          if (o.kind == K_ROT && (z ? z_rot(o) : o.name == "R_X")) continue;  // commutes with r
+          if (o.kind == K_MEAS && (z ? (o.name == "M" || o.name == "MR" || o.name == "R") : o.name == "MX"))
+            dropped[i] = 1;
+          break;
+        }
+      }
+    }
+
     int64_t kept_id = -1;
     std::vector<int64_t> obs_id(fl.n_obs, -1);
-    for (auto& po : fl.ops) {
+    for (size_t pi = 0; pi < fl.ops.size(); pi++) {
+      const PhysOp& po = fl.ops[pi];
       if (!(po.kind == K_MEAS && po.instr == cur_instr)) flush_flips_fast();
       cur_instr = po.kind == K_MEAS ? po.instr : -2;
       switch (po.kind) {
@@ -994,7 +1022,7 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
           c.physical_gate(po.name, po.q0, po.q1);
           break;
         case K_ROT:
-          c.rotation(po);
+          if (!dropped[pi]) c.rotation(po);
           break;
         case K_MEAS:
           c.measure(po, flips);

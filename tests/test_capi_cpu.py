@@ -50,7 +50,7 @@ def test_status_strings(nc):
     ("dense", gc.dense_random(), 20),
     ("lowmagic", gc.low_magic_gadgets(), 10),
     ("coherent_d3_r3", gc.surface_code_memory(d=3, rounds=3, p=1e-3, theta=0.02), 8),
-    ("coherent_d5_r1", gc.surface_code_memory(d=5, rounds=1, p=1e-3, theta=0.02), 24),
+    ("coherent_d5_r1", gc.surface_code_memory(d=5, rounds=1, p=1e-3, theta=0.02), 12),
 ])
 def test_compile_matches_oracle_schedule(nc, name, text, kmax):
     from oracle.circuit import flatten
@@ -105,7 +105,7 @@ def test_compile_errors(nc, text, code):
 
 
 def test_kmax_limit(nc):
-    text = "".join(f"H {q}\nT {q}\n" for q in range(31)) + "M 0\n"
+    text = "".join(f"H {q}\nT {q}\n" for q in range(31)) + "H 0\nM 0\n"
     with pytest.raises(nc.NcError) as e:
         nc.compile(text)
     assert e.value.name == "NC_E_KMAX"
