@@ -457,14 +457,16 @@ def _touches(op, q: int) -> bool:
 
 
 def measured_rotations(ops) -> set:
-    """Rotations that only a global phase can tell apart from the identity
-    (an HIR peephole in the spirit of Sec. 3.1's optimisation passes): a Z
-    rotation (T, T_DAG, R_Z) on q whose next instruction touching q, other
-    Z rotations aside, is a Z measurement or reset of q (M, MR, R), or an
-    R_X on q followed likewise by MX. Instructions on other qubits commute
-    with it, and exp(-i t Z) before a Z measurement multiplies each outcome
-    branch by a phase, so probabilities, outcomes and every later state are
-    unchanged. Returns the indices of those rotations in ``ops``."""
+    """Rotations that only a global phase can tell apart from the identity:
+    the special case of Sec. 3.1's HIR reordering (non-Cliffords pushed past
+    the measurements they commute with) in which the rotation, once past its
+    qubit's next measurement, acts on an eigenstate. A Z rotation (T, T_DAG,
+    R_Z) on q whose next instruction touching q, other Z rotations aside, is
+    a Z measurement or reset of q (M, MR, R), or an R_X on q followed likewise
+    by MX. Instructions on other qubits commute with it, and exp(-i t Z)
+    before a Z measurement multiplies each outcome branch by a phase, so
+    probabilities, outcomes and every later state are unchanged. Returns the
+    indices of those rotations in ``ops``."""
     out = set()
     for i, op in enumerate(ops):
         if op.kind != "gate" or len(op.qubits) != 1 or op.name not in _Z_ROT + ("R_X",):

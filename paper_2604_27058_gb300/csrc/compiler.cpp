@@ -984,7 +984,9 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
       flips.clear();
     };
 
-    // HIR peephole: a Z rotation (T, T_DAG, R_Z) whose qubit's next
+    // HIR peephole (the special case of Sec. 3.1's stage-2 reordering in
+    // which a rotation pushed past its qubit's next measurement acts on an
+    // eigenstate): a Z rotation (T, T_DAG, R_Z) whose qubit's next
     // instruction, other Z rotations aside, is a Z measurement or reset, or
     // an R_X followed likewise by MX, only multiplies each outcome branch by
     // a phase (the instructions in between act on other qubits and commute
