@@ -86,7 +86,19 @@ typedef struct {
   uint32_t outputs;       /* NC_OUT_* bits */
   int postselect;         /* NC_PS_NONE or NC_PS_ALL_DETECTORS */
   uint64_t shot_offset;   /* global index of this call's first shot */
-  const char* tune;       /* NULL = built-in heuristic; "w=<1|2|4>,g=<words>" */
+  const char* tune;       /* NULL = the shape nc_autotune chose, else the
+                             built-in heuristic. Otherwise comma-separated
+                             key=value pairs: g (32-shot words per executor
+                             tile), t (threads per CTA), w (words per owner
+                             thread: 1, 2, 4), b (0: no bucketed noise),
+                             ps (1: pre-sample faults even for small calls),
+                             sw (0: active vectors never in shared memory),
+                             px (shared prefix: 0 off, 2 always), a (0: no
+                             record-level path for k_max = 0), aw (its words
+                             per tile: 8, 16, 32), ai (0: faults sampled in
+                             the tile kernel), av (shots per item pass), ac
+                             (item-list capacity per tile), ao (1: item
+                             passes overlapped on a side stream) */
   int noiseless;          /* 1 = disable every noise site (reference runs) */
   uint32_t stratified;    /* 0 = independent noise sites (default);
                              1 = stratified importance sampling: every shot
