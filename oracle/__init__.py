@@ -34,6 +34,8 @@ distribution;
 O-D == O-B and O-A == O-B record-for-record (and P(m=1) to 1e-12) on random
 small circuits; O-A == O-D on the d=5 surface-code memory; mirror circuits.
 
-Parity unpinned: O-A's amplitudes at active dimension k > 14 (the dense
-oracle cannot reach them; only invariants and mirror circuits pin them).
+Parity unpinned: O-A's amplitudes at active dimension k > 14 in general (the
+dense oracle cannot reach them). What pins them there: invariants, mirror
+circuits, and closed-form measurement probabilities along a k = 16 / 18
+cascade on a product of entangled two-qubit blocks.
 """

@@ -264,3 +264,36 @@ def test_factored_state_matches_dense_expansion(seed):
         ef = _pauli_expectations_factored(f, fx, fz, phi, act, n)
         for w in ed:
             assert abs(ed[w] - ef[w]) < 1e-10, (w, ed[w], ef[w])
+
+
+def _pair_probabilities(order_x=True):
+    """Exact P(m = 1) of MX on qubit a, then on b given a's outcome, for the
+    two-qubit block CZ (T|+>)^2, by brute force on its 4 amplitudes."""
+    w = np.exp(1j * math.pi / 4)
+    v = np.array([1, w, w, -w * w], dtype=complex) / 2  # index 2 * bit_a + bit_b
+    h = np.array([[1, 1], [1, -1]]) / math.sqrt(2)
+    vx = np.kron(h, h) @ v  # X basis of both qubits
+    pa = abs(vx[2]) ** 2 + abs(vx[3]) ** 2
+    pb = {0: abs(vx[1]) ** 2 / (abs(vx[0]) ** 2 + abs(vx[1]) ** 2),
+          1: abs(vx[3]) ** 2 / (abs(vx[2]) ** 2 + abs(vx[3]) ** 2)}
+    return pa, pb
+
+
+@pytest.mark.parametrize("n", [16, 18])
+def test_large_k_probabilities_closed_form(n):
+    """Active dimension above the dense oracle's reach: H and T on n qubits
+    (k = n), CZ on disjoint pairs, then MX on every qubit. The state is a
+    product of identical two-qubit blocks, so every measurement probability
+    along the cascade (k = n down to 1) is fixed by the block alone."""
+    text = "".join(f"H {q}\nT {q}\n" for q in range(n))
+    text += "".join(f"CZ {q} {q + 1}\n" for q in range(0, n, 2))
+    text += "MX " + " ".join(map(str, range(n))) + "\n"
+    sim = FactoredSim(text, k_limit=n)
+    assert sim.k_max == n
+    pa, pb = _pair_probabilities()
+    for shot in range(3):
+        tr = {}
+        meas = sim.run_raw(5, shot, trace=tr)[0]
+        for q in range(0, n, 2):
+            assert tr["p1"][q] == pytest.approx(pa, abs=1e-12)
+            assert tr["p1"][q + 1] == pytest.approx(pb[meas[q]], abs=1e-12)
