@@ -99,3 +99,19 @@ def test_stratified_fault_sets_through_the_noise_tables(nc):
         want = assemble(sim.flat, sim.run_raw(9, s, faults=f)[0], sim.ref_det, sim.ref_obs, False)
         got = emu.run(9, s, faults=f)
         assert (got["meas"], got["det"], got["obs"]) == (want.meas, want.det, want.obs), s
+
+
+def test_sweep_mirror_circuits(nc):
+    """Two of the sweep's mirror circuits with the most T gates (k_max up to
+    14): every shot's records equal the oracle's."""
+    circs = [gc.sweep_mirror(i) for i in range(64)]
+    picks = sorted(range(64), key=lambda i: (-circs[i].t, circs[i].n * circs[i].depth))[:2]
+    for i in picks:
+        assert _check(nc, circs[i].text, 4, 5005 + i) >= 3
+
+
+def test_coherent_d5_one_round(nc):
+    """k_max = 12 after the HIR peephole (24 without it)."""
+    text = gc.surface_code_memory(d=5, rounds=1, p=1e-3, theta=0.02)
+    assert nc.compile(text).info.k_max == 12
+    assert _check(nc, text, 6, 31) >= 5
