@@ -149,6 +149,23 @@ typedef struct {
  * message is written to err (if err_len > 0). The text is not retained. */
 nc_status nc_compile(const char* text, size_t len, nc_program** out, char* err, size_t err_len);
 
+/* Compile flags. The compiler's HIR passes (Sec. 3.1, stage 2) change the
+ * bytecode, the k-schedule and the intermediate states, never a probability
+ * or a record; each flag turns one pass off, so that a program can be
+ * compared step by step with a plain run of the method (App. B).
+ *   NC_COMPILE_NO_PEEPHOLE: keep every rotation. By default a Z rotation
+ *     (T, T_DAG, R_Z) whose qubit's next instruction, other Z rotations
+ *     aside, is a Z measurement or reset (or an R_X followed likewise by MX)
+ *     is dropped: pushed past that measurement it acts on an eigenstate and
+ *     contributes a phase per outcome branch only. */
+#define NC_COMPILE_NO_PEEPHOLE 1u
+#define NC_COMPILE_FLAGS_ALL 1u
+
+/* nc_compile with compile flags (NC_COMPILE_* bits; nc_compile passes 0).
+ * An unknown flag bit is NC_E_ARG. */
+nc_status nc_compile_ex(const char* text, size_t len, uint32_t flags, nc_program** out, char* err,
+                        size_t err_len);
+
 /* Fill *info for a compiled program. */
 nc_status nc_program_info(const nc_program* prog, nc_info* info);
 
@@ -250,7 +267,15 @@ nc_status nc_autotune(nc_program* prog, uint64_t shots, const nc_sample_opts* op
  *   - opts->precision must be NC_FP32_BATCHED (else NC_E_ARG); opts->tune is
  *     ignored.
  *   - NC_E_ARG if the program blob plus its workspace cannot fit in
- *     NC_NOALLOC_SCRATCH_BYTES (large k_max or very long programs).
+ *     NC_NOALLOC_SCRATCH_BYTES (large k_max or very long programs). The
+ *     64-shot reference launch runs with FP64 amplitudes, as nc_sample's
+ *     does, and needs twice the FP32 workspace of one tile.
+ *   - NC_E_UNSUPPORTED if one 32-shot tile's frame planes and record slots
+ *     exceed the shared memory of a CTA (tens of thousands of qubits).
+ *   - Launch shapes come from a fixed table by k_max, and the speed-ups of
+ *     nc_sample that need allocations (vectors in shared memory, the shared
+ *     noiseless prefix, pre-sampled noise) are not used: records equal
+ *     nc_sample's, speed can differ.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
  *   - Every call reuses the same array and leaves the last call's contents in
@@ -272,7 +297,10 @@ const char* nc_status_str(nc_status st);
  * measurement event `event` and return its frame and active state vector.
  * frame_xz: 2 * ceil(n_qubits / 32) words (x bits of virtual qubits, then z
  * bits); amps: at least 2 * 2^k_max doubles (re, im interleaved), converted
- * to FP64; *k: active dimension at that point. Host pointers. */
+ * to FP64; *k: active dimension at that point. Host pointers. A program
+ * whose noiseless prefix (nc_info.prefix_ops) ends with 15 or more active
+ * axes starts from that prefix's state computed once, as sampling calls do;
+ * otherwise the shot runs the instruction list from the start. */
 nc_status nc_debug_dump(const nc_program* prog, uint64_t seed, uint64_t shot, uint32_t event,
                         int precision, uint32_t* frame_xz, double* amps, uint32_t* k,
                         void* cuda_stream);

@@ -253,7 +253,6 @@ class FactoredSim:
 
     def _plan(self):
         n = self.n
-        dropped = measured_rotations(self.flat.ops)
         self.img = {}
         for q in range(n):
             self.img[("X", q)] = (1 << q, 0, 0)
@@ -263,8 +262,6 @@ class FactoredSim:
         for i, op in enumerate(self.flat.ops):
             if op.kind == "gate" and op.name not in ("T", "T_DAG", "R_Z", "R_X", "R_Y"):
                 self._physical_gate(op.name, op.qubits)
-            elif op.kind == "gate" and i in dropped:
-                continue  # diagonal in the basis of the next measurement of its qubit
             elif op.kind == "gate":
                 q = op.qubits[0]
                 if op.name in ROT_GEN:
@@ -445,43 +442,6 @@ class FactoredSim:
     def sample(self, seed: int, shot: int, postselect: bool = False) -> ShotRecords:
         meas = self.run_raw(seed, shot)[0]
         return assemble(self.flat, meas, self.ref_det, self.ref_obs, postselect)
-
-
-_Z_ROT = ("T", "T_DAG", "R_Z")
-
-
-def _touches(op, q: int) -> bool:
-    if op.kind == "probe":
-        return any(qq == q for qq, _ in op.paulis)
-    return q in op.qubits
-
-
-def measured_rotations(ops) -> set:
-    """Rotations that only a global phase can tell apart from the identity:
-    the special case of Sec. 3.1's HIR reordering (non-Cliffords pushed past
-    the measurements they commute with) in which the rotation, once past its
-    qubit's next measurement, acts on an eigenstate. A Z rotation (T, T_DAG,
-    R_Z) on q whose next instruction touching q, other Z rotations aside, is
-    a Z measurement or reset of q (M, MR, R), or an R_X on q followed likewise
-    by MX. Instructions on other qubits commute with it, and exp(-i t Z)
-    before a Z measurement multiplies each outcome branch by a phase, so
-    probabilities, outcomes and every later state are unchanged. Returns the
-    indices of those rotations in ``ops``."""
-    out = set()
-    for i, op in enumerate(ops):
-        if op.kind != "gate" or len(op.qubits) != 1 or op.name not in _Z_ROT + ("R_X",):
-            continue
-        z = op.name in _Z_ROT
-        q = op.qubits[0]
-        for o in ops[i + 1:]:
-            if o.kind in ("det", "obs") or not _touches(o, q):
-                continue
-            if o.kind == "gate" and (o.name in _Z_ROT if z else o.name == "R_X"):
-                continue  # commutes with this rotation
-            if o.kind == "meas" and (o.name in ("M", "MR", "R") if z else o.name == "MX"):
-                out.add(i)
-            break
-    return out
 
 
 def probe_value(a: dict, fx: int, fz: int, phi: np.ndarray) -> float:

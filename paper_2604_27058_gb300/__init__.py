@@ -68,11 +68,15 @@ class Program:
             self._h = None
 
 
-def compile(text: str) -> Program:  # noqa: A001 - mirrors nc_compile
+def compile(text: str, peephole: bool = True) -> Program:  # noqa: A001 - mirrors nc_compile
+    """nc_compile_ex; peephole=False sets NC_COMPILE_NO_PEEPHOLE (every
+    rotation kept, so the k-schedule and intermediate states are those of the
+    plain method)."""
     data = text.encode()
     h = ctypes.c_void_p()
     err = ctypes.create_string_buffer(512)
-    code = _nc.lib().nc_compile(data, len(data), ctypes.byref(h), err, 512)
+    flags = 0 if peephole else _nc.NC_COMPILE_NO_PEEPHOLE
+    code = _nc.lib().nc_compile_ex(data, len(data), flags, ctypes.byref(h), err, 512)
     _nc.check(code, err.value.decode(errors="replace"))
     return Program(h.value)
 

@@ -25,6 +25,7 @@ NC_OUT_HOST = 16
 NC_OUT_EXPVAL = 32
 NC_NOALLOC_SCRATCH_BYTES = 64 << 20
 NC_OUT_ALL = NC_OUT_MEAS | NC_OUT_DET | NC_OUT_OBS | NC_OUT_KEPT | NC_OUT_EXPVAL
+NC_COMPILE_NO_PEEPHOLE = 1
 NC_PS_NONE = 0
 NC_PS_ALL_DETECTORS = 1
 
@@ -32,7 +33,7 @@ STATUS = {0: "NC_OK", 1: "NC_E_PARSE", 2: "NC_E_UNSUPPORTED", 3: "NC_E_KMAX",
           4: "NC_E_NONDET_DETECTOR", 5: "NC_E_ARG", 6: "NC_E_OOM", 7: "NC_E_CUDA",
           8: "NC_E_TIMEOUT", 9: "NC_E_INTERNAL"}
 
-EXPORTS = ["nc_compile", "nc_program_info", "nc_program_serialize", "nc_program_deserialize",
+EXPORTS = ["nc_compile", "nc_compile_ex", "nc_program_info", "nc_program_serialize", "nc_program_deserialize",
            "nc_sample", "nc_sample_batch", "nc_program_free", "nc_status_str", "nc_debug_dump",
            "nc_abi_version", "nc_sample_noalloc", "nc_program_prepare", "nc_sample_batch_async",
            "nc_autotune", "nc_stratum_weights", "nc_strata_prepare"]
@@ -82,6 +83,7 @@ def lib() -> ctypes.CDLL:
     L = ctypes.CDLL(LIB_PATH)
     vp, sz, u32, u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint64
     L.nc_compile.argtypes = [ctypes.c_char_p, sz, ctypes.POINTER(vp), ctypes.c_char_p, sz]
+    L.nc_compile_ex.argtypes = [ctypes.c_char_p, sz, u32, ctypes.POINTER(vp), ctypes.c_char_p, sz]
     L.nc_program_info.argtypes = [vp, ctypes.POINTER(Info)]
     L.nc_program_serialize.argtypes = [vp, vp, ctypes.POINTER(sz)]
     L.nc_program_deserialize.argtypes = [vp, sz, ctypes.POINTER(vp)]
@@ -104,7 +106,7 @@ def lib() -> ctypes.CDLL:
     L.nc_strata_prepare.argtypes = [vp, u32, vp]
     L.nc_abi_version.argtypes = []
     L.nc_abi_version.restype = u32
-    for name in ("nc_compile", "nc_program_info", "nc_program_serialize", "nc_program_deserialize",
+    for name in ("nc_compile", "nc_compile_ex", "nc_program_info", "nc_program_serialize", "nc_program_deserialize",
                  "nc_sample", "nc_sample_batch", "nc_debug_dump", "nc_program_prepare", "nc_sample_batch_async",
                  "nc_autotune", "nc_stratum_weights", "nc_strata_prepare"):
         getattr(L, name).restype = ctypes.c_int

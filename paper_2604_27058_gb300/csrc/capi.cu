@@ -657,8 +657,9 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
     }
     if (strat && !bk && !L.flist) return NC_E_OOM;  // stratified shots need their fault lists
     // the shared prefix (program.h prefix_end) once for the whole call, when
-    // its traffic over all shots outweighs one launch per instruction
-    if (h.prefix_end > 0 && h.prefix_k > 0 && tu.PX && stop_event == 0xffffffffu) {
+    // its traffic over all shots outweighs one launch per instruction; a
+    // debug stop (the unfused list, from prefix_end) takes it only when forced
+    if (h.prefix_end > 0 && h.prefix_k > 0 && tu.PX && (stop_event == 0xffffffffu || tu.PX == 2)) {
       const double saved = (double)prog->cp.counts.prefix_bytes * (fp64 ? 2.0 : 1.0) * (double)shots;
       if (tu.PX == 2 || (h.prefix_k >= 6 && saved > 64.0 * 1024 * 1024)) {
         void* vec = nullptr;
@@ -667,7 +668,8 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
         NC_TRY(launch_prefix(reinterpret_cast<const Op*>(prog->cp.blob.data() + h.off_ops), h.prefix_end, fp64, vec,
                              n_sm, stream, &nl));
         L.init_vec = vec;
-        L.start_op = h.n_fops ? h.f_start : h.prefix_end;  // the executor runs the fused list when there is one
+        // the executor runs the fused list when there is one, except at a debug stop
+        L.start_op = h.n_fops && stop_event == 0xffffffffu ? h.f_start : h.prefix_end;
         L.start_k = h.prefix_k;
         if (tm) {
           tm->launches += nl;
@@ -934,12 +936,17 @@ done:
 extern "C" {
 
 nc_status nc_compile(const char* text, size_t len, nc_program** out, char* err, size_t err_len) {
+  return nc_compile_ex(text, len, 0u, out, err, err_len);
+}
+
+nc_status nc_compile_ex(const char* text, size_t len, uint32_t flags, nc_program** out, char* err,
+                        size_t err_len) {
   if (out) *out = nullptr;
-  if (!text || !out) return NC_E_ARG;
+  if (!text || !out || (flags & ~(uint32_t)NC_COMPILE_FLAGS_ALL)) return NC_E_ARG;
   nc_program* p = new (std::nothrow) nc_program();
   if (!p) return NC_E_OOM;
   std::string msg;
-  int rc = compile_program(std::string(text, len), p->cp, msg);
+  int rc = compile_program(std::string(text, len), flags, p->cp, msg);
   if (rc != 0) {
     if (err && err_len) snprintf(err, err_len, "%s", msg.c_str());
     delete p;
@@ -1231,8 +1238,10 @@ nc_status nc_debug_dump(const nc_program* prog, uint64_t seed, uint64_t shot, ui
     NC_TRY(cudaMemsetAsync(cnt, 0, 8, stream));
     {
       CallOut o{nullptr, nullptr, nullptr, nullptr};
+      // vectors of 2^15 amplitudes and more live in HBM: their noiseless
+      // prefix is computed once (as a sampling call does), not per shot
       char tune[32];
-      snprintf(tune, sizeof(tune), "g=4,t=%u", h.k_max > 10 ? 512u : 128u);
+      snprintf(tune, sizeof(tune), "g=4,t=%u,px=%u", h.k_max > 10 ? 512u : 128u, h.prefix_k >= 15 ? 2u : 0u);
       st = enqueue(prog, *dc, 128, seed, base, precision, 0, tune, o, (unsigned long long*)cnt, (uint32_t*)err,
                    scratch, stream, event, shot - base, (double*)d_amps, (uint32_t*)d_frame, (uint32_t*)d_k);
       if (st != NC_OK) goto done;

@@ -948,7 +948,7 @@ std::vector<uint32_t> mask_planes(const std::vector<uint32_t>& masks, uint32_t o
 // ---------------------------------------------------------------------------
 // Entry point
 // ---------------------------------------------------------------------------
-int compile_program(const std::string& text, CompiledProgram& out, std::string& err) {
+int compile_program(const std::string& text, uint32_t flags, CompiledProgram& out, std::string& err) {
   try {
     std::vector<std::string> lines;
     {
@@ -992,7 +992,7 @@ int compile_program(const std::string& text, CompiledProgram& out, std::string& 
     // a phase (the instructions in between act on other qubits and commute
     // with it): it is dropped, with no change to any probability or state.
     std::vector<char> dropped(fl.ops.size(), 0);
-    {
+    if (!(flags & kNoPeephole)) {
       auto touches = [](const PhysOp& o, int q) {
         if (o.kind == K_PROBE) return std::find(o.recs.begin(), o.recs.end(), (int64_t)q) != o.recs.end();
         return o.q0 == q || o.q1 == q;

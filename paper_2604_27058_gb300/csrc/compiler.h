@@ -25,8 +25,11 @@ struct CompiledProgram {
   nc_info_counts counts;
 };
 
+// Compile flags (the NC_COMPILE_* bits of nc.h): each turns one HIR pass off.
+constexpr uint32_t kNoPeephole = 1u;  // keep rotations diagonal in their qubit's next measurement basis
+
 // Returns 0 on success or an nc_status code with a message in err.
-int compile_program(const std::string& text, CompiledProgram& out, std::string& err);
+int compile_program(const std::string& text, uint32_t flags, CompiledProgram& out, std::string& err);
 
 // Appends the record-level propagation tables (program.h) to a blob of a
 // program with k_max = 0 (affine.cpp).

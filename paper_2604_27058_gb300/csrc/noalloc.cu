@@ -119,8 +119,11 @@ DevProg view(const ProgHeader& h, const uint8_t* base) {
   return d;
 }
 
-// Launch shape by peak active dimension (same table as the default of
-// nc_sample's FP32 batched form).
+// Launch shape by peak active dimension. This is a fixed table of its own,
+// not nc_sample's tuned choice: its tiles are smaller for small k_max, and
+// the speed-ups of nc_sample that need allocations (active vectors in shared
+// memory, the shared noiseless prefix, pre-sampled noise) are not used. The
+// records do not depend on the launch shape.
 void shape(uint32_t k_max, uint32_t* G, uint32_t* T) {
   if (k_max == 0) { *G = 128; *T = 128; }
   else if (k_max <= 6) { *G = 32; *T = 256; }
@@ -129,9 +132,10 @@ void shape(uint32_t k_max, uint32_t* G, uint32_t* T) {
   else { *G = 1; *T = 1024; }
 }
 
-// One executor launch whose amplitude workspace starts at `work` and may use
+// One executor launch (FP32 amplitudes, or FP64 for the reference launches
+// as in nc_sample) whose amplitude workspace starts at `work` and may use
 // `work_bytes`.
-nc_status launch(const DevProg& d, uint64_t shots, uint64_t seed, uint64_t shot_offset, uint32_t flags,
+nc_status launch(const DevProg& d, bool fp64, uint64_t shots, uint64_t seed, uint64_t shot_offset, uint32_t flags,
                  uint32_t* meas, uint32_t* det, uint32_t* obs, uint32_t* kept, unsigned long long* kept_count,
                  uint32_t* err, uint8_t* work, uint64_t work_bytes, cudaStream_t stream) {
   LaunchParams L;
@@ -152,6 +156,7 @@ nc_status launch(const DevProg& d, uint64_t shots, uint64_t seed, uint64_t shot_
   uint32_t G, T;
   shape(d.k_max, &G, &T);
   while (G > 1 && batched_smem_bytes(d, G, 1, false) > 220 * 1024) G >>= 1;
+  if (batched_smem_bytes(d, G, 1, false) > 220 * 1024) return NC_E_UNSUPPORTED;  // frame planes too large
   if (T < G) T = G;
   L.G = G;
   L.n_tiles = (uint32_t)((L.row_words32 + G - 1) / G);
@@ -159,19 +164,19 @@ nc_status launch(const DevProg& d, uint64_t shots, uint64_t seed, uint64_t shot_
   int per_sm = 0, n_sm = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return NC_E_CUDA;
   if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return NC_E_CUDA;
-  if (batched_occupancy(false, 1, false, T, smem, &per_sm) != cudaSuccess) return NC_E_CUDA;
+  if (batched_occupancy(fp64, 1, false, T, smem, &per_sm) != cudaSuccess) return NC_E_CUDA;
   if (per_sm < 1) return NC_E_UNSUPPORTED;
   uint64_t grid = std::min<uint64_t>(L.n_tiles, (uint64_t)per_sm * n_sm);
   if (d.k_max > 0) {
     L.work_stride = ((uint64_t)1 << d.k_max) * 32ull * G;
-    const uint64_t per_cta = L.work_stride * sizeof(float) * 2 * (d.n_fops && d.f_perm ? 2 : 1);
+    const uint64_t per_cta = L.work_stride * (fp64 ? sizeof(double) : sizeof(float)) * 2 * (d.n_fops && d.f_perm ? 2 : 1);
     const uint64_t fit = work_bytes / per_cta;
     if (fit == 0) return NC_E_ARG;  // one tile's amplitudes exceed the fixed scratch
     grid = std::min<uint64_t>(grid, fit);
     L.work = work;
   }
   if (grid == 0) return NC_OK;
-  if (launch_batched(L, false, 1, false, (uint32_t)grid, T, smem, stream) != cudaSuccess) return NC_E_CUDA;
+  if (launch_batched(L, fp64, 1, false, (uint32_t)grid, T, smem, stream) != cudaSuccess) return NC_E_CUDA;
   return NC_OK;
 }
 
@@ -219,14 +224,17 @@ extern "C" nc_status nc_sample_noalloc(const nc_program* prog, uint64_t shots, u
 
   if (cudaMemcpyAsync(dblob, blob.data(), blob.size(), cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return NC_E_CUDA;
+  // kept counter and error word; the error word is cleared once here and
+  // read after the last launch, so it reports every launch of the call
+  if (cudaMemsetAsync(cnt, 0, 16, stream) != cudaSuccess) return NC_E_CUDA;
   // reference parities of detectors / observables (64 noiseless shots)
   if (h.n_det + h.n_obs) {
     uint32_t* rdet = (uint32_t*)(base + off_ref);
     uint32_t* robs = rdet + 2 * h.n_det;
-    if (cudaMemsetAsync(cnt, 0, 16, stream) != cudaSuccess) return NC_E_CUDA;
     // the reference trajectory: every measurement takes its more likely
-    // outcome (0 on a tie), so all 64 shots agree
-    st = launch(d, 64, 0, 0, LF_NOISELESS | LF_REFERENCE | LF_ARGMAX | LF_OUT_DET | LF_OUT_OBS, nullptr, rdet,
+    // outcome (0 on a tie), so all 64 shots agree; FP64 amplitudes, as in
+    // nc_sample, so that a near-even choice is taken the same way
+    st = launch(d, true, 64, 0, 0, LF_NOISELESS | LF_REFERENCE | LF_ARGMAX | LF_OUT_DET | LF_OUT_OBS, nullptr, rdet,
                 robs, nullptr, cnt, err, base + off_work, work_bytes, stream);
     if (st != NC_OK) return st;
     // rows are read back and checked in fixed stack chunks (no host heap use)
@@ -257,7 +265,7 @@ extern "C" nc_status nc_sample_noalloc(const nc_program* prog, uint64_t shots, u
     }
     // 64 sampled noiseless shots: a detector that differs from its
     // reference in more than a quarter of them is not deterministic
-    st = launch(d, 64, 0, 0, LF_NOISELESS | LF_REFERENCE | LF_OUT_DET | LF_OUT_OBS, nullptr, rdet, robs, nullptr,
+    st = launch(d, true, 64, 0, 0, LF_NOISELESS | LF_REFERENCE | LF_OUT_DET | LF_OUT_OBS, nullptr, rdet, robs, nullptr,
                 cnt, err, base + off_work, work_bytes, stream);
     if (st != NC_OK) return st;
     for (uint32_t r0 = 0; r0 < n_rows; r0 += kRows) {
@@ -281,7 +289,7 @@ extern "C" nc_status nc_sample_noalloc(const nc_program* prog, uint64_t shots, u
                          reinterpret_cast<const uint32_t*>(dblob + h.off_obs_ref), stream) != cudaSuccess)
       return NC_E_CUDA;
   }
-  if (cudaMemsetAsync(cnt, 0, 16, stream) != cudaSuccess) return NC_E_CUDA;
+  if (cudaMemsetAsync(cnt, 0, 8, stream) != cudaSuccess) return NC_E_CUDA;  // the counter only
   uint32_t flags = 0;
   if (o.outputs & NC_OUT_MEAS) flags |= LF_OUT_MEAS;
   if (o.outputs & NC_OUT_DET) flags |= LF_OUT_DET;
@@ -290,7 +298,7 @@ extern "C" nc_status nc_sample_noalloc(const nc_program* prog, uint64_t shots, u
   if (o.postselect == NC_PS_ALL_DETECTORS) flags |= LF_POSTSELECT;
   if (o.noiseless) flags |= LF_NOISELESS;
   if (shots) {
-    st = launch(d, shots, seed, o.shot_offset, flags, (uint32_t*)out->meas, (uint32_t*)out->det,
+    st = launch(d, false, shots, seed, o.shot_offset, flags, (uint32_t*)out->meas, (uint32_t*)out->det,
                 (uint32_t*)out->obs, (uint32_t*)out->kept, cnt, err, base + off_work, work_bytes, stream);
     if (st != NC_OK) return st;
   }

@@ -81,3 +81,106 @@ def state_error(phi_gpu: np.ndarray, phi_ref: np.ndarray) -> float:
     ov = np.vdot(phi_ref, phi_gpu)
     ph = ov / abs(ov) if abs(ov) > 0 else 1.0
     return float(np.linalg.norm(phi_gpu - ph * phi_ref) / np.linalg.norm(phi_ref))
+
+
+# ---------------------------------------------------------------------------
+# Slow oracle jobs in parallel (k = 20 workloads: tens of seconds per shot).
+# The pool uses "spawn" so that no worker is forked from a process holding a
+# CUDA context; start it before the first GPU call of the test.
+# ---------------------------------------------------------------------------
+_SIMS: dict = {}
+
+
+def _oracle_job(args):
+    text, k_limit, kind, seed, shot, stop_event = args
+    from oracle.factored import FactoredSim
+    sim = _SIMS.get(text)
+    if sim is None:
+        sim = _SIMS[text] = FactoredSim(text, k_limit=k_limit)
+    if kind == "dump":
+        _, frame, phi, act = sim.run_raw(seed, shot, stop_event=stop_event)
+        return frame, phi, act
+    tr = {}
+    meas = sim.run_raw(seed, shot, trace=tr)[0]
+    return meas, tr.get("p1", {})
+
+
+def oracle_jobs(text: str, jobs, k_limit: int = 24, workers: int | None = None):
+    """Run FactoredSim jobs ("dump", seed, shot, event) -> (frame, phi, act)
+    and ("run", seed, shot) -> (raw records, {event: P(m = 1)}) in a spawn
+    process pool; results in job order."""
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    args = [(text, k_limit, j[0], j[1], j[2], j[3] if len(j) > 3 else -1) for j in jobs]
+    n = workers or max(1, min(len(args), os.cpu_count() or 1))
+    with ProcessPoolExecutor(max_workers=n, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_oracle_job, args))
+
+
+# ---------------------------------------------------------------------------
+# Rates: logical-error-rate agreement as a two-proportion test at 99 %
+# ---------------------------------------------------------------------------
+Z99 = 2.576
+
+
+def two_proportion_ok(k1: int, n1: int, k2: int, n2: int, z: float = Z99) -> bool:
+    """|k1/n1 - k2/n2| <= z * sqrt(pbar (1 - pbar) (1/n1 + 1/n2)), pbar the
+    pooled rate (equal rates required when pbar is 0 or 1)."""
+    pbar = (k1 + k2) / (n1 + n2)
+    se = (pbar * (1 - pbar) * (1 / n1 + 1 / n2)) ** 0.5
+    return abs(k1 / n1 - k2 / n2) <= z * se
+
+
+_RATE_SIM = None
+
+
+def _rate_init(text):
+    global _RATE_SIM
+    from oracle.factored import FactoredSim
+    _RATE_SIM = FactoredSim(text, k_limit=24)
+
+
+def _rate_chunk(args):
+    seed, start, count, postselect = args
+    kept = obs_fail = any_fail = 0
+    for s in range(start, start + count):
+        r = _RATE_SIM.sample(seed, s, postselect=postselect)
+        if r.kept:
+            kept += 1
+            obs_fail += 1 if (r.obs and r.obs[0]) else 0
+            any_fail += 1 if any(r.meas) else 0
+    return kept, obs_fail, any_fail
+
+
+def oracle_rates(text: str, seed: int, shots: int, postselect: bool = False, workers: int | None = None):
+    """Oracle counts over global shots 0..shots-1 in a spawn pool: (shots,
+    kept, kept with observable 0 flipped, kept with any nonzero record)."""
+    import multiprocessing as mp
+    import os
+    n = workers or (os.cpu_count() or 1)
+    chunk = max(1, shots // (4 * n))
+    jobs = [(seed, a, min(chunk, shots - a), postselect) for a in range(0, shots, chunk)]
+    with mp.get_context("spawn").Pool(n, initializer=_rate_init, initargs=(text,)) as pool:
+        parts = pool.map(_rate_chunk, jobs)
+    return (shots,) + tuple(sum(p[i] for p in parts) for i in range(3))
+
+
+def _popcount_rows(words) -> int:
+    a = np.ascontiguousarray(words.cpu().numpy()).view(np.uint8)
+    return int(np.unpackbits(a).sum())
+
+
+def gpu_rates(prog, shots: int, seed: int, postselect: bool = False):
+    """The same counts from one nc_sample call (reduced with torch on the
+    device, bits counted on the host)."""
+    import paper_2604_27058_gb300 as nc
+    res = nc.sample(prog, shots, seed, postselect=postselect)
+    i = prog.info
+    kept = res["kept"][0]
+    obs_fail = _popcount_rows(res["obs"][0] & kept) if i.n_obs else 0
+    any_m = None
+    for r in range(i.n_meas):
+        any_m = res["meas"][r].clone() if any_m is None else any_m | res["meas"][r]
+    any_fail = _popcount_rows(any_m & kept) if any_m is not None else 0
+    return shots, _popcount_rows(kept), obs_fail, any_fail

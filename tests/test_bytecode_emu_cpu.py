@@ -1,8 +1,10 @@
 """The compiled program, run by a plain Python interpreter of its instruction
 list (tests/helpers/bytecode_emu.py), against the factored oracle, shot by
 shot (CPU, no GPU). This checks the compiler's instructions, masks, noise
-tables, record slots, probes and HIR peephole end to end. Records must be
-equal except flagged near-ties; probes within 1e-10."""
+tables, record slots, probes and HIR peephole end to end. The oracle is the
+plain method (no HIR pass), so the programs compiled with the peephole on
+check that the rule changes no record. Records must be equal except flagged
+near-ties; probes within 1e-10."""
 
 import os
 import sys
@@ -27,11 +29,11 @@ def nc():
     return m
 
 
-def _check(nc, text, shots, seed, postselect=False, max_flag=2):
-    prog = nc.compile(text)
+def _check(nc, text, shots, seed, postselect=False, max_flag=2, peephole=True):
+    prog = nc.compile(text, peephole=peephole)
     fl = flatten(text)
     emu = Program(prog.serialize(), fl.site_p, fl.site_kind)
-    sim = FactoredSim(text)
+    sim = FactoredSim(text, k_limit=24)
     assert emu.ref_det == sim.ref_det and emu.ref_obs == sim.ref_obs
     n = flagged = 0
     for s in range(shots):
@@ -55,10 +57,11 @@ def _check(nc, text, shots, seed, postselect=False, max_flag=2):
     return n
 
 
+@pytest.mark.parametrize("peephole", [True, False])
 @pytest.mark.parametrize("seed", range(8))
-def test_random_circuits(nc, seed):
+def test_random_circuits(nc, seed, peephole):
     text = gc.random_small(3100 + seed, n=6, n_ops=90, p_noise=0.06 if seed % 2 else 0.0, t_frac=0.3)
-    assert _check(nc, text, 40, 17 + seed) >= 38
+    assert _check(nc, text, 40, 17 + seed, peephole=peephole) >= 38
 
 
 @pytest.mark.parametrize("seed", range(4))
@@ -111,7 +114,19 @@ def test_sweep_mirror_circuits(nc):
 
 
 def test_coherent_d5_one_round(nc):
-    """k_max = 12 after the HIR peephole (24 without it)."""
+    """k_max = 12 after the HIR peephole; the plain oracle reaches 24 on the
+    same circuit and gives the same records."""
     text = gc.surface_code_memory(d=5, rounds=1, p=1e-3, theta=0.02)
     assert nc.compile(text).info.k_max == 12
+    assert FactoredSim(text, k_limit=24).k_max == 24
     assert _check(nc, text, 6, 31) >= 5
+
+
+def test_peephole_fires_on_most_random_circuits(nc):
+    """The random circuits above exercise the rule: it removes rotations
+    (fewer array instructions) in at least a quarter of them."""
+    fired = 0
+    for seed in range(8):
+        text = gc.random_small(3100 + seed, n=6, n_ops=90, p_noise=0.0, t_frac=0.3)
+        fired += nc.compile(text).info.n_array_ops < nc.compile(text, peephole=False).info.n_array_ops
+    assert fired >= 2

@@ -64,13 +64,26 @@ def test_compile_matches_oracle_schedule(nc, name, text, kmax):
 
 
 def test_k_schedule_matches_oracle_plan(nc):
+    """With the HIR peephole off, the compiled k_max is the plain method's
+    (the oracle's plan); with it on (the default) it can only be lower."""
     from oracle.factored import FactoredSim
     for seed in range(10):
         text = gc.random_small(900 + seed, n=6, n_ops=80, t_frac=0.3)
-        assert nc.compile(text).info.k_max == FactoredSim(text).k_max
-    for d, r in ((3, 1), (3, 3), (5, 1)):
+        plain = FactoredSim(text).k_max
+        assert nc.compile(text, peephole=False).info.k_max == plain
+        assert nc.compile(text).info.k_max <= plain
+    for (d, r), (opt, plain) in zip(((3, 1), (3, 3), (5, 1)), ((4, 8), (8, 8), (12, 24))):
         text = gc.surface_code_memory(d=d, rounds=r, p=1e-3, theta=0.02)
-        assert nc.compile(text).info.k_max == FactoredSim(text, k_limit=24).k_max
+        assert nc.compile(text, peephole=False).info.k_max == FactoredSim(text, k_limit=24).k_max == plain
+        assert nc.compile(text).info.k_max == opt
+
+
+def test_unknown_compile_flag_rejected(nc):
+    import ctypes
+    from paper_2604_27058_gb300 import _nc
+    h = ctypes.c_void_p()
+    code = _nc.lib().nc_compile_ex(b"H 0\nM 0\n", 8, 1 << 7, ctypes.byref(h), None, 0)
+    assert _nc.STATUS[code] == "NC_E_ARG" and not h.value
 
 
 def test_serialize_roundtrip(nc):
@@ -150,7 +163,9 @@ def test_array_bytes_match_the_oracle_plan(nc, name):
     text = {"tiny": gc.tiny_random(), "lowmagic": gc.low_magic_gadgets(),
             "coherent": gc.surface_code_memory(d=3, rounds=3, p=1e-3, theta=0.02),
             "small": gc.random_small(77, n=6, n_ops=100, t_frac=0.3)}[name]
-    assert nc.compile(text).info.array_bytes_fp32 == pytest.approx(_plan_array_bytes(FactoredSim(text)), rel=1e-12)
+    got = nc.compile(text, peephole=False).info.array_bytes_fp32
+    assert got == pytest.approx(_plan_array_bytes(FactoredSim(text)), rel=1e-12)
+    assert nc.compile(text).info.array_bytes_fp32 <= got
     assert nc.compile(gc.surface_code_memory(d=3, rounds=2)).info.array_bytes_fp32 == 0.0
 
 

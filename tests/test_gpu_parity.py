@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 from gen import circuits as gc
+from oracle.circuit import flatten
 from oracle.dense import DenseSim
 from oracle.factored import FactoredSim
 from oracle.records import assemble
@@ -227,9 +228,10 @@ def test_dense_small_records_and_amplitudes(nc, precision):
     n_ok, flagged = _check(_factored_run(sim, 3003), sim.ref_det, sim.ref_obs, sim.flat, g, 3003, range(shots))
     assert flagged <= 4
     tol = FP32_AMP_TOL if precision == "fp32" else FP64_AMP_TOL
+    plain = nc.compile(text, peephole=False)  # intermediate states of the plain method
     for shot in (0, 5, 130):
         for ev in (0, 3, 7):
-            fx, fz, phi, k = nc.debug_dump(prog, 3003, shot, ev, precision=precision)
+            fx, fz, phi, k = nc.debug_dump(plain, 3003, shot, ev, precision=precision)
             _, (ox, oz), ophi, act = sim.run_raw(3003, shot, stop_event=ev)
             assert k == len(act)
             assert (fx, fz) == (ox, oz)
@@ -265,10 +267,38 @@ def test_dense_k20_fp32_vs_fp64(nc):
     assert abs(np.linalg.norm(p64) - 1) < 1e-10
 
 
+def test_dense_k20_40_layers_vs_oracle(nc):
+    """The dense workload at its stated shape (n = 20, 40 layers, k = 20):
+    FP32 and FP64-batched amplitudes before the final measurements against
+    the FP64 oracle on two shots (the dumps start from the shared noiseless
+    prefix, as sampling calls do), and the records of the 4096-shot call on
+    four shots, near-ties flagged. The oracle runs in a spawn pool."""
+    from parity import oracle_jobs
+    text = gc.dense_random(seed=3, n=20, layers=40)
+    dump_shots, rec_shots = (0, 77), range(4)
+    res = oracle_jobs(text, [("dump", 3003, s, 0) for s in dump_shots] + [("run", 3003, s) for s in rec_shots])
+    plain = nc.compile(text, peephole=False)  # the intermediate states of the plain method
+    assert plain.info.k_max == 20 and plain.info.prefix_k == 20
+    for j, s in enumerate(dump_shots):
+        (ox, oz), ophi, act = res[j]
+        assert len(act) == 20
+        for precision, tol in (("fp32", FP32_AMP_TOL), ("fp64_batched", FP64_AMP_TOL)):
+            fx, fz, phi, k = nc.debug_dump(plain, 3003, s, 0, precision=precision)
+            assert k == 20 and (fx, fz) == (ox, oz)
+            assert state_error(phi, ophi) <= tol, (s, precision)
+    prog = nc.compile(text)
+    runs = res[len(dump_shots):]
+    flat = flatten(text)  # no detectors or observables: empty references
+    for precision, shots in (("fp32", 4096), ("fp64_batched", 64)):
+        g = gpu_records(prog, shots, 3003, precision=precision)
+        n_ok, flagged = _check(lambda s: runs[s], [], [], flat, g, 3003, rec_shots)
+        assert n_ok + flagged == len(rec_shots) and flagged <= 1
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64_batched", "fp64"])
 def test_dense_k13_amplitudes_vs_oracle(nc, precision):
     text = gc.dense_random(seed=3, n=14, layers=10)
-    prog = nc.compile(text)
+    prog = nc.compile(text, peephole=False)
     sim = FactoredSim(text)
     assert prog.info.k_max == sim.k_max == 13
     tol = FP32_AMP_TOL if precision == "fp32" else FP64_AMP_TOL
@@ -553,11 +583,13 @@ def test_coherent_surface_code(nc, precision, tune):
 
 
 def test_coherent_surface_code_amplitudes(nc):
-    """The FP32 and FP64 active vectors of the coherent circuit equal the
+    """The FP32 and FP64 active vectors of the coherent circuit, compiled
+    without the HIR peephole (the plain method's k-schedule), equal the
     oracle's just before several measurement events."""
     text = gc.surface_code_memory(d=3, rounds=1, p=1e-3, theta=0.02)
-    prog = nc.compile(text)
+    prog = nc.compile(text, peephole=False)
     sim = FactoredSim(text)
+    assert prog.info.k_max == sim.k_max == 8
     for ev in (8, 12, 16, 20):
         for s in (0, 5):
             _, (ox, oz), phi_ref, act = sim.run_raw(7, s, stop_event=ev)
@@ -566,6 +598,24 @@ def test_coherent_surface_code_amplitudes(nc):
                 assert k == len(act), (ev, s, precision)
                 assert (fx, fz) == (ox, oz)
                 assert state_error(amps, phi_ref) <= tol, (ev, s, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_peephole_keeps_records(nc, precision):
+    """The HIR peephole drops rotations only a phase per measurement branch
+    can see: programs compiled with it (k_max 4) and without it (k_max 8)
+    give the plain oracle's records shot by shot, near-ties aside."""
+    text = gc.surface_code_memory(d=3, rounds=1, p=1e-2, theta=0.05)
+    opt, plain = nc.compile(text), nc.compile(text, peephole=False)
+    assert (opt.info.k_max, plain.info.k_max) == (4, 8)
+    sim = FactoredSim(text)
+    shots = 500
+    for prog in (opt, plain):
+        g = gpu_records(prog, shots, 6116, precision=precision)
+        n_ok, flagged = _check(_factored_run(sim, 6116), sim.ref_det, sim.ref_obs, sim.flat, g, 6116,
+                               range(shots))
+        assert flagged <= 2 and n_ok + flagged == shots
+        assert int(g["det"].sum()) > 0
 
 
 # ---------------------------------------------------------------------------

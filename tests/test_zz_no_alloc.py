@@ -42,6 +42,8 @@ CASES = {
     "surface_d5_r25": (lambda: gc.surface_code_memory(d=5, rounds=25, p=1e-3), 100_000, False),
     "tiny_k6": (lambda: gc.tiny_random(seed=1), 20_000, False),
     "low_magic_k10": (lambda: gc.low_magic_gadgets(), 9_000, True),
+    # near-deterministic detectors: the reference trajectory must be nc_sample's
+    "coherent_d3_r3": (lambda: gc.surface_code_memory(d=3, rounds=3, p=1e-3, theta=0.02), 6_000, False),
 }
 
 
@@ -69,3 +71,22 @@ def test_noalloc_rejects_oversized_workspace(nc):
     assert prog.info.k_max == 20  # one 32-shot tile needs 256 MiB of amplitudes
     code, _, _ = _noalloc(nc, prog, 64, 1)
     assert _nc.STATUS[code] == "NC_E_ARG"
+
+
+def test_noalloc_matches_the_oracle(nc):
+    """Records of the allocation-free call against the FP64 oracle, shot by
+    shot (near-ties flagged), on the tiny workload."""
+    from parity import compare
+    from oracle.factored import FactoredSim
+    text = gc.tiny_random(seed=1)
+    prog = nc.compile(text)
+    shots = 700
+    code, bufs, _ = _noalloc(nc, prog, shots, 1001)
+    assert code == 0
+    info = prog.info
+    g = {"meas": nc.unpack_rows(bufs["meas"], shots)[: info.n_meas],
+         "det": nc.unpack_rows(bufs["det"], shots)[: info.n_det],
+         "obs": nc.unpack_rows(bufs["obs"], shots)[: info.n_obs],
+         "kept": nc.unpack_rows(bufs["kept"], shots)[0]}
+    n_ok, flagged = compare(FactoredSim(text), g, range(shots), 1001)
+    assert flagged <= 3 and n_ok + flagged == shots
