@@ -334,12 +334,23 @@ void append_affine(std::vector<uint8_t>& blob) {
     for (uint32_t r = R; r-- > 0;)
       if (parent[r] != kNone) base.rows[r] ^= base.rows[parent[r]];
   }
-  // chains of two or more rows, head first
+  // chains, head first: every row lies on exactly one (a row with neither
+  // parent nor child is a chain of one), longest chains first, so that the
+  // chains one warp resolves side by side have about the same length
   std::vector<uint32_t> chain_off, chain;
-  for (uint32_t r = 0; r < R; r++) {
-    if (parent[r] != kNone || child[r] == kNone) continue;
-    chain_off.push_back((uint32_t)chain.size());
-    for (uint32_t x = r; x != kNone; x = child[x]) chain.push_back(x);
+  {
+    std::vector<std::vector<uint32_t>> chs;
+    for (uint32_t r = 0; r < R; r++) {
+      if (parent[r] != kNone) continue;
+      chs.emplace_back();
+      for (uint32_t x = r; x != kNone; x = child[x]) chs.back().push_back(x);
+    }
+    std::stable_sort(chs.begin(), chs.end(),
+                     [](const std::vector<uint32_t>& a, const std::vector<uint32_t>& b) { return a.size() > b.size(); });
+    for (const auto& c : chs) {
+      chain_off.push_back((uint32_t)chain.size());
+      chain.insert(chain.end(), c.begin(), c.end());
+    }
   }
   const uint32_t n_chains = (uint32_t)chain_off.size();
   chain_off.push_back((uint32_t)chain.size());
@@ -351,19 +362,26 @@ void append_affine(std::vector<uint8_t>& blob) {
     for (uint32_t j = 0; j < rand_rows.size(); j++)
       for (uint32_t r : rand_rows[j]) per_row[r].push_back(j);
     for (uint32_t r = 0; r < R; r++) {
+      // the sampler packs a row's term count in 7 bits and its first entry
+      // in 24 (the bytecode executor serves programs beyond that)
+      if (per_row[r].size() >= 128) return;
       rowev_off[r] = (uint32_t)rowev.size();
       rowev.insert(rowev.end(), per_row[r].begin(), per_row[r].end());
     }
     rowev_off[R] = (uint32_t)rowev.size();
+    if (rowev.size() >= (1u << 24)) return;
   }
-  // fault columns in chunks of 8 u16 rows (padding: row R, a scratch row)
+  // fault columns in chunks of 8 u16 chain positions (the sampler keeps
+  // row chain[j] at position j of its tile; padding: R)
   if (R >= 0xFFFFu) return;
+  std::vector<uint32_t> pos_of(R);
+  for (uint32_t j = 0; j < (uint32_t)chain.size(); j++) pos_of[chain[j]] = j;
   std::vector<uint16_t> chunks;
   for (size_t c = 0; c < col_rows.size(); c++) {
     col_off[c] = (uint32_t)(chunks.size() / 8);
     const auto& rows = col_rows[c];
     for (size_t j = 0; j < rows.size(); j += 8)
-      for (size_t e = 0; e < 8; e++) chunks.push_back((uint16_t)(j + e < rows.size() ? rows[j + e] : R));
+      for (size_t e = 0; e < 8; e++) chunks.push_back((uint16_t)(j + e < rows.size() ? pos_of[rows[j + e]] : R));
   }
   col_off[col_rows.size()] = (uint32_t)(chunks.size() / 8);
   if (chunks.size() / 8 >= (1u << 22)) return;

@@ -91,14 +91,14 @@ __device__ __forceinline__ uint32_t aff_draw_strat(const DevProg& p, uint2 key, 
 }
 
 // XOR `bit` into the tile column `col` at the (up to) eight rows of a chunk;
-// padding entries (row index R, the scratch row) are skipped.
+// padding entries (row index R) go to `dump`, a word of the caller's that
+// nothing reads, so that every entry is one unconditional atomic.
 template <uint32_t STR>
-__device__ __forceinline__ void xor_chunk(uint32_t* col, uint4 ch, uint32_t bit, uint32_t R) {
+__device__ __forceinline__ void xor_chunk(uint32_t* col, uint4 ch, uint32_t bit, uint32_t R, uint32_t* dump) {
   const uint32_t r[8] = {ch.x & 0xFFFFu, ch.x >> 16, ch.y & 0xFFFFu, ch.y >> 16,
                          ch.z & 0xFFFFu, ch.z >> 16, ch.w & 0xFFFFu, ch.w >> 16};
 #pragma unroll
-  for (uint32_t e = 0; e < 8; e++)
-    if (r[e] < R) atomicXor(col + r[e] * STR, bit);
+  for (uint32_t e = 0; e < 8; e++) atomicXor(r[e] < R ? col + r[e] * STR : dump, bit);
 }
 
 // Warp-inclusive prefix sum.
@@ -111,48 +111,72 @@ __device__ __forceinline__ uint32_t warp_incl(uint32_t v, uint32_t lane) {
   return v;
 }
 
+// Fault items of the tile kernel: (first chunk << 14) | (chunks << 10) |
+// shot in the tile, one per fault (a fault of more than kItemMaxChunks
+// chunks takes several); first chunks below 2^18.
+constexpr uint32_t kItemMaxChunks = 15;
+__device__ __forceinline__ uint32_t fault_item(uint32_t c0, uint32_t nch, uint32_t shot) {
+  return (c0 << 14) | (nch << 10) | shot;
+}
+
 // affine_items: fault sampling alone, at high occupancy (no record tile).
 // One warp per tile of `pool` shots (tile g of the launch = call-local shots
 // (tile0 + g) * pool ...), lanes refilled as their shots end; every fault's
-// chunk items (chunk << 10 | shot in the tile) go to
-// the pool's list items[g * cap ...], and counts[g] receives the number of
-// items (a count above cap means the list overflowed).
+// item goes to the pool's list items[g * cap ...], and counts[g] receives
+// the number of items (a count above cap means the list overflowed).
 __global__ void __launch_bounds__(512, 2) affine_items(LaunchParams L, uint32_t pool0, uint32_t n_pools,
                                                        uint32_t* items, uint32_t cap, uint32_t* counts,
                                                        uint32_t pool) {
   const DevProg& p = L.p;
-  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lane = threadIdx.x & 31u, lt = (1u << lane) - 1u;
   const uint32_t wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const uint2 key = key_of(L.seed);
   for (uint32_t g = wg; g < n_pools; g += nw) {
     const uint64_t s0 = (uint64_t)(pool0 + g) * pool;  // call-local first shot
     const uint64_t left = s0 < L.shots ? L.shots - s0 : 0;
     const uint32_t n = left < pool ? (uint32_t)left : pool;
+    const uint64_t base = L.shot_offset + s0;  // global first shot
     uint32_t* out = items + (size_t)g * cap;
+    // lane slot sh -> tile-local shot: in a full tile (sh mod W) * 32 + sh / W
+    // with W = pool / 32 words, so that consecutive items (one per live
+    // lane) name different 32-shot words of the tile and the tile kernel's
+    // atomics on them fall in different banks; the identity in a ragged tile
+    const uint32_t wpool = pool >> 5, wshift = __ffs(wpool) - 1;  // pool = 32 * 2^wshift
+    const bool spread = n == pool;
     uint32_t sh = lane, nxt = 32, st = 0, cnt = 0, r = p.sg_k;
     const bool any = p.n_sites > 0 && (!p.sg || p.sg_k > 0);
     bool live = sh < n && any;
     while (__any_sync(0xffffffffu, live)) {
       uint32_t c0 = 0, nch = 0;
       bool fin = false;
+      const uint32_t it0 = spread ? ((sh & (wpool - 1u)) << 5) | (sh >> wshift) : sh;
       if (live) {
         if (p.sg) {
-          st = aff_draw_strat(p, key, L.shot_offset + s0 + sh, st, r, &c0, &nch);
+          st = aff_draw_strat(p, key, base + it0, st, r, &c0, &nch);
           fin = --r == 0 || st >= p.n_sites;
         } else {
-          st = aff_draw(p, key, L.shot_offset + s0 + sh, st, &c0, &nch);
+          st = aff_draw(p, key, base + it0, st, &c0, &nch);
           fin = st >= p.n_sites;
         }
       }
-      const uint32_t incl = warp_incl(nch, lane);
-      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-      const uint32_t it0 = sh;
-      for (uint32_t j = 0, pos = cnt + incl - nch; j < nch; j++, pos++)
-        if (pos < cap) out[pos] = ((c0 + j) << 10) | it0;
-      cnt += total;
+      const uint32_t big = __ballot_sync(0xffffffffu, nch > kItemMaxChunks);
+      if (!big) {
+        // at most one item per lane: place by ballot
+        const uint32_t has = __ballot_sync(0xffffffffu, nch != 0);
+        const uint32_t pos = cnt + __popc(has & lt);
+        if (nch && pos < cap) out[pos] = fault_item(c0, nch, it0);
+        cnt += __popc(has);
+      } else {
+        const uint32_t k = (nch + kItemMaxChunks - 1) / kItemMaxChunks;
+        const uint32_t incl = warp_incl(k, lane);
+        uint32_t pos = cnt + incl - k;
+        for (uint32_t c = 0; c < nch; c += kItemMaxChunks, pos++)
+          if (pos < cap) out[pos] = fault_item(c0 + c, min(kItemMaxChunks, nch - c), it0);
+        cnt += __shfl_sync(0xffffffffu, incl, 31);
+      }
       const uint32_t done = __ballot_sync(0xffffffffu, fin);
       if (fin) {
-        sh = nxt + __popc(done & ((1u << lane) - 1u));
+        sh = nxt + __popc(done & lt);
         st = 0;
         r = p.sg_k;
         live = sh < n;
@@ -163,35 +187,24 @@ __global__ void __launch_bounds__(512, 2) affine_items(LaunchParams L, uint32_t 
   }
 }
 
+// Fault sampling inside the tile kernel (no item list for the tile): lane
+// refill over the warp's 32 shots, chunk items through the warp's list LW,
+// applied to TILE with atomic XORs. The warp's shots are tile-local warp,
+// warp + WPT, warp + 2 WPT, ...: one per 32-shot word (WPT = 32), so the
+// atomics of one list pass fall in different banks. Kept out of line so
+// that its registers do not crowd the rest of the kernel.
 template <int WPT>
-__global__ void __launch_bounds__(kAffTpw * WPT, 65536 / (kAffTpw * WPT * 64)) sample_affine(LaunchParams L) {
-  extern __shared__ __align__(16) uint32_t sm[];
+__device__ __noinline__ void sample_tile_faults(const LaunchParams& L, uint32_t* TILE, uint32_t* LW, uint32_t* dump,
+                                                uint32_t tile, uint32_t lane, uint32_t warp) {
   const DevProg& p = L.p;
-  constexpr uint32_t S = 32u * WPT, T = kAffTpw * WPT, STR = WPT + 1;
-  static_assert(S / (T / 32) == kAffPool, "one fused-sampling pool per warp");
-  const uint32_t R = p.aff_rows, NR = p.aff_n_rand, t = threadIdx.x, lane = t & 31u, warp = t >> 5;
-  // word offsets, each region 16-byte aligned (MW rows are read as uint4)
-  const uint32_t o_mw = ((R + 1) * STR + 3u) & ~3u;
-  uint32_t* TILE = sm;                                // (R + 1) rows; row R is scratch
-  uint32_t* MW = sm + o_mw;                           // random bits [NR][WPT]
-  uint32_t* LW = MW + NR * WPT + warp * kAffList;     // this warp's chunk list
-  // per-launch tables staged once: row info (bit 0: constant ^ reference
-  // parities of the row and its parent; bits 1..: first random-event entry)
-  // and the chains as u16 rows
-  uint32_t* RI = MW + NR * WPT + (T / 32) * kAffList;  // [R + 1]
-  uint16_t* CH = reinterpret_cast<uint16_t*>(RI + R + 1);                    // [n_chain_rows]
-  uint16_t* CHOFF = CH + ((p.aff_n_chain_rows + 1) & ~1u);                  // [n_chains + 1]
-  const bool noisy = !(L.flags & LF_NOISELESS) && p.n_sites > 0;
+  constexpr uint32_t S = 32u * WPT;
+  const uint32_t R = p.aff_rows;
   const uint2 key = key_of(L.seed);
-  const uint32_t n_det_end = p.n_meas + p.n_det;
-
-  // eight atomic XORs of one chunk into the column of shot s (tile-local)
-  auto apply_chunk = [&](uint32_t chunk, uint32_t s) {
-    const uint4 ch = __ldg(p.aff_chunks + chunk);
-    uint32_t* col = TILE + (s >> 5);
-    const uint32_t bit = 1u << (s & 31u);
-    xor_chunk<STR>(col, ch, bit, R);
-  };
+  const uint64_t tile_s0 = L.shot_offset + (uint64_t)tile * S;
+  const uint64_t base = (uint64_t)tile * S;  // call-local first shot of the tile
+  const uint64_t left = base < L.shots ? L.shots - base : 0;
+  const uint32_t n_tile = left < S ? (uint32_t)left : S;
+  const uint32_t pool_n = n_tile > warp ? min(kAffPool, (n_tile - warp + WPT - 1) / WPT) : 0u;
   // the warp applies its list (at most kAffList = 4 x 32 items), two chunk
   // loads per lane in flight before their atomics
   auto flush = [&](uint32_t n) {
@@ -211,11 +224,78 @@ __global__ void __launch_bounds__(kAffTpw * WPT, 65536 / (kAffTpw * WPT * 64)) s
       }
 #pragma unroll
       for (uint32_t u = 0; u < 2; u++)
-        if (lane + 32u * (k0 + u) < n) xor_chunk<STR>(TILE + (sh[u] >> 5), ch[u], 1u << (sh[u] & 31u), R);
+        if (lane + 32u * (k0 + u) < n) xor_chunk<WPT>(TILE + (sh[u] >> 5), ch[u], 1u << (sh[u] & 31u), R, dump);
     }
     __syncwarp();
   };
+  uint32_t sh = lane, nxt = 32, st = 0, cnt = 0, r = p.sg_k;
+  bool live = sh < pool_n && (!p.sg || p.sg_k > 0);
+  while (__any_sync(0xffffffffu, live)) {
+    uint32_t c0 = 0, nch = 0;
+    bool fin = false;
+    const uint32_t s_tile = sh * WPT + warp;
+    if (live) {
+      if (p.sg) {
+        st = aff_draw_strat(p, key, tile_s0 + s_tile, st, r, &c0, &nch);
+        fin = --r == 0 || st >= p.n_sites;
+      } else {
+        st = aff_draw(p, key, tile_s0 + s_tile, st, &c0, &nch);
+        fin = st >= p.n_sites;
+      }
+    }
+    // warp prefix of the chunk counts
+    const uint32_t incl = warp_incl(nch, lane);
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (cnt + total > kAffList) {
+      flush(cnt);
+      cnt = 0;
+    }
+    if (total > kAffList) {
+      for (uint32_t j = 0; j < nch; j++)
+        xor_chunk<WPT>(TILE + (s_tile >> 5), __ldg(p.aff_chunks + c0 + j), 1u << (s_tile & 31u), R, dump);
+    } else {
+      for (uint32_t j = 0, pos = cnt + incl - nch; j < nch; j++, pos++) LW[pos] = ((c0 + j) << 10) | s_tile;
+      cnt += total;
+    }
+    // hand finished lanes the next shots of the pool
+    const uint32_t done = __ballot_sync(0xffffffffu, fin);
+    if (fin) {
+      sh = nxt + __popc(done & ((1u << lane) - 1u));
+      st = 0;
+      r = p.sg_k;
+      live = sh < pool_n;
+    }
+    nxt += __popc(done);
+  }
+  flush(cnt);
+}
 
+template <int WPT>
+__global__ void __launch_bounds__(kAffTpw * WPT, 65536 / (kAffTpw * WPT * 64)) sample_affine(LaunchParams L) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  const DevProg& p = L.p;
+  constexpr uint32_t S = 32u * WPT, T = kAffTpw * WPT, NWARP = T / 32;
+  constexpr uint32_t QPL = WPT / 4;   // lanes per row in the output pass, one 16-byte quad each
+  constexpr uint32_t CPW = 32 / QPL;  // chains one warp resolves side by side
+  static_assert(S / NWARP == kAffPool, "one fused-sampling pool per warp");
+  const uint32_t R = p.aff_rows, NR = p.aff_n_rand, t = threadIdx.x, lane = t & 31u, warp = t >> 5;
+  // word offsets; every region 16-byte aligned (WPT is a multiple of 4)
+  uint32_t* TILE = sm;                                // R rows of WPT words, zero between tiles
+  uint32_t* MW = sm + R * WPT;                        // random bits [NR][WPT]
+  uint32_t* LW = MW + NR * WPT + warp * kAffList;     // this warp's chunk list
+  // per-launch tables staged once, by chain position j (the tile keeps row
+  // chain[j] at position j): the output row (null: not written), row info
+  // (bit 0: constant ^ reference parities of the row and its parent; bits
+  // 1..7: its number of random-bit terms; bits 8..: its first term), each
+  // warp's range of single-row steps, and the chain offsets
+  uint32_t** ROWP = reinterpret_cast<uint32_t**>(MW + NR * WPT + NWARP * kAffList);  // [R]
+  uint32_t* RI = reinterpret_cast<uint32_t*>(ROWP + R);  // [R]
+  uint32_t* SR = RI + R;                                 // [NWARP + 2]
+  uint32_t* dump = SR + NWARP + 2 + lane;                // [32]: padding entries' atomics
+  uint16_t* CHOFF = reinterpret_cast<uint16_t*>(SR + NWARP + 2 + 32);  // [n_chains + 1]
+  const bool noisy = !(L.flags & LF_NOISELESS) && p.n_sites > 0;
+  const uint2 key = key_of(L.seed);
+  const uint32_t n_det_end = p.n_meas + p.n_det;
 
   {
     auto ref = [&](uint32_t r) -> uint32_t {
@@ -223,17 +303,65 @@ __global__ void __launch_bounds__(kAffTpw * WPT, 65536 / (kAffTpw * WPT * 64)) s
              : r < n_det_end       ? __ldg(p.det_ref + (r - p.n_meas))
                                    : __ldg(p.obs_ref + (r - n_det_end));
     };
-    for (uint32_t r = t; r <= R; r += T) {
-      uint32_t c = 0;
-      if (r < R) {
-        c = __ldg(p.aff_const + r) ^ ref(r);
-        const uint32_t par = __ldg(p.aff_parent + r);
-        if (par != 0xFFFFFFFFu) c ^= ref(par);
+    for (uint32_t j = t; j < R; j += T) {
+      const uint32_t r = __ldg(p.aff_chain + j);
+      uint32_t c = __ldg(p.aff_const + r) ^ ref(r);
+      const uint32_t par = __ldg(p.aff_parent + r);
+      if (par != 0xFFFFFFFFu) c ^= ref(par);
+      const uint32_t e0 = __ldg(p.aff_rowev_off + r), ne = __ldg(p.aff_rowev_off + r + 1) - e0;
+      RI[j] = (e0 << 8) | (ne << 1) | (c & 1u);
+      uint32_t* dst = nullptr;
+      if (r < p.n_meas) {
+        if (L.flags & LF_OUT_MEAS) dst = L.meas + (size_t)r * L.row_words32;
+      } else if (r < n_det_end) {
+        if (L.flags & LF_OUT_DET) dst = L.det + (size_t)(r - p.n_meas) * L.row_words32;
+      } else if (L.flags & LF_OUT_OBS) {
+        dst = L.obs + (size_t)(r - n_det_end) * L.row_words32;
       }
-      RI[r] = (__ldg(p.aff_rowev_off + r) << 1) | (c & 1u);
+      ROWP[j] = dst;
     }
-    for (uint32_t j = t; j < p.aff_n_chain_rows; j += T) CH[j] = (uint16_t)__ldg(p.aff_chain + j);
     for (uint32_t j = t; j <= p.aff_n_chains; j += T) CHOFF[j] = (uint16_t)__ldg(p.aff_chain_off + j);
+    for (uint32_t i = t; i < R * (WPT / 4); i += T) reinterpret_cast<uint4*>(TILE)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    // Work split of the output pass. Chains of two or more rows (the first
+    // n_long, longest first) are walked CPW at a time per warp, one row per
+    // step; the single rows after them are cut into steps of CPW rows, and
+    // warp w takes the steps [SR[w], SR[w + 1]), sized so that every warp
+    // has about the same number of steps in all.
+    if (warp == 0) {
+      // lane w < NWARP: warp w's chain steps; n_long by a search over the
+      // chain lengths (non-increasing)
+      uint32_t lo = 0, hi = p.aff_n_chains;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (CHOFF[mid + 1] - CHOFF[mid] >= 2) lo = mid + 1;
+        else hi = mid;
+      }
+      const uint32_t n_long = lo;
+      // warp w walks the chains w * CPW + cw (+ k NWARP CPW) side by side: its
+      // chain steps are the lengths of the first chain of each such group
+      // (chains are longest first)
+      uint32_t cs = 0;
+      if (lane < NWARP)
+        for (uint32_t c = lane * CPW; c < n_long; c += NWARP * CPW) cs += CHOFF[c + 1] - CHOFF[c];
+      const uint32_t n_ss = (R - CHOFF[n_long] + CPW - 1) / CPW;
+      uint32_t tot = cs;
+      for (uint32_t d = 16; d; d >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, d);
+      uint32_t target = (tot + n_ss + NWARP - 1) / NWARP;
+      uint32_t quota = 0;
+      for (;; target++) {
+        quota = lane < NWARP && cs < target ? target - cs : 0u;
+        uint32_t room = quota;
+        for (uint32_t d = 16; d; d >>= 1) room += __shfl_xor_sync(0xffffffffu, room, d);
+        if (room >= n_ss) break;
+      }
+      const uint32_t incl = warp_incl(quota, lane);
+      if (lane < NWARP) SR[lane] = min(n_ss, incl - quota);
+      if (lane == 0) {
+        SR[NWARP] = n_ss;
+        SR[NWARP + 1] = n_long;
+      }
+    }
     __syncthreads();
   }
 
@@ -253,178 +381,125 @@ __global__ void __launch_bounds__(kAffTpw * WPT, 65536 / (kAffTpw * WPT * 64)) s
       const uint32_t j = i / GR, grp = i % GR;
       const uint64_t g = (tile_s0 >> 7) + grp;
       const uint4 tb = philox(make_uint4((uint32_t)g, (uint32_t)(g >> 32), TAG_MT, __ldg(p.aff_rand_ev + j)), key);
-      uint32_t* dst = MW + j * WPT + grp * 4u;
-      dst[0] = ~tb.x;
-      dst[1] = ~tb.y;
-      dst[2] = ~tb.z;
-      dst[3] = ~tb.w;
+      *reinterpret_cast<uint4*>(MW + j * WPT + grp * 4u) = make_uint4(~tb.x, ~tb.y, ~tb.z, ~tb.w);
     }
-    __syncthreads();
-    // 2. constants, reference parities and random-bit terms, four words per thread
-    constexpr uint32_t QPR = WPT / 4;  // 4-word quarters per row
-    for (uint32_t i = t; i < R * QPR; i += T) {
-      const uint32_t r = i / QPR, q = (i % QPR) * 4u;
-      const uint32_t ri = RI[r];
-      const uint32_t c = (ri & 1u) ? ~0u : 0u;
-      const uint32_t e0 = ri >> 1, e1 = RI[r + 1] >> 1;
-      uint4 v = make_uint4(c, c, c, c);
-      for (uint32_t e = e0; e < e1; e++) {
-        const uint4 x = *reinterpret_cast<const uint4*>(MW + __ldg(p.aff_rowev + e) * WPT + q);
-        v.x ^= x.x;
-        v.y ^= x.y;
-        v.z ^= x.z;
-        v.w ^= x.w;
-      }
-      uint32_t* dst = TILE + r * STR + q;
-      dst[0] = v.x;
-      dst[1] = v.y;
-      dst[2] = v.z;
-      dst[3] = v.w;
-    }
-    __syncthreads();
-    // 3a. apply the tile's pre-sampled items, two per thread at a time
+    // 2. faults into the zeroed tile: pre-sampled items, one per fault
     if (noisy && titems) {
-      const uint32_t n = tcnt;
-      for (uint32_t i0 = 0; i0 < n; i0 += 2 * T) {
-        uint4 ch[2];
-        uint32_t sh[2];
-#pragma unroll
-        for (uint32_t u = 0; u < 2; u++) {
-          const uint32_t i = i0 + u * T + t;
-          if (i < n) {
-            const uint32_t it = __ldg(titems + i);
-            ch[u] = __ldg(p.aff_chunks + (it >> 10));
-            sh[u] = it & 1023u;
-          }
-        }
-#pragma unroll
-        for (uint32_t u = 0; u < 2; u++)
-          if (i0 + u * T + t < n) xor_chunk<STR>(TILE + (sh[u] >> 5), ch[u], 1u << (sh[u] & 31u), R);
+      for (uint32_t i = t; i < tcnt; i += T) {
+        const uint32_t it = __ldg(titems + i);
+        const uint32_t sh = it & 1023u, nch = (it >> 10) & 15u, c0 = it >> 14;
+        uint32_t* col = TILE + (sh >> 5);
+        const uint32_t bit = 1u << (sh & 31u);
+        for (uint32_t c = 0; c < nch; c++) xor_chunk<WPT>(col, __ldg(p.aff_chunks + c0 + c), bit, R, dump);
       }
     }
-    // 3b. otherwise fault sampling with lane refill; chunk items through the warp list
-    if (noisy && !titems) {
-      const uint64_t pool0 = (uint64_t)tile * S + warp * kAffPool;  // call-local first shot of the pool
-      const uint64_t left = pool0 < L.shots ? L.shots - pool0 : 0;
-      const uint32_t pool_n = left < kAffPool ? (uint32_t)left : kAffPool;
-      uint32_t sh = lane, nxt = 32, st = 0, cnt = 0, r = p.sg_k;
-      bool live = sh < pool_n && (!p.sg || p.sg_k > 0);
-      while (__any_sync(0xffffffffu, live)) {
-        uint32_t c0 = 0, nch = 0;
-        bool fin = false;
-        if (live) {
-          if (p.sg) {
-            st = aff_draw_strat(p, key, L.shot_offset + pool0 + sh, st, r, &c0, &nch);
-            fin = --r == 0 || st >= p.n_sites;
-          } else {
-            st = aff_draw(p, key, L.shot_offset + pool0 + sh, st, &c0, &nch);
-            fin = st >= p.n_sites;
-          }
-        }
-        // warp prefix of the chunk counts
-        const uint32_t incl = warp_incl(nch, lane);
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        const uint32_t s_tile = warp * kAffPool + sh;
-        if (cnt + total > kAffList) {
-          flush(cnt);
-          cnt = 0;
-        }
-        if (total > kAffList) {
-          for (uint32_t j = 0; j < nch; j++) apply_chunk(c0 + j, s_tile);
-        } else {
-          for (uint32_t j = 0, pos = cnt + incl - nch; j < nch; j++, pos++) LW[pos] = ((c0 + j) << 10) | s_tile;
-          cnt += total;
-        }
-        // hand finished lanes the next shots of the pool
-        const uint32_t done = __ballot_sync(0xffffffffu, fin);
-        if (fin) {
-          sh = nxt + __popc(done & ((1u << lane) - 1u));
-          st = 0;
-          r = p.sg_k;
-          live = sh < pool_n;
-        }
-        nxt += __popc(done);
-      }
-      flush(cnt);
-    }
+    // otherwise fault sampling in the tile kernel
+    if (noisy && !titems) sample_tile_faults<WPT>(L, TILE, LW, dump, tile, lane, warp);
     __syncthreads();
-    // 4. delta rows to record rows: a running XOR down each chain, per word
-    for (uint32_t i = t; i < p.aff_n_chains * WPT; i += T) {
-      const uint32_t ch = i / WPT, w = i % WPT;
-      const uint32_t j0 = CHOFF[ch], j1 = CHOFF[ch + 1];
-      uint32_t v = 0, j = j0;
-      for (; j + 4 <= j1; j += 4) {  // four rows' loads in flight
-        uint32_t* x0 = TILE + CH[j] * STR + w;
-        uint32_t* x1 = TILE + CH[j + 1] * STR + w;
-        uint32_t* x2 = TILE + CH[j + 2] * STR + w;
-        uint32_t* x3 = TILE + CH[j + 3] * STR + w;
-        const uint32_t a0 = *x0, a1 = *x1, a2 = *x2, a3 = *x3;
-        v ^= a0;
-        *x0 = v;
-        v ^= a1;
-        *x1 = v;
-        v ^= a2;
-        *x2 = v;
-        v ^= a3;
-        *x3 = v;
-      }
-      for (; j < j1; j++) {
-        uint32_t* x = TILE + CH[j] * STR + w;
-        v ^= *x;
-        *x = v;
-      }
-    }
-    __syncthreads();
-    // 5. rows out, then the kept row: four words per thread (16-byte stores)
-    // when rows are 16-byte aligned (row_words32 % 4 == 0), else two. Shot
-    // masks and the row-end check only in the last tile.
+    // 3. the output pass. Each delta row is read and zeroed for the next
+    // tile, its constant and random-bit terms are added, the XOR down its
+    // chain turns it into its record row, which goes straight to HBM. QPL
+    // lanes cover a row (16-byte quads); a warp holds CPW row slots.
     const uint64_t gw0 = (uint64_t)tile * WPT;
     const bool full = (uint64_t)(tile + 1) * S <= L.shots && gw0 + WPT <= L.row_words32;
+    const bool fast = full && (L.row_words32 & 3u) == 0;
     auto valid = [&](uint64_t gw) -> uint32_t {
       const uint64_t s0 = gw * 32u;
       return s0 + 32 <= L.shots ? ~0u : s0 < L.shots ? (1u << (uint32_t)(L.shots - s0)) - 1u : 0u;
     };
-    // rows [r0, r0 + nr) of the tile to base (kept row: r0 = R, constant)
-    auto write_rows = [&](uint32_t* base, uint32_t r0, uint32_t nr) {
+    // the quad v of a record row at words gw .. gw + 3 of dst (rows are
+    // 8-byte aligned; 16-byte stores when row_words32 % 4 == 0)
+    auto put = [&](uint32_t* dst, uint64_t gw, uint4 v) {
+      if (fast) {
+        *reinterpret_cast<uint4*>(dst) = v;
+        return;
+      }
+      if (gw >= L.row_words32) return;  // row_words32 is even: gw + 1 is out too
+      v.x &= valid(gw);
+      v.y &= valid(gw + 1);
+      v.z &= valid(gw + 2);
+      v.w &= valid(gw + 3);
       if ((L.row_words32 & 3u) == 0) {
-        constexpr uint32_t PR = WPT / 4;
-        for (uint32_t i = t; i < nr * PR; i += T) {
-          const uint32_t rr = i / PR, w4 = (i % PR) * 4u;
-          const uint64_t gw = gw0 + w4;
-          uint4 v;
-          if (r0 < R) {
-            const uint32_t* src = TILE + (r0 + rr) * STR + w4;
-            v = make_uint4(src[0], src[1], src[2], src[3]);
-          } else {
-            v = make_uint4(~0u, ~0u, ~0u, ~0u);
-          }
-          if (!full) {
-            if (gw >= L.row_words32) continue;  // gw + 3 is in range too
-            v.x &= valid(gw);
-            v.y &= valid(gw + 1);
-            v.z &= valid(gw + 2);
-            v.w &= valid(gw + 3);
-          }
-          *reinterpret_cast<uint4*>(base + (size_t)rr * L.row_words32 + gw) = v;
-        }
+        *reinterpret_cast<uint4*>(dst) = v;
       } else {
-        constexpr uint32_t PR = WPT / 2;
-        for (uint32_t i = t; i < nr * PR; i += T) {
-          const uint32_t rr = i / PR, w2 = (i % PR) * 2u;
-          const uint64_t gw = gw0 + w2;
-          if (gw >= L.row_words32) continue;  // row_words32 is even
-          uint2 v = r0 < R ? make_uint2(TILE[(r0 + rr) * STR + w2], TILE[(r0 + rr) * STR + w2 + 1])
-                           : make_uint2(~0u, ~0u);
-          v.x &= valid(gw);
-          v.y &= valid(gw + 1);
-          *reinterpret_cast<uint2*>(base + (size_t)rr * L.row_words32 + gw) = v;
-        }
+        *reinterpret_cast<uint2*>(dst) = make_uint2(v.x, v.y);
+        if (gw + 2 < L.row_words32) *reinterpret_cast<uint2*>(dst + 2) = make_uint2(v.z, v.w);
       }
     };
-    if (L.flags & LF_OUT_MEAS) write_rows(L.meas, 0, p.n_meas);
-    if (L.flags & LF_OUT_DET) write_rows(L.det, p.n_meas, p.n_det);
-    if (L.flags & LF_OUT_OBS) write_rows(L.obs, n_det_end, p.n_obs);
-    if (L.flags & LF_OUT_KEPT) write_rows(L.kept, R, 1);
+    {
+      const uint32_t qd = lane % QPL, cw = lane / QPL;
+      const uint64_t gw = gw0 + 4u * qd;
+      // the delta at position j with its row's constant and random-bit
+      // terms added (x: the tile's cell, already read; the cell is cleared)
+      auto term = [&](uint32_t j, uint4 x) -> uint4 {
+        const uint32_t ri = RI[j];
+        const uint32_t cm = 0u - (ri & 1u);
+        x.x ^= cm;
+        x.y ^= cm;
+        x.z ^= cm;
+        x.w ^= cm;
+        const uint32_t ne = (ri >> 1) & 127u;
+        for (uint32_t e = ri >> 8, e1 = (ri >> 8) + ne; e < e1; e++) {
+          const uint4 m = *reinterpret_cast<const uint4*>(MW + __ldg(p.aff_rowev + e) * WPT + 4u * qd);
+          x.x ^= m.x;
+          x.y ^= m.y;
+          x.z ^= m.z;
+          x.w ^= m.w;
+        }
+        return x;
+      };
+      auto cell = [&](uint32_t j) -> uint4* { return reinterpret_cast<uint4*>(TILE + j * WPT) + qd; };
+      auto emit = [&](uint32_t j, uint4 v) {
+        uint32_t* dst = ROWP[j];
+        if (dst) put(dst + gw, gw, v);
+      };
+      const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+      // chains of two or more rows: lane slot cw of warp w walks chain
+      // w * CPW + cw + k * NWARP * CPW down its positions, keeping the running
+      // XOR of the deltas
+      const uint32_t n_long = SR[NWARP + 1];
+      for (uint32_t c = warp * CPW + cw; c < n_long; c += NWARP * CPW) {
+        const uint32_t j1 = CHOFF[c + 1];
+        uint4 v = zero;
+        for (uint32_t j = CHOFF[c]; j < j1; j++) {
+          const uint4 x = term(j, *cell(j));
+          *cell(j) = zero;
+          v.x ^= x.x;
+          v.y ^= x.y;
+          v.z ^= x.z;
+          v.w ^= x.w;
+          emit(j, v);
+        }
+      }
+      // rows on no chain: CPW of them per step, this warp's steps, two steps
+      // per pass (both cells read before either is cleared)
+      {
+        const uint32_t j0 = CHOFF[n_long] + cw, q1 = SR[warp + 1];
+        uint32_t q = SR[warp];
+        for (; q + 2 <= q1; q += 2) {
+          const uint32_t ja = j0 + q * CPW, jb = ja + CPW;
+          const bool oa = ja < R, ob = jb < R;
+          uint4 xa = zero, xb = zero;
+          if (oa) xa = *cell(ja);
+          if (ob) xb = *cell(jb);
+          if (oa) *cell(ja) = zero;
+          if (ob) *cell(jb) = zero;
+          if (oa) emit(ja, term(ja, xa));
+          if (ob) emit(jb, term(jb, xb));
+        }
+        if (q < q1) {
+          const uint32_t j = j0 + q * CPW;
+          if (j < R) {
+            const uint4 x = *cell(j);
+            *cell(j) = zero;
+            emit(j, term(j, x));
+          }
+        }
+      }
+      // the kept row: every shot of the tile
+      if ((L.flags & LF_OUT_KEPT) && t < QPL)
+        put(L.kept + gw0 + 4u * t, gw0 + 4u * t, make_uint4(~0u, ~0u, ~0u, ~0u));
+    }
     if (t == 0 && (uint64_t)tile * S < L.shots) {
       const uint64_t left = L.shots - (uint64_t)tile * S;
       atomicAdd(L.kept_count, (unsigned long long)(left < S ? left : S));
@@ -433,13 +508,13 @@ __global__ void __launch_bounds__(kAffTpw * WPT, 65536 / (kAffTpw * WPT * 64)) s
   }
 }
 
-// Shared memory of one CTA: the record tile
-// (with its scratch row and padding word), the random-bit words and one
-// chunk list per warp.
+// Shared memory of one CTA: the record tile, the random-bit words, one
+// chunk list per warp, the output row pointers, row info, the warps' step
+// ranges, 32 dump words and the chain offsets.
 size_t affine_smem_bytes(const DevProg& p, uint32_t wpt) {
-  const size_t o_mw = ((size_t)(wpt + 1) * (p.aff_rows + 1) + 3) & ~(size_t)3;
-  const size_t staged = (size_t)p.aff_rows + 1 + ((size_t)p.aff_n_chain_rows + 1) / 2 + ((size_t)p.aff_n_chains + 2) / 2;
-  return 4 * (o_mw + (size_t)wpt * p.aff_n_rand + (size_t)(wpt * kAffTpw / 32) * kAffList + staged);
+  const size_t R = p.aff_rows, nwarp = wpt * kAffTpw / 32;
+  const size_t staged = 2 * R + R + (nwarp + 2) + 32 + ((size_t)p.aff_n_chains + 2) / 2;
+  return 4 * (R * wpt + (size_t)wpt * p.aff_n_rand + nwarp * kAffList + staged);
 }
 
 template <int WPT>

@@ -474,7 +474,8 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
       NC_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
       // with the item passes overlapped, the tile kernel keeps one CTA of
       // 512 threads per SM so that an item-pass CTA fits beside it
-      const bool items = tu.AI && !(lflags & LF_NOISELESS) && h.n_sites > 0;
+      // (item lists name first chunks below 2^18: affine_kernel.cu fault_item)
+      const bool items = tu.AI && !(lflags & LF_NOISELESS) && h.n_sites > 0 && h.aff_n_chunks < (1u << 18);
       const bool overlap = items && tu.AO;
       uint32_t wpt = 0;
       int best_warps = 0, best_ctas = 0;

@@ -129,8 +129,8 @@ struct ProgHeader {
   uint32_t aff_n_chunks;           // 8-row chunks of the fault columns
   float aff_chunks_per_shot;       // expected chunks of a shot's faults
   uint32_t n_guide;                // survival guide-table entries
-  uint32_t aff_n_chains;           // delta-row chains of two or more rows
-  uint32_t aff_n_chain_rows;       // rows on those chains
+  uint32_t aff_n_chains;           // delta-row chains (every row on one; longest first)
+  uint32_t aff_n_chain_rows;       // rows on those chains (= aff_rows)
   uint32_t n_probes;               // expectation-value probes (OP_EXPVAL rows)
   // shared prefix: ops [0, prefix_end) are frame / array / rotation
   // instructions only (no noise, measurement or record), so every shot
@@ -183,12 +183,15 @@ inline uint32_t guide_key(uint64_t t, uint32_t shift) {
 // the rows flipped by fault option f = site * kRecPerSite + option.
 //   const: u32 per row (0 / 1); rowev_off: rows + 1 u32; rowev: u32 ordinals
 //   rand_ev: u32 event per ordinal; col_off: n_sites * kRecPerSite + 1 u32
-//   chunk offsets; col: chunks of 8 u16 rows (16 bytes), each column's rows
-//   ascending and padded with row index `rows` (a scratch row).
+//   chunk offsets; col: chunks of 8 u16 chain positions (16 bytes), padded
+//   with `rows` (no row).
 //   Rows are stored in delta form: the value above is delta_r, and the
 //   record row is delta_r ^ (record row parent[r]) (parent 0xFFFFFFFF: none);
-//   chain_off / chain list each chain of two or more rows head first, so a
-//   running XOR down a chain turns deltas into rows. Detector and
+//   chain_off / chain list the chains head first, every row on exactly one
+//   (rows with neither parent nor child are chains of one), longest first;
+//   position j of the concatenated list holds row chain[j], and the sampler
+//   keeps row chain[j] at position j of its tile. A running XOR down a chain
+//   turns deltas into rows. Detector and
 //   observable reference parities apply to record rows, so delta_r takes
 //   ref(r) ^ ref(parent[r]).
 //   frec: 16 bytes per site, so that one load after the search gives a
@@ -208,7 +211,7 @@ constexpr uint32_t kRecPerSite = 15;
 // row): its fault flips the slot and, if the shot is kept, the output bit.
 
 constexpr uint32_t kMagic = 0x4E435047u;  // "NCPG"
-constexpr uint32_t kVersion = 13;
+constexpr uint32_t kVersion = 14;
 constexpr uint32_t kMaxK = 30;
 constexpr uint32_t kMaxQubits = 4096;
 

@@ -70,6 +70,9 @@ def _tables(blob: bytes):
     for ch in chains:  # chains follow parent links, head first
         assert parent[ch[0]] == 0xFFFFFFFF
         assert all(parent[ch[j]] == ch[j - 1] for j in range(1, len(ch)))
+    # every row on exactly one chain, longest chains first
+    assert sorted(int(r) for ch in chains for r in ch) == list(range(rows))
+    assert all(len(chains[i]) >= len(chains[i + 1]) for i in range(len(chains) - 1))
     return {
         "chains": chains,
         "rows": rows, "n_meas": n_meas, "n_det": n_det,
@@ -87,12 +90,13 @@ def _rows(t, faults, m):
     for r in range(t["rows"]):
         for e in t["rowev"][t["rowev_off"][r]:t["rowev_off"][r + 1]]:
             v[r] ^= m[e]
+    pos_row = np.concatenate(t["chains"])  # chunk entries are chain positions
     for site, opt in faults.items():
         c = site * REC_PER_SITE + opt
         for ch in t["chunks"][t["col_off"][c]:t["col_off"][c + 1]]:
-            for r in ch:
-                if r != t["rows"]:  # padding entries name the scratch row
-                    v[r] ^= 1
+            for j in ch:
+                if j != t["rows"]:  # padding entries
+                    v[pos_row[j]] ^= 1
     for ch in t["chains"]:  # delta rows to record rows
         acc = 0
         for r in ch:
