@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnc.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["compiler.cpp", "affine.cpp", "fuse.cpp", "strata.cpp", "kernels.cu", "affine_kernel.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["compiler.cpp", "affine.cpp", "fuse.cpp", "strata.cpp", "kernels.cu", "affine_kernel.cu", "capi.cu", "noalloc.cu", "warp_kernel.cu"]
 HEADERS = ["program.h", "compiler.h", "kernels.cuh"]
 
 

@@ -32,6 +32,10 @@ cudaError_t launch_presample(const LaunchParams& L, cudaStream_t st);
 cudaError_t launch_prefix(const Op* host_ops, uint32_t n, bool fp64, void* vec, int n_sm, cudaStream_t st,
                           uint32_t* launches);
 size_t affine_smem_bytes(const DevProg& p, uint32_t wpt);
+bool warp_supported(const DevProg& p);
+size_t warp_smem_bytes(const DevProg& p, bool fp64, uint32_t nwarps);
+cudaError_t launch_warp(const LaunchParams& L, bool fp64, uint32_t nwarps, uint32_t grid, size_t smem,
+                        cudaStream_t st, int* per_sm);
 cudaError_t launch_affine(const LaunchParams& L, uint32_t wpt, uint32_t grid, size_t smem, cudaStream_t st,
                           int* per_sm);
 cudaError_t launch_affine_items(const LaunchParams& L, uint32_t tile0, uint32_t n_tiles, uint32_t* items,
@@ -201,6 +205,8 @@ struct Tuning {
   uint32_t G, T, W, B, A, AW, AI, AV, AC, PS, AO;  // PS = 1: pre-sample faults even for small calls
   uint32_t SW = 1;                                 // SW = 0: active vectors never in shared memory
   uint32_t PX = 1;  // shared prefix: 0 off, 1 when it saves enough traffic, 2 whenever it has array work
+  uint32_t LW = 0;  // 1: warp-per-shot layout (exec_warp) for programs with active axes
+  uint32_t WN = 0;  // its warps per CTA (0: 8, fewer if the vectors do not fit)
 };
 
 Tuning choose_tuning(const DevProg& d, const char* tune, uint64_t shots, int n_sm) {
@@ -229,6 +235,8 @@ Tuning choose_tuning(const DevProg& d, const char* tune, uint64_t shots, int n_s
       else if (sscanf(s, "ao=%u", &v) == 1) t.AO = v;
       else if (sscanf(s, "sw=%u", &v) == 1) t.SW = v;
       else if (sscanf(s, "px=%u", &v) == 1) t.PX = v;
+      else if (sscanf(s, "lw=%u", &v) == 1) t.LW = v;
+      else if (sscanf(s, "wn=%u", &v) == 1) t.WN = v;
       const char* c = strchr(s, ',');
       if (!c) break;
       s = c + 1;
@@ -563,6 +571,28 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
             tm->launches += 1;
           }
           if (overlap) NC_TRY(cudaEventRecord(ev.ev[3 + bsel], stream));
+        }
+        return NC_OK;
+      }
+    }
+    // warp-per-shot layout: one warp per shot, its vector in shared memory
+    if (tu.LW == 1 && h.k_max > 0 && warp_supported(L.p)) {
+      const bool fp64w = precision == NC_FP64_BATCHED;
+      uint32_t nw = tu.WN ? std::min<uint32_t>(tu.WN, 8) : 8;
+      while (nw > 1 && warp_smem_bytes(L.p, fp64w, nw) > 200 * 1024) nw--;
+      const size_t smem = warp_smem_bytes(L.p, fp64w, nw);
+      int per_sm = 0;
+      if (smem <= 227 * 1024 && launch_warp(L, fp64w, nw, 0, smem, stream, &per_sm) == cudaSuccess && per_sm > 0) {
+        int n_sm = 0, dev = 0;
+        NC_TRY(cudaGetDevice(&dev));
+        NC_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+        const uint64_t grid = std::min<uint64_t>(L.row_words32, (uint64_t)per_sm * n_sm);
+        if (grid == 0) return NC_OK;
+        if (tm) NC_TRY(tm->begin(stream));
+        NC_TRY(launch_warp(L, fp64w, nw, (uint32_t)grid, smem, stream, nullptr));
+        if (tm) {
+          NC_TRY(tm->end(stream));
+          tm->launches += 1;
         }
         return NC_OK;
       }

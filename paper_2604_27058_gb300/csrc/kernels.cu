@@ -1051,13 +1051,10 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
                   size_t i0 = (size_t)insert0(j, pa) * S + s, i1 = i0 + ((size_t)1 << pa) * S;
                   C u = work[i0], v = work[i1];
                   if (xm) {
-                    double ux = u.x, uy = u.y, vx = v.x, vy = v.y;
-                    double px = ux + vx, py = uy + vy, mx = ux - vx, my = uy - vy;
-                    a0 += 0.5 * (px * px + py * py);
-                    a1 += 0.5 * (mx * mx + my * my);
+                    mterm_x(u, v, a0, a1);
                   } else {
-                    a0 += cnorm2(u);
-                    a1 += cnorm2(v);
+                    a0 += mterm(u);
+                    a1 += mterm(v);
                   }
                 }
                 atomicAdd(&RED[s], a0);

@@ -249,6 +249,27 @@ __device__ __forceinline__ uint32_t next_fault_r(const DevProg& p, uint64_t seed
   return (i << 4) | __umulhi(wz, k);
 }
 
+// Terms of the measurement sums S_0, S_1 (App. B.2), accumulated in FP64 by
+// the caller. With FP32 amplitudes a term is formed in FP32 (|a|^2 as one
+// product and one fused multiply-add: at most two roundings, relative error
+// below 2^-23 per term, which does not accumulate since every term is
+// non-negative) and converted once; with FP64 amplitudes it is formed in FP64.
+// The FP64 units are the scarce ones on this GPU, so this keeps one
+// conversion and one FP64 add per amplitude in the FP32 form.
+__device__ __forceinline__ double mterm(float2 a) { return (double)fmaf(a.x, a.x, a.y * a.y); }
+__device__ __forceinline__ double mterm(double2 a) { return a.x * a.x + a.y * a.y; }
+// X measurement: the folds (u + v) / sqrt 2 and (u - v) / sqrt 2, squared.
+__device__ __forceinline__ void mterm_x(float2 u, float2 v, double& a0, double& a1) {
+  const float px = u.x + v.x, py = u.y + v.y, mx = u.x - v.x, my = u.y - v.y;
+  a0 += (double)(0.5f * fmaf(px, px, py * py));
+  a1 += (double)(0.5f * fmaf(mx, mx, my * my));
+}
+__device__ __forceinline__ void mterm_x(double2 u, double2 v, double& a0, double& a1) {
+  const double px = u.x + v.x, py = u.y + v.y, mx = u.x - v.x, my = u.y - v.y;
+  a0 += 0.5 * (px * px + py * py);
+  a1 += 0.5 * (mx * mx + my * my);
+}
+
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
   unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");

@@ -52,7 +52,7 @@ def _check(nc, text, shots, seed, precision, tune=None, postselect=False, shot_i
 
 
 @pytest.mark.parametrize("precision,tune", [("fp32", None), ("fp32", "g=2,t=64"), ("fp64", None),
-                                            ("fp64_batched", None)])
+                                            ("fp64_batched", None), ("fp32", "lw=1"), ("fp64_batched", "lw=1")])
 @pytest.mark.parametrize("seed", range(4))
 def test_random_circuits_with_probes(nc, seed, precision, tune):
     text = gc.with_probes(gc.random_small(900 + seed, n=6, n_ops=90, p_noise=0.05, t_frac=0.3), seed, count=10)
@@ -71,12 +71,12 @@ def test_closed_forms(nc, precision):
     assert np.max(np.abs(ev - np.array(want)[:, None])) <= TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_low_magic_postselected_probes(nc, precision):
+@pytest.mark.parametrize("precision,tune", [("fp32", None), ("fp64", None), ("fp32", "lw=1")])
+def test_low_magic_postselected_probes(nc, precision, tune):
     """Probes in the postselected low-magic workload: a shot rejected before
     a probe reports 0 there."""
     text = gc.with_probes(gc.low_magic_gadgets(), 5, count=6, max_weight=4)
-    n, ev = _check(nc, text, 150, 4004, precision, postselect=True)
+    n, ev = _check(nc, text, 150, 4004, precision, tune=tune, postselect=True)
     assert n >= 145
 
 

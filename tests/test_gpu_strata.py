@@ -68,7 +68,7 @@ def test_surface_code_strata_bit_exact(nc, kk, precision, tune):
 
 @pytest.mark.parametrize("kk", [0, 2, 5])
 @pytest.mark.parametrize("precision,tune", [("fp32", None), ("fp32", "g=32,t=256"), ("fp32", "g=2,t=64"),
-                                            ("fp64", None), ("fp64_batched", None)])
+                                            ("fp64", None), ("fp64_batched", None), ("fp32", "lw=1")])
 def test_tiny_workload_strata(nc, kk, precision, tune):
     """Active axes (k_max <= 6): the batched executor with per-shot fault
     lists (default), with bucketed faults (g=32,t=256), FP64 forms."""
@@ -83,13 +83,13 @@ def test_tiny_workload_strata(nc, kk, precision, tune):
     assert n_ok + flagged == len(range(0, shots, 3))
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_low_magic_strata_postselected(nc, precision):
+@pytest.mark.parametrize("precision,tune", [("fp32", None), ("fp64", None), ("fp32", "lw=1")])
+def test_low_magic_strata_postselected(nc, precision, tune):
     text = gc.low_magic_gadgets()
     prog = nc.compile(text)
     sim = FactoredSim(text)
     shots, seed, kk = 200, 4004, 2
-    g = gpu_records(prog, shots, seed, precision=precision, postselect=True, stratum=kk)
+    g = gpu_records(prog, shots, seed, precision=precision, tune=tune, postselect=True, stratum=kk)
     n_ok, flagged = compare(sim, g, range(shots), seed, postselect=True, faults=_faults(sim, seed, kk))
     assert flagged <= 3
     assert g["shots_kept"] == int(g["kept"].sum())
