@@ -149,17 +149,32 @@ typedef struct {
  * message is written to err (if err_len > 0). The text is not retained. */
 nc_status nc_compile(const char* text, size_t len, nc_program** out, char* err, size_t err_len);
 
-/* Compile flags. The compiler's HIR passes (Sec. 3.1, stage 2) change the
- * bytecode, the k-schedule and the intermediate states, never a probability
- * or a record; each flag turns one pass off, so that a program can be
- * compared step by step with a plain run of the method (App. B).
- *   NC_COMPILE_NO_PEEPHOLE: keep every rotation. By default a Z rotation
- *     (T, T_DAG, R_Z) whose qubit's next instruction, other Z rotations
- *     aside, is a Z measurement or reset (or an R_X followed likewise by MX)
- *     is dropped: pushed past that measurement it acts on an eigenstate and
- *     contributes a phase per outcome branch only. */
+/* Compile flags. The compiler's HIR passes (Sec. 3.1, stage 2) act on every
+ * active operation written as a Pauli of the t = 0 frame (the Heisenberg
+ * image through the physical Cliffords before it); two operations commute iff
+ * their Paulis do. The passes change the bytecode, the k-schedule and the
+ * intermediate states, never a probability or a record; each flag turns one
+ * pass off, so that a program can be compared step by step with a plain run
+ * of the method (App. B). NC_COMPILE_PLAIN turns them all off.
+ *   NC_COMPILE_NO_PEEPHOLE: keep every rotation. By default a rotation whose
+ *     axis is measured later, with every operation in between commuting with
+ *     it (for instance a T before its qubit's Z measurement), is dropped: next
+ *     to the measurement it contributes a phase per outcome branch only.
+ *   NC_COMPILE_NO_REORDER: keep circuit order. By default a measurement moves
+ *     ahead of the rotations it commutes with, and a rotation after the
+ *     measurements it commutes with, so the active dimension contracts
+ *     before it grows; noise sites keep their order, measurements keep their
+ *     place among detectors, nothing passes an EXPVAL probe.
+ *   NC_COMPILE_NO_FUSE: no phase fusion. By default two rotations about the
+ *     same axis with only commuting operations between them become one (T T
+ *     is one pi/4 rotation), and a rotation whose angle is then a multiple of
+ *     pi/4 (a Clifford, a Pauli or the identity, e.g. T T_DAG) leaves the list
+ *     after conjugating every later operation. */
 #define NC_COMPILE_NO_PEEPHOLE 1u
-#define NC_COMPILE_FLAGS_ALL 1u
+#define NC_COMPILE_NO_REORDER 2u
+#define NC_COMPILE_NO_FUSE 4u
+#define NC_COMPILE_PLAIN 7u
+#define NC_COMPILE_FLAGS_ALL 7u
 
 /* nc_compile with compile flags (NC_COMPILE_* bits; nc_compile passes 0).
  * An unknown flag bit is NC_E_ARG. */

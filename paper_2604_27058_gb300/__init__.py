@@ -68,14 +68,16 @@ class Program:
             self._h = None
 
 
-def compile(text: str, peephole: bool = True) -> Program:  # noqa: A001 - mirrors nc_compile
-    """nc_compile_ex; peephole=False sets NC_COMPILE_NO_PEEPHOLE (every
-    rotation kept, so the k-schedule and intermediate states are those of the
-    plain method)."""
+def compile(text: str, peephole: bool = True, flags: int | None = None) -> Program:  # noqa: A001 - mirrors nc_compile
+    """nc_compile_ex. peephole=False compiles the plain method
+    (NC_COMPILE_PLAIN: no HIR pass, so the k-schedule and intermediate states
+    are those of App. B); flags, when given, are the NC_COMPILE_* bits
+    themselves."""
     data = text.encode()
     h = ctypes.c_void_p()
     err = ctypes.create_string_buffer(512)
-    flags = 0 if peephole else _nc.NC_COMPILE_NO_PEEPHOLE
+    if flags is None:
+        flags = 0 if peephole else _nc.NC_COMPILE_PLAIN
     code = _nc.lib().nc_compile_ex(data, len(data), flags, ctypes.byref(h), err, 512)
     _nc.check(code, err.value.decode(errors="replace"))
     return Program(h.value)

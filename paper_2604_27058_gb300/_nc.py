@@ -26,6 +26,9 @@ NC_OUT_EXPVAL = 32
 NC_NOALLOC_SCRATCH_BYTES = 64 << 20
 NC_OUT_ALL = NC_OUT_MEAS | NC_OUT_DET | NC_OUT_OBS | NC_OUT_KEPT | NC_OUT_EXPVAL
 NC_COMPILE_NO_PEEPHOLE = 1
+NC_COMPILE_NO_REORDER = 2
+NC_COMPILE_NO_FUSE = 4
+NC_COMPILE_PLAIN = 7
 NC_PS_NONE = 0
 NC_PS_ALL_DETECTORS = 1
 

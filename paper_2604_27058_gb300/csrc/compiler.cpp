@@ -585,6 +585,18 @@ struct Compiler {
     return acc;
   }
 
+  // M(P) for a Pauli P = i^ph X^x Z^z given by its bits (the images of its
+  // X factors, then of its Z factors, in that order).
+  Pauli map_pauli(const Pauli& q) const {
+    Pauli acc(nw64);
+    acc.ph = q.ph & 3;
+    for (int j = 0; j < n; j++)
+      if (q.xb(j)) pmul_inplace(acc, img[2 * j]);
+    for (int j = 0; j < n; j++)
+      if (q.zb(j)) pmul_inplace(acc, img[2 * j + 1]);
+    return acc;
+  }
+
   Pauli map_letter(int q, char l) {
     // X = X, Z = Z, Y = i X Z
     if (l == 'X') return map_local({q}, 1, 0, 0);
@@ -747,38 +759,17 @@ struct Compiler {
     code.push_back({o, u, -1});
   }
 
-  // Virtual masks of the K options of a noise site acting on physical qubits.
-  uint32_t noise_masks(uint8_t kind, int q0, int q1) {
-    static const char* letters = "IXYZ";
+  // Virtual masks of the K options of a noise site, each given as a Pauli of
+  // the HIR frame.
+  uint32_t noise_masks(const std::vector<Pauli>& opts) {
     uint32_t off = (uint32_t)masks.size();
-    auto put_letters = [&](char la, char lb) {
-      Pauli acc(nw64);
-      if (la != 'I') pmul_inplace(acc, map_letter(q0, la));
-      if (lb != 'I') pmul_inplace(acc, map_letter(q1, lb));
-      add_mask(acc, true, true);
-    };
-    switch (kind) {
-      case SITE_X: put_letters('X', 'I'); break;
-      case SITE_Y: put_letters('Y', 'I'); break;
-      case SITE_Z: put_letters('Z', 'I'); break;
-      case SITE_D1: put_letters('X', 'I'); put_letters('Y', 'I'); put_letters('Z', 'I'); break;
-      case SITE_D2:
-        for (int j = 1; j < 16; j++) put_letters(letters[j >> 2], letters[j & 3]);
-        break;
-    }
+    for (const Pauli& o : opts) add_mask(map_pauli(o), true, true);
     return off;
   }
 
-  void rotation(const PhysOp& o) {
-    char letter = 'Z';
-    double theta;
-    if (o.name == "T") theta = M_PI / 8;
-    else if (o.name == "T_DAG") theta = -M_PI / 8;
-    else {
-      letter = o.name.back();
-      theta = o.arg / 2.0;
-    }
-    Pauli p = map_letter(o.q0, letter);
+  // exp(-i theta P) for P given in the HIR frame.
+  void rotation(const Pauli& hp, double theta) {
+    Pauli p = map_pauli(hp);
     char kind;
     int a;
     int v = localize(p, kind, a);
@@ -812,12 +803,11 @@ struct Compiler {
 
   // Expectation-value probe (Sec. 3.2): M(P) for the product P; the frame
   // sign and the active-vector reduction are per shot (OP_EXPVAL).
-  void probe(const PhysOp& o) {
-    Pauli p(nw64);
-    for (size_t j = 0; j < o.recs.size(); j++) pmul_inplace(p, map_letter((int)o.recs[j], o.name[j]));
+  void probe(const Pauli& hp, int64_t index) {
+    Pauli p = map_pauli(hp);
     Op e = mk(OP_EXPVAL);
     e.i0 = add_mask(p, true, true);
-    e.i3 = (uint32_t)o.index;
+    e.i3 = (uint32_t)index;
     e.pa = (uint8_t)(p.ph & 3);
     for (int q = 0; q < n; q++) {
       if (pos_of[q] < 0) {
@@ -831,8 +821,9 @@ struct Compiler {
     emit(e);
   }
 
-  void measure(const PhysOp& o, std::vector<int64_t>& flips_of_instr) {
-    Pauli p = map_letter(o.q0, o.xbasis ? 'X' : 'Z');
+  // Measurement of hp (HIR frame); a reset adds the conditional Pauli he.
+  void measure(const PhysOp& o, const Pauli& hp, const Pauli& he) {
+    Pauli p = map_pauli(hp);
     int64_t id = next_id++;
     bool active_z = false;
     for (int q = 0; q < n && !active_z; q++)
@@ -886,15 +877,14 @@ struct Compiler {
       }
     }
     if (o.reset) {
-      Pauli e = map_letter(o.q0, 'X');
+      Pauli e = map_pauli(he);
       Op f = mk(OP_FEEDFORWARD);
       f.i0 = add_mask(e, true, true);
       emit(f, {id}, -1);
     }
     if (o.record >= 0) {
-      if ((int64_t)record_id.size() != o.record) fail(9, "record numbering");
-      record_id.push_back(id);
-      if (o.site >= 0) flips_of_instr.push_back(o.site);
+      if (o.record >= (int64_t)record_id.size() || record_id[o.record] >= 0) fail(9, "record numbering");
+      record_id[o.record] = id;
     }
   }
 };
@@ -946,6 +936,214 @@ std::vector<uint32_t> mask_planes(const std::vector<uint32_t>& masks, uint32_t o
 }
 
 // ---------------------------------------------------------------------------
+// HIR (Sec. 3.1, stages 1-2): every active operation as a Pauli of the t = 0
+// frame, P -> U^dagger P U with U the physical Cliffords before it (Def. 1).
+// The back end localises the list in order; its U_C then holds only the
+// localising Cliffords, and mapping through it gives the same Pauli as one
+// walk through physical gates and localisations together, so an untouched
+// list compiles to the same bytecode. Two operations commute iff their Paulis
+// do (symplectic parity), which is all the passes below use.
+// ---------------------------------------------------------------------------
+namespace {
+
+enum HKind : uint8_t { H_ROT, H_MEAS, H_FLIP, H_NOISE, H_FF, H_DET, H_OBS, H_PROBE };
+
+struct Hir {
+  HKind kind = H_ROT;
+  uint32_t src = 0;         // physical operation (Flattener::ops index)
+  Pauli p;                  // rotation axis, measured, feed-forward or probe Pauli
+  Pauli e;                  // R / MR: the conditional X after the measurement
+  std::vector<Pauli> opts;  // noise options
+  double theta = 0.0;       // rotation exp(-i theta p)
+  bool reset = false;
+  int64_t rec = -1;         // record written (MEAS) or read (FLIP, FF)
+  bool dead = false;
+};
+
+constexpr size_t kHirScan = 1u << 16;  // longest stretch a pass looks through
+
+bool commute(const Pauli& a, const Pauli& b) {
+  int c = 0;
+  for (size_t w = 0; w < a.x.size(); w++) c += popc64((a.x[w] & b.z[w]) ^ (a.z[w] & b.x[w]));
+  return (c & 1) == 0;
+}
+
+bool same_axis(const Pauli& a, const Pauli& b) { return a.x == b.x && a.z == b.z; }
+
+// f on every Pauli through which h acts on the state (none for the
+// classical operations); false as soon as f is.
+template <class F>
+bool each_pauli(const Hir& h, F f) {
+  switch (h.kind) {
+    case H_ROT: case H_FF: case H_PROBE: return f(h.p);
+    case H_MEAS: return f(h.p) && (!h.reset || f(h.e));
+    case H_NOISE:
+      for (const Pauli& o : h.opts)
+        if (!f(o)) return false;
+      return true;
+    default: return true;
+  }
+}
+
+bool reads_record(const Hir& h, int64_t r, const std::vector<PhysOp>& ops) {
+  if (r < 0) return false;
+  if (h.kind == H_FLIP || h.kind == H_FF) return h.rec == r;
+  if (h.kind == H_DET || h.kind == H_OBS) {
+    const auto& rs = ops[h.src].recs;
+    return std::find(rs.begin(), rs.end(), r) != rs.end();
+  }
+  return false;
+}
+
+// a and b, adjacent, may trade places without changing a probability, a
+// state that is later observed, or a record.
+bool swappable(const Hir& a, const Hir& b, const std::vector<PhysOp>& ops) {
+  if (a.dead || b.dead) return true;
+  // a probe reads the state where it stands
+  if (a.kind == H_PROBE || b.kind == H_PROBE) return false;
+  // noise sites keep their order (the survival sampler visits them so)
+  const bool na = a.kind == H_NOISE || a.kind == H_FLIP, nb = b.kind == H_NOISE || b.kind == H_FLIP;
+  if (na && nb) return false;
+  // measurements keep their place among detectors: a shot rejected by
+  // postselection has zero records after its failing detector
+  // measurements keep their order: a draw is compared with the outcome's
+  // probability given the outcomes before it, so two correlated commuting
+  // measurements swapped give other records for the same draws
+  const bool ma = a.kind == H_MEAS, mb = b.kind == H_MEAS;
+  if (ma && mb) return false;
+  if ((ma && (b.kind == H_DET || b.kind == H_OBS)) || (mb && (a.kind == H_DET || a.kind == H_OBS))) return false;
+  if ((ma && reads_record(b, a.rec, ops)) || (mb && reads_record(a, b.rec, ops))) return false;
+  return each_pauli(a, [&](const Pauli& pa) { return each_pauli(b, [&](const Pauli& pb) { return commute(pa, pb); }); });
+}
+
+// Phase fusion: a rotation about the axis of an earlier one, everything in
+// between commuting with it, joins that one (angles add; opposite signs of
+// the two Paulis subtract).
+bool hir_fuse(std::vector<Hir>& L, const std::vector<PhysOp>& ops) {
+  bool changed = false;
+  for (size_t i = 0; i < L.size(); i++) {
+    Hir& r = L[i];
+    if (r.dead || r.kind != H_ROT) continue;
+    size_t steps = 0;
+    for (size_t j = i; j-- > 0 && steps < kHirScan;) {
+      Hir& o = L[j];
+      if (o.dead) continue;
+      steps++;
+      if (o.kind == H_ROT && same_axis(o.p, r.p)) {
+        const int d = ((r.p.ph - o.p.ph) % 4 + 4) % 4;  // r.p = i^d o.p, d = 0 or 2
+        o.theta += d == 0 ? r.theta : -r.theta;
+        r.dead = true;
+        changed = true;
+        break;
+      }
+      if (!swappable(o, r, ops)) break;
+    }
+  }
+  return changed;
+}
+
+// Q <- C^dagger Q C on every Pauli of h, C = exp(-i m pi/4 P), m = 1, 2, 3.
+// For Q anticommuting with P, C^dagger Q C = exp(i m pi/2 P) Q: -Q for
+// m = 2, -i Q P for m = 1 and i Q P for m = 3 (3 pi/4 = -pi/4 up to a global
+// phase).
+void hir_conjugate(Hir& h, const Pauli& P, int m) {
+  auto f = [&](Pauli& q) {
+    if (commute(q, P)) return;
+    if (m == 2) {
+      q.ph = (q.ph + 2) & 3;
+      return;
+    }
+    pmul_inplace(q, P);
+    q.ph = (q.ph + (m == 1 ? 3 : 1)) & 3;
+  };
+  switch (h.kind) {
+    case H_ROT: case H_FF: case H_PROBE: f(h.p); break;
+    case H_MEAS:
+      f(h.p);
+      if (h.reset) f(h.e);
+      break;
+    case H_NOISE:
+      for (Pauli& o : h.opts) f(o);
+      break;
+    default: break;
+  }
+}
+
+// Inverse cancellation and Clifford re-absorption: after fusion, a rotation
+// whose angle is a multiple of pi/4 is a Clifford (pi/4), a Pauli (pi/2) or
+// the identity (0, pi) up to a global phase. It is moved past every later
+// operation, each conjugated by it, and then acts after the last record:
+// it leaves the list.
+bool hir_absorb_cliffords(std::vector<Hir>& L) {
+  bool changed = false;
+  for (size_t i = 0; i < L.size(); i++) {
+    Hir& r = L[i];
+    if (r.dead || r.kind != H_ROT) continue;
+    const double q = r.theta / (M_PI / 4);
+    const double m = std::nearbyint(q);
+    if (std::fabs(q - m) > 1e-9 || std::fabs(m) > 1e9) continue;
+    const int mm = (int)((((int64_t)m) % 4 + 4) % 4);
+    r.dead = true;
+    changed = true;
+    if (mm == 0) continue;
+    for (size_t j = i + 1; j < L.size(); j++)
+      if (!L[j].dead) hir_conjugate(L[j], r.p, mm);
+  }
+  return changed;
+}
+
+// A rotation whose axis is measured later, everything in between commuting
+// with it, acts just before that measurement on a state the projector then
+// fixes: exp(-i theta P) Pi_m = e^{-+i theta} Pi_m, a phase per outcome
+// branch. It is dropped.
+void hir_absorb_into_measurements(std::vector<Hir>& L, const std::vector<PhysOp>& ops) {
+  for (size_t i = 0; i < L.size(); i++) {
+    Hir& r = L[i];
+    if (r.dead || r.kind != H_ROT) continue;
+    size_t steps = 0;
+    for (size_t j = i + 1; j < L.size() && steps < kHirScan; j++) {
+      const Hir& o = L[j];
+      if (o.dead) continue;
+      steps++;
+      if (o.kind == H_MEAS && same_axis(o.p, r.p)) {
+        r.dead = true;
+        break;
+      }
+      if (!swappable(r, o, ops)) break;
+    }
+  }
+}
+
+// Commuting reorder: measurements earlier, rotations later, so that the
+// active dimension contracts before it grows. A measurement moves before the
+// earliest rotation it can pass (every operation it passes commutes with
+// it); a rotation moves after the last measurement it can pass. Nothing
+// moves that would pass no such operation.
+void hir_reorder(std::vector<Hir>& L, const std::vector<PhysOp>& ops) {
+  L.erase(std::remove_if(L.begin(), L.end(), [](const Hir& h) { return h.dead; }), L.end());
+  for (size_t i = 0; i < L.size(); i++) {
+    if (L[i].kind != H_MEAS) continue;
+    size_t best = i;
+    for (size_t j = i, steps = 0; j-- > 0 && steps < kHirScan; steps++) {
+      if (!swappable(L[j], L[i], ops)) break;
+      if (L[j].kind == H_ROT) best = j;
+    }
+    if (best < i) std::rotate(L.begin() + best, L.begin() + i, L.begin() + i + 1);
+  }
+  for (size_t i = L.size(); i-- > 0;) {
+    if (L[i].kind != H_ROT) continue;
+    size_t best = i;
+    for (size_t j = i + 1, steps = 0; j < L.size() && steps < kHirScan; j++, steps++) {
+      if (!swappable(L[i], L[j], ops)) break;
+      if (L[j].kind == H_MEAS) best = j;
+    }
+    if (best > i) std::rotate(L.begin() + i, L.begin() + i + 1, L.begin() + best + 1);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // Entry point
 // ---------------------------------------------------------------------------
 int compile_program(const std::string& text, uint32_t flags, CompiledProgram& out, std::string& err) {
@@ -969,80 +1167,139 @@ int compile_program(const std::string& text, uint32_t flags, CompiledProgram& ou
     Flattener fl;
     fl.run(block);
 
-    Compiler c((int)fl.n_q);
-    // Flip sites of one measurement instruction are emitted together after
-    // all of its measurements (a flip changes only its record, never the
-    // frame, so deferring it past the instruction's other targets is exact).
-    std::vector<int64_t> flips;
-    int cur_instr = -2;
-    // index flip-site -> record for speed
+    // ---------------- front end: the HIR ----------------
+    // Flip sites of one measurement instruction follow all of its
+    // measurements (a flip changes only its record, never the frame, so
+    // deferring it past the instruction's other targets is exact).
+    // flip site -> its record
     std::vector<int64_t> flip_record(fl.site_p.size(), -1);
     for (auto& po : fl.ops)
       if (po.kind == K_MEAS && po.site >= 0) flip_record[po.site] = po.record;
-    auto flush_flips_fast = [&]() {
-      for (int64_t s : flips) c.noise_site(s, SITE_FLIP, fl.site_p[s], 0, c.record_id[flip_record[s]]);
-      flips.clear();
-    };
-
-    // HIR peephole (the special case of Sec. 3.1's stage-2 reordering in
-    // which a rotation pushed past its qubit's next measurement acts on an
-    // eigenstate): a Z rotation (T, T_DAG, R_Z) whose qubit's next
-    // instruction, other Z rotations aside, is a Z measurement or reset, or
-    // an R_X followed likewise by MX, only multiplies each outcome branch by
-    // a phase (the instructions in between act on other qubits and commute
-    // with it): it is dropped, with no change to any probability or state.
-    std::vector<char> dropped(fl.ops.size(), 0);
-    if (!(flags & kNoPeephole)) {
-      auto touches = [](const PhysOp& o, int q) {
-        if (o.kind == K_PROBE) return std::find(o.recs.begin(), o.recs.end(), (int64_t)q) != o.recs.end();
-        return o.q0 == q || o.q1 == q;
+    std::vector<Hir> hir;
+    {
+      Compiler fe((int)fl.n_q);  // physical Cliffords only: img = U^dagger P U
+      const int nw = fe.nw64;
+      std::vector<Hir> flips;
+      int cur_instr = -2;
+      auto letter_of = [](const PhysOp& o) {
+        return o.name == "T" || o.name == "T_DAG" ? 'Z' : o.name.back();
       };
-      auto z_rot = [](const PhysOp& o) { return o.name == "T" || o.name == "T_DAG" || o.name == "R_Z"; };
-      for (size_t i = 0; i < fl.ops.size(); i++) {
-        const PhysOp& r = fl.ops[i];
-        if (r.kind != K_ROT || (!z_rot(r) && r.name != "R_X")) continue;
-        const bool z = z_rot(r);
-        for (size_t j = i + 1; j < fl.ops.size(); j++) {
-          const PhysOp& o = fl.ops[j];
-          if (o.kind == K_DET || o.kind == K_OBS || !touches(o, r.q0)) continue;
-          if (o.kind == K_ROT && (z ? z_rot(o) : o.name == "R_X")) continue;  // commutes with r
-          if (o.kind == K_MEAS && (z ? (o.name == "M" || o.name == "MR" || o.name == "R") : o.name == "MX"))
-            dropped[i] = 1;
-          break;
+      for (size_t pi = 0; pi < fl.ops.size(); pi++) {
+        const PhysOp& po = fl.ops[pi];
+        if (!(po.kind == K_MEAS && po.instr == cur_instr)) {
+          for (auto& f : flips) hir.push_back(std::move(f));
+          flips.clear();
         }
+        cur_instr = po.kind == K_MEAS ? po.instr : -2;
+        Hir h;
+        h.src = (uint32_t)pi;
+        h.p = Pauli(nw);
+        switch (po.kind) {
+          case K_GATE:
+            fe.physical_gate(po.name, po.q0, po.q1);
+            continue;
+          case K_ROT:
+            h.kind = H_ROT;
+            h.p = fe.map_letter(po.q0, letter_of(po));
+            h.theta = po.name == "T" ? M_PI / 8 : po.name == "T_DAG" ? -M_PI / 8 : po.arg / 2.0;
+            break;
+          case K_MEAS:
+            h.kind = H_MEAS;
+            h.p = fe.map_letter(po.q0, po.xbasis ? 'X' : 'Z');
+            h.reset = po.reset;
+            if (po.reset) h.e = fe.map_letter(po.q0, 'X');
+            h.rec = po.record;
+            if (po.record >= 0 && po.site >= 0) {
+              Hir f;
+              f.kind = H_FLIP;
+              f.src = (uint32_t)pi;
+              f.rec = po.record;
+              flips.push_back(std::move(f));
+            }
+            break;
+          case K_NOISE: {
+            h.kind = H_NOISE;
+            static const char* letters = "IXYZ";
+            auto opt = [&](char la, char lb) {
+              Pauli acc(nw);
+              if (la != 'I') pmul_inplace(acc, fe.map_letter(po.q0, la));
+              if (lb != 'I') pmul_inplace(acc, fe.map_letter(po.q1, lb));
+              h.opts.push_back(acc);
+            };
+            switch (fl.site_kind[po.site]) {
+              case SITE_X: opt('X', 'I'); break;
+              case SITE_Y: opt('Y', 'I'); break;
+              case SITE_Z: opt('Z', 'I'); break;
+              case SITE_D1: opt('X', 'I'); opt('Y', 'I'); opt('Z', 'I'); break;
+              case SITE_D2:
+                for (int j = 1; j < 16; j++) opt(letters[j >> 2], letters[j & 3]);
+                break;
+            }
+            break;
+          }
+          case K_FF:
+            h.kind = H_FF;
+            h.p = fe.map_letter(po.q0, po.name[0]);
+            h.rec = po.recs[0];
+            break;
+          case K_DET: h.kind = H_DET; break;
+          case K_OBS: h.kind = H_OBS; break;
+          case K_PROBE:
+            h.kind = H_PROBE;
+            for (size_t j = 0; j < po.recs.size(); j++) pmul_inplace(h.p, fe.map_letter((int)po.recs[j], po.name[j]));
+            break;
+        }
+        hir.push_back(std::move(h));
       }
+      for (auto& f : flips) hir.push_back(std::move(f));
     }
 
+    // ---------------- middle end: HIR passes (Sec. 3.1, stage 2) ----------------
+    // Programs without rotations are left as they are (the passes act only
+    // around rotations).
+    bool any_rot = false;
+    for (const Hir& h : hir) any_rot |= h.kind == H_ROT;
+    if (any_rot) {
+      if (!(flags & kNoFuse))
+        for (int it = 0; it < 4; it++) {
+          const bool a = hir_fuse(hir, fl.ops);
+          const bool b = hir_absorb_cliffords(hir);
+          if (!a && !b) break;
+        }
+      if (!(flags & kNoPeephole)) hir_absorb_into_measurements(hir, fl.ops);
+      if (!(flags & kNoReorder)) hir_reorder(hir, fl.ops);
+    }
+
+    // ---------------- back end: localisation and bytecode ----------------
+    Compiler c((int)fl.n_q);
+    c.record_id.assign((size_t)fl.rec, -1);
     int64_t kept_id = -1;
     std::vector<int64_t> obs_id(fl.n_obs, -1);
-    for (size_t pi = 0; pi < fl.ops.size(); pi++) {
-      const PhysOp& po = fl.ops[pi];
-      if (!(po.kind == K_MEAS && po.instr == cur_instr)) flush_flips_fast();
-      cur_instr = po.kind == K_MEAS ? po.instr : -2;
-      switch (po.kind) {
-        case K_GATE:
-          c.physical_gate(po.name, po.q0, po.q1);
+    for (const Hir& h : hir) {
+      if (h.dead) continue;
+      const PhysOp& po = fl.ops[h.src];
+      switch (h.kind) {
+        case H_ROT:
+          c.rotation(h.p, h.theta);
           break;
-        case K_ROT:
-          if (!dropped[pi]) c.rotation(po);
+        case H_MEAS:
+          c.measure(po, h.p, h.e);
           break;
-        case K_MEAS:
-          c.measure(po, flips);
+        case H_FLIP:
+          c.noise_site(po.site, SITE_FLIP, fl.site_p[po.site], 0, c.record_id[po.record]);
           break;
-        case K_NOISE: {
-          uint8_t kind = fl.site_kind[po.site];
-          uint32_t eff = c.noise_masks(kind, po.q0, po.q1);
-          c.noise_site(po.site, kind, po.arg, eff, -1);
+        case H_NOISE: {
+          uint32_t eff = c.noise_masks(h.opts);
+          c.noise_site(po.site, fl.site_kind[po.site], po.arg, eff, -1);
           break;
         }
-        case K_FF: {
-          Pauli e = c.map_letter(po.q0, po.name[0]);
+        case H_FF: {
           Op f = c.mk(OP_FEEDFORWARD);
-          f.i0 = c.add_mask(e, true, true);
+          f.i0 = c.add_mask(c.map_pauli(h.p), true, true);
           c.emit(f, {c.record_id[po.recs[0]]}, -1);
           break;
         }
-        case K_DET: {
+        case H_DET: {
           Op d = c.mk(OP_DETECTOR);
           d.i3 = (uint32_t)po.index;
           std::vector<int64_t> u;
@@ -1051,10 +1308,10 @@ int compile_program(const std::string& text, uint32_t flags, CompiledProgram& ou
           c.emit(d, u, -1);
           break;
         }
-        case K_PROBE:
-          c.probe(po);
+        case H_PROBE:
+          c.probe(h.p, po.index);
           break;
-        case K_OBS: {
+        case H_OBS: {
           if (obs_id[po.index] < 0) obs_id[po.index] = c.next_id++;
           Op d = c.mk(OP_OBS_INCLUDE);
           std::vector<int64_t> u;
@@ -1066,7 +1323,6 @@ int compile_program(const std::string& text, uint32_t flags, CompiledProgram& ou
         }
       }
     }
-    flush_flips_fast();
     c.flush_outputs();
     // observables never included still get an (all-zero) accumulator
     for (int64_t o = 0; o < fl.n_obs; o++)

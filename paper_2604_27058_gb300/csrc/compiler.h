@@ -26,7 +26,9 @@ struct CompiledProgram {
 };
 
 // Compile flags (the NC_COMPILE_* bits of nc.h): each turns one HIR pass off.
-constexpr uint32_t kNoPeephole = 1u;  // keep rotations diagonal in their qubit's next measurement basis
+constexpr uint32_t kNoPeephole = 1u;  // keep rotations whose axis is measured next
+constexpr uint32_t kNoReorder = 2u;   // keep measurements and rotations in circuit order
+constexpr uint32_t kNoFuse = 4u;      // no phase fusion, cancellation or Clifford re-absorption
 
 // Returns 0 on success or an nc_status code with a message in err.
 int compile_program(const std::string& text, uint32_t flags, CompiledProgram& out, std::string& err);

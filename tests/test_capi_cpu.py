@@ -120,7 +120,13 @@ def test_compile_errors(nc, text, code):
 def test_kmax_limit(nc):
     text = "".join(f"H {q}\nT {q}\n" for q in range(31)) + "H 0\nM 0\n"
     with pytest.raises(nc.NcError) as e:
-        nc.compile(text)
+        nc.compile(text, peephole=False)
+    assert e.value.name == "NC_E_KMAX"
+    # the HIR reorder measures qubit 0 right after its own rotation (it
+    # commutes with the other 30), so the optimised program stays at 30 axes
+    assert nc.compile(text).info.k_max == 30
+    with pytest.raises(nc.NcError) as e:
+        nc.compile("".join(f"H {q}\nT {q}\n" for q in range(31)))
     assert e.value.name == "NC_E_KMAX"
 
 
@@ -177,7 +183,7 @@ def test_shared_prefix_matches_the_oracle_plan(nc, name):
     from oracle.factored import FactoredSim
     text = {"dense": gc.dense_random(), "dense_small": gc.dense_random(seed=33, n=10, layers=12),
             "tiny": gc.tiny_random(), "surface": gc.surface_code_memory(d=3, rounds=2)}[name]
-    info = nc.compile(text).info
+    info = nc.compile(text, peephole=False).info  # the plain method, as the oracle's plan
     sim = FactoredSim(text)
     k = 0
     for st in sim.steps:

@@ -147,7 +147,7 @@ def _run_fused(ops, terms, perm, probes=None):
 
 @pytest.mark.parametrize("seed,n,layers", [(3, 8, 10), (4, 9, 12), (5, 10, 8)])
 def test_fused_list_builds_the_same_vector(nc, seed, n, layers):
-    blob = nc.compile(gc.dense_random(seed=seed, n=n, layers=layers)).serialize()
+    blob = nc.compile(gc.dense_random(seed=seed, n=n, layers=layers), peephole=False).serialize()
     u = struct.unpack_from(HEAD, blob, 0)
     n_ops = u[4]
     n_fops, n_fterms, n_fperm = u[32], u[33], u[34]
