@@ -44,16 +44,17 @@ def workload_name(args) -> str:
 def workload(name: str):
     from gen import circuits as gc
     if name == "surface":
-        return ("surface_code_d5_r25_p1e-3", gc.surface_code_memory(d=5, rounds=25, p=1e-3), 100_000_000)
+        return ("surface_code_d5_r25_p1e-3", gc.surface_code_memory(d=5, rounds=25, p=1e-3), 100_000_000, False)
     if name == "tiny":
-        return ("tiny_n12_l30_t6", gc.tiny_random(seed=1), 10_000)
+        return ("tiny_n12_l30_t6", gc.tiny_random(seed=1), 10_000, False)
     if name == "dense":
-        return ("dense_n20_l40", gc.dense_random(seed=3, n=20, layers=40), 4096)
+        return ("dense_n20_l40", gc.dense_random(seed=3, n=20, layers=40), 4096, False)
     if name == "lowmagic":
-        return ("low_magic_n50_k10_p5e-4", gc.low_magic_gadgets(), 100_000_000)
+        # postselection on every detector being zero
+        return ("low_magic_n50_k10_p5e-4_postselected", gc.low_magic_gadgets(), 100_000_000, True)
     if name == "coherent":
         return ("coherent_surface_d3_r3_p1e-3_theta0.02",
-                gc.surface_code_memory(d=3, rounds=3, p=1e-3, theta=0.02), 10_000_000)
+                gc.surface_code_memory(d=3, rounds=3, p=1e-3, theta=0.02), 10_000_000, False)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -214,7 +215,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    _, text, shots = workload(args.workload)
+    _, text, shots, _ = workload(args.workload)
     wname = workload_name(args)
     cores = os.cpu_count() or 1
     rates = []
@@ -245,7 +246,7 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    _, text, shots = workload(args.workload)
+    _, text, shots, ps = workload(args.workload)
     wname = workload_name(args)
     if args.shots:
         shots = args.shots
@@ -272,13 +273,17 @@ def run_ours(args):
     from paper_2604_27058_gb300 import shard
     offset, shots = shard.weak(shots, rank)
     stream = torch.cuda.current_stream()
+    # launch shape chosen by the autotuner (nc_autotune) unless given
+    shape = args.tune
+    if shape is None and not args.no_autotune:
+        shape = nc.autotune(prog, min(shots, 1 << 22), postselect=ps, stratum=args.stratum)
 
     def step(precision="fp32", out=None, host=False):
         if host:
             return nc.sample_host(prog, shots, 2002, precision=precision, shot_offset=offset, out=out,
-                                  tune=args.tune, stratum=args.stratum)
+                                  tune=args.tune, stratum=args.stratum, postselect=ps)
         return nc.sample(prog, shots, 2002, precision=precision, shot_offset=offset, out=out or bufs,
-                         tune=args.tune, stratum=args.stratum)
+                         tune=args.tune, stratum=args.stratum, postselect=ps)
 
     def barrier():
         if world > 1:
@@ -359,11 +364,33 @@ def run_ours(args):
     if not args.no_e2e:
         hb = nc.alloc_host_records(prog, shots)
         e_steps = max(1, min(args.steps, 3))
-        mse, _, _, _ = timed("fp32", e_steps, 1, host=True, out=hb)
+        mse, _, _, rh = timed("fp32", e_steps, 1, host=True, out=hb)
         d2h = sum(b.nbytes for k, b in hb.items() if k != "words_per_record" and b is not None)
         e2e = {"value": shots * world * e_steps / (mse / 1000.0), "unit": "shots/s",
-               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h),
+               "path": "kernels write the pinned host buffers directly" if rh.get("path", 0) & 2
+               else "device staging, chunked, copies overlapped on a side stream"}
         del hb
+        # host-link peak: a plain pinned device-to-host copy (2 GiB or a step's
+        # bytes, whichever is smaller), CUDA events on the same stream
+        nbytes = int(min(d2h, 2 << 30)) // 8 * 8
+        if nbytes > 0:
+            src = torch.ones(nbytes // 8, dtype=torch.int64, device="cuda")
+            dst = torch.empty(nbytes // 8, dtype=torch.int64, pin_memory=True)
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            for _ in range(3):
+                dst.copy_(src, non_blocking=True)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            gbs = 3 * nbytes / (c0.elapsed_time(c1) / 1000.0) / 1e9
+            e2e["host_link"] = {"d2h_gbs": gbs, "bytes": nbytes,
+                                "how": "torch pinned copy_ from device, 3 copies, CUDA events"}
+            e2e["host_link_frac"] = e2e["value"] * (d2h / shots) / 1e9 / gbs
+            del src, dst
 
     # roofline of the dominant kernel (the record-tile kernel of the k_max = 0
     # path, else the batched executor): algorithmic bytes = the records it
@@ -398,7 +425,8 @@ def run_ours(args):
             "config": {"workload": wname, "shots_per_step_per_gpu": shots, "n_qubits": info.n_qubits,
                        "k_max": info.k_max, "noise_sites": info.n_noise_sites,
                        "record_bits_per_shot": info.n_meas + info.n_det + info.n_obs + 1,
-                       "precision": "fp32_batched", "l2": "records per step >> L2 (no flush needed)",
+                       "precision": "fp32_batched", "postselect": ps, "launch_shape": shape or "heuristic",
+                       "l2": "records per step >> L2 (no flush needed)",
                        "parallelism": f"replicas{world}"},
             **({} if args.stratum is None else
                {"stratum": {"faults_per_shot": args.stratum,

@@ -863,6 +863,86 @@ nc_sample_opts default_opts() {
   return o;
 }
 
+// Host outputs the device cannot address: the call's shots run in chunks
+// (global shot offsets advance with the chunk, so the records are those of
+// one call), each into one of two device staging buffers, and each finished
+// chunk's record columns are copied to the caller's rows on a side stream
+// while the next chunk runs. The caller's stream waits for the last copy.
+nc_status sample_staged(const nc_program* prog, DevCopy& dc, uint64_t shots, uint64_t seed, const nc_sample_opts& o,
+                        uint32_t lflags, const char* tune, CallOut host, unsigned long long* kept_count, uint32_t* err,
+                        Scratch& scratch, cudaStream_t stream, Timing* tm, uint32_t stratum) {
+  nc_status st = NC_OK;
+  const ProgHeader& h = header(prog);
+  const uint64_t wpr = (shots + 63) / 64;
+  const uint32_t rows[4] = {host.meas ? h.n_meas : 0u, host.det ? h.n_det : 0u, host.obs ? h.n_obs : 0u,
+                            host.kept ? 1u : 0u};
+  const uint32_t n_rows = rows[0] + rows[1] + rows[2] + rows[3];
+  const uint32_t n_probes = host.expval ? h.n_probes : 0u;
+  // chunk: at most 2^24 shots and 1 GiB of staging per buffer, 128-aligned
+  const uint64_t per_shot = (uint64_t)n_rows / 8 + 1 + (uint64_t)n_probes * 8;
+  uint64_t chunk = std::min<uint64_t>(1ull << 24, std::max<uint64_t>(128, (1ull << 30) / per_shot)) & ~127ull;
+  {
+    const char* hc = tune ? strstr(tune, "hc=") : nullptr;  // chunk override (tests)
+    unsigned long long v = 0;
+    if (hc && sscanf(hc, "hc=%llu", &v) == 1 && v >= 128) chunk = (uint64_t)v & ~127ull;
+  }
+  chunk = std::min<uint64_t>(chunk, (shots + 127) & ~127ull);
+  const uint64_t cw = (chunk + 63) / 64;  // words per staged row
+  const size_t rec_b = (size_t)n_rows * cw * 8, ev_b = (size_t)n_probes * chunk * 8;
+  void* buf[2] = {nullptr, nullptr};
+  SideStream side;
+  Events ev;  // [0] start, [1..2] chunk computed into buffer b, [3..4] buffer b copied out
+  NC_TRY(scratch.get(&buf[0], rec_b + ev_b));
+  NC_TRY(scratch.get(&buf[1], rec_b + ev_b));
+  {
+    int dev = 0;
+    NC_TRY(cudaGetDevice(&dev));
+    NC_TRY(side.acquire(dev));
+  }
+  NC_TRY(ev.make(5));
+  NC_TRY(cudaEventRecord(ev.ev[0], stream));
+  NC_TRY(cudaStreamWaitEvent(side.s, ev.ev[0], 0));
+  for (uint64_t c0 = 0, ci = 0; c0 < shots; c0 += chunk, ci++) {
+    const uint64_t cs = std::min(chunk, shots - c0), csw = (cs + 63) / 64;
+    const uint32_t b = (uint32_t)(ci & 1);
+    uint8_t* base = (uint8_t*)buf[b];
+    if (ci >= 2) NC_TRY(cudaStreamWaitEvent(stream, ev.ev[3 + b], 0));  // buffer b drained
+    CallOut d{nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint32_t* r = (uint32_t*)base;
+    const size_t rstride = csw * 2;  // u32 words per staged row of this chunk
+    if (rows[0]) { d.meas = r; r += rows[0] * rstride; }
+    if (rows[1]) { d.det = r; r += rows[1] * rstride; }
+    if (rows[2]) { d.obs = r; r += rows[2] * rstride; }
+    if (rows[3]) { d.kept = r; r += rows[3] * rstride; }
+    if (n_probes) d.expval = (double*)(base + rec_b);
+    st = enqueue(prog, dc, cs, seed, o.shot_offset + c0, o.precision, lflags, tune, d, kept_count, err, scratch, stream,
+                 0xffffffffu, 0, nullptr, nullptr, nullptr, tm, stratum);
+    if (st != NC_OK) goto done;
+    NC_TRY(cudaEventRecord(ev.ev[1 + b], stream));
+    NC_TRY(cudaStreamWaitEvent(side.s, ev.ev[1 + b], 0));
+    {
+      const uint32_t* src = (const uint32_t*)base;
+      uint32_t* dst[4] = {host.meas, host.det, host.obs, host.kept};
+      for (int j = 0; j < 4; j++) {
+        if (!rows[j]) continue;
+        NC_TRY(cudaMemcpy2DAsync((uint64_t*)dst[j] + c0 / 64, wpr * 8, src, csw * 8, csw * 8, rows[j],
+                                 cudaMemcpyDeviceToHost, side.s));
+        src += rows[j] * rstride;
+      }
+      if (n_probes)
+        NC_TRY(cudaMemcpy2DAsync(host.expval + c0, shots * 8, base + rec_b, cs * 8, cs * 8, n_probes,
+                                 cudaMemcpyDeviceToHost, side.s));
+    }
+    NC_TRY(cudaEventRecord(ev.ev[3 + b], side.s));
+  }
+  // the caller's stream (and with it the scratch release) waits for every copy
+  NC_TRY(cudaEventRecord(ev.ev[0], side.s));
+  NC_TRY(cudaStreamWaitEvent(stream, ev.ev[0], 0));
+  if (tm) tm->path |= 4u;
+done:
+  return st;
+}
+
 nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, const uint64_t* seeds, uint32_t n,
                       const nc_sample_opts* opts_in, nc_records* outs, cudaStream_t stream) {
   if (!progs || !shots || !seeds || !outs) return NC_E_ARG;
@@ -914,31 +994,55 @@ nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, con
     for (uint32_t i = 0; i < n; i++) {
       if (shots[i] == 0) continue;
       const ProgHeader& h = header(progs[i]);
-      uint64_t row_bytes = outs[i].words_per_record * 8;
       CallOut co{(uint32_t*)outs[i].meas, (uint32_t*)outs[i].det, (uint32_t*)outs[i].obs,
                  (uint32_t*)outs[i].kept, (o.outputs & NC_OUT_EXPVAL) ? outs[i].expval : nullptr};
-      const size_t ev_bytes = (size_t)h.n_probes * shots[i] * sizeof(double);
-      if (host) {
-        void* d = nullptr;
-        if ((o.outputs & NC_OUT_MEAS) && h.n_meas) { NC_TRY(scratch.get(&d, row_bytes * h.n_meas)); co.meas = (uint32_t*)d; }
-        if ((o.outputs & NC_OUT_DET) && h.n_det) { NC_TRY(scratch.get(&d, row_bytes * h.n_det)); co.det = (uint32_t*)d; }
-        if ((o.outputs & NC_OUT_OBS) && h.n_obs) { NC_TRY(scratch.get(&d, row_bytes * h.n_obs)); co.obs = (uint32_t*)d; }
-        if (o.outputs & NC_OUT_KEPT) { NC_TRY(scratch.get(&d, row_bytes)); co.kept = (uint32_t*)d; }
-        if (co.expval && h.n_probes) { NC_TRY(scratch.get(&d, ev_bytes)); co.expval = (double*)d; }
-      }
       const char* tn = o.tune ? o.tune : (dcs[i]->tuned.empty() ? nullptr : dcs[i]->tuned.c_str());
-      st = enqueue(progs[i], *dcs[i], shots[i], seeds[i], o.shot_offset, o.precision, launch_flags(o), tn, co,
-                   (unsigned long long*)counters + i, (uint32_t*)err, scratch, stream, 0xffffffffu, 0, nullptr,
-                   nullptr, nullptr, &tms[i], stratum);
-      if (st != NC_OK) goto done;
-      if (i + 1 == n) NC_TRY(cudaEventRecord(ev1, stream));
+      const uint32_t lf = launch_flags(o);
       if (host) {
-        if (co.meas && outs[i].meas) NC_TRY(cudaMemcpyAsync(outs[i].meas, co.meas, row_bytes * h.n_meas, cudaMemcpyDeviceToHost, stream));
-        if (co.det && outs[i].det) NC_TRY(cudaMemcpyAsync(outs[i].det, co.det, row_bytes * h.n_det, cudaMemcpyDeviceToHost, stream));
-        if (co.obs && outs[i].obs) NC_TRY(cudaMemcpyAsync(outs[i].obs, co.obs, row_bytes * h.n_obs, cudaMemcpyDeviceToHost, stream));
-        if (co.kept && outs[i].kept) NC_TRY(cudaMemcpyAsync(outs[i].kept, co.kept, row_bytes, cudaMemcpyDeviceToHost, stream));
-        if (co.expval && h.n_probes) NC_TRY(cudaMemcpyAsync(outs[i].expval, co.expval, ev_bytes, cudaMemcpyDeviceToHost, stream));
+        // host outputs: written by the kernels themselves when the device can
+        // address the caller's (pinned) buffers, else staged in device
+        // memory chunk by chunk with the copies overlapped
+        // (the executors' record-flip atomics need native host atomics)
+        int native_atomics = 0, cur_dev = 0;
+        NC_TRY(cudaGetDevice(&cur_dev));
+        NC_TRY(cudaDeviceGetAttribute(&native_atomics, cudaDevAttrHostNativeAtomicSupported, cur_dev));
+        bool direct = native_atomics && !(tn && strstr(tn, "hd=0"));
+        CallOut dv = co;
+        auto dev_ptr = [&](void* hp, void** dp) {
+          if (!hp) return;
+          cudaPointerAttributes a;
+          if (cudaPointerGetAttributes(&a, hp) != cudaSuccess || a.type != cudaMemoryTypeHost || !a.devicePointer) {
+            cudaGetLastError();
+            direct = false;
+            return;
+          }
+          *dp = a.devicePointer;
+        };
+        if (direct) {
+          dev_ptr(co.meas, (void**)&dv.meas);
+          dev_ptr(co.det, (void**)&dv.det);
+          dev_ptr(co.obs, (void**)&dv.obs);
+          dev_ptr(co.kept, (void**)&dv.kept);
+          dev_ptr(co.expval, (void**)&dv.expval);
+        }
+        if (direct) {
+          st = enqueue(progs[i], *dcs[i], shots[i], seeds[i], o.shot_offset, o.precision, lf, tn, dv,
+                       (unsigned long long*)counters + i, (uint32_t*)err, scratch, stream, 0xffffffffu, 0, nullptr,
+                       nullptr, nullptr, &tms[i], stratum);
+          if (st != NC_OK) goto done;
+          tms[i].path |= 2u;
+        } else {
+          st = sample_staged(progs[i], *dcs[i], shots[i], seeds[i], o, lf, tn, co, (unsigned long long*)counters + i,
+                             (uint32_t*)err, scratch, stream, &tms[i], stratum);
+          if (st != NC_OK) goto done;
+        }
+      } else {
+        st = enqueue(progs[i], *dcs[i], shots[i], seeds[i], o.shot_offset, o.precision, lf, tn, co,
+                     (unsigned long long*)counters + i, (uint32_t*)err, scratch, stream, 0xffffffffu, 0, nullptr,
+                     nullptr, nullptr, &tms[i], stratum);
+        if (st != NC_OK) goto done;
       }
+      if (i + 1 == n) NC_TRY(cudaEventRecord(ev1, stream));
     }
     NC_TRY(cudaMemcpyAsync(kept.data(), counters, 8 * (size_t)n, cudaMemcpyDeviceToHost, stream));
     uint32_t herr = 0;
@@ -1121,25 +1225,50 @@ nc_status nc_sample_batch_async(const nc_program* const* progs, const uint64_t* 
         (dcs[i]->sg_rows < o.stratum || p->strata.valid.size() <= o.stratum || !p->strata.valid[o.stratum]))
       return NC_E_ARG;
   }
-  nc_status st = NC_OK;
-  {
-    Scratch scratch(stream);
-    for (uint32_t i = 0; i < n; i++) {
-      outs[i].shots_run = shots[i];
-      outs[i].shots_kept = 0;
-      outs[i].kernel_ms = outs[i].exec_ms = 0.0;
-      outs[i].launches = 0;
-      outs[i].path = 0;
-      if (shots[i] == 0) continue;
-      CallOut co{(uint32_t*)outs[i].meas, (uint32_t*)outs[i].det, (uint32_t*)outs[i].obs, (uint32_t*)outs[i].kept,
-                 (o.outputs & NC_OUT_EXPVAL) ? outs[i].expval : nullptr};
-      const char* tn = o.tune ? o.tune : (dcs[i]->tuned.empty() ? nullptr : dcs[i]->tuned.c_str());
-      st = enqueue(progs[i], *dcs[i], shots[i], seeds[i], o.shot_offset, o.precision, launch_flags(o) | LF_ASYNC,
-                   tn, co, kept_dev + i, err_dev, scratch, stream, 0xffffffffu, 0, nullptr, nullptr, nullptr,
-                   nullptr, stratum);
-      if (st != NC_OK) break;
-    }
+  // The programs run on up to kBranches side streams forked from the
+  // caller's stream and joined back into it (program i on branch i mod the
+  // branch count, in order within a branch), so that a captured graph holds
+  // independent branches and small programs run beside large ones.
+  constexpr uint32_t kBranches = 16;
+  std::vector<uint32_t> live;
+  for (uint32_t i = 0; i < n; i++) {
+    outs[i].shots_run = shots[i];
+    outs[i].shots_kept = 0;
+    outs[i].kernel_ms = outs[i].exec_ms = 0.0;
+    outs[i].launches = 0;
+    outs[i].path = 0;
+    if (shots[i]) live.push_back(i);
   }
+  if (live.empty()) return NC_OK;
+  const uint32_t nb = std::min<uint32_t>(kBranches, (uint32_t)live.size());
+  nc_status st = NC_OK;
+  std::vector<SideStream> side(nb);
+  Events ev;
+  NC_TRY(ev.make(1 + nb));
+  NC_TRY(cudaEventRecord(ev.ev[0], stream));
+  for (uint32_t b = 0; b < nb; b++) {
+    NC_TRY(side[b].acquire(dev));
+    NC_TRY(cudaStreamWaitEvent(side[b].s, ev.ev[0], 0));
+  }
+  for (uint32_t b = 0; b < nb; b++) {
+    {
+      Scratch scratch(side[b].s);  // released on its branch, before the join
+      for (size_t j = b; j < live.size() && st == NC_OK; j += nb) {
+        const uint32_t i = live[j];
+        CallOut co{(uint32_t*)outs[i].meas, (uint32_t*)outs[i].det, (uint32_t*)outs[i].obs,
+                   (uint32_t*)outs[i].kept, (o.outputs & NC_OUT_EXPVAL) ? outs[i].expval : nullptr};
+        const char* tn = o.tune ? o.tune : (dcs[i]->tuned.empty() ? nullptr : dcs[i]->tuned.c_str());
+        st = enqueue(progs[i], *dcs[i], shots[i], seeds[i], o.shot_offset, o.precision,
+                     launch_flags(o) | LF_ASYNC, tn, co, kept_dev + i, err_dev, scratch, side[b].s, 0xffffffffu, 0,
+                     nullptr, nullptr, nullptr, nullptr, stratum);
+      }
+    }
+    // every branch is joined, also after an error, so that a capture can end
+    cudaError_t e1 = cudaEventRecord(ev.ev[1 + b], side[b].s);
+    cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(stream, ev.ev[1 + b], 0) : e1;
+    if (e2 != cudaSuccess && st == NC_OK) st = cuda_status(e2);
+  }
+done:
   return st;
 }
 
@@ -1169,6 +1298,9 @@ nc_status nc_autotune(nc_program* prog, uint64_t shots, const nc_sample_opts* op
           continue;
         cand.push_back("g=" + std::to_string(g) + ",t=" + std::to_string(t));
       }
+    // the warp-per-shot layout (vectors in shared memory, frame in registers)
+    if (warp_supported(d) && h.k_max <= 13)
+      for (const char* c : {"lw=1", "lw=1,wn=4", "lw=1,wn=2"}) cand.push_back(c);
   }
   Scratch scratch(stream);
   void *meas = nullptr, *det = nullptr, *obs = nullptr, *kept = nullptr;

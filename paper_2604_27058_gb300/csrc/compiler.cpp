@@ -1146,7 +1146,66 @@ void hir_reorder(std::vector<Hir>& L, const std::vector<PhysOp>& ops) {
 // ---------------------------------------------------------------------------
 // Entry point
 // ---------------------------------------------------------------------------
+namespace {
+int compile_once(const std::string& text, uint32_t flags, CompiledProgram& out, std::string& err);
+
+// Array-traversal bytes per shot a program costs the batched executor: its
+// whole count, less the shared noiseless prefix (run once per call, every
+// shot then starts from one copy of its vector) where the executor takes it
+// (at least 6 axes).
+double per_shot_cost(const CompiledProgram& c) {
+  const ProgHeader& h = *reinterpret_cast<const ProgHeader*>(c.blob.data());
+  double b = c.counts.array_bytes;
+  if (h.prefix_end > 0 && h.prefix_k >= 6) b -= c.counts.prefix_bytes - 8.0 * std::ldexp(1.0, (int)h.prefix_k);
+  return b;
+}
+}  // namespace
+
 int compile_program(const std::string& text, uint32_t flags, CompiledProgram& out, std::string& err) {
+  // The HIR passes never change a record, but they can raise the per-shot
+  // cost: the reorder pulls measurements ahead of rotations, which can end
+  // the shared noiseless prefix sooner, and a re-absorbed Clifford can turn
+  // later measured Paulis into ones whose localisation takes more array
+  // instructions. Every subset of the passes the flags leave on is compiled
+  // (most passes first) and the cheapest per shot kept, the one with more
+  // passes on a tie. Programs without active axes compile once.
+  CompiledProgram best;
+  double best_cost = 0.0;
+  int first_rc = -1;
+  std::string first_err;
+  for (uint32_t off = 0; off <= kNoPeephole + kNoReorder + kNoFuse; off++) {
+    if (off & ~(kNoPeephole | kNoReorder | kNoFuse)) continue;
+    if ((flags & off) != 0 && off != 0) continue;  // passes already off are not varied
+    CompiledProgram c;
+    std::string e;
+    const int rc = compile_once(text, flags | off, c, e);
+    if (first_rc < 0) {
+      first_rc = rc;
+      first_err = e;
+    }
+    if (rc != 0) {
+      if (rc == 3) continue;  // over the active-dimension limit with these passes
+      err = e;
+      return rc;
+    }
+    const ProgHeader& h = *reinterpret_cast<const ProgHeader*>(c.blob.data());
+    const double cost = per_shot_cost(c);
+    if (best.blob.empty() || cost < best_cost) {
+      best_cost = cost;
+      best = std::move(c);
+    }
+    if (h.k_max == 0) break;  // nothing to gain (and no rotation left for the passes)
+  }
+  if (best.blob.empty()) {
+    err = first_err;
+    return first_rc;
+  }
+  out = std::move(best);
+  return 0;
+}
+
+namespace {
+int compile_once(const std::string& text, uint32_t flags, CompiledProgram& out, std::string& err) {
   try {
     std::vector<std::string> lines;
     {
@@ -1759,5 +1818,6 @@ int compile_program(const std::string& text, uint32_t flags, CompiledProgram& ou
     return 9;
   }
 }
+}  // namespace
 
 }  // namespace nc

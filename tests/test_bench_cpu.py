@@ -17,8 +17,8 @@ import bench  # noqa: E402
 
 def test_workloads_and_names():
     for name in ("surface", "tiny", "dense", "lowmagic", "coherent"):
-        wname, text, shots = bench.workload(name)
-        assert wname and text and shots > 0
+        wname, text, shots, ps = bench.workload(name)
+        assert wname and text and shots > 0 and ps == (name == "lowmagic")
 
     class A:
         workload = "surface"

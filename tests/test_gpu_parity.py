@@ -403,6 +403,29 @@ def test_host_output_path_equals_device(nc):
     assert d["shots_kept"] == h["shots_kept"] == 1000
 
 
+@pytest.mark.parametrize("case", ["surface", "low_magic_postselected", "fig4"])
+def test_host_outputs_direct_and_staged(nc, case):
+    """Host outputs reach the caller's pinned buffers straight from the
+    kernels (pinned memory the device addresses, with native host atomics:
+    path bit 2) or through device staging chunk by chunk with the copies
+    overlapped (forced by hd=0; hc= sets the chunk, here three chunks with a
+    ragged last one: path bit 4). Both equal the device-buffer records."""
+    text, ps = {"surface": (gc.surface_code_memory(d=3, rounds=4, p=0.01), False),
+                "low_magic_postselected": (gc.low_magic_gadgets(), True),
+                "fig4": (gc.fig4_example(0.05), False)}[case]
+    prog = nc.compile(text)
+    shots = 3000
+    d = nc.sample(prog, shots, 5, postselect=ps)
+    for tune, bit in ((None, 2), ("hd=0,hc=1024", 4), ("hd=0", 4)):
+        h = nc.sample_host(prog, shots, 5, postselect=ps, tune=tune)
+        if tune is None and not h["path"] & 2:
+            continue  # this device cannot write the caller's pinned memory directly
+        assert h["path"] & bit, (tune, h["path"])
+        for key in ("meas", "det", "obs", "kept"):
+            assert (d[key].cpu().numpy() == h[key]).all(), (tune, key)
+        assert d["shots_kept"] == h["shots_kept"]
+
+
 def test_deserialized_program_same_records(nc):
     text = gc.low_magic_gadgets()
     p = nc.compile(text)

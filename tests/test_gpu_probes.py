@@ -122,6 +122,11 @@ def test_host_and_graph_paths_equal_device(nc):
     # order of the additions
     d = float(np.max(np.abs(a["expval"].cpu().numpy() - h["expval"])))
     assert d <= 1e-12, d
+    # staged host outputs: probe rows copied chunk by chunk (three chunks)
+    h2 = nc.sample_host(prog, 3000, 8, tune="hd=0,hc=1024")
+    assert h2["path"] & 4
+    d = float(np.max(np.abs(a["expval"].cpu().numpy() - h2["expval"])))
+    assert d <= 1e-12, d
     nc.prepare(prog)
     outs = [nc.alloc_records(prog, 3000)]
     kept = torch.zeros(1, dtype=torch.int64, device="cuda")
