@@ -64,7 +64,7 @@ def record_bytes_per_shot(info) -> float:
 
 def kernel_sha() -> str:
     h = hashlib.sha256()
-    for f in ("kernels.cu", "kernels.cuh", "program.h", "affine_kernel.cu"):
+    for f in ("kernels.cu", "kernels.cuh", "program.h", "affine_kernel.cu", "warp_kernel.cu"):
         h.update(open(os.path.join(ROOT, "paper_2604_27058_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -409,7 +409,7 @@ def run_ours(args):
     affine = info.k_max == 0 and "a=0" not in (args.tune or "")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": (tr * shots) if tr else None,
-            "kernel": "sample_affine" if affine else "exec_batched",
+            "kernel": "sample_affine" if affine else "exec_warp" if "lw=1" in (shape or "") else "exec_batched",
             "peak_source": f"{peak_src} (hbm_gbs, burst copy)",
             "algorithmic_bytes_per_launch": alg, "kernel_ms": exec_ms, "call_ms": call_ms,
             "bytes_model": "records written + active-vector traversals of the unfused instruction list "

@@ -25,7 +25,7 @@ size_t batched_smem_bytes(const DevProg& p, uint32_t G, uint32_t W, bool bk, uin
 cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, bool bk, uint32_t grid, uint32_t threads,
                            size_t smem, cudaStream_t st);
 cudaError_t batched_occupancy(bool fp64, uint32_t W, bool bk, uint32_t threads, size_t smem, int* blocks_per_sm);
-cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st);
+cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st, bool fp32);
 cudaError_t launch_patch_ref(Op* ops, uint32_t n_ops, const uint32_t* det_ref, const uint32_t* obs_ref,
                              cudaStream_t st);
 cudaError_t launch_presample(const LaunchParams& L, cudaStream_t st);
@@ -206,6 +206,7 @@ struct Tuning {
   uint32_t SW = 1;                                 // SW = 0: active vectors never in shared memory
   uint32_t PX = 1;  // shared prefix: 0 off, 1 when it saves enough traffic, 2 whenever it has array work
   uint32_t LW = 0;  // 1: warp-per-shot layout (exec_warp) for programs with active axes
+  uint32_t LP = 0;  // 1: thread-per-shot layout (exec_plain<float>) for programs with active axes
   uint32_t WN = 0;  // its warps per CTA (0: 8, fewer if the vectors do not fit)
 };
 
@@ -236,6 +237,7 @@ Tuning choose_tuning(const DevProg& d, const char* tune, uint64_t shots, int n_s
       else if (sscanf(s, "sw=%u", &v) == 1) t.SW = v;
       else if (sscanf(s, "px=%u", &v) == 1) t.PX = v;
       else if (sscanf(s, "lw=%u", &v) == 1) t.LW = v;
+      else if (sscanf(s, "lp=%u", &v) == 1) t.LP = v;
       else if (sscanf(s, "wn=%u", &v) == 1) t.WN = v;
       const char* c = strchr(s, ',');
       if (!c) break;
@@ -446,16 +448,25 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
   L.dump_amps = dump_amps;
   L.dump_frame = dump_frame;
   L.dump_k = dump_k;
-  if (precision == NC_FP64_PLAIN) {
+  // thread-per-shot layout: the plain FP64 form, or the FP32 batched form's
+  // layout for small vectors (tune lp=1)
+  bool lp32 = false;
+  if (precision == NC_FP32_BATCHED && h.k_max > 0 && !strat && tune && strstr(tune, "lp=1")) {
+    int n_sm_q = 0, dev_q = 0;
+    NC_TRY(cudaGetDevice(&dev_q));
+    NC_TRY(cudaDeviceGetAttribute(&n_sm_q, cudaDevAttrMultiProcessorCount, dev_q));
+    lp32 = choose_tuning(L.p, tune, shots, n_sm_q).LP == 1 && plain_supported(L.p);
+  }
+  if (precision == NC_FP64_PLAIN || lp32) {
     if (!plain_supported(L.p)) return NC_E_UNSUPPORTED;
-    // one FP64 vector of 2^k amplitudes per shot: launches over shot ranges
-    // whose vectors fit in a quarter of the free memory
+    // one vector of 2^k amplitudes per shot: launches over shot ranges whose
+    // vectors fit in a quarter of the free memory
     const uint64_t padded = L.row_words32 * 32;
     uint64_t chunk = padded;
     if (h.k_max > 0) {
       size_t free_b = 0;
       NC_TRY(free_memory(lflags, &free_b));
-      const uint64_t per_shot = ((uint64_t)1 << h.k_max) * sizeof(double) * 2;
+      const uint64_t per_shot = ((uint64_t)1 << h.k_max) * (lp32 ? sizeof(float) : sizeof(double)) * 2;
       chunk = std::min<uint64_t>(padded, std::max<uint64_t>(128, (free_b / 4 / per_shot) & ~127ull));
       NC_TRY(scratch.get(&L.work, per_shot * chunk));
     }
@@ -463,7 +474,7 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
       L.plain_base = b0;
       L.plain_n = std::min(chunk, padded - b0);
       if (tm) NC_TRY(tm->begin(stream));
-      NC_TRY(launch_plain(L, stream));
+      NC_TRY(launch_plain(L, stream, lp32));
       if (tm) {
         NC_TRY(tm->end(stream));
         tm->launches += 1;
@@ -1301,6 +1312,8 @@ nc_status nc_autotune(nc_program* prog, uint64_t shots, const nc_sample_opts* op
     // the warp-per-shot layout (vectors in shared memory, frame in registers)
     if (warp_supported(d) && h.k_max <= 13)
       for (const char* c : {"lw=1", "lw=1,wn=4", "lw=1,wn=2"}) cand.push_back(c);
+    // the thread-per-shot layout (vectors in global memory, no barriers)
+    if (plain_supported(d) && h.k_max <= 12) cand.push_back("lp=1");
   }
   Scratch scratch(stream);
   void *meas = nullptr, *det = nullptr, *obs = nullptr, *kept = nullptr;

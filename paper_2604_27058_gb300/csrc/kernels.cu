@@ -1324,12 +1324,18 @@ cudaError_t launch_presample(const LaunchParams& L, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// Plain FP64 executor: one thread per shot.
+// Thread-per-shot executor: one thread per shot, its 2^k amplitudes in global
+// memory (amplitude-major, shot-minor, so a warp's accesses coalesce).
+// exec_plain<double> is the plain FP64 form; exec_plain<float> keeps FP32
+// amplitudes with FP64 measurement sums (the batched form's precision), a
+// layout for small vectors and short calls.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kPlainMaxW = 8;       // N <= 256
 constexpr uint32_t kPlainMaxSlots = 2048;
 
+template <typename real>
 __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
+  using C = typename Cx<real>::T;
   const DevProg& p = L.p;
   // this launch covers call-local shots [plain_base, plain_base + plain_n)
   const uint64_t sl = L.plain_base + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1343,9 +1349,15 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
   uint32_t x[kPlainMaxW], z[kPlainMaxW], slots[kPlainMaxSlots / 32];
   for (uint32_t w = 0; w < kPlainMaxW; w++) x[w] = z[w] = 0;
   for (uint32_t w = 0; w < kPlainMaxSlots / 32; w++) slots[w] = 0;
-  double2* A = reinterpret_cast<double2*>(L.work);
+  C* A = reinterpret_cast<C*>(L.work);
   const uint64_t stride = L.plain_n;
-  auto amp = [&](uint32_t i) -> double2& { return A[(size_t)i * stride + (sl - L.plain_base)]; };
+  auto amp = [&](uint32_t i) -> C& { return A[(size_t)i * stride + (sl - L.plain_base)]; };
+  auto mk = [](real re, real im) -> C {
+    C c;
+    c.x = re;
+    c.y = im;
+    return c;
+  };
   auto getb = [](const uint32_t* v, uint32_t q) -> uint32_t { return (v[q >> 5] >> (q & 31)) & 1u; };
   auto setb = [](uint32_t* v, uint32_t q, uint32_t b) {
     v[q >> 5] = (v[q >> 5] & ~(1u << (q & 31))) | (b << (q & 31));
@@ -1359,8 +1371,8 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
   uint32_t nr = p.sg_k;  // stratified: faults this shot still holds
   uint32_t nf = (valid && !(L.flags & LF_NOISELESS) && p.n_sites) ? next_fault_r(p, L.seed, s, 0, nr) : kNoFault;
   uint32_t k = 0;
-  if (p.k_max > 0) amp(0) = make_double2(1.0, 0.0);
-  const double rs = 0.70710678118654752440;
+  if (p.k_max > 0) amp(0) = mk((real)1, (real)0);
+  const real rs = (real)0.70710678118654752440;
 
   for (uint32_t pc = 0; pc < p.n_ops; pc++) {
     const Op op = p.ops[pc];
@@ -1371,8 +1383,8 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
           L.dump_frame[p.nw + w] = z[w];
         }
         for (uint32_t i = 0; i < (1u << k); i++) {
-          L.dump_amps[2 * i] = amp(i).x;
-          L.dump_amps[2 * i + 1] = amp(i).y;
+          L.dump_amps[2 * i] = (double)amp(i).x;
+          L.dump_amps[2 * i + 1] = (double)amp(i).y;
         }
         *L.dump_k = k;
       }
@@ -1389,9 +1401,9 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
           const uint32_t half = 1u << (k - 1);
           for (uint32_t j = 0; j < half; j++) {
             uint32_t i0 = insert0(j, op.pa), i1 = i0 | (1u << op.pa);
-            double2 u = amp(i0), v = amp(i1);
-            amp(i0) = make_double2((u.x + v.x) * rs, (u.y + v.y) * rs);
-            amp(i1) = make_double2((u.x - v.x) * rs, (u.y - v.y) * rs);
+            C u = amp(i0), v = amp(i1);
+            amp(i0) = mk((u.x + v.x) * rs, (u.y + v.y) * rs);
+            amp(i1) = mk((u.x - v.x) * rs, (u.y - v.y) * rs);
           }
         }
         break;
@@ -1403,8 +1415,8 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
           const uint32_t half = 1u << (k - 1);
           for (uint32_t j = 0; j < half; j++) {
             uint32_t i1 = insert0(j, op.pa) | (1u << op.pa);
-            double2 u = amp(i1);
-            amp(i1) = make_double2(-u.y, u.x);
+            C u = amp(i1);
+            amp(i1) = mk(-u.y, u.x);
           }
         }
         break;
@@ -1417,7 +1429,7 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
           for (uint32_t j = 0; j < (1u << (k - 2)); j++) {
             uint32_t base = insert0(insert0(j, lo), hi);
             uint32_t i0 = base | (1u << op.pa), i1 = i0 | (1u << op.pb);
-            double2 u = amp(i0);
+            C u = amp(i0);
             amp(i0) = amp(i1);
             amp(i1) = u;
           }
@@ -1432,39 +1444,40 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
           const uint32_t lo = min(op.pa, op.pb), hi = max(op.pa, op.pb);
           for (uint32_t j = 0; j < (1u << (k - 2)); j++) {
             uint32_t i = insert0(insert0(j, lo), hi) | (1u << op.pa) | (1u << op.pb);
-            double2 u = amp(i);
-            amp(i) = make_double2(-u.x, -u.y);
+            C u = amp(i);
+            amp(i) = mk(-u.x, -u.y);
           }
         }
         break;
       }
       case OP_EXPAND_ROT: {
-        const double c2 = op.cs * rs, s2 = (getb(x, op.a) ? -op.sn : op.sn) * rs;
+        const real c2 = (real)(op.cs * 0.70710678118654752440),
+                   s2 = (real)((getb(x, op.a) ? -op.sn : op.sn) * 0.70710678118654752440);
         const uint32_t n = 1u << k;
         for (uint32_t i = 0; i < n; i++) {
-          double2 u = amp(i);
-          amp(i) = make_double2(u.x * rs, u.y * rs);
-          amp(i + n) = make_double2(u.x * c2 - u.y * s2, u.x * s2 + u.y * c2);
+          C u = amp(i);
+          amp(i) = mk(u.x * rs, u.y * rs);
+          amp(i + n) = mk(u.x * c2 - u.y * s2, u.x * s2 + u.y * c2);
         }
         k++;
         break;
       }
       case OP_ROT_Z: {
-        const double c2 = op.cs, s2 = getb(x, op.a) ? -op.sn : op.sn;
+        const real c2 = (real)op.cs, s2 = (real)(getb(x, op.a) ? -op.sn : op.sn);
         for (uint32_t j = 0; j < (1u << (k - 1)); j++) {
           uint32_t i1 = insert0(j, op.pa) | (1u << op.pa);
-          double2 u = amp(i1);
-          amp(i1) = make_double2(u.x * c2 - u.y * s2, u.x * s2 + u.y * c2);
+          C u = amp(i1);
+          amp(i1) = mk(u.x * c2 - u.y * s2, u.x * s2 + u.y * c2);
         }
         break;
       }
       case OP_ROT_X: {
-        const double c1 = op.cs, s1 = getb(z, op.a) ? -op.sn : op.sn;
+        const real c1 = (real)op.cs, s1 = (real)(getb(z, op.a) ? -op.sn : op.sn);
         for (uint32_t j = 0; j < (1u << (k - 1)); j++) {
           uint32_t i0 = insert0(j, op.pa), i1 = i0 | (1u << op.pa);
-          double2 a = amp(i0), b = amp(i1);
-          amp(i0) = make_double2(c1 * a.x + s1 * b.y, c1 * a.y - s1 * b.x);
-          amp(i1) = make_double2(s1 * a.y + c1 * b.x, -s1 * a.x + c1 * b.y);
+          C a = amp(i0), b = amp(i1);
+          amp(i0) = mk(c1 * a.x + s1 * b.y, c1 * a.y - s1 * b.x);
+          amp(i1) = mk(s1 * a.y + c1 * b.x, -s1 * a.x + c1 * b.y);
         }
         break;
       }
@@ -1502,14 +1515,14 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
         double S0 = 0.0, S1 = 0.0;
         for (uint32_t j = 0; j < half; j++) {
           uint32_t i0 = insert0(j, pa), i1 = i0 | (1u << pa);
-          double2 u = amp(i0), v = amp(i1);
+          C u = amp(i0), v = amp(i1);
           if (xm) {
-            double px = u.x + v.x, py = u.y + v.y, mx = u.x - v.x, my = u.y - v.y;
-            S0 += 0.5 * (px * px + py * py);
-            S1 += 0.5 * (mx * mx + my * my);
+            const real px = u.x + v.x, py = u.y + v.y, mx = u.x - v.x, my = u.y - v.y;
+            S0 += 0.5 * (double)(px * px + py * py);
+            S1 += 0.5 * (double)(mx * mx + my * my);
           } else {
-            S0 += u.x * u.x + u.y * u.y;
-            S1 += v.x * v.x + v.y * v.y;
+            S0 += (double)(u.x * u.x + u.y * u.y);
+            S1 += (double)(v.x * v.x + v.y * v.y);
           }
         }
         const uint32_t pbit = xm ? getb(z, op.a) : getb(x, op.a);
@@ -1520,31 +1533,30 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
         const uint32_t m = !valid ? 0u : (L.flags & LF_ARGMAX) ? (p1 > 0.5 ? 1u : 0u) : draw_outcome(L.seed, s, op.i0, top, p1);
         const uint32_t b = m ^ abit ^ pbit;
         const double sb = b ? S1 : S0;
-        const double sc = sb > 0.0 ? 1.0 / sqrt(sb) : 0.0;
+        const real sc = (real)(sb > 0.0 ? 1.0 / sqrt(sb) : 0.0);
         if (pa == top_pos) {
           for (uint32_t j = 0; j < half; j++) {
-            double2 o0 = amp(j), o1 = amp(j + half), v;
-            if (xm) v = b ? make_double2((o0.x - o1.x) * rs, (o0.y - o1.y) * rs)
-                          : make_double2((o0.x + o1.x) * rs, (o0.y + o1.y) * rs);
+            C o0 = amp(j), o1 = amp(j + half), v;
+            if (xm) v = b ? mk((o0.x - o1.x) * rs, (o0.y - o1.y) * rs) : mk((o0.x + o1.x) * rs, (o0.y + o1.y) * rs);
             else v = b ? o1 : o0;
-            amp(j) = make_double2(v.x * sc, v.y * sc);
+            amp(j) = mk(v.x * sc, v.y * sc);
           }
         } else {
           for (uint32_t j = 0; j < (1u << (k - 2)); j++) {
             uint32_t base = insert0(insert0(j, pa), top_pos);
             uint32_t p00 = base, p10 = base | (1u << pa), p01 = base | (1u << top_pos), p11 = p10 | (1u << top_pos);
-            double2 n0, n1;
+            C n0, n1;
             if (xm) {
-              double2 o00 = amp(p00), o10 = amp(p10), o01 = amp(p01), o11 = amp(p11);
-              double sg = b ? -1.0 : 1.0;
-              n0 = make_double2((o00.x + sg * o10.x) * rs, (o00.y + sg * o10.y) * rs);
-              n1 = make_double2((o01.x + sg * o11.x) * rs, (o01.y + sg * o11.y) * rs);
+              C o00 = amp(p00), o10 = amp(p10), o01 = amp(p01), o11 = amp(p11);
+              const real sg = b ? (real)-1 : (real)1;
+              n0 = mk((o00.x + sg * o10.x) * rs, (o00.y + sg * o10.y) * rs);
+              n1 = mk((o01.x + sg * o11.x) * rs, (o01.y + sg * o11.y) * rs);
             } else {
               n0 = b ? amp(p10) : amp(p00);
               n1 = b ? amp(p11) : amp(p01);
             }
-            amp(p00) = make_double2(n0.x * sc, n0.y * sc);
-            amp(p10) = make_double2(n1.x * sc, n1.y * sc);
+            amp(p00) = mk(n0.x * sc, n0.y * sc);
+            amp(p10) = mk(n1.x * sc, n1.y * sc);
           }
         }
         k--;
@@ -1589,7 +1601,8 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
           if (k > 0) {
             double acc = 0.0, nrm = 0.0;
             for (uint32_t j = 0; j < (1u << k); j++) {
-              const double2 a = amp(j), b = amp(j ^ op.i1);
+              const C ac = amp(j), bc = amp(j ^ op.i1);
+              const double2 a = make_double2((double)ac.x, (double)ac.y), b = make_double2((double)bc.x, (double)bc.y);
               const double t1 = odd ? b.x * a.y - b.y * a.x : b.x * a.x + b.y * a.y;
               acc += (__popc(j & op.i2) & 1u) ? -t1 : t1;
               nrm += a.x * a.x + a.y * a.y;
@@ -1836,10 +1849,13 @@ cudaError_t launch_prefix(const Op* host_ops, uint32_t n, bool fp64, void* vec, 
   return cudaSuccess;
 }
 
-cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st) {
+// fp32: FP32 amplitudes (the thread-per-shot layout of the batched form),
+// else the plain FP64 form.
+cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st, bool fp32) {
   const uint32_t threads = 128;
   const uint64_t blocks = (L.plain_n + threads - 1) / threads;
-  exec_plain<<<(uint32_t)blocks, threads, 0, st>>>(L);
+  if (fp32) exec_plain<float><<<(uint32_t)blocks, threads, 0, st>>>(L);
+  else exec_plain<double><<<(uint32_t)blocks, threads, 0, st>>>(L);
   return cudaGetLastError();
 }
 

@@ -240,12 +240,17 @@ def test_dense_small_records_and_amplitudes(nc, precision):
 
 def test_dense_k20_mirror_returns_to_zero(nc):
     """n = 20, 12 layers of random H/S/T + CX matchings, then U^dagger: the
-    active dimension reaches 20 and every record is 0 (FP32 batched)."""
+    active dimension reaches 20 and every record is 0 (FP32 batched). The
+    plain method is compiled: the HIR passes cancel every T against its
+    T_DAG and leave no active axis (checked too)."""
     text = gc.dense_random(seed=3, n=20, layers=12, mirror=True)
-    prog = nc.compile(text)
+    prog = nc.compile(text, peephole=False)
     assert prog.info.k_max == 20
     g = gpu_records(prog, 32, 3003, precision="fp32")
     assert int(g["meas"].sum()) == 0
+    opt = nc.compile(text)
+    assert opt.info.k_max == 0
+    assert int(gpu_records(opt, 32, 3003, precision="fp32")["meas"].sum()) == 0
 
 
 def test_dense_k20_fp32_vs_fp64(nc):
@@ -253,7 +258,7 @@ def test_dense_k20_fp32_vs_fp64(nc):
     (records, flagged near-ties aside, and the amplitudes just before the
     final measurements)."""
     text = gc.dense_random(seed=3, n=20, layers=12)
-    prog = nc.compile(text)
+    prog = nc.compile(text, peephole=False)  # the HIR reorder measures earlier (k_max 17)
     assert prog.info.k_max == 20
     shots = 32
     a = gpu_records(prog, shots, 3003, precision="fp32")

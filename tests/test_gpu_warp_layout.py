@@ -1,5 +1,7 @@
-"""The warp-per-shot layout (exec_warp, tune "lw=1"): every shot on one
-warp, its active vector in shared memory, its frame in registers. Records
+"""The warp-per-shot layout (exec_warp, tune "lw=1": every shot on one
+warp, its active vector in shared memory, its frame in registers) and the
+FP32 thread-per-shot layout (exec_plain<float>, tune "lp=1": every shot on
+one thread, its vector in global memory, FP64 measurement sums). Records
 against the dense oracle (random small circuits with every instruction kind)
 and the factored oracle (the workloads), near-ties flagged; records equal
 those of the tile layout shot by shot except near-ties; tile boundaries and
@@ -30,7 +32,7 @@ def nc():
 
 
 @pytest.mark.parametrize("precision,tune", [("fp32", "lw=1"), ("fp64_batched", "lw=1"), ("fp32", "lw=1,wn=1"),
-                                            ("fp32", "lw=1,wn=3")])
+                                            ("fp32", "lw=1,wn=3"), ("fp32", "lp=1")])
 @pytest.mark.parametrize("seed", range(10))
 def test_random_small_vs_dense(nc, seed, precision, tune):
     n = 3 + seed % 5
@@ -56,7 +58,8 @@ def test_random_small_vs_dense(nc, seed, precision, tune):
 @pytest.mark.parametrize("name,shots,postselect", [("tiny", 2500, False), ("lowmagic", 400, True),
                                                    ("coherent", 400, False), ("dense10", 300, False),
                                                    ("fig4", 777, False)])
-def test_workloads_vs_oracle(nc, name, shots, postselect):
+@pytest.mark.parametrize("tune", ["lw=1", "lp=1"])
+def test_workloads_vs_oracle(nc, name, shots, postselect, tune):
     text = {"tiny": lambda: gc.tiny_random(seed=1), "lowmagic": gc.low_magic_gadgets,
             "coherent": lambda: gc.surface_code_memory(d=3, rounds=3, p=1e-3, theta=0.02),
             "dense10": lambda: gc.dense_random(seed=33, n=10, layers=12),
@@ -64,20 +67,21 @@ def test_workloads_vs_oracle(nc, name, shots, postselect):
     prog = nc.compile(text)
     assert prog.info.k_max > 0
     sim = FactoredSim(text)
-    g = gpu_records(prog, shots, 77, tune="lw=1", postselect=postselect)
+    g = gpu_records(prog, shots, 77, tune=tune, postselect=postselect)
     n_ok, flagged = compare(sim, g, range(shots), 77, postselect=postselect)
     assert n_ok + flagged == shots and flagged <= 3
     assert g["shots_kept"] == int(g["kept"].sum())
 
 
 @pytest.mark.parametrize("shots", [1, 31, 32, 33, 65, 1000, 70_001])
-def test_equals_tile_layout(nc, shots):
+@pytest.mark.parametrize("tune", ["lw=1", "lp=1"])
+def test_equals_tile_layout(nc, shots, tune):
     """Ragged counts and many tiles: the warp layout's records equal the tile
     layout's on every shot whose draws are not near-ties (postselected
     low-magic workload)."""
     text = gc.low_magic_gadgets()
     prog = nc.compile(text)
-    a = gpu_records(prog, shots, 4004, tune="lw=1", postselect=True)
+    a = gpu_records(prog, shots, 4004, tune=tune, postselect=True)
     b = gpu_records(prog, shots, 4004, postselect=True)
     same = (a["meas"] == b["meas"]).all(axis=0) & (a["det"] == b["det"]).all(axis=0) & (a["kept"] == b["kept"])
     assert int((~same).sum()) <= max(2, shots // 20000)
@@ -87,12 +91,13 @@ def test_equals_tile_layout(nc, shots):
         assert int(raw[0, -1] >> np.uint64(shots % 64)) == 0
 
 
-def test_shot_offset(nc):
+@pytest.mark.parametrize("tune", ["lw=1", "lp=1"])
+def test_shot_offset(nc, tune):
     text = gc.tiny_random(seed=2)
     prog = nc.compile(text)
-    full = gpu_records(prog, 512, 77, tune="lw=1")
-    a = gpu_records(prog, 256, 77, tune="lw=1", shot_offset=0)
-    b = gpu_records(prog, 256, 77, tune="lw=1", shot_offset=256)
+    full = gpu_records(prog, 512, 77, tune=tune)
+    a = gpu_records(prog, 256, 77, tune=tune, shot_offset=0)
+    b = gpu_records(prog, 256, 77, tune=tune, shot_offset=256)
     assert (np.concatenate([a["meas"], b["meas"]], axis=1) == full["meas"]).all()
 
 
