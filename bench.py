@@ -409,7 +409,8 @@ def run_ours(args):
     affine = info.k_max == 0 and "a=0" not in (args.tune or "")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": (tr * shots) if tr else None,
-            "kernel": "sample_affine" if affine else "exec_warp" if "lw=1" in (shape or "") else "exec_batched",
+            "kernel": "sample_affine" if affine else "exec_warp" if "lw=1" in (shape or "")
+            else "exec_plain<float>" if "lp=1" in (shape or "") else "exec_batched",
             "peak_source": f"{peak_src} (hbm_gbs, burst copy)",
             "algorithmic_bytes_per_launch": alg, "kernel_ms": exec_ms, "call_ms": call_ms,
             "bytes_model": "records written + active-vector traversals of the unfused instruction list "
@@ -485,8 +486,9 @@ def run_sweep(args):
     kept = torch.zeros(len(progs), dtype=torch.int64, device="cuda")
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
     g = torch.cuda.CUDAGraph()
+    one = "mp=1" if args.sweep_one_launch else None
     with torch.cuda.graph(g):
-        nc.sample_batch_async(progs, shots, seeds, outs, kept, err)
+        nc.sample_batch_async(progs, shots, seeds, outs, kept, err, tune=one)
     for _ in range(args.warmup):
         g.replay()
     clocks = Clocks(torch.cuda.current_device())
@@ -523,7 +525,11 @@ def run_sweep(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "sweep_64_circuits", "shots_per_step_per_gpu": total,
                        "shots_scale": args.sweep_scale, "k_max": [p.info.k_max for p in progs],
-                       "graph": "one CUDA graph of nc_sample_batch_async per step", "parallelism": f"replicas{world}"},
+                       "graph": "one CUDA graph of nc_sample_batch_async per step: "
+                                + ("ONE persistent thread-per-shot executor launch over a work list of every "
+                                   "circuit's 128-shot items" if one else
+                                   "up to 16 branches, each circuit with its autotuned launch shape"),
+                       "parallelism": f"replicas{world}"},
             "per_circuit_shots_per_s": {"min": min(per), "median": float(np.median(per)), "max": max(per)},
             "failure_rate": {"min": min(fail), "median": float(np.median(fail)), "max": max(fail)},
             "autotuned": tuned,
@@ -552,6 +558,8 @@ def main():
     ap.add_argument("--tune", default=None, help="executor tuning override, e.g. g=64,t=64")
     ap.add_argument("--sweep-scale", type=float, default=0.01, help="sweep workload: shots per circuit scale")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--sweep-one-launch", action="store_true",
+                    help="sweep workload: every circuit in one executor launch (tune mp=1)")
     ap.add_argument("--stratum", type=int, default=None,
                     help="stratified importance sampling: exactly K faults per shot")
     args = ap.parse_args()

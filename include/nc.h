@@ -74,7 +74,12 @@ typedef struct {
 #define NC_OUT_DET 2u
 #define NC_OUT_OBS 4u
 #define NC_OUT_KEPT 8u
-#define NC_OUT_HOST 16u    /* record pointers are host memory (copied back) */
+#define NC_OUT_HOST 16u    /* record pointers are host memory: the kernels write
+                              them directly when the device can address them
+                              (pinned memory, native host atomics; path bit 2),
+                              else the call runs in shot chunks through two
+                              device staging buffers whose copies overlap the
+                              next chunk (path bit 4; tune "hd=0" forces it) */
 #define NC_OUT_EXPVAL 32u  /* expectation-value probes (nc_records.expval) */
 
 /* postselect */
@@ -98,7 +103,11 @@ typedef struct {
                              per tile: 8, 16, 32), ai (0: faults sampled in
                              the tile kernel), av (shots per item pass), ac
                              (item-list capacity per tile), ao (1: item
-                             passes overlapped on a side stream) */
+                             passes overlapped on a side stream), lw (1:
+                             warp-per-shot layout), wn (its warps per CTA),
+                             lp (1: FP32 thread-per-shot layout), hd (0:
+                             host outputs staged, not written directly), hc
+                             (shots per staged chunk) */
   int noiseless;          /* 1 = disable every noise site (reference runs) */
   uint32_t stratified;    /* 0 = independent noise sites (default);
                              1 = stratified importance sampling: every shot
@@ -220,7 +229,12 @@ nc_status nc_program_prepare(const nc_program* prog, void* cuda_stream);
  * caller-owned and zeroed by the caller: kept_dev[i] accumulates program
  * i's kept shots and err_dev receives a nonzero value if a kernel reported
  * an internal error. outs[i].shots_run is set; shots_kept, kernel_ms,
- * exec_ms and launches are 0. Scratch comes from the stream-ordered pool. */
+ * exec_ms and launches are 0. Scratch comes from the stream-ordered pool.
+ * The programs run on up to 16 internal streams forked from cuda_stream (an
+ * event recorded on it) and joined back into it (events it waits for), so
+ * that small programs run beside large ones and a captured graph holds one
+ * branch per group of programs; all work is ordered after what cuda_stream
+ * held at the call and before what it is given next. */
 nc_status nc_sample_batch_async(const nc_program* const* progs, const uint64_t* shots,
                                 const uint64_t* seeds, uint32_t n, const nc_sample_opts* opts,
                                 nc_records* outs, unsigned long long* kept_dev, uint32_t* err_dev,
@@ -257,7 +271,9 @@ nc_status nc_stratum_weights(const nc_program* prog, uint32_t k_max, double* wei
 nc_status nc_strata_prepare(const nc_program* prog, uint32_t k_max, void* cuda_stream);
 
 /* Launch-shape autotuner (shots per CTA, CTA size, warp- or word-per-shot
- * layout of the record tile, fault pre-sampling): times the candidates for
+ * layout of the record tile, fault pre-sampling; for programs with active
+ * axes also the warp-per-shot layout "lw=1" and the FP32 thread-per-shot
+ * layout "lp=1"): times the candidates for
  * this program on min(shots, 2^22) shots with opts' outputs and keeps the
  * fastest for later calls on this device whose opts->tune is NULL. best
  * (if best_len > 0) receives the chosen shape as a tune string. The

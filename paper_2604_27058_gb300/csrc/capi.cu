@@ -26,6 +26,10 @@ cudaError_t launch_batched(const LaunchParams& L, bool fp64, uint32_t W, bool bk
                            size_t smem, cudaStream_t st);
 cudaError_t batched_occupancy(bool fp64, uint32_t W, bool bk, uint32_t threads, size_t smem, int* blocks_per_sm);
 cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st, bool fp32);
+cudaError_t launch_plain_multi(const LaunchParams* hLs, uint32_t n, const uint64_t* h_items, LaunchParams* dLs,
+                               unsigned long long* item0, unsigned long long* next, void* work, uint32_t grid,
+                               bool fp32, cudaStream_t st);
+cudaError_t plain_multi_occupancy(bool fp32, int* per_sm);
 cudaError_t launch_patch_ref(Op* ops, uint32_t n_ops, const uint32_t* det_ref, const uint32_t* obs_ref,
                              cudaStream_t st);
 cudaError_t launch_presample(const LaunchParams& L, cudaStream_t st);
@@ -730,6 +734,96 @@ done:
   return st;
 }
 
+uint32_t launch_flags(const nc_sample_opts& o);
+
+// Many programs in ONE executor launch (tune "mp=1" on a batch): the
+// thread-per-shot layout over a work list of 128-shot items, programs
+// ordered by their estimated cost per shot (longest first) so that the
+// persistent CTAs finish together. FP32 amplitudes (NC_FP32_BATCHED) or
+// FP64 (NC_FP64_PLAIN); no stratified calls, host outputs or debug stops.
+// Returns NC_E_UNSUPPORTED when a program does not fit the layout.
+nc_status enqueue_multi(const nc_program* const* progs, const std::vector<DevCopy*>& dcs, const uint64_t* shots,
+                        const uint64_t* seeds, uint32_t n, const nc_sample_opts& o, const CallOut* cos,
+                        unsigned long long* kept_count, uint32_t* err, Scratch& scratch, cudaStream_t stream,
+                        Timing* tm) {
+  nc_status st = NC_OK;
+  const bool fp32 = o.precision == NC_FP32_BATCHED;
+  if (!fp32 && o.precision != NC_FP64_PLAIN) return NC_E_UNSUPPORTED;
+  if (o.stratified || (o.outputs & NC_OUT_HOST)) return NC_E_UNSUPPORTED;
+  std::vector<uint32_t> order;
+  std::vector<double> cost(n, 0.0);
+  uint32_t kmax = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    const ProgHeader& h = header(progs[i]);
+    const DevProg d = dev_view(h, dcs[i]->blob);
+    if (!plain_supported(d) || h.k_max > 20) return NC_E_UNSUPPORTED;
+    if (!shots[i]) continue;
+    order.push_back(i);
+    kmax = std::max(kmax, h.k_max);
+    cost[i] = progs[i]->cp.counts.array_bytes + 64.0 * h.n_ops;
+  }
+  if (order.empty()) return NC_OK;
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
+  std::vector<LaunchParams> Ls(order.size());
+  std::vector<uint64_t> items(order.size());
+  for (size_t j = 0; j < order.size(); j++) {
+    const uint32_t i = order[j];
+    const ProgHeader& h = header(progs[i]);
+    LaunchParams& L = Ls[j];
+    std::memset(&L, 0, sizeof(L));
+    L.p = dev_view(h, dcs[i]->blob);
+    L.seed = seeds[i];
+    L.shot_offset = o.shot_offset;
+    L.shots = shots[i];
+    L.meas = cos[i].meas;
+    L.det = cos[i].det;
+    L.obs = cos[i].obs;
+    L.kept = cos[i].kept;
+    L.expval = cos[i].expval;
+    uint32_t lf = launch_flags(o);
+    if (!cos[i].expval || !h.n_probes) lf &= ~(uint32_t)LF_OUT_EXPVAL;
+    L.flags = lf;
+    L.row_words32 = 2 * ((shots[i] + 63) / 64);
+    L.kept_count = kept_count + i;
+    L.err = err;
+    L.stop_event = 0xffffffffu;
+    items[j] = (L.row_words32 * 32 + 127) / 128;
+  }
+  int per_sm = 0, n_sm = 0, dev = 0;
+  NC_TRY(cudaGetDevice(&dev));
+  NC_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  NC_TRY(plain_multi_occupancy(fp32, &per_sm));
+  if (per_sm < 1) return NC_E_UNSUPPORTED;
+  {
+    uint64_t total_items = 0;
+    for (uint64_t v : items) total_items += v;
+    uint64_t grid = std::min<uint64_t>((uint64_t)per_sm * n_sm, total_items);
+    // one vector slot per thread of the launch, within half the free memory
+    const uint64_t per_slot = kmax ? ((uint64_t)1 << kmax) * (fp32 ? 8 : 16) : 0;
+    if (per_slot) {
+      size_t free_b = 0;
+      NC_TRY(free_memory(LF_ASYNC, &free_b));
+      grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, free_b / 2 / (per_slot * 128)));
+    }
+    void *dLs = nullptr, *item0 = nullptr, *next = nullptr, *work = nullptr;
+    NC_TRY(scratch.get(&dLs, Ls.size() * sizeof(LaunchParams)));
+    NC_TRY(scratch.get(&item0, (Ls.size() + 1) * 8));
+    NC_TRY(scratch.get(&next, 8));
+    if (per_slot) NC_TRY(scratch.get(&work, per_slot * 128 * grid));
+    if (tm) NC_TRY(tm->begin(stream));
+    NC_TRY(launch_plain_multi(Ls.data(), (uint32_t)Ls.size(), items.data(), (LaunchParams*)dLs,
+                              (unsigned long long*)item0, (unsigned long long*)next, work, (uint32_t)grid, fp32,
+                              stream));
+    if (tm) {
+      NC_TRY(tm->end(stream));
+      tm->launches += 1 + (uint32_t)Ls.size();
+      tm->path |= 8u;
+    }
+  }
+done:
+  return st;
+}
+
 // Noiseless 64-shot reference launch: raw detector / observable parities.
 nc_status ensure_reference(nc_program* p, DevCopy& dc, cudaStream_t stream) {
   if (dc.ref_ready) return dc.ref_status;
@@ -1002,7 +1096,19 @@ nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, con
     NC_TRY(cudaMemsetAsync(counters, 0, 8 * (size_t)std::max<uint32_t>(n, 1), stream));
     NC_TRY(cudaMemsetAsync(err, 0, 4, stream));
     NC_TRY(cudaEventRecord(ev0, stream));
-    for (uint32_t i = 0; i < n; i++) {
+    // every program in one executor launch
+    const bool mp = o.tune && strstr(o.tune, "mp=1") && !host && !o.stratified;
+    if (mp) {
+      std::vector<CallOut> cos(n);
+      for (uint32_t i = 0; i < n; i++)
+        cos[i] = CallOut{(uint32_t*)outs[i].meas, (uint32_t*)outs[i].det, (uint32_t*)outs[i].obs,
+                         (uint32_t*)outs[i].kept, (o.outputs & NC_OUT_EXPVAL) ? outs[i].expval : nullptr};
+      st = enqueue_multi(progs, dcs, shots, seeds, n, o, cos.data(), (unsigned long long*)counters, (uint32_t*)err,
+                         scratch, stream, &tms[0]);
+      if (st != NC_OK) goto done;
+      NC_TRY(cudaEventRecord(ev1, stream));
+    }
+    for (uint32_t i = 0; i < n && !mp; i++) {
       if (shots[i] == 0) continue;
       const ProgHeader& h = header(progs[i]);
       CallOut co{(uint32_t*)outs[i].meas, (uint32_t*)outs[i].det, (uint32_t*)outs[i].obs,
@@ -1060,14 +1166,16 @@ nc_status sample_many(const nc_program* const* progs, const uint64_t* shots, con
     NC_TRY(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, stream));
     NC_TRY(cudaStreamSynchronize(stream));
     if (herr) st = NC_E_INTERNAL;
-    if (shots[n - 1] != 0 && cudaEventElapsedTime(&kernel_ms, ev0, ev1) != cudaSuccess) kernel_ms = 0.f;
+    if ((shots[n - 1] != 0 || mp) && cudaEventElapsedTime(&kernel_ms, ev0, ev1) != cudaSuccess) kernel_ms = 0.f;
+    if (mp)
+      for (uint32_t i = 1; i < n; i++) tms[i].path = tms[0].path;
   }
   NC_TRY(cudaStreamSynchronize(stream));
   for (uint32_t i = 0; i < n; i++) {
     outs[i].shots_run = shots[i];
     outs[i].shots_kept = kept[i];
     outs[i].kernel_ms = kernel_ms;
-    outs[i].exec_ms = shots[i] ? tms[i].ms() : 0.0;
+    outs[i].exec_ms = shots[i] ? (tms[i].path & 8u ? tms[0].ms() : tms[i].ms()) : 0.0;
     outs[i].launches = tms[i].launches;
     outs[i].path = tms[i].path;
   }
@@ -1251,8 +1359,17 @@ nc_status nc_sample_batch_async(const nc_program* const* progs, const uint64_t* 
     if (shots[i]) live.push_back(i);
   }
   if (live.empty()) return NC_OK;
-  const uint32_t nb = std::min<uint32_t>(kBranches, (uint32_t)live.size());
   nc_status st = NC_OK;
+  if (o.tune && strstr(o.tune, "mp=1") && !o.stratified) {
+    // every program in one executor launch on the caller's stream
+    std::vector<CallOut> cos(n);
+    for (uint32_t i = 0; i < n; i++)
+      cos[i] = CallOut{(uint32_t*)outs[i].meas, (uint32_t*)outs[i].det, (uint32_t*)outs[i].obs,
+                       (uint32_t*)outs[i].kept, (o.outputs & NC_OUT_EXPVAL) ? outs[i].expval : nullptr};
+    Scratch scratch(stream);
+    return enqueue_multi(progs, dcs, shots, seeds, n, o, cos.data(), kept_dev, err_dev, scratch, stream, nullptr);
+  }
+  const uint32_t nb = std::min<uint32_t>(kBranches, (uint32_t)live.size());
   std::vector<SideStream> side(nb);
   Events ev;
   NC_TRY(ev.make(1 + nb));

@@ -1333,14 +1333,14 @@ cudaError_t launch_presample(const LaunchParams& L, cudaStream_t st) {
 constexpr uint32_t kPlainMaxW = 8;       // N <= 256
 constexpr uint32_t kPlainMaxSlots = 2048;
 
+// Call-local shot sl of the program L describes, by one thread of a full
+// warp (32 consecutive shots); amplitude i of the shot lives at
+// work[i * stride + slot].
 template <typename real>
-__global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
+__device__ __forceinline__ void plain_shot(const LaunchParams& L, uint64_t sl, void* work, uint64_t stride,
+                                           uint64_t slot) {
   using C = typename Cx<real>::T;
   const DevProg& p = L.p;
-  // this launch covers call-local shots [plain_base, plain_base + plain_n)
-  const uint64_t sl = L.plain_base + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint64_t padded = L.row_words32 * 32u;
-  if ((sl & ~31ull) >= padded || sl - L.plain_base >= L.plain_n) return;  // whole warps only
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t word = sl >> 5;
   const bool valid = sl < L.shots;
@@ -1349,9 +1349,8 @@ __global__ void __launch_bounds__(128) exec_plain(LaunchParams L) {
   uint32_t x[kPlainMaxW], z[kPlainMaxW], slots[kPlainMaxSlots / 32];
   for (uint32_t w = 0; w < kPlainMaxW; w++) x[w] = z[w] = 0;
   for (uint32_t w = 0; w < kPlainMaxSlots / 32; w++) slots[w] = 0;
-  C* A = reinterpret_cast<C*>(L.work);
-  const uint64_t stride = L.plain_n;
-  auto amp = [&](uint32_t i) -> C& { return A[(size_t)i * stride + (sl - L.plain_base)]; };
+  C* A = reinterpret_cast<C*>(work);
+  auto amp = [&](uint32_t i) -> C& { return A[(size_t)i * stride + slot]; };
   auto mk = [](real re, real im) -> C {
     C c;
     c.x = re;
@@ -1849,6 +1848,77 @@ cudaError_t launch_prefix(const Op* host_ops, uint32_t n, bool fp64, void* vec, 
   return cudaSuccess;
 }
 
+template <typename real>
+__global__ void __launch_bounds__(128) exec_plain(const __grid_constant__ LaunchParams L) {
+  // this launch covers call-local shots [plain_base, plain_base + plain_n)
+  const uint64_t sl = L.plain_base + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t padded = L.row_words32 * 32u;
+  if ((sl & ~31ull) >= padded || sl - L.plain_base >= L.plain_n) return;  // whole warps only
+  plain_shot<real>(L, sl, L.work, L.plain_n, sl - L.plain_base);
+}
+
+// Many programs in one persistent launch (the batching row of Sec. 3.2):
+// item j is 128 shots of one program, program i owning items
+// [item0[i], item0[i + 1]) (programs ordered longest first by the host).
+// CTAs take items from the counter `next`, stage the item's launch
+// parameters in shared memory, and run one shot per thread; each thread
+// keeps one vector slot of the workspace (2^k_max of the batch amplitudes,
+// slot = global thread index, stride = threads of the launch).
+template <typename real>
+__global__ void __launch_bounds__(128) exec_plain_multi(const LaunchParams* __restrict__ Ls,
+                                                        const unsigned long long* __restrict__ item0,
+                                                        uint32_t n_progs, unsigned long long* next, void* work) {
+  static_assert(sizeof(LaunchParams) % 4 == 0, "launch parameters copied as words");
+  __shared__ __align__(16) uint32_t lsh[sizeof(LaunchParams) / 4];
+  __shared__ unsigned long long it_sh;
+  __shared__ uint32_t prog_sh;
+  const LaunchParams& L = *reinterpret_cast<const LaunchParams*>(lsh);
+  const uint64_t n_items = item0[n_progs];
+  const uint64_t slot = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint32_t cur = 0xffffffffu;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long it = atomicAdd(next, 1ull);
+      uint32_t lo = 0, hi = n_progs;  // the program with item0[i] <= it < item0[i + 1]
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (item0[mid] <= it) lo = mid;
+        else hi = mid;
+      }
+      it_sh = it;
+      prog_sh = lo;
+    }
+    __syncthreads();
+    const unsigned long long it = it_sh;
+    const uint32_t pi = prog_sh;
+    if (it >= n_items) break;
+    if (pi != cur) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(Ls + pi);
+      for (uint32_t w = threadIdx.x; w < sizeof(LaunchParams) / 4; w += blockDim.x) lsh[w] = src[w];
+      cur = pi;
+      __syncthreads();
+    }
+    const uint64_t sl = (it - item0[pi]) * blockDim.x + threadIdx.x;
+    if ((sl & ~31ull) < L.row_words32 * 32u) plain_shot<real>(L, sl, work, stride, slot);
+    __syncthreads();  // the item and parameters stay until every thread is done
+  }
+}
+
+// Stores one program's launch parameters (and its first item) for the
+// multi-program launch: a kernel, so that a captured graph needs no host
+// memory at replay.
+__global__ void store_params(const __grid_constant__ LaunchParams L, LaunchParams* dst, unsigned long long* item0,
+                             unsigned long long first, unsigned long long end, uint32_t last) {
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&L);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (uint32_t w = threadIdx.x; w < sizeof(LaunchParams) / 4; w += blockDim.x) d[w] = src[w];
+  if (threadIdx.x == 0) {
+    item0[0] = first;
+    if (last) item0[1] = end;
+  }
+}
+
 // fp32: FP32 amplitudes (the thread-per-shot layout of the batched form),
 // else the plain FP64 form.
 cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st, bool fp32) {
@@ -1857,6 +1927,33 @@ cudaError_t launch_plain(const LaunchParams& L, cudaStream_t st, bool fp32) {
   if (fp32) exec_plain<float><<<(uint32_t)blocks, threads, 0, st>>>(L);
   else exec_plain<double><<<(uint32_t)blocks, threads, 0, st>>>(L);
   return cudaGetLastError();
+}
+
+// The multi-program thread-per-shot launch: parameters stored by one small
+// launch per program, then one persistent launch of `grid` CTAs over every
+// program's items. Ls: n device LaunchParams; item0: n + 1 device u64; next:
+// a device u64 zeroed here; work: grid * 128 * 2^k_max amplitudes.
+cudaError_t launch_plain_multi(const LaunchParams* hLs, uint32_t n, const uint64_t* h_items, LaunchParams* dLs,
+                               unsigned long long* item0, unsigned long long* next, void* work, uint32_t grid,
+                               bool fp32, cudaStream_t st) {
+  uint64_t acc = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    store_params<<<1, 128, 0, st>>>(hLs[i], dLs + i, item0 + i, acc, acc + h_items[i], i + 1 == n);
+    acc += h_items[i];
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  if (fp32) exec_plain_multi<float><<<grid, 128, 0, st>>>(dLs, item0, n, next, work);
+  else exec_plain_multi<double><<<grid, 128, 0, st>>>(dLs, item0, n, next, work);
+  return cudaGetLastError();
+}
+
+// resident CTAs of the multi-program launch per SM
+cudaError_t plain_multi_occupancy(bool fp32, int* per_sm) {
+  return fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, exec_plain_multi<float>, 128, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, exec_plain_multi<double>, 128, 0);
 }
 
 bool plain_supported(const DevProg& p) {

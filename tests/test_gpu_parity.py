@@ -19,7 +19,7 @@ from oracle.factored import FactoredSim
 from oracle.records import assemble
 from oracle.stabilizer import FrameSim
 
-from parity import gpu_records, near_tie, state_error, unpack
+from parity import compare, gpu_records, near_tie, state_error, unpack
 
 pytestmark = pytest.mark.gpu
 
@@ -426,8 +426,9 @@ def test_host_outputs_direct_and_staged(nc, case):
         if tune is None and not h["path"] & 2:
             continue  # this device cannot write the caller's pinned memory directly
         assert h["path"] & bit, (tune, h["path"])
-        for key in ("meas", "det", "obs", "kept"):
-            assert (d[key].cpu().numpy() == h[key]).all(), (tune, key)
+        info = prog.info
+        for key, n in (("meas", info.n_meas), ("det", info.n_det), ("obs", info.n_obs), ("kept", 1)):
+            assert (d[key][:n].cpu().numpy() == h[key][:n]).all(), (tune, key)
         assert d["shots_kept"] == h["shots_kept"]
 
 
@@ -450,6 +451,70 @@ def test_batch_equals_individual(nc):
     for p, s, sd, r in zip(progs, shots, seeds, res):
         one = nc.sample(p, s, sd)
         assert (one["meas"].cpu().numpy() == r["meas"].cpu().numpy()).all()
+
+
+@pytest.mark.parametrize("postselect", [False, True])
+def test_one_launch_batch_equals_individual(nc, postselect):
+    """tune "mp=1": every program of a batch (k_max 0 to 10, ragged shot
+    counts) in one persistent thread-per-shot launch over a work list of
+    128-shot items. Its records equal the thread-per-shot layout run program
+    by program (same arithmetic), bit for bit; and the oracle's on sampled
+    shots."""
+    texts = [gc.surface_code_memory(d=3, rounds=2, p=0.02), gc.tiny_random(seed=4), gc.fig4_example(0.1),
+             gc.low_magic_gadgets(), gc.dense_random(seed=33, n=10, layers=12),
+             gc.surface_code_memory(d=3, rounds=1, p=1e-3, theta=0.02)]
+    progs = [nc.compile(t) for t in texts]
+    shots = [1000, 3001, 65, 777, 129, 2048]
+    seeds = [1, 2, 3, 4, 5, 6]
+    res = nc.sample_batch(progs, shots, seeds, tune="mp=1", postselect=postselect)
+    for p, s, sd, r, t in zip(progs, shots, seeds, res, texts):
+        assert r["path"] & 8
+        one = nc.sample(p, s, sd, tune="lp=1", postselect=postselect)
+        info = p.info
+        for key, n in (("meas", info.n_meas), ("det", info.n_det), ("obs", info.n_obs), ("kept", 1)):
+            assert torch_equal(one[key][:n], r[key][:n]), key
+        assert one["shots_kept"] == r["shots_kept"]
+        sim = FactoredSim(t)
+        g = {k: nc.unpack_rows(r[k], s)[:n] for k, n in (("meas", info.n_meas), ("det", info.n_det),
+                                                         ("obs", info.n_obs), ("kept", 1))}
+        g["kept"] = g["kept"][0]
+        n_ok, flagged = compare(sim, g, range(0, s, max(1, s // 40)), sd, postselect=postselect)
+        assert flagged <= 2
+
+
+def test_one_launch_graph_equals_batch(nc):
+    """nc_sample_batch_async with tune "mp=1" captured in a CUDA graph (six
+    sweep circuits): one executor launch, the records of nc_sample_batch
+    with the same tune, on two replays."""
+    import torch
+    sweep = gc.sweep_batch(64)
+    picks = sorted(range(64), key=lambda i: (gc.sweep_mirror(i).n, i))[:6]
+    progs = [nc.compile(sweep[i].text) for i in picks]
+    shots = [5_000 + 1_000 * j for j in range(len(progs))]
+    seeds = [5005 + i for i in picks]
+    ref = nc.sample_batch(progs, shots, seeds, tune="mp=1")
+    for p in progs:
+        nc.prepare(p)
+    outs = [nc.alloc_records(p, s) for p, s in zip(progs, shots)]
+    kept = torch.zeros(len(progs), dtype=torch.int64, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        nc.sample_batch_async(progs, shots, seeds, outs, kept, err, tune="mp=1")
+    for _ in range(2):
+        for o in outs:
+            for key in ("meas", "det", "obs", "kept"):
+                if o[key] is not None:
+                    o[key].zero_()
+        kept.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
+        for p, o, r in zip(progs, outs, ref):
+            info = p.info
+            for key, n in (("meas", info.n_meas), ("det", info.n_det), ("obs", info.n_obs), ("kept", 1)):
+                assert torch_equal(o[key][:n], r[key][:n]), key
+        assert [int(x) for x in kept.cpu()] == shots
 
 
 def test_noiseless_option(nc):
@@ -670,8 +735,9 @@ def test_shared_prefix_equals_per_shot_execution(nc, precision):
 
 
 def test_shared_prefix_k20_mirror_returns_to_zero(nc):
-    """The k = 20 mirror circuit through the shared prefix: every record 0."""
-    prog = nc.compile(gc.dense_random(seed=3, n=20, layers=12, mirror=True))
+    """The k = 20 mirror circuit through the shared prefix: every record 0
+    (the plain method: the HIR passes collapse the mirror to k_max = 0)."""
+    prog = nc.compile(gc.dense_random(seed=3, n=20, layers=12, mirror=True), peephole=False)
     res = nc.sample(prog, 256, 3)
     assert res["path"] & 1
     assert int(res["meas"][: prog.info.n_meas].count_nonzero()) == 0
