@@ -410,6 +410,11 @@ struct Timing {
 constexpr uint32_t kNoStratum = 0xffffffffu;
 constexpr uint32_t kMaxStratum = 127;  // per-shot fault lists hold up to 127 entries
 
+nc_status enqueue_multi_flags(const nc_program* const* progs, const std::vector<DevCopy*>& dcs,
+                              const uint64_t* shots, const uint64_t* seeds, uint32_t n, const nc_sample_opts& o,
+                              uint32_t lflags, const CallOut* cos, unsigned long long* kept_count, uint32_t* err,
+                              Scratch& scratch, cudaStream_t stream, Timing* tm);
+
 // Enqueue one sampling launch. kept_count must point to a zeroed device u64.
 nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uint64_t seed,
                   uint64_t shot_offset, int precision, uint32_t lflags, const char* tune, CallOut o,
@@ -452,6 +457,23 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
   L.dump_amps = dump_amps;
   L.dump_frame = dump_frame;
   L.dump_k = dump_k;
+  // the persistent thread-per-shot launch for one program (tune mp=1; mg=
+  // sets its resident CTAs per SM)
+  if (precision == NC_FP32_BATCHED && tune && strstr(tune, "mp=1") && !strat && stop_event == 0xffffffffu &&
+      h.k_max > 0 && plain_supported(L.p)) {
+    nc_sample_opts o1;
+    std::memset(&o1, 0, sizeof(o1));
+    o1.precision = NC_FP32_BATCHED;
+    o1.shot_offset = shot_offset;
+    o1.tune = tune;
+    const nc_program* one = prog;
+    std::vector<DevCopy*> d1{const_cast<DevCopy*>(&dc)};
+    CallOut c1 = o;
+    if (!(lflags & LF_OUT_EXPVAL)) c1.expval = nullptr;
+    st = enqueue_multi_flags(&one, d1, &shots, &seed, 1, o1, lflags, &c1, kept_count, err, scratch, stream, tm);
+    if (st != NC_E_UNSUPPORTED) return st;
+    st = NC_OK;
+  }
   // thread-per-shot layout: the plain FP64 form, or the FP32 batched form's
   // layout for small vectors (tune lp=1)
   bool lp32 = false;
@@ -742,10 +764,10 @@ uint32_t launch_flags(const nc_sample_opts& o);
 // persistent CTAs finish together. FP32 amplitudes (NC_FP32_BATCHED) or
 // FP64 (NC_FP64_PLAIN); no stratified calls, host outputs or debug stops.
 // Returns NC_E_UNSUPPORTED when a program does not fit the layout.
-nc_status enqueue_multi(const nc_program* const* progs, const std::vector<DevCopy*>& dcs, const uint64_t* shots,
-                        const uint64_t* seeds, uint32_t n, const nc_sample_opts& o, const CallOut* cos,
-                        unsigned long long* kept_count, uint32_t* err, Scratch& scratch, cudaStream_t stream,
-                        Timing* tm) {
+nc_status enqueue_multi_flags(const nc_program* const* progs, const std::vector<DevCopy*>& dcs,
+                              const uint64_t* shots, const uint64_t* seeds, uint32_t n, const nc_sample_opts& o,
+                              uint32_t lflags, const CallOut* cos, unsigned long long* kept_count, uint32_t* err,
+                              Scratch& scratch, cudaStream_t stream, Timing* tm) {
   nc_status st = NC_OK;
   const bool fp32 = o.precision == NC_FP32_BATCHED;
   if (!fp32 && o.precision != NC_FP64_PLAIN) return NC_E_UNSUPPORTED;
@@ -780,11 +802,11 @@ nc_status enqueue_multi(const nc_program* const* progs, const std::vector<DevCop
     L.obs = cos[i].obs;
     L.kept = cos[i].kept;
     L.expval = cos[i].expval;
-    uint32_t lf = launch_flags(o);
+    uint32_t lf = lflags;
     if (!cos[i].expval || !h.n_probes) lf &= ~(uint32_t)LF_OUT_EXPVAL;
     L.flags = lf;
     L.row_words32 = 2 * ((shots[i] + 63) / 64);
-    L.kept_count = kept_count + i;
+    L.kept_count = kept_count + (n == 1 ? 0 : i);
     L.err = err;
     L.stop_event = 0xffffffffu;
     items[j] = (L.row_words32 * 32 + 127) / 128;
@@ -794,6 +816,12 @@ nc_status enqueue_multi(const nc_program* const* progs, const std::vector<DevCop
   NC_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   NC_TRY(plain_multi_occupancy(fp32, &per_sm));
   if (per_sm < 1) return NC_E_UNSUPPORTED;
+  {
+    // mg: resident CTAs per SM (fewer vector slots: a working set that stays in L2)
+    const char* mg = o.tune ? strstr(o.tune, "mg=") : nullptr;
+    unsigned v = 0;
+    if (mg && sscanf(mg, "mg=%u", &v) == 1 && v >= 1) per_sm = std::min<int>(per_sm, (int)v);
+  }
   {
     uint64_t total_items = 0;
     for (uint64_t v : items) total_items += v;
@@ -822,6 +850,14 @@ nc_status enqueue_multi(const nc_program* const* progs, const std::vector<DevCop
   }
 done:
   return st;
+}
+
+nc_status enqueue_multi(const nc_program* const* progs, const std::vector<DevCopy*>& dcs, const uint64_t* shots,
+                        const uint64_t* seeds, uint32_t n, const nc_sample_opts& o, const CallOut* cos,
+                        unsigned long long* kept_count, uint32_t* err, Scratch& scratch, cudaStream_t stream,
+                        Timing* tm) {
+  return enqueue_multi_flags(progs, dcs, shots, seeds, n, o, launch_flags(o), cos, kept_count, err, scratch, stream,
+                             tm);
 }
 
 // Noiseless 64-shot reference launch: raw detector / observable parities.
@@ -1429,8 +1465,11 @@ nc_status nc_autotune(nc_program* prog, uint64_t shots, const nc_sample_opts* op
     // the warp-per-shot layout (vectors in shared memory, frame in registers)
     if (warp_supported(d) && h.k_max <= 13)
       for (const char* c : {"lw=1", "lw=1,wn=4", "lw=1,wn=2"}) cand.push_back(c);
-    // the thread-per-shot layout (vectors in global memory, no barriers)
-    if (plain_supported(d) && h.k_max <= 12) cand.push_back("lp=1");
+    // the thread-per-shot layout (vectors in global memory, no barriers), and
+    // its persistent form with one vector slot per resident thread (fewer
+    // resident CTAs: the vectors stay in L2)
+    if (plain_supported(d) && h.k_max <= 12)
+      for (const char* c : {"lp=1", "mp=1", "mp=1,mg=4", "mp=1,mg=2", "mp=1,mg=1"}) cand.push_back(c);
   }
   Scratch scratch(stream);
   void *meas = nullptr, *det = nullptr, *obs = nullptr, *kept = nullptr;

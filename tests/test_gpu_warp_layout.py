@@ -1,7 +1,9 @@
 """The warp-per-shot layout (exec_warp, tune "lw=1": every shot on one
 warp, its active vector in shared memory, its frame in registers) and the
 FP32 thread-per-shot layout (exec_plain<float>, tune "lp=1": every shot on
-one thread, its vector in global memory, FP64 measurement sums). Records
+one thread, its vector in global memory, FP64 measurement sums), also in its
+persistent form (exec_plain_multi, tune "mp=1", "mg" resident CTAs per SM:
+one vector slot per resident thread, reused shot after shot). Records
 against the dense oracle (random small circuits with every instruction kind)
 and the factored oracle (the workloads), near-ties flagged; records equal
 those of the tile layout shot by shot except near-ties; tile boundaries and
@@ -58,7 +60,7 @@ def test_random_small_vs_dense(nc, seed, precision, tune):
 @pytest.mark.parametrize("name,shots,postselect", [("tiny", 2500, False), ("lowmagic", 400, True),
                                                    ("coherent", 400, False), ("dense10", 300, False),
                                                    ("fig4", 777, False)])
-@pytest.mark.parametrize("tune", ["lw=1", "lp=1"])
+@pytest.mark.parametrize("tune", ["lw=1", "lp=1", "mp=1,mg=1"])
 def test_workloads_vs_oracle(nc, name, shots, postselect, tune):
     text = {"tiny": lambda: gc.tiny_random(seed=1), "lowmagic": gc.low_magic_gadgets,
             "coherent": lambda: gc.surface_code_memory(d=3, rounds=3, p=1e-3, theta=0.02),
@@ -74,7 +76,7 @@ def test_workloads_vs_oracle(nc, name, shots, postselect, tune):
 
 
 @pytest.mark.parametrize("shots", [1, 31, 32, 33, 65, 1000, 70_001])
-@pytest.mark.parametrize("tune", ["lw=1", "lp=1"])
+@pytest.mark.parametrize("tune", ["lw=1", "lp=1", "mp=1", "mp=1,mg=1"])
 def test_equals_tile_layout(nc, shots, tune):
     """Ragged counts and many tiles: the warp layout's records equal the tile
     layout's on every shot whose draws are not near-ties (postselected
@@ -91,7 +93,7 @@ def test_equals_tile_layout(nc, shots, tune):
         assert int(raw[0, -1] >> np.uint64(shots % 64)) == 0
 
 
-@pytest.mark.parametrize("tune", ["lw=1", "lp=1"])
+@pytest.mark.parametrize("tune", ["lw=1", "lp=1", "mp=1,mg=2"])
 def test_shot_offset(nc, tune):
     text = gc.tiny_random(seed=2)
     prog = nc.compile(text)
