@@ -76,15 +76,17 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def ncu_traffic(workload_name: str):
+def ncu_traffic(workload_name: str, shape=None):
     """DRAM bytes per shot from the committed ncu summary, if it was taken
-    on the current kernel source."""
+    on the current kernel source and in the same launch shape."""
     try:
         d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
     except Exception:
         return None
     e = d.get(workload_name)
     if not e or e.get("kernel_sha") != kernel_sha():
+        return None
+    if shape and e.get("launch_shape") and e["launch_shape"] != shape:
         return None
     return e.get("dram_bytes_per_shot")
 
@@ -405,7 +407,7 @@ def run_ours(args):
         per_shot += 8.0 * 2 ** info.prefix_k - info.prefix_bytes_fp32
     alg = per_shot * shots
     achieved = alg / (exec_ms / 1000.0) / 1e9
-    tr = ncu_traffic(wname)
+    tr = ncu_traffic(wname, shape)
     affine = info.k_max == 0 and "a=0" not in (args.tune or "")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": (tr * shots) if tr else None,
