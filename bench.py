@@ -415,6 +415,9 @@ def run_ours(args):
             else "exec_plain<float>" if "lp=1" in (shape or "") else "exec_batched",
             "peak_source": f"{peak_src} (hbm_gbs, burst copy)",
             "algorithmic_bytes_per_launch": alg, "kernel_ms": exec_ms, "call_ms": call_ms,
+            # the DRAM-measured fraction beside the effective one: committed ncu
+            # bytes per shot x shots over the same kernel time
+            "traffic_frac": (tr * shots / (exec_ms / 1000.0) / 1e9 / peaks["hbm_gbs"]) if tr else None,
             "bytes_model": "records written + active-vector traversals of the unfused instruction list "
                            "(Sec. 2.6 traversal count, 8 B per FP32 amplitude); fused passes, vectors kept in "
                            "shared memory and a shared prefix read as effective bandwidth above the copy peak"}

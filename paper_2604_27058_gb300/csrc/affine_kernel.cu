@@ -31,6 +31,11 @@
 
 namespace nc {
 
+template <bool B>
+struct Flag {
+  static constexpr bool value = B;
+};
+
 constexpr uint32_t kAffTpw = 32;    // threads per 32-shot word of the tile: one warp per word
 constexpr uint32_t kAffPool = 32;   // shots per warp (fused sampling): S / warps
 constexpr uint32_t kAffList = 128;  // chunk items per warp list
@@ -111,13 +116,11 @@ __device__ __forceinline__ uint32_t warp_incl(uint32_t v, uint32_t lane) {
   return v;
 }
 
-// Fault items of the tile kernel: (first chunk << 14) | (chunks << 10) |
-// shot in the tile, one per fault (a fault of more than kItemMaxChunks
-// chunks takes several); first chunks below 2^18.
-constexpr uint32_t kItemMaxChunks = 15;
-__device__ __forceinline__ uint32_t fault_item(uint32_t c0, uint32_t nch, uint32_t shot) {
-  return (c0 << 14) | (nch << 10) | shot;
-}
+// Fault items of the tile kernel: (chunk << 10) | shot in the tile, one per
+// 8-row chunk of a fault's column (about one per fault for the surface code),
+// so that applying a list is one chunk per lane with no loop; chunks below
+// 2^22.
+__device__ __forceinline__ uint32_t chunk_item(uint32_t chunk, uint32_t shot) { return (chunk << 10) | shot; }
 
 // affine_items: fault sampling alone, at high occupancy (no record tile).
 // One warp per tile of `pool` shots (tile g of the launch = call-local shots
@@ -159,20 +162,14 @@ __global__ void __launch_bounds__(512, 2) affine_items(LaunchParams L, uint32_t 
           fin = st >= p.n_sites;
         }
       }
-      const uint32_t big = __ballot_sync(0xffffffffu, nch > kItemMaxChunks);
-      if (!big) {
-        // at most one item per lane: place by ballot
-        const uint32_t has = __ballot_sync(0xffffffffu, nch != 0);
+      // one item per chunk, placed by ballot: every lane's first chunk, then
+      // one round per further chunk of the (rare) multi-chunk faults
+      for (uint32_t c = 0;; c++) {
+        const uint32_t has = __ballot_sync(0xffffffffu, nch > c);
+        if (!has) break;
         const uint32_t pos = cnt + __popc(has & lt);
-        if (nch && pos < cap) out[pos] = fault_item(c0, nch, it0);
+        if (nch > c && pos < cap) out[pos] = chunk_item(c0 + c, it0);
         cnt += __popc(has);
-      } else {
-        const uint32_t k = (nch + kItemMaxChunks - 1) / kItemMaxChunks;
-        const uint32_t incl = warp_incl(k, lane);
-        uint32_t pos = cnt + incl - k;
-        for (uint32_t c = 0; c < nch; c += kItemMaxChunks, pos++)
-          if (pos < cap) out[pos] = fault_item(c0 + c, min(kItemMaxChunks, nch - c), it0);
-        cnt += __shfl_sync(0xffffffffu, incl, 31);
       }
       const uint32_t done = __ballot_sync(0xffffffffu, fin);
       if (fin) {
@@ -383,14 +380,19 @@ __global__ void __launch_bounds__(kAffTpw * WPT, 65536 / (kAffTpw * WPT * 64)) s
       const uint4 tb = philox(make_uint4((uint32_t)g, (uint32_t)(g >> 32), TAG_MT, __ldg(p.aff_rand_ev + j)), key);
       *reinterpret_cast<uint4*>(MW + j * WPT + grp * 4u) = make_uint4(~tb.x, ~tb.y, ~tb.z, ~tb.w);
     }
-    // 2. faults into the zeroed tile: pre-sampled items, one per fault
+    // 2. faults into the zeroed tile: pre-sampled items, one chunk per lane,
+    // two chunk loads in flight before their atomics
     if (noisy && titems) {
-      for (uint32_t i = t; i < tcnt; i += T) {
-        const uint32_t it = __ldg(titems + i);
-        const uint32_t sh = it & 1023u, nch = (it >> 10) & 15u, c0 = it >> 14;
-        uint32_t* col = TILE + (sh >> 5);
-        const uint32_t bit = 1u << (sh & 31u);
-        for (uint32_t c = 0; c < nch; c++) xor_chunk<WPT>(col, __ldg(p.aff_chunks + c0 + c), bit, R, dump);
+      uint32_t i = t;
+      for (; i + T < tcnt; i += 2 * T) {
+        const uint32_t ia = __ldg(titems + i), ib = __ldg(titems + i + T);
+        const uint4 ca = __ldg(p.aff_chunks + (ia >> 10)), cb = __ldg(p.aff_chunks + (ib >> 10));
+        xor_chunk<WPT>(TILE + ((ia & 1023u) >> 5), ca, 1u << (ia & 31u), R, dump);
+        xor_chunk<WPT>(TILE + ((ib & 1023u) >> 5), cb, 1u << (ib & 31u), R, dump);
+      }
+      if (i < tcnt) {
+        const uint32_t ia = __ldg(titems + i);
+        xor_chunk<WPT>(TILE + ((ia & 1023u) >> 5), __ldg(p.aff_chunks + (ia >> 10)), 1u << (ia & 31u), R, dump);
       }
     }
     // otherwise fault sampling in the tile kernel
@@ -408,25 +410,28 @@ __global__ void __launch_bounds__(kAffTpw * WPT, 65536 / (kAffTpw * WPT * 64)) s
       return s0 + 32 <= L.shots ? ~0u : s0 < L.shots ? (1u << (uint32_t)(L.shots - s0)) - 1u : 0u;
     };
     // the quad v of a record row at words gw .. gw + 3 of dst (rows are
-    // 8-byte aligned; 16-byte stores when row_words32 % 4 == 0)
-    auto put = [&](uint32_t* dst, uint64_t gw, uint4 v) {
-      if (fast) {
-        *reinterpret_cast<uint4*>(dst) = v;
-        return;
-      }
-      if (gw >= L.row_words32) return;  // row_words32 is even: gw + 1 is out too
-      v.x &= valid(gw);
-      v.y &= valid(gw + 1);
-      v.z &= valid(gw + 2);
-      v.w &= valid(gw + 3);
-      if ((L.row_words32 & 3u) == 0) {
+    // 8-byte aligned; 16-byte stores when row_words32 % 4 == 0). FAST (a
+    // full tile, rows of a multiple of 4 words): the plain 16-byte store; the
+    // output pass below is instantiated for both, so a full tile's loop
+    // carries no ragged-edge code.
+    auto put_any = [&](auto fast_tag, uint32_t* dst, uint64_t gw, uint4 v) {
+      if constexpr (decltype(fast_tag)::value) {
         *reinterpret_cast<uint4*>(dst) = v;
       } else {
-        *reinterpret_cast<uint2*>(dst) = make_uint2(v.x, v.y);
-        if (gw + 2 < L.row_words32) *reinterpret_cast<uint2*>(dst + 2) = make_uint2(v.z, v.w);
+        if (gw >= L.row_words32) return;  // row_words32 is even: gw + 1 is out too
+        v.x &= valid(gw);
+        v.y &= valid(gw + 1);
+        v.z &= valid(gw + 2);
+        v.w &= valid(gw + 3);
+        if ((L.row_words32 & 3u) == 0) {
+          *reinterpret_cast<uint4*>(dst) = v;
+        } else {
+          *reinterpret_cast<uint2*>(dst) = make_uint2(v.x, v.y);
+          if (gw + 2 < L.row_words32) *reinterpret_cast<uint2*>(dst + 2) = make_uint2(v.z, v.w);
+        }
       }
     };
-    {
+    auto out_pass = [&](auto fast_tag) {
       const uint32_t qd = lane % QPL, cw = lane / QPL;
       const uint64_t gw = gw0 + 4u * qd;
       // the delta at position j with its row's constant and random-bit
@@ -451,7 +456,7 @@ __global__ void __launch_bounds__(kAffTpw * WPT, 65536 / (kAffTpw * WPT * 64)) s
       auto cell = [&](uint32_t j) -> uint4* { return reinterpret_cast<uint4*>(TILE + j * WPT) + qd; };
       auto emit = [&](uint32_t j, uint4 v) {
         uint32_t* dst = ROWP[j];
-        if (dst) put(dst + gw, gw, v);
+        if (dst) put_any(fast_tag, dst + gw, gw, v);
       };
       const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
       // chains of two or more rows: lane slot cw of warp w walks chain
@@ -496,9 +501,15 @@ __global__ void __launch_bounds__(kAffTpw * WPT, 65536 / (kAffTpw * WPT * 64)) s
           }
         }
       }
+    };
+    if (fast) out_pass(Flag<true>{});
+    else out_pass(Flag<false>{});
+    {
       // the kept row: every shot of the tile
-      if ((L.flags & LF_OUT_KEPT) && t < QPL)
-        put(L.kept + gw0 + 4u * t, gw0 + 4u * t, make_uint4(~0u, ~0u, ~0u, ~0u));
+      if ((L.flags & LF_OUT_KEPT) && t < QPL) {
+        if (fast) put_any(Flag<true>{}, L.kept + gw0 + 4u * t, gw0 + 4u * t, make_uint4(~0u, ~0u, ~0u, ~0u));
+        else put_any(Flag<false>{}, L.kept + gw0 + 4u * t, gw0 + 4u * t, make_uint4(~0u, ~0u, ~0u, ~0u));
+      }
     }
     if (t == 0 && (uint64_t)tile * S < L.shots) {
       const uint64_t left = L.shots - (uint64_t)tile * S;

@@ -519,8 +519,8 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
       NC_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
       // with the item passes overlapped, the tile kernel keeps one CTA of
       // 512 threads per SM so that an item-pass CTA fits beside it
-      // (item lists name first chunks below 2^18: affine_kernel.cu fault_item)
-      const bool items = tu.AI && !(lflags & LF_NOISELESS) && h.n_sites > 0 && h.aff_n_chunks < (1u << 18);
+      // (item lists name chunks below 2^22: affine_kernel.cu chunk_item)
+      const bool items = tu.AI && !(lflags & LF_NOISELESS) && h.n_sites > 0 && h.aff_n_chunks < (1u << 22);
       const bool overlap = items && tu.AO;
       uint32_t wpt = 0;
       int best_warps = 0, best_ctas = 0;
@@ -549,7 +549,11 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
         uint32_t cap = 0;
         uint32_t *ibuf = nullptr, *cbuf = nullptr;
         if (items) {
-          const uint64_t wave_shots = tu.AV ? tu.AV : (8ull << 20);
+          // default pass: one tile per warp of the item kernel (2 CTAs of 16
+          // warps per SM), so no warp is left with a second tile while the
+          // others idle; the pass's item lists (16 KB per tile for the surface
+          // code) then stay in L2 for the tile kernel
+          const uint64_t wave_shots = tu.AV ? tu.AV : 32ull * (uint64_t)n_sm * tile_shots;
           wave = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, wave_shots / tile_shots));
           // list capacity per tile: mean + 10 sigma (a chunk count per fault
           // of at most 15, so the variance is below 16 x the mean) + slack
