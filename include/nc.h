@@ -107,7 +107,8 @@ typedef struct {
                              warp-per-shot layout), wn (its warps per CTA),
                              lp (1: FP32 thread-per-shot layout), hd (0:
                              host outputs staged, not written directly), hc
-                             (shots per staged chunk) */
+                             (shots per staged chunk), aq (resident
+                             item-kernel CTAs per SM: 2, 3, 4) */
   int noiseless;          /* 1 = disable every noise site (reference runs) */
   uint32_t stratified;    /* 0 = independent noise sites (default);
                              1 = stratified importance sampling: every shot

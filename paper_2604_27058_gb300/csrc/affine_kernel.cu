@@ -127,9 +127,10 @@ __device__ __forceinline__ uint32_t chunk_item(uint32_t chunk, uint32_t shot) { 
 // (tile0 + g) * pool ...), lanes refilled as their shots end; every fault's
 // item goes to the pool's list items[g * cap ...], and counts[g] receives
 // the number of items (a count above cap means the list overflowed).
-__global__ void __launch_bounds__(512, 2) affine_items(LaunchParams L, uint32_t pool0, uint32_t n_pools,
-                                                       uint32_t* items, uint32_t cap, uint32_t* counts,
-                                                       uint32_t pool) {
+template <int MINB>
+__global__ void __launch_bounds__(512, MINB) affine_items(LaunchParams L, uint32_t pool0, uint32_t n_pools,
+                                                          uint32_t* items, uint32_t cap, uint32_t* counts,
+                                                          uint32_t pool) {
   const DevProg& p = L.p;
   const uint32_t lane = threadIdx.x & 31u, lt = (1u << lane) - 1u;
   const uint32_t wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -538,10 +539,16 @@ static cudaError_t aff_one(const LaunchParams& L, uint32_t grid, size_t smem, cu
   return cudaGetLastError();
 }
 
-// Item lists for the tiles [tile0, tile0 + n_tiles) of a call.
+// Item lists for the tiles [tile0, tile0 + n_tiles) of a call; minb = 2, 3
+// or 4 resident 512-thread CTAs per SM (register cap 64, 42, 32): more warps
+// to hide the Philox and search latencies.
 cudaError_t launch_affine_items(const LaunchParams& L, uint32_t tile0, uint32_t n_tiles, uint32_t* items,
-                                uint32_t cap, uint32_t* counts, uint32_t tile_shots, uint32_t grid, cudaStream_t st) {
-  affine_items<<<grid, 512, 0, st>>>(L, tile0, n_tiles, items, cap, counts, tile_shots);
+                                uint32_t cap, uint32_t* counts, uint32_t tile_shots, uint32_t grid, cudaStream_t st,
+                                uint32_t minb) {
+  if (minb == 2) affine_items<2><<<grid, 512, 0, st>>>(L, tile0, n_tiles, items, cap, counts, tile_shots);
+  else if (minb == 3) affine_items<3><<<grid, 512, 0, st>>>(L, tile0, n_tiles, items, cap, counts, tile_shots);
+  else if (minb == 4) affine_items<4><<<grid, 512, 0, st>>>(L, tile0, n_tiles, items, cap, counts, tile_shots);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

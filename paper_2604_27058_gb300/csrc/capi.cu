@@ -43,7 +43,8 @@ cudaError_t launch_warp(const LaunchParams& L, bool fp64, uint32_t nwarps, uint3
 cudaError_t launch_affine(const LaunchParams& L, uint32_t wpt, uint32_t grid, size_t smem, cudaStream_t st,
                           int* per_sm);
 cudaError_t launch_affine_items(const LaunchParams& L, uint32_t tile0, uint32_t n_tiles, uint32_t* items,
-                                uint32_t cap, uint32_t* counts, uint32_t tile_shots, uint32_t grid, cudaStream_t st);
+                                uint32_t cap, uint32_t* counts, uint32_t tile_shots, uint32_t grid, cudaStream_t st,
+                                uint32_t minb);
 cudaError_t launch_bucket(const LaunchParams& L, uint32_t n_wt, uint32_t* ents, uint32_t* offs, uint64_t cap_total,
                           unsigned long long* total, uint32_t* ovf, cudaStream_t st);
 bool plain_supported(const DevProg& p);
@@ -211,6 +212,7 @@ struct Tuning {
   uint32_t PX = 1;  // shared prefix: 0 off, 1 when it saves enough traffic, 2 whenever it has array work
   uint32_t LW = 0;  // 1: warp-per-shot layout (exec_warp) for programs with active axes
   uint32_t LP = 0;  // 1: thread-per-shot layout (exec_plain<float>) for programs with active axes
+  uint32_t AQ = 4;  // resident item-kernel CTAs per SM (2, 3, 4)
   uint32_t WN = 0;  // its warps per CTA (0: 8, fewer if the vectors do not fit)
 };
 
@@ -242,6 +244,7 @@ Tuning choose_tuning(const DevProg& d, const char* tune, uint64_t shots, int n_s
       else if (sscanf(s, "px=%u", &v) == 1) t.PX = v;
       else if (sscanf(s, "lw=%u", &v) == 1) t.LW = v;
       else if (sscanf(s, "lp=%u", &v) == 1) t.LP = v;
+      else if (sscanf(s, "aq=%u", &v) == 1) t.AQ = v;
       else if (sscanf(s, "wn=%u", &v) == 1) t.WN = v;
       const char* c = strchr(s, ',');
       if (!c) break;
@@ -249,6 +252,7 @@ Tuning choose_tuning(const DevProg& d, const char* tune, uint64_t shots, int n_s
     }
   }
   if (t.W != 1 && t.W != 2 && t.W != 4) t.W = 1;
+  if (t.AQ < 2 || t.AQ > 4) t.AQ = 4;
   if (t.G < t.W) t.W = t.G;
   // keep the shared-memory footprint under the opt-in limit
   while (t.G > t.W && batched_smem_bytes(d, t.G, t.W, false) > 220 * 1024) t.G >>= 1;
@@ -549,11 +553,11 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
         uint32_t cap = 0;
         uint32_t *ibuf = nullptr, *cbuf = nullptr;
         if (items) {
-          // default pass: one tile per warp of the item kernel (2 CTAs of 16
+          // default pass: one tile per warp of the item kernel (AQ CTAs of 16
           // warps per SM), so no warp is left with a second tile while the
           // others idle; the pass's item lists (16 KB per tile for the surface
-          // code) then stay in L2 for the tile kernel
-          const uint64_t wave_shots = tu.AV ? tu.AV : 32ull * (uint64_t)n_sm * tile_shots;
+          // code) then mostly stay in L2 for the tile kernel
+          const uint64_t wave_shots = tu.AV ? tu.AV : 16ull * tu.AQ * (uint64_t)n_sm * tile_shots;
           wave = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, wave_shots / tile_shots));
           // list capacity per tile: mean + 10 sigma (a chunk count per fault
           // of at most 15, so the variance is below 16 x the mean) + slack
@@ -593,8 +597,8 @@ nc_status enqueue(const nc_program* prog, const DevCopy& dc, uint64_t shots, uin
             uint32_t* ib = ibuf + (size_t)bsel * wave * cap;
             uint32_t* cb = cbuf + (size_t)bsel * wave;
             if (overlap && pass >= 2) NC_TRY(cudaStreamWaitEvent(istream, ev.ev[3 + bsel], 0));
-            const uint32_t grid = std::min<uint32_t>((nt + 15) / 16, 2 * (uint32_t)n_sm);
-            NC_TRY(launch_affine_items(L, t0, nt, ib, cap, cb, tile_shots, grid, istream));
+            const uint32_t grid = std::min<uint32_t>((nt + 15) / 16, tu.AQ * (uint32_t)n_sm);
+            NC_TRY(launch_affine_items(L, t0, nt, ib, cap, cb, tile_shots, grid, istream, tu.AQ));
             if (overlap) {
               NC_TRY(cudaEventRecord(ev.ev[1 + bsel], istream));
               NC_TRY(cudaStreamWaitEvent(stream, ev.ev[1 + bsel], 0));
@@ -1455,7 +1459,8 @@ nc_status nc_autotune(nc_program* prog, uint64_t shots, const nc_sample_opts* op
   // candidate launch shapes
   std::vector<std::string> cand;
   if (h.k_max == 0 && h.aff_ok) {
-    for (const char* c : {"aw=32", "aw=16", "aw=8", "aw=32,ai=0", "a=0"}) cand.push_back(c);
+    for (const char* c : {"aw=32", "aw=32,aq=3", "aw=32,aq=2", "aw=16", "aw=8", "aw=32,ai=0", "a=0"})
+      cand.push_back(c);
   } else {
     const uint32_t gs[] = {1, 2, 4, 8, 16, 32, 64, 128};
     const uint32_t ts[] = {256, 512, 1024};
