@@ -222,7 +222,10 @@ void append_fused(std::vector<uint8_t>& blob) {
       case OP_EXPVAL:
       case OP_MEAS_ACTIVE_Z:
       case OP_MEAS_ACTIVE_X: {
-        // the vector in logical order with every pending phase applied
+        // the vector in logical order with every pending phase applied; a
+        // gather right before a measurement also forms its sums (one pass
+        // over the vector instead of two)
+        Op mo = o;
         if (!s.identity()) {
           Op m{};
           m.code = OP_PERMF;
@@ -231,6 +234,12 @@ void append_fused(std::vector<uint8_t>& blob) {
           for (uint32_t t = 0; t < s.k; t++) perm.push_back(s.col[t]);
           perm.push_back(s.c);
           take_terms(m, nullptr);
+          if (o.code != OP_EXPVAL && s.k >= 1) {
+            m.flags |= FLAG_SUMS;
+            m.pa = o.pa;
+            m.pb = o.code == OP_MEAS_ACTIVE_X ? 1 : 0;
+            mo.flags |= FLAG_PRESUMMED;
+          }
           out.push_back(m);
           any_perm = true;
           for (uint32_t t = 0; t < s.k; t++) s.col[t] = s.rinv[t] = 1u << t;
@@ -238,7 +247,7 @@ void append_fused(std::vector<uint8_t>& blob) {
         } else {
           flush_diag();
         }
-        out.push_back(o);
+        out.push_back(mo);
         if (o.code != OP_EXPVAL) s.k--;  // a probe keeps every axis
         for (uint32_t t = 0; t < s.k; t++) s.col[t] = s.rinv[t] = 1u << t;
         break;

@@ -897,21 +897,62 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
               // gather into logical order: new[i] = phase(q) old[q], q = A i ^ c
               const uint32_t* cols = p.fperm + op.i0;
               const uint32_t kk = op.i1, c0 = __ldg(cols + kk);
-              for (uint32_t s = t % S; s < S; s += T)
-                for (uint32_t j = sub; j < dim; j += R) {
-                  uint32_t q = c0, bits = j;
-                  while (bits) {
-                    q ^= __ldg(cols + (__ffs(bits) - 1));
-                    bits &= bits - 1;
-                  }
-                  if (q >= dim) {  // cannot happen for a well-formed list
-                    atomicOr(L.err, 2u);
-                    continue;
-                  }
-                  C v = work[(size_t)q * S + s], dummy = v;
-                  phase2(v, dummy, q, q, s, false);
-                  work2[(size_t)j * S + s] = v;
+              auto src = [&](uint32_t j) -> uint32_t {
+                uint32_t q = c0, bits = j;
+                while (bits) {
+                  q ^= __ldg(cols + (__ffs(bits) - 1));
+                  bits &= bits - 1;
                 }
+                return q;
+              };
+              if (op.flags & FLAG_SUMS) {
+                // gathered in the next measurement's amplitude pairs, whose
+                // FP64 sums are formed on the way (the measurement's own
+                // reduction, same pairs in the same order per thread)
+                const uint32_t mpa = op.pa;
+                const bool xm = op.pb != 0;
+                for (uint32_t s = t; s < S; s += T) {
+                  RED[s] = 0.0;
+                  RED[S + s] = 0.0;
+                }
+                __syncthreads();
+                for (uint32_t s = t % S; s < S; s += T) {
+                  double a0 = 0.0, a1 = 0.0;
+                  for (uint32_t j = sub; j < dim / 2; j += R) {
+                    const uint32_t j0 = insert0(j, mpa), j1 = j0 | (1u << mpa);
+                    const uint32_t q0 = src(j0), q1 = src(j1);
+                    if ((q0 | q1) >= dim) {  // cannot happen for a well-formed list
+                      atomicOr(L.err, 2u);
+                      continue;
+                    }
+                    C v0 = work[(size_t)q0 * S + s], v1 = work[(size_t)q1 * S + s], d0 = v0, d1 = v1;
+                    phase2(v0, d0, q0, q0, s, false);
+                    phase2(v1, d1, q1, q1, s, false);
+                    work2[(size_t)j0 * S + s] = v0;
+                    work2[(size_t)j1 * S + s] = v1;
+                    if (xm) {
+                      mterm_x(v0, v1, a0, a1);
+                    } else {
+                      a0 += mterm(v0);
+                      a1 += mterm(v1);
+                    }
+                  }
+                  atomicAdd(&RED[s], a0);
+                  atomicAdd(&RED[S + s], a1);
+                }
+              } else {
+                for (uint32_t s = t % S; s < S; s += T)
+                  for (uint32_t j = sub; j < dim; j += R) {
+                    const uint32_t q = src(j);
+                    if (q >= dim) {  // cannot happen for a well-formed list
+                      atomicOr(L.err, 2u);
+                      continue;
+                    }
+                    C v = work[(size_t)q * S + s], dummy = v;
+                    phase2(v, dummy, q, q, s, false);
+                    work2[(size_t)j * S + s] = v;
+                  }
+              }
               __syncthreads();
               C* const x = work;
               work = work2;
@@ -1040,25 +1081,27 @@ __global__ void __launch_bounds__(BIG ? 1024 : 256, 1) exec_batched(LaunchParams
               const bool xm = code == OP_MEAS_ACTIVE_X;
               const uint32_t half = 1u << (k - 1);
               const real rs = (real)0.70710678118654752440;
-              for (uint32_t s = t; s < S; s += T) {
-                RED[s] = 0.0;
-                RED[S + s] = 0.0;
-              }
-              __syncthreads();
-              for (uint32_t s = t % S; s < S; s += T) {
-                double a0 = 0.0, a1 = 0.0;
-                for (uint32_t j = sub; j < half; j += R) {
-                  size_t i0 = (size_t)insert0(j, pa) * S + s, i1 = i0 + ((size_t)1 << pa) * S;
-                  C u = work[i0], v = work[i1];
-                  if (xm) {
-                    mterm_x(u, v, a0, a1);
-                  } else {
-                    a0 += mterm(u);
-                    a1 += mterm(v);
-                  }
+              if (!(op.flags & FLAG_PRESUMMED)) {  // else the gather before formed the sums
+                for (uint32_t s = t; s < S; s += T) {
+                  RED[s] = 0.0;
+                  RED[S + s] = 0.0;
                 }
-                atomicAdd(&RED[s], a0);
-                atomicAdd(&RED[S + s], a1);
+                __syncthreads();
+                for (uint32_t s = t % S; s < S; s += T) {
+                  double a0 = 0.0, a1 = 0.0;
+                  for (uint32_t j = sub; j < half; j += R) {
+                    size_t i0 = (size_t)insert0(j, pa) * S + s, i1 = i0 + ((size_t)1 << pa) * S;
+                    C u = work[i0], v = work[i1];
+                    if (xm) {
+                      mterm_x(u, v, a0, a1);
+                    } else {
+                      a0 += mterm(u);
+                      a1 += mterm(v);
+                    }
+                  }
+                  atomicAdd(&RED[s], a0);
+                  atomicAdd(&RED[S + s], a1);
+                }
               }
               __syncthreads();
               if (owner) {

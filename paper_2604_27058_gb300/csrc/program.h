@@ -69,7 +69,11 @@ static_assert(sizeof(FTerm) == 32, "FTerm must be 32 bytes");
 
 // FLAG_REF (DETECTOR, OBS_OUT): the noiseless reference parity is 1. It is
 // set on the device copy after the reference launch (patch_ref_flags).
-enum : uint8_t { FLAG_SIGN = 1, FLAG_OUT = 2, FLAG_RESET = 4, FLAG_REF = 8 };
+// Fused list only: FLAG_SUMS on an OP_PERMF gather directly before an active
+// measurement: the gather also accumulates that measurement's FP64 sums
+// (measured logical position in pa, pb = 1 for an X measurement), and the
+// measurement carries FLAG_PRESUMMED and skips its own reduction pass.
+enum : uint8_t { FLAG_SIGN = 1, FLAG_OUT = 2, FLAG_RESET = 4, FLAG_REF = 8, FLAG_SUMS = 16, FLAG_PRESUMMED = 32 };
 
 struct Op {
   uint8_t code;
