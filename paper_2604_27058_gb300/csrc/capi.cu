@@ -1459,8 +1459,9 @@ nc_status nc_autotune(nc_program* prog, uint64_t shots, const nc_sample_opts* op
   // candidate launch shapes
   std::vector<std::string> cand;
   if (h.k_max == 0 && h.aff_ok) {
-    for (const char* c : {"aw=32", "aw=32,aq=3", "aw=32,aq=2", "aw=16", "aw=8", "aw=32,ai=0", "a=0"})
-      cand.push_back(c);
+    // (the item kernel's residency, aq, stays at its default of 4: 2 and 3
+    // were slower in longer timings than the autotuner's short ones resolve)
+    for (const char* c : {"aw=32", "aw=16", "aw=8", "aw=32,ai=0", "a=0"}) cand.push_back(c);
   } else {
     const uint32_t gs[] = {1, 2, 4, 8, 16, 32, 64, 128};
     const uint32_t ts[] = {256, 512, 1024};
