@@ -42,7 +42,8 @@ def _ops(blob, off, n):
         code, flags, a, bq, pa, pb = struct.unpack_from("<BBHHBB", b, 0)
         i0, i1, i2, i3 = struct.unpack_from("<4I", b, 8)
         cs, sn = struct.unpack_from("<2d", b, 8)
-        out.append(dict(code=CODES[code], a=a, b=bq, pa=pa, pb=pb, i0=i0, i1=i1, i2=i2, i3=i3, cs=cs, sn=sn))
+        out.append(dict(code=CODES[code], flags=flags, a=a, b=bq, pa=pa, pb=pb, i0=i0, i1=i1, i2=i2, i3=i3, cs=cs,
+                        sn=sn))
     return out
 
 
@@ -207,3 +208,30 @@ def test_fused_list_in_logical_order_at_every_probe(nc, seed):
     assert len(pa) == len(pb) == 6
     for a, b in zip(pa, pb):
         assert np.allclose(a, b, atol=1e-12)
+
+
+@pytest.mark.parametrize("name", ["dense20", "dense10", "coherent"])
+def test_gathers_that_form_measurement_sums(nc, name):
+    """A gather flagged to form the next measurement's sums (FLAG_SUMS = 16)
+    is followed directly by that active measurement, flagged as presummed
+    (FLAG_PRESUMMED = 32), whose measured position and basis it names; every
+    presummed measurement has such a gather; probes never do."""
+    text = {"dense20": gc.dense_random(seed=3, n=20, layers=40), "dense10": gc.dense_random(seed=33, n=10, layers=12),
+            "coherent": gc.surface_code_memory(d=3, rounds=3, p=1e-3, theta=0.02)}[name]
+    blob = nc.compile(text).serialize()
+    u = struct.unpack_from(HEAD, blob, 0)
+    offs = dict(zip(OFF_NAMES, struct.unpack_from(f"<{len(OFF_NAMES)}Q", blob, HEAD_BYTES)))
+    fops = _ops(blob, offs["fops"], u[32])
+    n_sums = 0
+    for i, o in enumerate(fops):
+        if o["code"] == "PERMF" and o["flags"] & 16:
+            n_sums += 1
+            m = fops[i + 1]
+            assert m["code"] in ("MEAS_ACTIVE_Z", "MEAS_ACTIVE_X") and m["flags"] & 32
+            assert o["pa"] == m["pa"] and o["pb"] == (m["code"] == "MEAS_ACTIVE_X")
+            assert m["pa"] < o["i1"]  # the measured position lies inside the gathered vector
+        if o["flags"] & 32 and o["code"].startswith("MEAS_ACTIVE"):
+            assert fops[i - 1]["code"] == "PERMF" and fops[i - 1]["flags"] & 16
+        if o["code"] == "EXPVAL":
+            assert not o["flags"] & 32
+    assert n_sums >= (16 if name == "dense20" else 1)
