@@ -1096,7 +1096,8 @@ bool hir_absorb_cliffords(std::vector<Hir>& L) {
 // with it, acts just before that measurement on a state the projector then
 // fixes: exp(-i theta P) Pi_m = e^{-+i theta} Pi_m, a phase per outcome
 // branch. It is dropped.
-void hir_absorb_into_measurements(std::vector<Hir>& L, const std::vector<PhysOp>& ops) {
+bool hir_absorb_into_measurements(std::vector<Hir>& L, const std::vector<PhysOp>& ops) {
+  bool changed = false;
   for (size_t i = 0; i < L.size(); i++) {
     Hir& r = L[i];
     if (r.dead || r.kind != H_ROT) continue;
@@ -1107,11 +1108,13 @@ void hir_absorb_into_measurements(std::vector<Hir>& L, const std::vector<PhysOp>
       steps++;
       if (o.kind == H_MEAS && same_axis(o.p, r.p)) {
         r.dead = true;
+        changed = true;
         break;
       }
       if (!swappable(r, o, ops)) break;
     }
   }
+  return changed;
 }
 
 // Commuting reorder: measurements earlier, rotations later, so that the
@@ -1119,7 +1122,8 @@ void hir_absorb_into_measurements(std::vector<Hir>& L, const std::vector<PhysOp>
 // earliest rotation it can pass (every operation it passes commutes with
 // it); a rotation moves after the last measurement it can pass. Nothing
 // moves that would pass no such operation.
-void hir_reorder(std::vector<Hir>& L, const std::vector<PhysOp>& ops) {
+bool hir_reorder(std::vector<Hir>& L, const std::vector<PhysOp>& ops) {
+  bool changed = false;
   L.erase(std::remove_if(L.begin(), L.end(), [](const Hir& h) { return h.dead; }), L.end());
   for (size_t i = 0; i < L.size(); i++) {
     if (L[i].kind != H_MEAS) continue;
@@ -1128,7 +1132,10 @@ void hir_reorder(std::vector<Hir>& L, const std::vector<PhysOp>& ops) {
       if (!swappable(L[j], L[i], ops)) break;
       if (L[j].kind == H_ROT) best = j;
     }
-    if (best < i) std::rotate(L.begin() + best, L.begin() + i, L.begin() + i + 1);
+    if (best < i) {
+      std::rotate(L.begin() + best, L.begin() + i, L.begin() + i + 1);
+      changed = true;
+    }
   }
   for (size_t i = L.size(); i-- > 0;) {
     if (L[i].kind != H_ROT) continue;
@@ -1137,8 +1144,12 @@ void hir_reorder(std::vector<Hir>& L, const std::vector<PhysOp>& ops) {
       if (!swappable(L[i], L[j], ops)) break;
       if (L[j].kind == H_MEAS) best = j;
     }
-    if (best > i) std::rotate(L.begin() + i, L.begin() + i + 1, L.begin() + best + 1);
+    if (best > i) {
+      std::rotate(L.begin() + i, L.begin() + i + 1, L.begin() + best + 1);
+      changed = true;
+    }
   }
+  return changed;
 }
 
 }  // namespace
@@ -1147,7 +1158,6 @@ void hir_reorder(std::vector<Hir>& L, const std::vector<PhysOp>& ops) {
 // Entry point
 // ---------------------------------------------------------------------------
 namespace {
-int compile_once(const std::string& text, uint32_t flags, CompiledProgram& out, std::string& err);
 
 // Array-traversal bytes per shot a program costs the batched executor: its
 // whole count, less the shared noiseless prefix (run once per call, every
@@ -1161,51 +1171,18 @@ double per_shot_cost(const CompiledProgram& c) {
 }
 }  // namespace
 
-int compile_program(const std::string& text, uint32_t flags, CompiledProgram& out, std::string& err) {
-  // The HIR passes never change a record, but they can raise the per-shot
-  // cost: the reorder pulls measurements ahead of rotations, which can end
-  // the shared noiseless prefix sooner, and a re-absorbed Clifford can turn
-  // later measured Paulis into ones whose localisation takes more array
-  // instructions. Every subset of the passes the flags leave on is compiled
-  // (most passes first) and the cheapest per shot kept, the one with more
-  // passes on a tie. Programs without active axes compile once.
-  CompiledProgram best;
-  double best_cost = 0.0;
-  int first_rc = -1;
-  std::string first_err;
-  for (uint32_t off = 0; off <= kNoPeephole + kNoReorder + kNoFuse; off++) {
-    if (off & ~(kNoPeephole | kNoReorder | kNoFuse)) continue;
-    if ((flags & off) != 0 && off != 0) continue;  // passes already off are not varied
-    CompiledProgram c;
-    std::string e;
-    const int rc = compile_once(text, flags | off, c, e);
-    if (first_rc < 0) {
-      first_rc = rc;
-      first_err = e;
-    }
-    if (rc != 0) {
-      if (rc == 3) continue;  // over the active-dimension limit with these passes
-      err = e;
-      return rc;
-    }
-    const ProgHeader& h = *reinterpret_cast<const ProgHeader*>(c.blob.data());
-    const double cost = per_shot_cost(c);
-    if (best.blob.empty() || cost < best_cost) {
-      best_cost = cost;
-      best = std::move(c);
-    }
-    if (h.k_max == 0) break;  // nothing to gain (and no rotation left for the passes)
-  }
-  if (best.blob.empty()) {
-    err = first_err;
-    return first_rc;
-  }
-  out = std::move(best);
-  return 0;
-}
 
 namespace {
-int compile_once(const std::string& text, uint32_t flags, CompiledProgram& out, std::string& err) {
+// The circuit up to its HIR, built once per nc_compile: the flattened
+// operations and every active operation as a Pauli of the t = 0 frame.
+struct Front {
+  Flattener fl;
+  std::vector<int64_t> flip_record;  // flip site -> its record
+  std::vector<Hir> hir;
+  bool any_rot = false;
+};
+
+int front_end(const std::string& text, Front& f, std::string& err) {
   try {
     std::vector<std::string> lines;
     {
@@ -1223,7 +1200,7 @@ int compile_once(const std::string& text, uint32_t flags, CompiledProgram& out, 
     }
     size_t pos = 0;
     auto block = parse_lines(lines, pos, 0);
-    Flattener fl;
+    Flattener& fl = f.fl;
     fl.run(block);
 
     // ---------------- front end: the HIR ----------------
@@ -1231,10 +1208,11 @@ int compile_once(const std::string& text, uint32_t flags, CompiledProgram& out, 
     // measurements (a flip changes only its record, never the frame, so
     // deferring it past the instruction's other targets is exact).
     // flip site -> its record
-    std::vector<int64_t> flip_record(fl.site_p.size(), -1);
+    std::vector<int64_t>& flip_record = f.flip_record;
+    flip_record.assign(fl.site_p.size(), -1);
     for (auto& po : fl.ops)
       if (po.kind == K_MEAS && po.site >= 0) flip_record[po.site] = po.record;
-    std::vector<Hir> hir;
+    std::vector<Hir>& hir = f.hir;
     {
       Compiler fe((int)fl.n_q);  // physical Cliffords only: img = U^dagger P U
       const int nw = fe.nw64;
@@ -1313,22 +1291,43 @@ int compile_once(const std::string& text, uint32_t flags, CompiledProgram& out, 
       for (auto& f : flips) hir.push_back(std::move(f));
     }
 
-    // ---------------- middle end: HIR passes (Sec. 3.1, stage 2) ----------------
-    // Programs without rotations are left as they are (the passes act only
-    // around rotations).
-    bool any_rot = false;
-    for (const Hir& h : hir) any_rot |= h.kind == H_ROT;
-    if (any_rot) {
-      if (!(flags & kNoFuse))
-        for (int it = 0; it < 4; it++) {
-          const bool a = hir_fuse(hir, fl.ops);
-          const bool b = hir_absorb_cliffords(hir);
-          if (!a && !b) break;
-        }
-      if (!(flags & kNoPeephole)) hir_absorb_into_measurements(hir, fl.ops);
-      if (!(flags & kNoReorder)) hir_reorder(hir, fl.ops);
-    }
+    for (const Hir& h : hir) f.any_rot |= h.kind == H_ROT;
+    return 0;
+  } catch (CompileError& e) {
+    err = e.what();
+    return e.code;
+  } catch (std::bad_alloc&) {
+    err = "out of host memory";
+    return 6;
+  } catch (std::exception& e) {
+    err = e.what();
+    return 9;
+  }
+}
 
+// The HIR passes the flags leave on, in their order (Sec. 3.1, stage 2):
+// fusion and re-absorption to a fixed point, the peephole, the reorder.
+// Returns the kNoFuse / kNoPeephole / kNoReorder bits of the passes that
+// changed the list.
+uint32_t run_passes(std::vector<Hir>& hir, const std::vector<PhysOp>& ops, uint32_t flags) {
+  uint32_t changed = 0;
+  if (!(flags & kNoFuse))
+    for (int it = 0; it < 4; it++) {
+      const bool a = hir_fuse(hir, ops);
+      const bool b = hir_absorb_cliffords(hir);
+      if (!a && !b) break;
+      changed |= kNoFuse;
+    }
+  if (!(flags & kNoPeephole) && hir_absorb_into_measurements(hir, ops)) changed |= kNoPeephole;
+  if (!(flags & kNoReorder) && hir_reorder(hir, ops)) changed |= kNoReorder;
+  return changed;
+}
+
+// Localisation, bytecode and tables of one HIR list.
+int back_end(const Front& f, const std::vector<Hir>& hir, CompiledProgram& out, std::string& err) {
+  try {
+    const Flattener& fl = f.fl;
+    const std::vector<int64_t>& flip_record = f.flip_record;
     // ---------------- back end: localisation and bytecode ----------------
     Compiler c((int)fl.n_q);
     c.record_id.assign((size_t)fl.rec, -1);
@@ -1819,5 +1818,66 @@ int compile_once(const std::string& text, uint32_t flags, CompiledProgram& out, 
   }
 }
 }  // namespace
+
+int compile_program(const std::string& text, uint32_t flags, CompiledProgram& out, std::string& err) {
+  // The HIR passes never change a record, but they can raise the per-shot
+  // cost: the reorder pulls measurements ahead of rotations, which can end
+  // the shared noiseless prefix sooner, and a re-absorbed Clifford can turn
+  // later measured Paulis into ones whose localisation takes more array
+  // instructions. The front end runs once; the program with every pass the
+  // flags leave on is compiled first, then each subset of the passes that
+  // changed the list there (dropping passes that changed nothing gives the
+  // same list), and the cheapest per shot is kept, the one with more passes
+  // on a tie. Programs without rotations compile once.
+  Front f;
+  int rc = front_end(text, f, err);
+  if (rc != 0) return rc;
+  if (!f.any_rot) return back_end(f, f.hir, out, err);
+  CompiledProgram best;
+  double best_cost = 0.0;
+  int first_rc = -1;
+  std::string first_err;
+  auto consider = [&](const std::vector<Hir>& L) -> int {
+    CompiledProgram c;
+    std::string e;
+    const int r = back_end(f, L, c, e);
+    if (first_rc < 0) {
+      first_rc = r;
+      first_err = e;
+    }
+    if (r == 3) return 0;  // over the active-dimension limit with these passes
+    if (r != 0) {
+      err = e;
+      return r;
+    }
+    const double cost = per_shot_cost(c);
+    if (best.blob.empty() || cost < best_cost) {
+      best_cost = cost;
+      best = std::move(c);
+    }
+    return 0;
+  };
+  uint32_t active = 0;
+  {
+    std::vector<Hir> all = f.hir;
+    active = run_passes(all, f.fl.ops, flags);
+    rc = consider(all);
+    if (rc != 0) return rc;
+  }
+  const bool zero_k = !best.blob.empty() && reinterpret_cast<const ProgHeader*>(best.blob.data())->k_max == 0;
+  for (uint32_t off = 1; off <= kNoPeephole + kNoReorder + kNoFuse && !zero_k; off++) {
+    if (off & ~active) continue;  // only passes that changed the list are varied
+    std::vector<Hir> L = f.hir;
+    run_passes(L, f.fl.ops, flags | off);
+    rc = consider(L);
+    if (rc != 0) return rc;
+  }
+  if (best.blob.empty()) {
+    err = first_err;
+    return first_rc;
+  }
+  out = std::move(best);
+  return 0;
+}
 
 }  // namespace nc
