@@ -20,6 +20,10 @@
 // The probe interpreter follows the bytecode as the executors run it
 // (program.h); it never runs on a program with active-array instructions.
 #include <algorithm>
+#include <atomic>
+#include <exception>
+#include <mutex>
+#include <thread>
 #include <cstring>
 #include <iterator>
 #include <vector>
@@ -240,36 +244,66 @@ void append_affine(std::vector<uint8_t>& blob) {
   std::vector<std::vector<uint32_t>> rand_rows(rand_ev.size());
   std::vector<uint32_t> col_off((size_t)h.n_sites * kRecPerSite + 1, 0);
   std::vector<std::vector<uint32_t>> col_rows((size_t)h.n_sites * kRecPerSite);
-  uint64_t n_entries = 0;
-  Probe pr;
-  for (size_t i0 = 0; i0 < items.size(); i0 += 64) {
-    const size_t n = std::min<size_t>(64, items.size() - i0);
-    std::vector<uint64_t> rm(rand_ev.size(), 0);
-    std::vector<uint32_t> touched;
-    for (size_t l = 0; l < n; l++) {
-      const Item& it = items[i0 + l];
-      if (it.is_rand) {
-        rm[it.a] |= 1ull << l;
-      } else {
-        auto& v = site_faults[it.a];
-        if (v.empty()) touched.push_back(it.a);
-        v.push_back({it.b, 1ull << l});
+  // Batches of 64 items are independent, and every item's rows go to its
+  // own column, so the batches run on several host threads with the same
+  // result as one after the other.
+  const size_t n_batches = (items.size() + 63) / 64;
+  std::atomic<uint64_t> n_entries{0};
+  std::atomic<bool> over{false};
+  std::exception_ptr failure;
+  std::mutex failure_mu;
+  auto worker = [&](size_t first, size_t step) {
+    try {
+      Probe pr;
+      std::vector<std::vector<std::pair<uint32_t, uint64_t>>> site_faults(h.n_sites);
+      std::vector<uint64_t> rm(rand_ev.size(), 0);
+      std::vector<uint32_t> touched;
+      for (size_t bi = first; bi < n_batches && !over.load(std::memory_order_relaxed); bi += step) {
+        const size_t i0 = bi * 64, n = std::min<size_t>(64, items.size() - i0);
+        std::fill(rm.begin(), rm.end(), 0ull);
+        touched.clear();
+        for (size_t l = 0; l < n; l++) {
+          const Item& it = items[i0 + l];
+          if (it.is_rand) {
+            rm[it.a] |= 1ull << l;
+          } else {
+            auto& v = site_faults[it.a];
+            if (v.empty()) touched.push_back(it.a);
+            v.push_back({it.b, 1ull << l});
+          }
+        }
+        run_probe(b, rand_ord, rm, site_faults, pr);
+        for (uint32_t s : touched) site_faults[s].clear();
+        uint64_t k = 0;
+        for (uint32_t r = 0; r < R; r++) {
+          uint64_t d = pr.rows[r] ^ base.rows[r];
+          while (d) {
+            const uint32_t l = (uint32_t)__builtin_ctzll(d);
+            d &= d - 1;
+            const Item& it = items[i0 + l];
+            if (it.is_rand) rand_rows[it.a].push_back(r);
+            else col_rows[(size_t)it.a * kRecPerSite + it.b].push_back(r);
+            k++;
+          }
+        }
+        if (n_entries.fetch_add(k) + k > kMaxEntries) over = true;
       }
+    } catch (...) {
+      std::lock_guard<std::mutex> g(failure_mu);
+      if (!failure) failure = std::current_exception();
+      over = true;
     }
-    run_probe(b, rand_ord, rm, site_faults, pr);
-    for (uint32_t s : touched) site_faults[s].clear();
-    for (uint32_t r = 0; r < R; r++) {
-      uint64_t d = pr.rows[r] ^ base.rows[r];
-      while (d) {
-        const uint32_t l = (uint32_t)__builtin_ctzll(d);
-        d &= d - 1;
-        const Item& it = items[i0 + l];
-        if (it.is_rand) rand_rows[it.a].push_back(r);
-        else col_rows[(size_t)it.a * kRecPerSite + it.b].push_back(r);
-        if (++n_entries > kMaxEntries) return;
-      }
-    }
+  };
+  {
+    const size_t hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t n_threads = std::min<size_t>({hw, (size_t)32, std::max<size_t>(1, n_batches / 4)});
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < n_threads; t++) pool.emplace_back(worker, t, n_threads);
+    worker(0, n_threads);
+    for (auto& th : pool) th.join();
   }
+  if (failure) std::rethrow_exception(failure);
+  if (over) return;
 
   // ---- delta rows ----
   // A row that shares most of its support with an earlier row is stored as
@@ -290,30 +324,89 @@ void append_affine(std::vector<uint8_t>& blob) {
       for (uint32_t r : col_rows[c]) F[r].push_back(c);
     for (uint32_t j = 0; j < rand_rows.size(); j++)
       for (uint32_t r : rand_rows[j]) F[r].push_back(n_cols + j);
-    std::vector<uint32_t> cnt(R, 0), touched;
-    for (uint32_t r = 0; r < R; r++) {
-      if (F[r].empty()) continue;
+    // The parent of r is the earlier row without a child that maximises
+    // |F_r| - |F_r ^ F_p| = 2 |F_r & F_p| - |F_p| (> 0; the larger p on a
+    // tie), so the choice depends only on the overlaps, not on the order
+    // they are counted in. For up to kParR rows the overlaps of every row
+    // with its earlier rows are counted on several host threads first (the
+    // rows of mirror-like circuits share most of their supports, and the
+    // counting is the bulk of the work); the greedy choice then runs in
+    // row order as before.
+    constexpr uint32_t kParR = 4096;
+    auto count_overlaps = [&](uint32_t r, std::vector<uint32_t>& cnt, std::vector<uint32_t>& touched,
+                              bool skip_children) {
       touched.clear();
       for (uint32_t x : F[r])
         for (uint32_t p : rows_of(x)) {
           if (p >= r) break;
-          if (child[p] != kNone) continue;
+          if (skip_children && child[p] != kNone) continue;
           if (!cnt[p]++) touched.push_back(p);
         }
-      uint32_t best = kNone;
-      int64_t best_gain = 0;
-      for (uint32_t p : touched) {
-        // |F_r| - |F_r ^ F_p| = 2 |F_r & F_p| - |F_p|
-        const int64_t gain = 2 * (int64_t)cnt[p] - (int64_t)F[p].size();
-        if (gain > best_gain || (gain == best_gain && gain > 0 && p > best)) {
-          best_gain = gain;
-          best = p;
-        }
-        cnt[p] = 0;
+    };
+    auto choose = [&](uint32_t r, uint32_t p, uint32_t overlap, uint32_t& best, int64_t& best_gain) {
+      const int64_t gain = 2 * (int64_t)overlap - (int64_t)F[p].size();
+      if (gain > best_gain || (gain == best_gain && gain > 0 && p > best)) {
+        best_gain = gain;
+        best = p;
       }
-      if (best != kNone) {
-        parent[r] = best;
-        child[best] = r;
+      (void)r;
+    };
+    if (R <= kParR) {
+      std::vector<std::vector<std::pair<uint32_t, uint32_t>>> ov(R);  // row -> (earlier row, overlap)
+      auto counter = [&](uint32_t first, uint32_t step) {
+        std::vector<uint32_t> cnt(R, 0), touched;
+        for (uint32_t r = first; r < R; r += step) {
+          if (F[r].empty()) continue;
+          count_overlaps(r, cnt, touched, false);
+          ov[r].reserve(touched.size());
+          for (uint32_t p : touched) {
+            ov[r].push_back({p, cnt[p]});
+            cnt[p] = 0;
+          }
+        }
+      };
+      const uint32_t hw = std::max(1u, std::thread::hardware_concurrency());
+      const uint32_t n_threads = std::min<uint32_t>({hw, 32u, std::max<uint32_t>(1, R / 16)});
+      std::vector<std::thread> pool;
+      std::exception_ptr err;
+      std::mutex err_mu;
+      auto guarded = [&](uint32_t first, uint32_t step) {
+        try {
+          counter(first, step);
+        } catch (...) {
+          std::lock_guard<std::mutex> g(err_mu);
+          if (!err) err = std::current_exception();
+        }
+      };
+      for (uint32_t t = 1; t < n_threads; t++) pool.emplace_back(guarded, t, n_threads);
+      guarded(0, n_threads);
+      for (auto& th : pool) th.join();
+      if (err) std::rethrow_exception(err);
+      for (uint32_t r = 0; r < R; r++) {
+        uint32_t best = kNone;
+        int64_t best_gain = 0;
+        for (const auto& po : ov[r])
+          if (child[po.first] == kNone) choose(r, po.first, po.second, best, best_gain);
+        if (best != kNone) {
+          parent[r] = best;
+          child[best] = r;
+        }
+      }
+    } else {
+      std::vector<uint32_t> cnt(R, 0), touched;
+      for (uint32_t r = 0; r < R; r++) {
+        if (F[r].empty()) continue;
+        count_overlaps(r, cnt, touched, true);
+        uint32_t best = kNone;
+        int64_t best_gain = 0;
+        for (uint32_t p : touched) {
+          choose(r, p, cnt[p], best, best_gain);
+          cnt[p] = 0;
+        }
+        if (best != kNone) {
+          parent[r] = best;
+          child[best] = r;
+        }
       }
     }
     // supports in delta form, then the columns again (rows ascending)
