@@ -105,7 +105,11 @@ typedef struct {
                              (item-list capacity per tile), ao (1: item
                              passes overlapped on a side stream), lw (1:
                              warp-per-shot layout), wn (its warps per CTA),
-                             lp (1: FP32 thread-per-shot layout), hd (0:
+                             lp (1: FP32 thread-per-shot layout), mp (1:
+                             its persistent form, one vector slot per
+                             resident thread; on a batch, every program in
+                             one launch), mg (resident CTAs per SM of that
+                             launch), hd (0:
                              host outputs staged, not written directly), hc
                              (shots per staged chunk), aq (resident
                              item-kernel CTAs per SM: 2, 3, 4) */
