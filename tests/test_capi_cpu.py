@@ -195,3 +195,32 @@ def test_shared_prefix_matches_the_oracle_plan(nc, name):
     assert 0.0 <= info.prefix_bytes_fp32 <= info.array_bytes_fp32
     if name == "dense":
         assert info.prefix_k == 20 and info.prefix_bytes_fp32 > 0.99 * info.array_bytes_fp32 - 6e7
+
+
+def _per_shot_cost(info):
+    """The compiler's selection cost: unfused traversal bytes per shot, less a
+    shared prefix of at least 6 axes plus one copy of its vector."""
+    b = info.array_bytes_fp32
+    if info.prefix_ops > 0 and info.prefix_k >= 6:
+        b -= info.prefix_bytes_fp32 - 8.0 * 2 ** info.prefix_k
+    return b
+
+
+@pytest.mark.parametrize("name", ["dense20", "dense12", "coherent_d3r1", "coherent_d3r3", "lowmagic", "tiny",
+                                  "random"])
+def test_pass_search_never_costs_more(nc, name):
+    """nc_compile keeps the cheapest of the pass subsets it tries, so the
+    kept program costs at most what the plain program (every HIR pass off)
+    and the all-passes program would cost; compiling twice gives the same
+    bytes."""
+    text = {"dense20": lambda: gc.dense_random(seed=3, n=20, layers=40),
+            "dense12": lambda: gc.dense_random(seed=3, n=20, layers=12),
+            "coherent_d3r1": lambda: gc.surface_code_memory(d=3, rounds=1, p=1e-3, theta=0.02),
+            "coherent_d3r3": lambda: gc.surface_code_memory(d=3, rounds=3, p=1e-3, theta=0.02),
+            "lowmagic": gc.low_magic_gadgets, "tiny": lambda: gc.tiny_random(seed=1),
+            "random": lambda: gc.random_small(77, n=6, n_ops=100, t_frac=0.3)}[name]()
+    kept = nc.compile(text)
+    plain = nc.compile(text, peephole=False)
+    assert _per_shot_cost(kept.info) <= _per_shot_cost(plain.info) + 1e-6
+    assert kept.info.k_max <= plain.info.k_max or _per_shot_cost(kept.info) < _per_shot_cost(plain.info)
+    assert nc.compile(text).serialize() == kept.serialize()
